@@ -1,0 +1,410 @@
+"""Pins of the CPU oracle to what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a closed
+form, an invariant stated in the paper, a special case with a known answer,
+brute force on a tiny input, or a published reference value.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from scipy.linalg import null_space
+
+import chaingen as cg
+from oracle import coarsening, coarsest, interp, operators, rng, smoothing
+from oracle import setup as S
+from oracle import solve as So
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------- generator
+def test_splitmix64_reference_outputs():
+    """Published reference sequence of SplitMix64 for state 1234567."""
+    with open(os.path.join(GOLD, "splitmix64_seed1234567.txt")) as f:
+        ref = [int(l) for l in f if l.strip() and not l.startswith("#")]
+    got = rng.draw(1234567, 0, 5)
+    assert [int(v) for v in got] == ref
+
+
+def test_uniform_pm1_range_and_streams():
+    a = rng.uniform_pm1(7, 0, 10000)
+    b = rng.uniform_pm1(7, 1, 10000)
+    assert a.min() >= -1.0 and a.max() < 1.0
+    assert abs(a.mean()) < 0.05 and not np.array_equal(a, b)
+
+
+# --------------------------------------------------------------- B = I - A
+@pytest.mark.parametrize("ch", [cg.lattice2d(9, seed=3), cg.tandem(7), cg.birth_death(12)],
+                         ids=["lattice", "tandem", "birthdeath"])
+def test_B_column_sums_zero(ch):
+    """Section 5: 1^T B = 0 for column-stochastic A; diag(B) = 1 - a_ii."""
+    A = ch.csr()
+    B = operators.build_B(A)
+    assert np.abs(np.asarray(B.sum(axis=0))).max() <= 8 * np.finfo(float).eps
+    assert np.array_equal(B.toarray(), np.eye(ch.n) - A.toarray())
+    assert np.all(np.diff(B.indptr) >= 1)
+    assert np.all(B.diagonal() == 1.0 - A.diagonal())
+
+
+def test_validate_rejects_non_stochastic():
+    A = cg.tandem(5).csr()
+    A.data[3] *= 1.01
+    with pytest.raises(ValueError):
+        operators.validate_stochastic(A)
+
+
+# --------------------------------------------------------------- smoothing
+def test_jacobi_checkerboard_mode_contracts_by_0p4():
+    """Uniform walk on a bipartite lattice: y = (-1)^(i+j) deg is an
+    eigenvector of A with eigenvalue -1, so B y = 2 y and one sweep of
+    x + omega D^{-1}(0 - B x) with omega = 0.7 (d = 1) maps y to -0.4 y."""
+    ch = cg.uniform2d(8)
+    B = operators.build_B(ch.csr())
+    i, j = np.meshgrid(np.arange(8), np.arange(8), indexing="ij")
+    y = ((-1.0) ** (i + j)).ravel() * ch.meta["wdeg"]
+    out = smoothing.jacobi(B, operators.diag(B), y, None, 0.7)
+    assert np.allclose(out, -0.4 * y, rtol=0, atol=1e-13)
+
+
+def test_jacobi_fixes_stationary_vector():
+    ch = cg.lattice2d(10, seed=5)
+    B = operators.build_B(ch.csr())
+    x = ch.meta["wdeg"] / ch.meta["wdeg"].sum()
+    out = smoothing.jacobi(B, operators.diag(B), x, None, 0.7)
+    assert np.abs(out - x).max() <= 1e-16
+
+
+def test_multicolour_jacobi_equals_natural_and_gs_orders_converge():
+    """Jacobi is order independent; both GS orders are valid smoothers."""
+    ch = cg.tandem(9)
+    B = operators.build_B(ch.csr())
+    Bt = operators.transpose(B)
+    key = rng.draw(3, 77, ch.n)
+    col = smoothing.greedy_colouring(B, Bt, key)
+    Bs = (abs(B) + abs(Bt)).tocoo()
+    off = Bs.row != Bs.col
+    assert np.all(col[Bs.row[off]] != col[Bs.col[off]])          # proper colouring
+    x = rng.uniform_pm1(1, 0, ch.n)
+    d = operators.diag(B)
+    nat = smoothing.jacobi(B, d, x, None, 0.7)
+    mc = x.copy()
+    for c in range(col.max() + 1):                               # colour by colour
+        rows = np.flatnonzero(col == c)
+        mc[rows] = smoothing.jacobi(B, d, x, None, 0.7)[rows]
+    assert np.array_equal(nat, mc)
+    # the stationary vector is a fixed point of Gauss-Seidel in any order,
+    # and a perturbation of it shrinks in the B-residual
+    xs = So.dense_nullvector(ch.csr().toarray())
+    b = np.zeros(ch.n)
+    for order in (np.arange(ch.n), smoothing.multicolour_order(col)):
+        z = smoothing.gauss_seidel(B, xs, b, order)
+        assert np.abs(z - xs).max() <= 1e-15
+        zp = xs + 1e-3 * x
+        z = smoothing.gauss_seidel(B, zp, b, order)
+        assert np.linalg.norm(B @ z) < 0.6 * np.linalg.norm(B @ zp)
+
+
+# --------------------------------------------------------------- coarsening
+def test_geometric_split_and_sets_brute_force():
+    nx, ny = 7, 6
+    cf, cmap, cgrid = coarsening.geometric(nx, ny)
+    assert cgrid == (4, 3) and cf.sum() == 12
+    assert np.array_equal(cmap[cf], np.arange(12))
+    J = coarsening.geometric_sets(nx, ny, cf)
+    for s, Js in J.items():
+        i, j = divmod(s, ny)
+        brute = [t for t in range(nx * ny) if cf[t]
+                 and max(abs(t // ny - i), abs(t % ny - j)) <= 1]
+        assert Js == brute and 1 <= len(Js) <= 4
+        # (odd, even) and (even, odd) points see 2 (or 1 at a ragged edge)
+        if i % 2 == 1 and j % 2 == 1:
+            assert len(Js) == 4 - 2 * (i == nx - 1 or j == ny - 1) + (i == nx - 1 and j == ny - 1)
+
+
+def _jpl_rounds(B, Bt, key):
+    """Independent formulation: parallel rounds, a vertex joins when it beats
+    every undecided neighbour (larger key, then smaller index)."""
+    n = B.shape[0]
+    Bs = (abs(B) + abs(Bt)).tocoo()
+    off = Bs.row != Bs.col
+    r, c = Bs.row[off], Bs.col[off]
+    state = np.zeros(n, dtype=int)           # 0 undecided, 1 C, 2 F
+    while (state == 0).any():
+        und = state == 0
+        beats = (key[r] > key[c]) | ((key[r] == key[c]) & (r < c))
+        lose = und[r] & und[c] & ~beats
+        loser = np.zeros(n, bool)
+        loser[r[lose]] = True
+        win = und & ~loser
+        state[win] = 1
+        nb = np.zeros(n, bool)
+        nb[c[win[r]]] = True
+        state[(state == 0) & nb] = 2
+    return state == 1
+
+
+def test_greedy_mis_equals_parallel_rounds_and_is_maximal():
+    ch = cg.delaunay_walk(500, seed=11)
+    B = operators.build_B(ch.csr())
+    Bt = operators.transpose(B)
+    cf, cmap = coarsening.greedy_mis(B, Bt, seed=5, level=0)
+    key = coarsening.mis_priorities(B.shape[0], 5, 0)
+    assert np.array_equal(cf, _jpl_rounds(B, Bt, key))
+    Bs = (abs(B) + abs(Bt)).tocoo()
+    off = Bs.row != Bs.col
+    assert not np.any(cf[Bs.row[off]] & cf[Bs.col[off]])           # independent
+    hasC = np.zeros(B.shape[0], bool)
+    hasC[Bs.row[off][cf[Bs.col[off]]]] = True
+    assert np.all(cf | hasC)                                          # maximal
+
+
+def test_graph_sets_rank_by_strength_and_top_up():
+    ch = cg.delaunay_walk(400, seed=2)
+    B = operators.build_B(ch.csr())
+    Bt = operators.transpose(B)
+    cf, _ = coarsening.greedy_mis(B, Bt, seed=1, level=0)
+    J = coarsening.graph_sets(B, Bt, cf, c_min=3, c_max=4)
+    Bd = B.toarray()
+    S = np.abs(Bd) + np.abs(Bd.T)
+    np.fill_diagonal(S, 0)
+    for i, Ji in J.items():
+        d1 = [j for j in np.flatnonzero(S[i]) if cf[j]]
+        reach2 = {j for k in np.flatnonzero(S[i]) for j in np.flatnonzero(S[k])
+                  if cf[j] and j != i} | set(d1)
+        expect = min(len(d1), 4) if len(d1) >= 3 else min(3, len(reach2))
+        assert len(Ji) == expect and all(cf[j] for j in Ji)
+        assert set(Ji) <= reach2
+        best = sorted(d1, key=lambda j: (-S[i, j], j))[:4]
+        assert set(best) <= set(Ji)
+
+
+# --------------------------------------------------------------- LS fits
+def _bilinear_vectors(nx, ny):
+    i, j = np.meshgrid(np.arange(nx, dtype=float), np.arange(ny, dtype=float), indexing="ij")
+    i = i.ravel(); j = j.ravel()
+    return np.stack([np.ones_like(i), i, j, i * j, 0.1 * i * i + j, np.sin(i) + j * j * 0.05], axis=1)
+
+
+def test_ls_interpolation_reproduces_bilinear_weights():
+    """Test vectors 1, x, y, xy are reproduced exactly by bilinear weights
+    1/2 (edge points) and 1/4 (cell centres): with only those vectors the
+    weighted fit of eq. ls_interpolation must return them."""
+    nx = ny = 9
+    V = _bilinear_vectors(nx, ny)[:, :4]
+    cf, cmap, _ = coarsening.geometric(nx, ny)
+    J = coarsening.geometric_sets(nx, ny, cf)
+    s = np.array([1.0, 0.3, 0.2, 0.05])
+    P = interp.ls_interpolation(V, s, cf, cmap, J).toarray()
+    for i, Ji in J.items():
+        expect = 1.0 / len(Ji)
+        assert np.allclose(P[i, cmap[Ji]], expect, atol=1e-12)
+    assert np.allclose(P[cf], np.eye(int(cf.sum()))[cmap[cf]])        # eq. Pstructure
+    Qt = interp.ls_restriction_T(np.concatenate([np.ones((nx * ny, 1)), V], axis=1),
+                                 np.concatenate([[0.0], s]), cf, cmap, J).toarray()
+    for i, Ji in J.items():
+        assert np.allclose(Qt[i, cmap[Ji]], 1.0 / len(Ji), atol=1e-12)
+
+
+def test_ls_fit_matches_normal_equations_and_kkt():
+    r, c = 12, 4
+    g = np.random.default_rng(4)
+    X = g.standard_normal((r, c))
+    y = g.standard_normal(r)
+    p = interp.fit_row(X, y)
+    assert np.allclose(np.linalg.solve(X.T @ X, X.T @ y), p, rtol=1e-10, atol=1e-12)
+    q = interp.fit_row_sum_one(X, y)
+    K = np.zeros((c + 1, c + 1))
+    K[:c, :c] = X.T @ X
+    K[:c, c] = 1.0
+    K[c, :c] = 1.0
+    rhs = np.concatenate([X.T @ y, [1.0]])
+    assert np.allclose(np.linalg.solve(K, rhs)[:c], q, rtol=1e-10, atol=1e-12)
+    assert abs(q.sum() - 1.0) <= 4 * np.finfo(float).eps
+
+
+# --------------------------------------------------------------- products
+def test_spmatmul_dense_and_structural_zeros():
+    g = np.random.default_rng(0)
+    X = sp.random(30, 20, density=0.2, random_state=1, format="csr")
+    Y = sp.random(20, 25, density=0.2, random_state=2, format="csr")
+    Z = operators.spmatmul(X, Y)
+    assert np.allclose(Z.toarray(), X.toarray() @ Y.toarray(), atol=1e-15)
+    ind = ((abs(X) > 0).astype(float) @ (abs(Y) > 0).astype(float)).tocsr()
+    ind.sort_indices()
+    assert np.array_equal(Z.indptr, ind.indptr) and np.array_equal(Z.indices, ind.indices)
+    # exact cancellation keeps its slot
+    Xc = sp.csr_matrix(np.array([[1.0, 1.0]]))
+    Yc = sp.csr_matrix(np.array([[2.0], [-2.0]]))
+    Zc = operators.spmatmul(Xc, Yc)
+    assert Zc.nnz == 1 and Zc.data[0] == 0.0
+
+
+# --------------------------------------------------------------- hierarchy
+@pytest.fixture(scope="module")
+def tandem_hier():
+    ch = cg.tandem(24)
+    H = S.bamg_setup(ch.csr(), S.Params(r=8, max_levels=3, coarse_min=1, seed=2),
+                     grid=(ch.nx, ch.ny))
+    return ch, H
+
+
+def test_hierarchy_invariants(tandem_hier):
+    """Section 5: 1^T Q = 1^T, hence 1^T B_c = 0; eq. Pstructure; Section 4.2:
+    M_l, N_l symmetric positive definite; pattern(Q) = pattern(P)^T."""
+    ch, H = tandem_hier
+    for l, lev in enumerate(H.levels[:-1]):
+        nxt = H.levels[l + 1]
+        colsum_Q = np.asarray(lev.Q.sum(axis=0)).ravel()
+        assert np.abs(colsum_Q - 1).max() <= 1e-13
+        scale = np.abs(lev.B).max()
+        assert np.abs(np.asarray(nxt.B.sum(axis=0))).max() <= 1e-13 * scale * lev.n ** 0.5
+        Pd = lev.P.toarray()
+        assert np.array_equal(Pd[lev.cf], np.eye(nxt.n)[lev.cmap[lev.cf]])
+        assert np.array_equal(lev.Qt.indptr, lev.P.indptr) and np.array_equal(lev.Qt.indices, lev.P.indices)
+        for Mx in (nxt.M, nxt.N):
+            Md = Mx.toarray()
+            assert np.allclose(Md, Md.T, atol=1e-14)
+            np.linalg.cholesky(Md)
+        # dense triple products
+        Bd = lev.B.toarray()
+        Md = np.eye(lev.n) if lev.M is None else lev.M.toarray()
+        Nd = np.eye(lev.n) if lev.N is None else lev.N.toarray()
+        Qd = lev.Q.toarray()
+        assert np.allclose(nxt.B.toarray(), Qd @ Bd @ Pd, atol=1e-13)
+        assert np.allclose(nxt.M.toarray(), Qd @ Md @ Qd.T, atol=1e-13)
+        assert np.allclose(nxt.N.toarray(), Pd.T @ Nd @ Pd, atol=1e-13)
+    assert H.op_complexity() < 2.0 and H.grid_complexity() < 1.4   # Section 7: <= 1.8 / 1.4
+
+
+def test_coarsest_triplets_and_pseudoinverse(tandem_hier):
+    """eq. singular_vectors_coarsest residuals, u proportional to 1 for the
+    zero singular value (1^T B_L = 0), eq. singular_value reproduces sigma,
+    and the four Penrose conditions of B_L^+."""
+    _, H = tandem_hier
+    L = H.levels[-1]
+    Bd, Md, Nd = L.B.toarray(), L.M.toarray(), L.N.toarray()
+    sig, U, V = coarsest.generalized_triplets(Bd, Md, Nd, 8)
+    assert np.all(np.diff(sig) >= 0) and sig[0] < 1e-12 * np.abs(Bd).max()
+    for k in range(8):
+        u, v = U[:, k], V[:, k]
+        assert np.linalg.norm(Bd @ v - sig[k] * Md @ u) <= 1e-12
+        assert np.linalg.norm(Bd.T @ u - sig[k] * Nd @ v) <= 1e-12
+        assert abs(u @ Md @ u - 1) < 1e-12 and abs(v @ Nd @ v - 1) < 1e-12
+        rq = (u @ Bd @ v) / np.sqrt(u @ Md @ u) / np.sqrt(v @ Nd @ v)
+        assert abs(rq - sig[k]) <= 1e-12
+    u0 = U[:, 0] / U[0, 0]
+    assert np.abs(u0 - 1).max() < 1e-9
+    X = coarsest.pinv_drop_smallest(Bd)
+    assert np.allclose(Bd @ X @ Bd, Bd, atol=1e-11)
+    assert np.allclose(X @ Bd @ X, X, atol=1e-8 * np.abs(X).max())
+    assert np.allclose((Bd @ X).T, Bd @ X, atol=1e-10)
+    assert np.allclose((X @ Bd).T, X @ Bd, atol=1e-10)
+
+
+def test_vcycle_equals_two_grid_error_propagator():
+    """eq. error_propagator_twogrid: with zero start the two-level V-cycle is
+    z = C b and I - C B = S^nu_post (I - P B_c^+ Q B) S^nu_pre with
+    S = I - omega D^{-1} B."""
+    ch = cg.lattice2d(9, seed=8)
+    H = S.bamg_setup(ch.csr(), S.Params(r=6, max_levels=2, coarse_min=1, nu_pre=2, nu_post=3),
+                     grid=(ch.nx, ch.ny))
+    assert len(H.levels) == 2
+    n = ch.n
+    lev = H.levels[0]
+    Bd = lev.B.toarray()
+    C = np.stack([So.vcycle(H, e) for e in np.eye(n)], axis=1)
+    Sm = np.eye(n) - 0.7 * Bd / lev.d[:, None]
+    E = (np.linalg.matrix_power(Sm, 3)
+         @ (np.eye(n) - lev.P.toarray() @ H.Bpinv @ lev.Q.toarray() @ Bd)
+         @ np.linalg.matrix_power(Sm, 2))
+    assert np.allclose(np.eye(n) - C @ Bd, E, atol=1e-11)
+
+
+def test_gmres_full_krylov_reaches_nullvector():
+    """Theorem 1 (index-1 singular system): GMRES on the consistent residual
+    equation converges; with m = n steps it is exact."""
+    ch = cg.tandem(6)
+    A = ch.csr()
+    B = operators.build_B(A)
+    xs = So.dense_nullvector(A.toarray())
+    x0 = np.full(ch.n, 1.0 / ch.n)
+    x, its, hist = So.fgmres(B, x0, lambda b: b, tol=1e-14, restart=ch.n, max_iter=ch.n)
+    x = So.normalise_x(x)
+    assert np.abs(x - xs).sum() < 1e-10
+    x2, _, _ = So.gmres_left(B, x0, lambda b: b, tol=1e-14, restart=ch.n, max_iter=ch.n)
+    assert np.abs(So.normalise_x(x2) - xs).sum() < 1e-10
+
+
+# --------------------------------------------------------------- closed forms
+def test_config1_lattice_matches_weighted_degree():
+    """Weighted symmetric lattice: detailed balance gives x ~ weighted degree.
+    Setting: 32x32, r = 8, 2 levels, GMRES(20), tol 1e-10 in the 1-norm."""
+    ch = cg.lattice2d(32, seed=1)
+    H = S.bamg_setup(ch.csr(), S.Params(r=8, max_levels=2, coarse_min=1, seed=1),
+                     grid=(ch.nx, ch.ny))
+    x, its, hist = So.bamg_solve(H, tol=1e-10, restart=20)
+    xs = ch.meta["wdeg"] / ch.meta["wdeg"].sum()
+    assert So.rel_res_1(H.levels[0].B, x) <= 1e-10
+    assert np.abs(x - xs).sum() / np.abs(xs).sum() <= 1e-8
+    assert x.min() > 0 and its < 40
+
+
+def test_birth_death_closed_form():
+    """x_{k+1} / x_k = p(k -> k+1) / p(k+1 -> k) (detailed balance)."""
+    n = 65
+    ch = cg.birth_death(n)
+    up, dn = ch.meta["p_up"], ch.meta["p_dn"]
+    xs = np.ones(n)
+    for k in range(n - 1):
+        xs[k + 1] = xs[k] * up[k] / dn[k + 1]
+    xs /= xs.sum()
+    H = S.bamg_setup(ch.csr(), S.Params(r=6, coarse_min=29, c_max=2), grid=(n, 1))
+    x, its, _ = So.bamg_solve(H, tol=1e-12, restart=30)
+    assert np.abs(x - xs).sum() <= 1e-8
+
+
+def test_delaunay_walk_matches_degree():
+    """Uniform walk on an undirected graph: x ~ degree; MIS coarsening."""
+    ch = cg.delaunay_walk(1024, seed=3)
+    H = S.bamg_setup(ch.csr(), S.Params(r=8, coarse_min=100, coarsening="mis",
+                                         c_min=2, c_max=3, nu_pre=5, nu_post=5, seed=3))
+    x, its, _ = So.bamg_solve(H, tol=1e-10, restart=30)
+    xs = ch.meta["deg"] / ch.meta["deg"].sum()
+    assert np.abs(x - xs).sum() <= 1e-8
+    assert len(H.levels) >= 2
+
+
+def test_tandem_three_independent_solvers():
+    """Nonreversible chain: AMG-FGMRES, dense null space and power iteration."""
+    ch = cg.tandem(8)
+    xs = So.dense_nullvector(ch.csr().toarray())
+    assert xs.min() > 0                                   # Section 2: x > 0
+    H = S.bamg_setup(ch.csr(), S.Params(r=8, max_levels=2, coarse_min=1), grid=(8, 8))
+    x, _, _ = So.bamg_solve(H, tol=1e-12)
+    xp, _ = So.power_iteration(ch.csr(), tol=1e-15)
+    assert np.abs(x - xs).sum() <= 1e-10
+    assert np.abs(xp - xs).sum() <= 1e-10
+
+
+def test_paper_iteration_counts_context():
+    """Soft context check against Table tandem (n = 1089, paper's rates):
+    the paper's stopping norm and free parameters are not stated, so only
+    the order of magnitude is compared (parity of counts is unpinned)."""
+    with open(os.path.join(GOLD, "paper_tables.json")) as f:
+        tab = json.load(f)
+    ch = cg.tandem(33, lam=11 / 31, mu1=10 / 31, mu2=10 / 31)
+    H = S.bamg_setup(ch.csr(), S.Params(r=8, coarse_min=17 * 17), grid=(33, 33))
+    _, its, hist = So.bamg_solve(H, tol=1e-10, restart=50)
+    i7 = next(i for i, h in enumerate(hist) if h <= 1e-7)
+    assert i7 <= 3 * tab["tandem"]["bamg"][0]
+
+
+def test_birth_death_hierarchy_is_multilevel():
+    """Table birthdeath setting: geometric 1-D coarsening until n_c < 30."""
+    ch = cg.birth_death(129)
+    H = S.bamg_setup(ch.csr(), S.Params(r=6, coarse_min=29), grid=(129, 1))
+    assert [l.n for l in H.levels] == [129, 65, 33, 17]
+    assert max(len(v) for v in H.levels[0].J.values()) == 2
