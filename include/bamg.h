@@ -1,0 +1,181 @@
+/*
+ * bamg.h - C ABI of the GB300 bootstrap-AMG solver for the stationary vector
+ * of an irreducible Markov chain.
+ *
+ * Problem (Section 2, eq. steadystatesystemlinear): given the column-stochastic
+ * transition matrix A (a_ij = probability of the move j -> i, every column
+ * sums to one, A irreducible), find x > 0 with B x = 0, B = I - A.  The
+ * result is returned with ||x||_1 = 1.
+ *
+ * Method: one bootstrap setup cycle (Algorithm 1) builds interpolation P by
+ * weighted least squares (eq. ls_interpolation, eq. ls_weights), restriction Q
+ * by least squares constrained to 1^T Q = 1^T (Section 5), the Petrov-Galerkin
+ * coarse operators B_c = Q B P (Section 3) and approximate singular triplets;
+ * the solve phase runs GMRES on the residual equation (Section 6, eq.
+ * residual) preconditioned by a V-cycle (eq. error_propagator_twogrid).
+ *
+ * Conventions for every call:
+ *  - every function returns a bamg_status and never aborts or throws;
+ *    bamg_last_error() gives a one-line description of the last failure on
+ *    the calling thread;
+ *  - device pointers are CUDA device addresses of the current device;
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream); work is
+ *    stream-ordered and a hierarchy must be used from one stream at a time;
+ *  - the caller owns A and every vector passed in; the library owns the
+ *    hierarchy until bamg_destroy();
+ *  - on error the outputs are unspecified and no memory is leaked.
+ */
+#ifndef BAMG_H
+#define BAMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BAMG_OK = 0,
+  BAMG_ERR_ARG = 1,            /* invalid argument (null pointer, size, layout) */
+  BAMG_ERR_NOT_STOCHASTIC = 2, /* a_ij < 0 or a column sum differs from 1      */
+  BAMG_ERR_CUDA = 3,           /* a CUDA runtime call or launch failed          */
+  BAMG_ERR_OOM = 4,            /* device allocation failed                      */
+  BAMG_ERR_NOT_CONVERGED = 5,  /* max_iter reached above the tolerance          */
+  BAMG_ERR_BREAKDOWN = 6,      /* GMRES breakdown before convergence            */
+  BAMG_ERR_NUMERIC = 7,        /* non-positive coarse diagonal, non-SPD M_l/N_l,
+                                  singular fit, or a row beyond kernel limits   */
+  BAMG_ERR_TIMEOUT = 8,        /* a bounded device-side wait gave up            */
+  BAMG_ERR_UNSUPPORTED = 9     /* valid request outside this build's limits     */
+} bamg_status;
+
+enum { BAMG_COARSEN_GEOMETRIC = 0, BAMG_COARSEN_MIS = 1 };
+enum { BAMG_PREC_FP64 = 0, BAMG_PREC_MIXED = 1 };
+enum { BAMG_RESTRICT_LS = 0, BAMG_RESTRICT_AVERAGE = 1 };
+
+/* CSR of the column-stochastic A (row i = probabilities of entering state i).
+ * row_ptr[n+1], col_idx[nnz] (ascending within each row, 0 <= col < n),
+ * val[nnz].  on_device = 0: host pointers (copied at setup); 1: device
+ * pointers (read during bamg_setup only).  nx, ny: grid shape for geometric
+ * coarsening, state s = i*ny + j (0 when there is no grid). */
+typedef struct {
+  int64_t n;
+  int64_t nnz;
+  const int32_t* row_ptr;
+  const int32_t* col_idx;
+  const double* val;
+  int on_device;
+  int nx, ny;
+} bamg_csr;
+
+/* Setup parameters.  Defaults (bamg_params_default) follow Section 7:
+ * 3+3 weighted Jacobi sweeps with omega = 0.7, r = 8 test vectors, up to
+ * c = 4 interpolation points. */
+typedef struct {
+  int r;             /* test vectors per side, 1 <= r <= 32                   */
+  int max_levels;    /* hierarchy depth limit (>= 1)                           */
+  int coarse_min;    /* stop coarsening once n_l <= coarse_min                 */
+  int nu_setup;      /* Jacobi sweeps per level in each setup relaxation phase */
+  int nu_pre, nu_post; /* V-cycle pre/post Jacobi sweeps                       */
+  int c_min, c_max;  /* interpolation set size bounds (graph coarsening)       */
+  double omega;      /* Jacobi weight: x <- x + omega D^{-1}(b - B x)          */
+  int coarsening;    /* BAMG_COARSEN_GEOMETRIC (needs nx, ny) or _MIS          */
+  int precision;     /* BAMG_PREC_FP64 or BAMG_PREC_MIXED (FP32 V-cycle and
+                        setup relaxation inside FP64 GMRES)                    */
+  int restriction;   /* BAMG_RESTRICT_LS (Section 5) or _AVERAGE               */
+  uint64_t seed;     /* SplitMix64 seed of test vectors and MIS priorities     */
+  double stochastic_tol; /* |column sum - 1| allowed at validation (1e-12)     */
+  int max_coarse_dense;  /* largest coarsest level solved densely (<= 1024)    */
+} bamg_params;
+
+typedef struct {
+  int restart;       /* GMRES restart length m (>= 1)                          */
+  int max_iter;      /* total iteration limit                                  */
+  double tol;        /* stop when ||B x||_1 / ||x||_1 <= tol                   */
+} bamg_solve_params;
+
+typedef struct {
+  int iterations;    /* preconditioned GMRES iterations                        */
+  int iters_to_1e7;  /* first iteration with ||Bx||_2/||x||_2 estimate <= 1e-7 */
+  int levels;
+  double rel_res_1;  /* final true ||B x||_1 / ||x||_1                          */
+  double setup_ms, solve_ms;
+  double op_cplx, grid_cplx; /* eq. operator_complexity_def; sum n_l / n      */
+  double min_x;      /* smallest entry of the normalised x                     */
+} bamg_solve_info;
+
+typedef struct bamg_hierarchy bamg_hierarchy;
+
+bamg_status bamg_params_default(bamg_params* p);
+bamg_status bamg_solve_params_default(bamg_solve_params* p);
+
+/* Validates A (a_ij >= 0, sorted in-range indices, column sums within
+ * stochastic_tol of 1), forms B = I - A and runs one bootstrap setup cycle
+ * (Algorithm 1) on the device.  Irreducibility is a precondition that is not
+ * checked.  *out receives a library-owned hierarchy. */
+bamg_status bamg_setup(const bamg_csr* A, const bamg_params* p, void* stream,
+                       bamg_hierarchy** out);
+
+/* z = C r: one V-cycle from a zero initial guess on the finest level
+ * (Section 6, eq. iterate_preconditioner with e^(0) = 0).  r_dev, z_dev:
+ * device arrays of n doubles; they may not alias. */
+bamg_status bamg_vcycle(bamg_hierarchy* h, const double* r_dev, double* z_dev,
+                        void* stream);
+
+/* Solves B x = 0 by V-cycle-preconditioned flexible GMRES on the residual
+ * equation started from the setup's x^(0) (Section 6).  x_dev: device array
+ * of n doubles receiving x > 0 with ||x||_1 = 1.  info may be NULL.
+ * Returns BAMG_ERR_NOT_CONVERGED (x still written) when max_iter is hit. */
+bamg_status bamg_solve(bamg_hierarchy* h, double* x_dev, const bamg_solve_params* sp,
+                       bamg_solve_info* info, void* stream);
+
+/* Host-buffer convenience: bamg_setup + bamg_solve + copy of x to host memory
+ * (x_host: n doubles).  Uses the given stream and synchronises it. */
+bamg_status bamg_solve_host(const bamg_csr* A, const bamg_params* p,
+                            const bamg_solve_params* sp, double* x_host,
+                            bamg_solve_info* info, void* stream);
+
+void bamg_destroy(bamg_hierarchy* h);
+
+const char* bamg_status_string(bamg_status s);
+const char* bamg_last_error(void);
+
+/* Number of kernels this library has launched in the process so far. */
+uint64_t bamg_launch_count(void);
+
+/* ---------------------------------------------------------------- views --
+ * Read-only views of the device arrays of a hierarchy, valid until
+ * bamg_destroy.  Level 0 is the finest.  CSR arrays are int32 row_ptr[rows+1],
+ * int32 col[nnz], double val[nnz]; P and Qt are n_l x n_{l+1} with fine rows
+ * (Qt = Q^T), Q is n_{l+1} x n_l; M, N are NULL on level 0 (identity). */
+typedef struct {
+  int rows, cols, nnz;
+  const int32_t* row_ptr;
+  const int32_t* col;
+  const double* val;
+} bamg_csr_view;
+
+typedef struct {
+  int n;
+  bamg_csr_view B, M, N, P, Qt, Q;   /* P, Qt, Q empty on the coarsest level */
+  const int8_t* cf;                 /* 1 = coarse, 0 = fine (NULL on coarsest) */
+  const int32_t* cmap;              /* coarse index or -1                      */
+  const double* s;                  /* sqrt LS weights of V (r)                */
+  const double* t;                  /* sqrt LS weights of U (r, t[0] = 0)      */
+} bamg_level_view;
+
+int bamg_num_levels(const bamg_hierarchy* h);
+bamg_status bamg_level(const bamg_hierarchy* h, int l, bamg_level_view* out);
+
+/* Setup triplets on the finest level: sigma (host, r doubles), and device
+ * views of U, V (n x ld row-major, ld = block stride >= r) and x^(0). */
+bamg_status bamg_triplets(const bamg_hierarchy* h, double* sigma_host, int* ld,
+                          const double** U_dev, const double** V_dev,
+                          const double** x0_dev);
+
+/* Dense pseudo-inverse of the coarsest operator (n_L x n_L, row-major). */
+bamg_status bamg_coarse_pinv(const bamg_hierarchy* h, int* nL, const double** Bpinv_dev);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BAMG_H */

@@ -1,0 +1,146 @@
+/*
+ * bamg_steps.h - the individual device steps of the bootstrap-AMG hot path,
+ * exported for callers that assemble their own pipeline and for
+ * step-by-step verification.
+ *
+ * All pointers are device pointers unless named *_host.  Blocks of test
+ * vectors are n x ld row-major (row i holds its ld entries contiguously;
+ * columns >= r are padding); ld must be 4, 8, 16 or 32.  CSR arrays are int32
+ * row_ptr[rows+1] and int32 col[nnz] sorted ascending within each row.
+ * `prec` selects the value type of matrices and blocks: 0 = double,
+ * 1 = float.  Steps that size their output in two calls (count, then fill)
+ * read the count back to the host and synchronise `stream`.  Scratch space,
+ * where a step needs it, is taken from the stream-ordered device pool and
+ * returned before the call ends.  Errors: BAMG_ERR_ARG for bad sizes or
+ * null pointers, BAMG_ERR_CUDA for launch failures, the step-specific codes
+ * documented below.
+ */
+#ifndef BAMG_STEPS_H
+#define BAMG_STEPS_H
+
+#include "bamg.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Section 2, eq. steadystatesystemlinear: B = I - A with the diagonal always
+ * stored.  Count pass: *nnzB = nnz(A) + number of rows of A without a
+ * diagonal entry.  Fill pass writes B_row_ptr[n+1], B_col[nnzB], B_val. */
+bamg_status bamg_step_build_B_count(int n, const int32_t* A_rp, const int32_t* A_ci,
+                                    int64_t* nnzB, void* stream);
+bamg_status bamg_step_build_B(int n, const int32_t* A_rp, const int32_t* A_ci,
+                              const double* A_val, int32_t* B_rp, int32_t* B_ci,
+                              double* B_val, void* stream);
+
+/* Section 2: validation of a column-stochastic A (a_ij >= 0 and
+ * |sum_i a_ij - 1| <= tol).  *bad_host = number of offending columns plus
+ * entries (0 = valid). */
+bamg_status bamg_step_check_stochastic(int n, const int32_t* A_rp, const int32_t* A_ci,
+                                       const double* A_val, double tol,
+                                       int64_t* bad_host, void* stream);
+
+/* Transpose of a rows x cols CSR (values double).  Output row_ptr[cols+1],
+ * columns ascending. */
+bamg_status bamg_step_transpose(int rows, int cols, int nnz, const int32_t* rp,
+                                const int32_t* ci, const double* val, int32_t* t_rp,
+                                int32_t* t_ci, double* t_val, void* stream);
+
+/* Algorithm 1 smoothing loops with weighted Jacobi (Section 3; F = D/omega):
+ * Y = X + omega D^{-1} (R .* sigma - B X), sweep by sweep, where D is the
+ * diagonal of B, R is an optional right-hand side block (NULL = 0) scaled per
+ * column by sigma (NULL = 1), and keep_col0 = 1 leaves column 0 unchanged
+ * (the fixed left null vector u^(1) = 1 of Section 5).  dinv[i] = 1/b_ii.
+ * X and Y may not alias. */
+bamg_status bamg_step_relax_block(int prec, int n, int ld, const int32_t* rp,
+                                  const int32_t* ci, const void* val, const void* dinv,
+                                  const void* X, void* Y, const void* R,
+                                  const void* sigma, double omega, int keep_col0,
+                                  void* stream);
+
+/* Y = A X for a rows x cols CSR A and a cols x ld block X (Y rows x ld). */
+bamg_status bamg_step_spmm_block(int prec, int rows, int ld, const int32_t* rp,
+                                 const int32_t* ci, const void* val, const void* X,
+                                 void* Y, void* stream);
+
+/* eq. ls_weights with unit test vectors: for each column k < r,
+ * norm_host[k] = ||x_k||_2 and w_host[k] = ||x_k||_2 / ||B x_k||_2 (the
+ * square root of omega_k after normalising x_k).  When normalise = 1 the
+ * columns of X are scaled to unit norm in place (skip_col0 = 1 leaves
+ * column 0 alone and reports w_host[0] = 0).  FP64 accumulation. */
+bamg_status bamg_step_norms_weights(int prec, int n, int ld, int r, const int32_t* rp,
+                                    const int32_t* ci, const void* val, void* X,
+                                    int normalise, int skip_col0, double* norm_host,
+                                    double* w_host, void* stream);
+
+/* Geometric C/F splitting (Section 7): coarse = (i even, j even) on an
+ * nx x ny grid.  cf[n] int8 (1 = C), cmap[n] int32 coarse index or -1,
+ * and the interpolation sets J_i (C points of the 3x3 box, ascending) as a
+ * CSR over all n rows (coarse rows empty): J_rp[n+1], J_ci[<= 4n] with fine
+ * indices.  *nc_host = number of coarse points. */
+bamg_status bamg_step_coarsen_geometric(int nx, int ny, int8_t* cf, int32_t* cmap,
+                                        int32_t* J_rp, int32_t* J_ci, int* nc_host,
+                                        void* stream);
+
+/* Greedy maximal independent set on the symmetrised graph of B, vertices
+ * in decreasing SplitMix64 priority (seed, stream 4096 + level), equal
+ * priorities by increasing index; computed by parallel rounds that reach the
+ * same set.  Needs the patterns of B and B^T.  Writes cf, cmap. */
+bamg_status bamg_step_coarsen_mis(int n, const int32_t* B_rp, const int32_t* B_ci,
+                                  const int32_t* Bt_rp, const int32_t* Bt_ci,
+                                  uint64_t seed, int level, int8_t* cf, int32_t* cmap,
+                                  int* nc_host, void* stream);
+
+/* Interpolation sets on a graph: per fine point, coarse neighbours ranked by
+ * strength |b_ij| + |b_ji| (descending, ties by index), at most c_max, topped
+ * up to c_min from distance two by the largest strength product.  Output J
+ * CSR over all n rows (coarse rows empty), fine indices ascending; J_ci must
+ * hold n * c_max entries. */
+bamg_status bamg_step_graph_sets(int n, const int32_t* B_rp, const int32_t* B_ci,
+                                 const double* B_val, const int32_t* Bt_rp,
+                                 const int32_t* Bt_ci, const double* Bt_val,
+                                 const int8_t* cf, int c_min, int c_max, int32_t* J_rp,
+                                 int32_t* J_ci, void* stream);
+
+/* eq. ls_interpolation: for every fine row i with J_i non-empty, the weights
+ * p_i = argmin sum_{k<r} (w_k (v_i^(k) - sum_{j in J_i} p_ij v_j^(k)))^2, by
+ * Householder QR in FP64 (w = sqrt of the LS weights).  Output row-wise into
+ * out[J_rp[i] .. J_rp[i+1]).  constrained = 1 solves the restriction
+ * problem of Section 5 instead: rows k >= 1 only, subject to sum_j p_ij = 1.
+ * *rankdef_host = number of rows whose fit was rank deficient (pivots below
+ * 1e-13 relative were dropped). */
+bamg_status bamg_step_ls_fit(int prec, int n, int ld, int r, const int32_t* J_rp,
+                             const int32_t* J_ci, const void* X, const double* w,
+                             int constrained, double* out, int* rankdef_host,
+                             void* stream);
+
+/* Two-phase sparse product C = A B (A: m x k, B: k x p, values double) on the
+ * structural pattern (entries that cancel are kept).  Symbolic pass writes
+ * C_rp[m+1] and *nnzC_host; numeric pass fills C_ci (ascending) and C_val.
+ * BAMG_ERR_NUMERIC if a row has more than 8192 products. */
+bamg_status bamg_step_spgemm_symbolic(int m, const int32_t* A_rp, const int32_t* A_ci,
+                                      const int32_t* B_rp, const int32_t* B_ci,
+                                      int32_t* C_rp, int64_t* nnzC_host, void* stream);
+bamg_status bamg_step_spgemm_numeric(int m, const int32_t* A_rp, const int32_t* A_ci,
+                                     const double* A_val, const int32_t* B_rp,
+                                     const int32_t* B_ci, const double* B_val,
+                                     const int32_t* C_rp, int32_t* C_ci, double* C_val,
+                                     void* stream);
+
+/* eq. generalized_eigenvalue on the coarsest level: the r smallest
+ * generalized singular triplets of (B, M, N) (dense n x n row-major, M and N
+ * symmetric positive definite), sigma ascending, u^T M u = v^T N v = 1, sign
+ * fixed so the largest-magnitude entry of v is positive (for sigma below
+ * n*eps*sigma_max the largest entry of u is made positive as well).
+ * U, V: n x r row-major.  Bpinv (may be NULL): Moore-Penrose pseudo-inverse
+ * of B with its smallest singular value dropped (Section 3), row-major.
+ * Computed in the precision `prec` (inputs and outputs stay double).
+ * BAMG_ERR_NUMERIC if M or N is not positive definite; n <= 1024. */
+bamg_status bamg_step_coarsest(int prec, int n, int r, const double* B, const double* M,
+                               const double* N, double* sigma, double* U, double* V,
+                               double* Bpinv, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BAMG_STEPS_H */

@@ -1,0 +1,466 @@
+// Kernels over blocks of test vectors (n x LD, row-major) and vectors.
+//
+// Layout: a row of a block is LD contiguous values (LD*sizeof(T) bytes); a
+// group of LPR = LD / VW lanes owns one matrix row and each lane one 16-byte
+// vector of VW values, so the gather of a neighbour's row is one coalesced
+// LD*sizeof(T)-byte transaction.  CSR column/value of a nonzero is read once
+// per row group (broadcast to its lanes).
+#include "internal.cuh"
+
+namespace bamg {
+
+template <typename T, int LD>
+struct Blk {
+  static constexpr int VW = Vec16<T>::W;
+  static constexpr int LPR = LD / VW;
+  static constexpr int RPW = 32 / LPR;
+  static_assert(LD % VW == 0 && LPR >= 1 && LPR <= 32, "bad block width");
+};
+
+// Y = X + omega D^{-1} (sigma .* R - B X)   (Algorithm 1 smoothing loops;
+// weighted Jacobi, Section 3).  keep0: column 0 copied unchanged.
+template <typename T, int LD>
+__global__ void __launch_bounds__(256)
+relax_block_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                   const T* __restrict__ va, const T* __restrict__ dinv, const T* __restrict__ X,
+                   T* __restrict__ Y, const T* __restrict__ R, const T* __restrict__ sig, T omega,
+                   int keep0) {
+  using C = Blk<T, LD>;
+  int lane = threadIdx.x & 31;
+  int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int i = gw * C::RPW + lane / C::LPR;
+  int q = lane % C::LPR;
+  if (i >= n) return;
+  T acc[C::VW];
+#pragma unroll
+  for (int v = 0; v < C::VW; ++v) acc[v] = T(0);
+  int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
+  for (int p = p0; p < p1; ++p) {
+    int j = __ldg(ci + p);
+    T a = __ldg(va + p);
+    T xv[C::VW];
+    vload_ro(X + (size_t)j * LD + q * C::VW, xv);
+#pragma unroll
+    for (int v = 0; v < C::VW; ++v) acc[v] = fma(a, xv[v], acc[v]);
+  }
+  T xi[C::VW], y[C::VW];
+  vload_ro(X + (size_t)i * LD + q * C::VW, xi);
+  T di = __ldg(dinv + i);
+  if (R) {
+    T rv[C::VW];
+    vload_ro(R + (size_t)i * LD + q * C::VW, rv);
+#pragma unroll
+    for (int v = 0; v < C::VW; ++v) {
+      T s = sig ? __ldg(sig + q * C::VW + v) : T(1);
+      y[v] = xi[v] + (omega * (s * rv[v] - acc[v])) * di;
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < C::VW; ++v) y[v] = xi[v] + (omega * (-acc[v])) * di;
+  }
+  if (keep0 && q == 0) y[0] = xi[0];
+  vstore(Y + (size_t)i * LD + q * C::VW, y);
+}
+
+// Y = A X  (rows x LD) for a CSR A.
+template <typename T, int LD>
+__global__ void __launch_bounds__(256)
+spmm_block_kernel(int rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                  const T* __restrict__ va, const T* __restrict__ X, T* __restrict__ Y) {
+  using C = Blk<T, LD>;
+  int lane = threadIdx.x & 31;
+  int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int i = gw * C::RPW + lane / C::LPR;
+  int q = lane % C::LPR;
+  if (i >= rows) return;
+  T acc[C::VW];
+#pragma unroll
+  for (int v = 0; v < C::VW; ++v) acc[v] = T(0);
+  int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
+  for (int p = p0; p < p1; ++p) {
+    int j = __ldg(ci + p);
+    T a = __ldg(va + p);
+    T xv[C::VW];
+    vload_ro(X + (size_t)j * LD + q * C::VW, xv);
+#pragma unroll
+    for (int v = 0; v < C::VW; ++v) acc[v] = fma(a, xv[v], acc[v]);
+  }
+  vstore(Y + (size_t)i * LD + q * C::VW, acc);
+}
+
+// Per-block column sums of K products, written to part[block][K*LD].
+// mode 0 (norms): pair 0 = x.x, pair 1 = (Bx).(Bx) with Bx formed on the fly.
+// mode 1 (dots):  pair k = A_k . B_k for the supplied block pairs.
+template <typename T, int LD, int MODE>
+__global__ void __launch_bounds__(256)
+coldot_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+              const T* __restrict__ va, const T* __restrict__ X, const T* __restrict__ A0,
+              const T* __restrict__ B0, const T* __restrict__ A1, const T* __restrict__ B1,
+              const T* __restrict__ A2, const T* __restrict__ B2, int npairs,
+              double* __restrict__ part) {
+  using C = Blk<T, LD>;
+  constexpr int K = 3;
+  __shared__ double sh[8][K * LD];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int q = lane % C::LPR;
+  double acc[K][C::VW];
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int v = 0; v < C::VW; ++v) acc[k][v] = 0.0;
+  int rows_per_block = (blockDim.x >> 5) * C::RPW;
+  for (int i = blockIdx.x * rows_per_block + w * C::RPW + lane / C::LPR; i < n;
+       i += gridDim.x * rows_per_block) {
+    size_t o = (size_t)i * LD + q * C::VW;
+    if (MODE == 0) {
+      T bx[C::VW], xi[C::VW];
+#pragma unroll
+      for (int v = 0; v < C::VW; ++v) bx[v] = T(0);
+      for (int p = __ldg(rp + i); p < __ldg(rp + i + 1); ++p) {
+        int j = __ldg(ci + p);
+        T a = __ldg(va + p);
+        T xv[C::VW];
+        vload_ro(X + (size_t)j * LD + q * C::VW, xv);
+#pragma unroll
+        for (int v = 0; v < C::VW; ++v) bx[v] = fma(a, xv[v], bx[v]);
+      }
+      vload_ro(X + o, xi);
+#pragma unroll
+      for (int v = 0; v < C::VW; ++v) {
+        acc[0][v] += (double)xi[v] * (double)xi[v];
+        acc[1][v] += (double)bx[v] * (double)bx[v];
+      }
+    } else {
+      const T* As[3] = {A0, A1, A2};
+      const T* Bs[3] = {B0, B1, B2};
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if (k < npairs) {
+          T a[C::VW], b[C::VW];
+          vload_ro(As[k] + o, a);
+          vload_ro(Bs[k] + o, b);
+#pragma unroll
+          for (int v = 0; v < C::VW; ++v) acc[k][v] += (double)a[v] * (double)b[v];
+        }
+      }
+    }
+  }
+  // lanes with equal q hold the same columns: reduce over the row groups
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int v = 0; v < C::VW; ++v)
+      for (int o = 16; o >= C::LPR; o >>= 1) acc[k][v] += __shfl_xor_sync(0xffffffffu, acc[k][v], o);
+  if (lane < C::LPR) {
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int v = 0; v < C::VW; ++v) sh[w][k * LD + lane * C::VW + v] = acc[k][v];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < K * LD; t += blockDim.x) {
+    double s = 0.0;
+    for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) s += sh[ww][t];
+    part[(size_t)blockIdx.x * K * LD + t] = s;
+  }
+}
+
+// From sums [x.x | Bx.Bx]: scale_k = 1/||x_k||, w_k = ||x_k|| / ||B x_k||
+// (eq. ls_weights for the normalised vector).
+template <typename T, int LD>
+__global__ void weights_finalize_kernel(const double* __restrict__ sums, int r, int skip0,
+                                        T* __restrict__ scale, double* __restrict__ w,
+                                        double* __restrict__ norms) {
+  int k = threadIdx.x;
+  if (k >= LD) return;
+  double xx = sums[k], bb = sums[LD + k];
+  bool active = k < r && !(skip0 && k == 0);
+  double nx = sqrt(xx);
+  norms[k] = nx;
+  if (active && xx > 0.0 && bb > 0.0) {
+    scale[k] = T(1.0 / nx);
+    w[k] = nx / sqrt(bb);
+  } else {
+    scale[k] = T(1);
+    w[k] = 0.0;
+  }
+}
+
+template <typename T, int LD>
+__global__ void scale_cols_kernel(int n, T* __restrict__ X, const T* __restrict__ scale) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)n * LD) return;
+  X[t] *= scale[t % LD];
+}
+
+// eq. singular_value: sigma_k = u.Bv / (sqrt(u.Mu) sqrt(v.Nv)).
+template <typename T>
+__global__ void rayleigh_finalize_kernel(const double* __restrict__ sums, int LD, int r,
+                                         T* __restrict__ sig, double* __restrict__ sig64) {
+  int k = threadIdx.x;
+  if (k >= LD) return;
+  double num = sums[k], um = sums[LD + k], vn = sums[2 * LD + k];
+  double s = (k < r && um > 0.0 && vn > 0.0) ? num / (sqrt(um) * sqrt(vn)) : 0.0;
+  sig[k] = T(s);
+  if (sig64) sig64[k] = s;
+}
+
+// Test vectors (Section 4.2 random start, Section 5 u^(1) = 1): SplitMix64
+// uniform(-1,1), V column k from stream 2k, U column k from stream 2k+1.
+template <typename T, int LD>
+__global__ void init_vectors_kernel(int n, int r, uint64_t seed, T* __restrict__ U, T* __restrict__ V) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)n * LD) return;
+  int i = (int)(t / LD), k = (int)(t % LD);
+  if (k >= r) {
+    U[t] = T(0); V[t] = T(0);
+    return;
+  }
+  V[t] = T(splitmix_pm1(seed, 2ull * k, (uint64_t)i));
+  U[t] = k == 0 ? T(1) : T(splitmix_pm1(seed, 2ull * k + 1, (uint64_t)i));
+}
+
+// Canonical injection R (Algorithm 1): Xc[I, :] = X[cpt[I], :].
+template <typename T, int LD>
+__global__ void inject_kernel(int nc, const int32_t* __restrict__ cpt, const T* __restrict__ X,
+                              T* __restrict__ Xc) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)nc * LD) return;
+  int I = (int)(t / LD), k = (int)(t % LD);
+  Xc[t] = X[(size_t)cpt[I] * LD + k];
+}
+
+// ------------------------------------------------------- vector kernels
+// One group of G lanes per row; modes of the V-cycle and GMRES.
+enum VecMode { kJacobi = 0, kJacobiZero = 1, kResid = 2, kSpmv = 3, kSpmvAdd = 4 };
+
+template <typename T, int G, int MODE>
+__global__ void __launch_bounds__(256)
+csr_vec_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+               const T* __restrict__ va, const T* __restrict__ dinv, T omega, const T* __restrict__ x,
+               const T* __restrict__ b, T* __restrict__ y) {
+  int lane = threadIdx.x & 31;
+  int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / G);
+  int g = lane % G;
+  bool valid = i < n;  // every lane joins the shuffles below
+  T acc = T(0);
+  if (MODE != kJacobiZero) {
+    if (valid) {
+      int p1 = __ldg(rp + i + 1);
+      for (int p = __ldg(rp + i) + g; p < p1; p += G) acc = fma(__ldg(va + p), __ldg(x + __ldg(ci + p)), acc);
+    }
+    acc = group_sum<G>(acc);
+  }
+  if (!valid || g != 0) return;
+  if (MODE == kJacobi) y[i] = x[i] + (omega * (b[i] - acc)) * dinv[i];
+  else if (MODE == kJacobiZero) y[i] = (omega * b[i]) * dinv[i];
+  else if (MODE == kResid) y[i] = b[i] - acc;
+  else if (MODE == kSpmv) y[i] = acc;
+  else y[i] = y[i] + acc;
+}
+
+template <typename T>
+__global__ void dense_gemv_kernel(int n, const T* __restrict__ A, const T* __restrict__ x, T* __restrict__ y) {
+  int lane = threadIdx.x & 31;
+  int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (i >= n) return;
+  T acc = T(0);
+  for (int j = lane; j < n; j += 32) acc = fma(A[(size_t)i * n + j], x[j], acc);
+  acc = warp_sum(acc);
+  if (lane == 0) y[i] = acc;
+}
+
+template <typename S, typename D>
+__global__ void convert_kernel(size_t n, const S* __restrict__ a, D* __restrict__ b) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) b[t] = D(a[t]);
+}
+
+template <typename T>
+__global__ void diag_inv_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                const double* __restrict__ va, T* __restrict__ dinv,
+                                int* __restrict__ bad_row) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double d = 0.0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p)
+    if (ci[p] == i) d = va[p];
+  if (!(d > 0.0)) atomicMin(bad_row, i);
+  dinv[i] = T(1.0 / d);
+}
+
+// =================================================================== host
+template <typename T, int LD>
+static bamg_status relax_ld(int n, const int32_t* rp, const int32_t* ci, const T* va, const T* dinv,
+                            const T* X, T* Y, const T* R, const T* sig, T omega, int keep0,
+                            cudaStream_t s) {
+  using C = Blk<T, LD>;
+  unsigned blocks = cdiv(n, 8 * C::RPW);
+  return launch(relax_block_kernel<T, LD>, dim3(blocks), dim3(256), 0, s, n, rp, ci, va, dinv, X, Y, R,
+                sig, omega, keep0);
+}
+
+template <typename T, int LD>
+static bamg_status spmm_ld(int rows, const int32_t* rp, const int32_t* ci, const T* va, const T* X, T* Y,
+                           cudaStream_t s) {
+  using C = Blk<T, LD>;
+  return launch(spmm_block_kernel<T, LD>, dim3(cdiv(rows, 8 * C::RPW)), dim3(256), 0, s, rows, rp, ci, va,
+                X, Y);
+}
+
+#define BAMG_LD_DISPATCH(ld, CALL)                 \
+  switch (ld) {                                    \
+    case 4: { constexpr int LDC = 4; CALL; }       \
+    case 8: { constexpr int LDC = 8; CALL; }       \
+    case 16: { constexpr int LDC = 16; CALL; }     \
+    case 32: { constexpr int LDC = 32; CALL; }     \
+    default: set_error("block width %d not in {4,8,16,32}", ld); return BAMG_ERR_ARG; \
+  }
+
+template <typename T>
+bamg_status relax_block(int n, int ld, const int32_t* rp, const int32_t* ci, const T* va, const T* dinv,
+                        const T* X, T* Y, const T* R, const T* sig, T omega, int keep0, cudaStream_t s) {
+  BAMG_LD_DISPATCH(ld, return (relax_ld<T, LDC>(n, rp, ci, va, dinv, X, Y, R, sig, omega, keep0, s)));
+}
+
+template <typename T>
+bamg_status spmm_block(int rows, int ld, const int32_t* rp, const int32_t* ci, const T* va, const T* X,
+                       T* Y, cudaStream_t s) {
+  BAMG_LD_DISPATCH(ld, return (spmm_ld<T, LDC>(rows, rp, ci, va, X, Y, s)));
+}
+
+static int reduce_blocks(int n, int rows_per_block) {
+  int nb = (int)cdiv(n, rows_per_block);
+  int cap = 4 * num_sms();
+  return nb < cap ? (nb > 0 ? nb : 1) : cap;
+}
+
+template <typename T, int LD>
+static bamg_status norms_ld(int n, int r, const int32_t* rp, const int32_t* ci, const T* va, T* X,
+                            int normalise, int skip0, T* scale, double* w, double* norms, cudaStream_t s) {
+  using C = Blk<T, LD>;
+  int nb = reduce_blocks(n, 8 * C::RPW);
+  DevMem part, sums;
+  BAMG_TRY(part.alloc(sizeof(double) * nb * 3 * LD, s));
+  BAMG_TRY(sums.alloc(sizeof(double) * 3 * LD, s));
+  BAMG_TRY(launch(coldot_kernel<T, LD, 0>, dim3(nb), dim3(256), 0, s, n, rp, ci, va, (const T*)X,
+                  (const T*)nullptr, (const T*)nullptr, (const T*)nullptr, (const T*)nullptr,
+                  (const T*)nullptr, (const T*)nullptr, 0, part.as<double>()));
+  BAMG_TRY(reduce_partials(part.as<double>(), nb, 3 * LD, sums.as<double>(), s));
+  BAMG_TRY(launch(weights_finalize_kernel<T, LD>, dim3(1), dim3(32), 0, s, (const double*)sums.as<double>(),
+                  r, skip0, scale, w, norms));
+  if (normalise)
+    BAMG_TRY(launch(scale_cols_kernel<T, LD>, dim3(cdiv((long long)n * LD, 256)), dim3(256), 0, s, n, X,
+                    (const T*)scale));
+  return BAMG_OK;
+}
+
+template <typename T>
+bamg_status norms_weights(int n, int ld, int r, const int32_t* rp, const int32_t* ci, const T* va, T* X,
+                          int normalise, int skip0, T* scale, double* w, double* norms, cudaStream_t s) {
+  BAMG_LD_DISPATCH(ld, return (norms_ld<T, LDC>(n, r, rp, ci, va, X, normalise, skip0, scale, w, norms, s)));
+}
+
+template <typename T, int LD>
+static bamg_status dots_ld(int n, int npairs, const T* A0, const T* B0, const T* A1, const T* B1,
+                           const T* A2, const T* B2, double* sums, cudaStream_t s) {
+  using C = Blk<T, LD>;
+  int nb = reduce_blocks(n, 8 * C::RPW);
+  DevMem part;
+  BAMG_TRY(part.alloc(sizeof(double) * nb * 3 * LD, s));
+  BAMG_TRY(launch(coldot_kernel<T, LD, 1>, dim3(nb), dim3(256), 0, s, n, (const int32_t*)nullptr,
+                  (const int32_t*)nullptr, (const T*)nullptr, (const T*)nullptr, A0, B0, A1, B1, A2, B2,
+                  npairs, part.as<double>()));
+  return reduce_partials(part.as<double>(), nb, 3 * LD, sums, s);
+}
+
+template <typename T>
+bamg_status col_dots(int n, int ld, int npairs, const T* A0, const T* B0, const T* A1, const T* B1,
+                     const T* A2, const T* B2, double* sums, cudaStream_t s) {
+  BAMG_LD_DISPATCH(ld, return (dots_ld<T, LDC>(n, npairs, A0, B0, A1, B1, A2, B2, sums, s)));
+}
+
+template <typename T>
+bamg_status rayleigh_finalize(const double* sums, int ld, int r, T* sig, double* sig64, cudaStream_t s) {
+  return launch(rayleigh_finalize_kernel<T>, dim3(1), dim3(32), 0, s, sums, ld, r, sig, sig64);
+}
+
+template <typename T>
+bamg_status init_vectors(int n, int ld, int r, uint64_t seed, T* U, T* V, cudaStream_t s) {
+  unsigned g = cdiv((long long)n * ld, 256);
+  BAMG_LD_DISPATCH(ld, return launch(init_vectors_kernel<T, LDC>, dim3(g), dim3(256), 0, s, n, r, seed, U, V));
+}
+
+template <typename T>
+bamg_status inject(int nc, int ld, const int32_t* cpt, const T* X, T* Xc, cudaStream_t s) {
+  unsigned g = cdiv((long long)nc * ld, 256);
+  BAMG_LD_DISPATCH(ld, return launch(inject_kernel<T, LDC>, dim3(g), dim3(256), 0, s, nc, cpt, X, Xc));
+}
+
+template <typename T, int MODE>
+static bamg_status vec_g(int n, int G, const int32_t* rp, const int32_t* ci, const T* va, const T* dinv,
+                         T omega, const T* x, const T* b, T* y, cudaStream_t s) {
+  unsigned g = cdiv((long long)n * G, 256);
+  switch (G) {
+    case 2: return launch(csr_vec_kernel<T, 2, MODE>, dim3(g), dim3(256), 0, s, n, rp, ci, va, dinv, omega, x, b, y);
+    case 4: return launch(csr_vec_kernel<T, 4, MODE>, dim3(g), dim3(256), 0, s, n, rp, ci, va, dinv, omega, x, b, y);
+    case 8: return launch(csr_vec_kernel<T, 8, MODE>, dim3(g), dim3(256), 0, s, n, rp, ci, va, dinv, omega, x, b, y);
+    case 16: return launch(csr_vec_kernel<T, 16, MODE>, dim3(g), dim3(256), 0, s, n, rp, ci, va, dinv, omega, x, b, y);
+    default: return launch(csr_vec_kernel<T, 32, MODE>, dim3(g), dim3(256), 0, s, n, rp, ci, va, dinv, omega, x, b, y);
+  }
+}
+
+template <typename T>
+bamg_status csr_vec(int mode, int n, int G, const int32_t* rp, const int32_t* ci, const T* va, const T* dinv,
+                    T omega, const T* x, const T* b, T* y, cudaStream_t s) {
+  switch (mode) {
+    case kJacobi: return vec_g<T, kJacobi>(n, G, rp, ci, va, dinv, omega, x, b, y, s);
+    case kJacobiZero: return vec_g<T, kJacobiZero>(n, G, rp, ci, va, dinv, omega, x, b, y, s);
+    case kResid: return vec_g<T, kResid>(n, G, rp, ci, va, dinv, omega, x, b, y, s);
+    case kSpmv: return vec_g<T, kSpmv>(n, G, rp, ci, va, dinv, omega, x, b, y, s);
+    default: return vec_g<T, kSpmvAdd>(n, G, rp, ci, va, dinv, omega, x, b, y, s);
+  }
+}
+
+template <typename T>
+bamg_status dense_gemv(int n, const T* A, const T* x, T* y, cudaStream_t s) {
+  return launch(dense_gemv_kernel<T>, dim3(cdiv((long long)n * 32, 256)), dim3(256), 0, s, n, A, x, y);
+}
+
+template <typename S, typename D>
+bamg_status convert(size_t n, const S* a, D* b, cudaStream_t s) {
+  return launch(convert_kernel<S, D>, dim3(cdiv((long long)n, 256)), dim3(256), 0, s, n, a, b);
+}
+
+template <typename T>
+bamg_status diag_inv(int n, const int32_t* rp, const int32_t* ci, const double* va, T* dinv, int* bad_row,
+                     cudaStream_t s) {
+  return launch(diag_inv_kernel<T>, dim3(cdiv(n, 256)), dim3(256), 0, s, n, rp, ci, va, dinv, bad_row);
+}
+
+#define BAMG_INST(T)                                                                                       \
+  template bamg_status relax_block<T>(int, int, const int32_t*, const int32_t*, const T*, const T*,       \
+                                      const T*, T*, const T*, const T*, T, int, cudaStream_t);           \
+  template bamg_status spmm_block<T>(int, int, const int32_t*, const int32_t*, const T*, const T*, T*,    \
+                                     cudaStream_t);                                                     \
+  template bamg_status norms_weights<T>(int, int, int, const int32_t*, const int32_t*, const T*, T*, int, \
+                                        int, T*, double*, double*, cudaStream_t);                       \
+  template bamg_status col_dots<T>(int, int, int, const T*, const T*, const T*, const T*, const T*,       \
+                                   const T*, double*, cudaStream_t);                                    \
+  template bamg_status rayleigh_finalize<T>(const double*, int, int, T*, double*, cudaStream_t);         \
+  template bamg_status init_vectors<T>(int, int, int, uint64_t, T*, T*, cudaStream_t);                   \
+  template bamg_status inject<T>(int, int, const int32_t*, const T*, T*, cudaStream_t);                  \
+  template bamg_status csr_vec<T>(int, int, int, const int32_t*, const int32_t*, const T*, const T*, T,   \
+                                  const T*, const T*, T*, cudaStream_t);                                \
+  template bamg_status dense_gemv<T>(int, const T*, const T*, T*, cudaStream_t);                         \
+  template bamg_status diag_inv<T>(int, const int32_t*, const int32_t*, const double*, T*, int*,         \
+                                   cudaStream_t);
+
+BAMG_INST(float)
+BAMG_INST(double)
+template bamg_status convert<double, float>(size_t, const double*, float*, cudaStream_t);
+template bamg_status convert<float, double>(size_t, const float*, double*, cudaStream_t);
+template bamg_status convert<double, double>(size_t, const double*, double*, cudaStream_t);
+template bamg_status convert<float, float>(size_t, const float*, float*, cudaStream_t);
+
+}  // namespace bamg

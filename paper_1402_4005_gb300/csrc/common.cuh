@@ -1,0 +1,179 @@
+// Internal helpers shared by the translation units of libbamg.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <cstdio>
+#include <utility>
+
+#include "bamg.h"
+#include "bamg_steps.h"
+
+namespace bamg {
+
+// ------------------------------------------------------------ status plumbing
+void set_error(const char* fmt, ...);
+extern std::atomic<uint64_t> g_launches;
+
+#define BAMG_TRY(...)                                    \
+  do {                                                   \
+    bamg_status s_ = (__VA_ARGS__);                      \
+    if (s_ != BAMG_OK) return s_;                        \
+  } while (0)
+
+#define BAMG_CUDA(...)                                                          \
+  do {                                                                          \
+    cudaError_t e_ = (__VA_ARGS__);                                             \
+    if (e_ != cudaSuccess) {                                                    \
+      bamg::set_error("%s:%d %s: %s", __FILE__, __LINE__, #__VA_ARGS__,         \
+                      cudaGetErrorString(e_));                                  \
+      return e_ == cudaErrorMemoryAllocation ? BAMG_ERR_OOM : BAMG_ERR_CUDA;    \
+    }                                                                           \
+  } while (0)
+
+#define BAMG_CHECK_ARG(cond)                                         \
+  do {                                                               \
+    if (!(cond)) {                                                   \
+      bamg::set_error("%s:%d invalid argument: %s", __FILE__, __LINE__, #cond); \
+      return BAMG_ERR_ARG;                                           \
+    }                                                                \
+  } while (0)
+
+// Launch a kernel, count it and check the launch.
+template <typename... KArgs, typename... Args>
+inline bamg_status launch(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                          cudaStream_t s, Args&&... args) {
+  if (grid.x == 0 || grid.y == 0 || grid.z == 0) return BAMG_OK;
+  k<<<grid, block, smem, s>>>(std::forward<Args>(args)...);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("kernel launch failed: %s", cudaGetErrorString(e));
+    return BAMG_ERR_CUDA;
+  }
+  return BAMG_OK;
+}
+
+inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+// --------------------------------------------------- stream-ordered buffers
+// Device memory from the stream-ordered pool (cudaMallocAsync); freed on the
+// same stream.  The pool keeps freed blocks, so repeated setups re-use them.
+struct DevMem {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaStream_t s = nullptr;
+  DevMem() = default;
+  DevMem(const DevMem&) = delete;
+  DevMem& operator=(const DevMem&) = delete;
+  DevMem(DevMem&& o) noexcept { *this = std::move(o); }
+  DevMem& operator=(DevMem&& o) noexcept {
+    if (this != &o) {
+      release();
+      p = o.p; bytes = o.bytes; s = o.s;
+      o.p = nullptr; o.bytes = 0;
+    }
+    return *this;
+  }
+  ~DevMem() { release(); }
+  void release() {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+    bytes = 0;
+  }
+  bamg_status alloc(size_t nbytes, cudaStream_t st) {
+    release();
+    s = st;
+    if (nbytes == 0) nbytes = 16;
+    cudaError_t e = cudaMallocAsync(&p, nbytes, st);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      set_error("cudaMallocAsync(%zu) failed: %s", nbytes, cudaGetErrorString(e));
+      return BAMG_ERR_OOM;
+    }
+    bytes = nbytes;
+    return BAMG_OK;
+  }
+  template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+void configure_pool(int device);
+
+// ------------------------------------------------------------ device helpers
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+
+// SplitMix64 output function (Steele, Lea, Flood 2014; constants of Vigna's
+// public-domain splitmix64.c).  Counter-based: output k of a generator with
+// state s is mix(s + (k + 1) * gamma).
+__host__ __device__ inline uint64_t splitmix_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__host__ __device__ inline uint64_t splitmix_draw(uint64_t seed, uint64_t stream, uint64_t i) {
+  uint64_t ctr = (stream << 32) + i;
+  return splitmix_mix(seed + (ctr + 1ull) * kGamma);
+}
+// uniform(-1, 1): 53 high bits to [0, 1), then 2u - 1 (exact in double).
+__host__ __device__ inline double splitmix_pm1(uint64_t seed, uint64_t stream, uint64_t i) {
+  double u = (double)(splitmix_draw(seed, stream, i) >> 11) * 0x1.0p-53;
+  return 2.0 * u - 1.0;
+}
+
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int W = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int W = 2; };
+
+__device__ inline void vload(const float* p, float (&v)[4]) {
+  float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ inline void vload(const double* p, double (&v)[2]) {
+  double2 t = *reinterpret_cast<const double2*>(p);
+  v[0] = t.x; v[1] = t.y;
+}
+__device__ inline void vstore(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ inline void vstore(double* p, const double (&v)[2]) {
+  *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+}
+__device__ inline void vload_ro(const float* p, float (&v)[4]) {
+  float4 t = __ldg(reinterpret_cast<const float4*>(p));
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ inline void vload_ro(const double* p, double (&v)[2]) {
+  double2 t = __ldg(reinterpret_cast<const double2*>(p));
+  v[0] = t.x; v[1] = t.y;
+}
+
+template <typename T>
+__device__ inline T warp_sum(T v, unsigned mask = 0xffffffffu) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+  return v;
+}
+
+// Sum over aligned groups of G lanes (G power of two <= 32).
+template <int G, typename T>
+__device__ inline T group_sum(T v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ----------------------------------------------------- small internal APIs
+// Exclusive scan of n int32 counts into out[0..n] (out[n] = total), int64
+// total returned through total_host when non-null (synchronises the stream).
+bamg_status scan_counts(const int32_t* counts, int32_t* out, int n, cudaStream_t s,
+                        int64_t* total_host);
+
+// Deterministic reduction of per-block partial sums: partial[nb][K] -> out[K].
+bamg_status reduce_partials(const double* partial, int nb, int K, double* out,
+                            cudaStream_t s);
+
+int num_sms();
+
+}  // namespace bamg

@@ -1,0 +1,477 @@
+// Setup phase: B = I - A and one bootstrap cycle (Algorithm 1) on the device.
+//
+// Top-down, level by level: relax the test-vector blocks V (with B) and U
+// (with B^T, u^(1) = 1 fixed), normalise and weight them (eq. ls_weights),
+// split C/F, fit P rows and Q columns (eq. ls_interpolation, Section 5),
+// form B_{l+1} = Q B P, M_{l+1} = Q M Q^T, N_{l+1} = P^T N P, inject.  On the
+// coarsest level, the r smallest generalized singular triplets and B_L^+.
+// Bottom-up: interpolate the triplets (Q^T u, P v) and relax the
+// inhomogeneous systems B v = sigma M u, B^T u = sigma N v with the Rayleigh
+// quotient update (eq. singular_value).  Only sizes are read back to the
+// host; all arithmetic runs in the kernels.
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "hierarchy.cuh"
+
+namespace bamg {
+
+// ------------------------------------------------------------ small kernels
+__global__ void pad_block_kernel(int n, int r, int ld, const double* __restrict__ src, float* __restrict__ d32,
+                                 double* __restrict__ d64) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)n * ld) return;
+  int i = (int)(t / ld), k = (int)(t % ld);
+  double v = k < r ? src[(size_t)i * r + k] : 0.0;
+  if (d32) d32[t] = (float)v;
+  if (d64) d64[t] = v;
+}
+
+__global__ void column_kernel(int n, int ld, int k, const double* __restrict__ X, double* __restrict__ x) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = X[(size_t)i * ld + k];
+}
+
+// partial sums of x and |x| per block
+__global__ void sum_abs_kernel(int n, const double* __restrict__ x, double* __restrict__ part) {
+  __shared__ double sh[2][8];
+  double s = 0.0, a = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    s += x[i];
+    a += fabs(x[i]);
+  }
+  s = warp_sum(s); a = warp_sum(a);
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { sh[0][w] = s; sh[1][w] = a; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ts = 0, ta = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { ts += sh[0][k]; ta += sh[1][k]; }
+    part[2 * blockIdx.x] = ts;
+    part[2 * blockIdx.x + 1] = ta;
+  }
+}
+
+// x <- x * sign(sum) / ||x||_1  (positive orientation, unit 1-norm)
+__global__ void orient_kernel(int n, const double* __restrict__ sums, double* __restrict__ x) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double f = (sums[0] < 0.0 ? -1.0 : 1.0) / sums[1];
+  x[i] *= f;
+}
+
+bamg_status abs_sums(int n, const double* x, double* out, cudaStream_t s) {
+  int nb = (int)cdiv(n, 256);
+  if (nb > 4 * num_sms()) nb = 4 * num_sms();
+  DevMem part;
+  BAMG_TRY(part.alloc(sizeof(double) * 2 * nb, s));
+  BAMG_TRY(launch(sum_abs_kernel, dim3(nb), dim3(256), 0, s, n, x, part.as<double>()));
+  return reduce_partials(part.as<double>(), nb, 2, out, s);
+}
+
+bamg_status orient_normalise(int n, double* x, cudaStream_t s) {
+  DevMem sums;
+  BAMG_TRY(sums.alloc(sizeof(double) * 2, s));
+  BAMG_TRY(abs_sums(n, x, sums.as<double>(), s));
+  return launch(orient_kernel, dim3(cdiv(n, 256)), dim3(256), 0, s, n, (const double*)sums.as<double>(), x);
+}
+
+// ------------------------------------------------------------ csr helpers
+static bamg_status csr_transpose(const Csr& A, Csr& T, cudaStream_t s) {
+  BAMG_TRY(T.alloc(A.cols, A.rows, A.nnz, s));
+  return transpose_csr(A.rows, A.cols, A.nnz, A.r(), A.c(), A.v(), T.rp.as<int32_t>(), T.ci.as<int32_t>(),
+                       T.va.as<double>(), s);
+}
+
+static bamg_status csr_product(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
+  DevMem rp;
+  BAMG_TRY(rp.alloc(sizeof(int32_t) * (A.rows + 1), s));
+  int64_t nnz = 0;
+  BAMG_TRY(spgemm_symbolic(A.rows, A.r(), A.c(), B.r(), B.c(), rp.as<int32_t>(), &nnz, s));
+  C.rows = A.rows; C.cols = B.cols; C.nnz = (int)nnz;
+  C.rp = std::move(rp);
+  BAMG_TRY(C.ci.alloc(sizeof(int32_t) * (nnz > 0 ? nnz : 1), s));
+  BAMG_TRY(C.va.alloc(sizeof(double) * (nnz > 0 ? nnz : 1), s));
+  return spgemm_numeric(A.rows, A.r(), A.c(), A.v(), B.r(), B.c(), B.v(), C.r(), C.ci.as<int32_t>(),
+                        C.va.as<double>(), s);
+}
+
+// B^T, 1/diag(B) (Jacobi needs b_ii > 0: Section 3 / coarse levels), lanes.
+static bamg_status finish_level(bamg_hierarchy* h, Level& L, int l, cudaStream_t s) {
+  L.n = L.B.rows;
+  BAMG_TRY(csr_transpose(L.B, L.Bt, s));
+  BAMG_TRY(L.dinv.alloc(sizeof(double) * L.n, s));
+  DevMem bad;
+  BAMG_TRY(bad.alloc(sizeof(int), s));
+  int big = INT32_MAX;
+  BAMG_CUDA(cudaMemcpyAsync(bad.p, &big, sizeof(int), cudaMemcpyHostToDevice, s));
+  BAMG_TRY(diag_inv<double>(L.n, L.B.r(), L.B.c(), L.B.v(), L.dinv.as<double>(), bad.as<int>(), s));
+  int hb = 0;
+  BAMG_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BAMG_CUDA(cudaStreamSynchronize(s));
+  if (hb != INT32_MAX) {
+    set_error("level %d: non-positive diagonal of B at row %d", l, hb);
+    return BAMG_ERR_NUMERIC;
+  }
+  double avg = L.n ? (double)L.B.nnz / L.n : 1.0;
+  L.vec_g = avg <= 3 ? 2 : avg <= 6 ? 4 : avg <= 12 ? 8 : avg <= 24 ? 16 : 32;
+  if (h->mixed) {
+    BAMG_TRY(L.B.make32(s));
+    BAMG_TRY(L.Bt.make32(s));
+    BAMG_TRY(L.dinv32.alloc(sizeof(float) * L.n, s));
+    BAMG_TRY(convert<double, float>((size_t)L.n, L.dinv.as<double>(), L.dinv32.as<float>(), s));
+    if (!L.M.empty()) BAMG_TRY(L.M.make32(s));
+    if (!L.N.empty()) BAMG_TRY(L.N.make32(s));
+  }
+  return BAMG_OK;
+}
+
+template <typename T> static const T* dinv_of(const Level& L);
+template <> const double* dinv_of<double>(const Level& L) { return L.dinv.as<double>(); }
+template <> const float* dinv_of<float>(const Level& L) { return L.dinv32.as<float>(); }
+
+static bool is_coarsest(const bamg_hierarchy* h, const Level& L, int l) {
+  const bamg_params& p = h->p;
+  if (l + 1 >= p.max_levels || L.n <= p.coarse_min) return true;
+  if (p.coarsening == BAMG_COARSEN_GEOMETRIC && (L.nx < 3 && L.ny < 3)) return true;
+  return false;
+}
+
+// ------------------------------------------------------------ one level down
+template <typename T>
+static bamg_status coarsen_level(bamg_hierarchy* h, int l, DevMem& U, DevMem& V, DevMem& Uc, DevMem& Vc,
+                                 DevMem& tmpU, DevMem& tmpV, DevMem& scale, DevMem& norms, DevMem& rkd,
+                                 cudaStream_t s) {
+  const bamg_params& p = h->p;
+  const int ld = h->ld, r = p.r;
+  Level& L = h->lv[l];
+  const T om = T(p.omega);
+  const T* Bv = L.B.vals<T>();
+  const T* Btv = L.Bt.vals<T>();
+  const T* dv = dinv_of<T>(L);
+  // Algorithm 1, first smoothing loop: relax V with B and U with B^T
+  for (int it = 0; it < p.nu_setup; ++it) {
+    BAMG_TRY(relax_block<T>(L.n, ld, L.B.r(), L.B.c(), Bv, dv, V.as<T>(), tmpV.as<T>(), nullptr, nullptr, om,
+                            0, s));
+    std::swap(V, tmpV);
+    BAMG_TRY(relax_block<T>(L.n, ld, L.Bt.r(), L.Bt.c(), Btv, dv, U.as<T>(), tmpU.as<T>(), nullptr, nullptr,
+                            om, 1, s));
+    std::swap(U, tmpU);
+  }
+  // eq. ls_weights with unit vectors
+  BAMG_TRY(L.s.alloc(sizeof(double) * ld, s));
+  BAMG_TRY(L.t.alloc(sizeof(double) * ld, s));
+  BAMG_TRY(norms_weights<T>(L.n, ld, r, L.B.r(), L.B.c(), Bv, V.as<T>(), 1, 0, scale.as<T>(),
+                            L.s.as<double>(), norms.as<double>(), s));
+  BAMG_TRY(norms_weights<T>(L.n, ld, r, L.Bt.r(), L.Bt.c(), Btv, U.as<T>(), 1, 1, scale.as<T>(),
+                            L.t.as<double>(), norms.as<double>(), s));
+  // C/F splitting and interpolation sets
+  BAMG_TRY(L.cf.alloc(L.n, s));
+  BAMG_TRY(L.cmap.alloc(sizeof(int32_t) * L.n, s));
+  BAMG_TRY(L.Jrp.alloc(sizeof(int32_t) * (L.n + 1), s));
+  int nc = 0;
+  int cgx = 0, cgy = 0;
+  if (p.coarsening == BAMG_COARSEN_GEOMETRIC) {
+    BAMG_TRY(L.Jci.alloc(sizeof(int32_t) * 4 * (size_t)L.n, s));
+    BAMG_TRY(coarsen_geometric(L.nx, L.ny, L.cf.as<int8_t>(), L.cmap.as<int32_t>(), L.Jrp.as<int32_t>(),
+                               L.Jci.as<int32_t>(), &nc, s));
+    cgx = (L.nx + 1) / 2;
+    cgy = (L.ny + 1) / 2;
+  } else {
+    BAMG_TRY(coarsen_mis(L.n, L.B.r(), L.B.c(), L.Bt.r(), L.Bt.c(), p.seed, l, L.cf.as<int8_t>(),
+                         L.cmap.as<int32_t>(), &nc, s));
+    BAMG_TRY(L.Jci.alloc(sizeof(int32_t) * (size_t)p.c_max * L.n, s));
+    BAMG_TRY(graph_sets(L.n, L.B.r(), L.B.c(), L.B.v(), L.Bt.r(), L.Bt.c(), L.Bt.v(), L.cf.as<int8_t>(),
+                        p.c_min, p.c_max, L.Jrp.as<int32_t>(), L.Jci.as<int32_t>(), s));
+  }
+  if (nc < 1 || nc >= L.n) {
+    set_error("level %d: coarsening produced %d coarse points of %d", l, nc, L.n);
+    return BAMG_ERR_NUMERIC;
+  }
+  L.nc = nc;
+  BAMG_TRY(L.cpt.alloc(sizeof(int32_t) * nc, s));
+  BAMG_TRY(coarse_points(L.n, L.cf.as<int8_t>(), L.cmap.as<int32_t>(), L.cpt.as<int32_t>(), s));
+  int32_t njz = 0;
+  BAMG_CUDA(cudaMemcpyAsync(&njz, L.Jrp.as<int32_t>() + L.n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  BAMG_CUDA(cudaStreamSynchronize(s));
+  // P rows and Q columns (eq. ls_interpolation; Section 5)
+  DevMem fitP, fitQ;
+  BAMG_TRY(fitP.alloc(sizeof(double) * (njz > 0 ? njz : 1), s));
+  BAMG_TRY(fitQ.alloc(sizeof(double) * (njz > 0 ? njz : 1), s));
+  BAMG_TRY(ls_fit<T>(L.n, ld, r, L.Jrp.as<int32_t>(), L.Jci.as<int32_t>(), V.as<T>(), L.s.as<double>(), 0,
+                     fitP.as<double>(), rkd.as<int>(), s));
+  if (p.restriction == BAMG_RESTRICT_AVERAGE)
+    BAMG_TRY(average_fits(L.n, L.Jrp.as<int32_t>(), fitQ.as<double>(), s));
+  else
+    BAMG_TRY(ls_fit<T>(L.n, ld, r, L.Jrp.as<int32_t>(), L.Jci.as<int32_t>(), U.as<T>(), L.t.as<double>(), 1,
+                       fitQ.as<double>(), rkd.as<int>(), s));
+  int nnzP = njz + nc;
+  for (Csr* X : {&L.P, &L.Qt}) {
+    BAMG_TRY(X->alloc(L.n, nc, nnzP, s));
+    BAMG_TRY(transfer_pattern(L.n, L.cf.as<int8_t>(), L.cmap.as<int32_t>(), L.Jrp.as<int32_t>(),
+                              L.Jci.as<int32_t>(), X->rp.as<int32_t>(), X->ci.as<int32_t>(),
+                              X->va.as<double>(), s));
+  }
+  BAMG_TRY(scatter_fits(L.n, L.cf.as<int8_t>(), L.Jrp.as<int32_t>(), fitP.as<double>(), L.P.r(),
+                        L.P.va.as<double>(), s));
+  BAMG_TRY(scatter_fits(L.n, L.cf.as<int8_t>(), L.Jrp.as<int32_t>(), fitQ.as<double>(), L.Qt.r(),
+                        L.Qt.va.as<double>(), s));
+  BAMG_TRY(csr_transpose(L.Qt, L.Q, s));
+  BAMG_TRY(csr_transpose(L.P, L.Pt, s));
+  // Petrov-Galerkin operators (Section 3; Algorithm 1)
+  h->lv.emplace_back();
+  Level& Lc = h->lv[l + 1];
+  Level& Lf = h->lv[l];
+  {
+    Csr BP;
+    BAMG_TRY(csr_product(Lf.B, Lf.P, BP, s));
+    BAMG_TRY(csr_product(Lf.Q, BP, Lc.B, s));
+  }
+  if (Lf.M.empty()) {
+    BAMG_TRY(csr_product(Lf.Q, Lf.Qt, Lc.M, s));
+  } else {
+    Csr MQt;
+    BAMG_TRY(csr_product(Lf.M, Lf.Qt, MQt, s));
+    BAMG_TRY(csr_product(Lf.Q, MQt, Lc.M, s));
+  }
+  if (Lf.N.empty()) {
+    BAMG_TRY(csr_product(Lf.Pt, Lf.P, Lc.N, s));
+  } else {
+    Csr NP;
+    BAMG_TRY(csr_product(Lf.N, Lf.P, NP, s));
+    BAMG_TRY(csr_product(Lf.Pt, NP, Lc.N, s));
+  }
+  Lc.nx = cgx;
+  Lc.ny = cgy;
+  BAMG_TRY(finish_level(h, Lc, l + 1, s));
+  if (h->mixed) {
+    BAMG_TRY(Lf.P.make32(s));
+    BAMG_TRY(Lf.Qt.make32(s));
+    BAMG_TRY(Lf.Q.make32(s));
+  }
+  // injection of the test vectors
+  BAMG_TRY(Uc.alloc(sizeof(T) * (size_t)nc * ld, s));
+  BAMG_TRY(Vc.alloc(sizeof(T) * (size_t)nc * ld, s));
+  BAMG_TRY(inject<T>(nc, ld, Lf.cpt.as<int32_t>(), U.as<T>(), Uc.as<T>(), s));
+  BAMG_TRY(inject<T>(nc, ld, Lf.cpt.as<int32_t>(), V.as<T>(), Vc.as<T>(), s));
+  return BAMG_OK;
+}
+
+// Inhomogeneous relaxation with the Rayleigh update on level l.
+template <typename T>
+static bamg_status relax_triplets(bamg_hierarchy* h, int l, DevMem& U, DevMem& V, DevMem& sig, DevMem& sig64,
+                                  cudaStream_t s) {
+  const bamg_params& p = h->p;
+  const int ld = h->ld, r = p.r;
+  Level& L = h->lv[l];
+  size_t bytes = sizeof(T) * (size_t)L.n * ld;
+  DevMem tU, tV, MU, NV, BV, sums;
+  BAMG_TRY(tU.alloc(bytes, s));
+  BAMG_TRY(tV.alloc(bytes, s));
+  BAMG_TRY(BV.alloc(bytes, s));
+  if (!L.M.empty()) BAMG_TRY(MU.alloc(bytes, s));
+  if (!L.N.empty()) BAMG_TRY(NV.alloc(bytes, s));
+  BAMG_TRY(sums.alloc(sizeof(double) * 3 * ld, s));
+  const T om = T(p.omega);
+  const T* dv = dinv_of<T>(L);
+  for (int it = 0; it < p.nu_setup; ++it) {
+    const T* mu = U.as<T>();
+    const T* nv = V.as<T>();
+    if (!L.M.empty()) {
+      BAMG_TRY(spmm_block<T>(L.n, ld, L.M.r(), L.M.c(), L.M.vals<T>(), U.as<T>(), MU.as<T>(), s));
+      mu = MU.as<T>();
+    }
+    if (!L.N.empty()) {
+      BAMG_TRY(spmm_block<T>(L.n, ld, L.N.r(), L.N.c(), L.N.vals<T>(), V.as<T>(), NV.as<T>(), s));
+      nv = NV.as<T>();
+    }
+    // both from the previous iterates (Algorithm 1, second smoothing loop)
+    BAMG_TRY(relax_block<T>(L.n, ld, L.B.r(), L.B.c(), L.B.vals<T>(), dv, V.as<T>(), tV.as<T>(), mu,
+                            sig.as<T>(), om, 0, s));
+    BAMG_TRY(relax_block<T>(L.n, ld, L.Bt.r(), L.Bt.c(), L.Bt.vals<T>(), dv, U.as<T>(), tU.as<T>(), nv,
+                            sig.as<T>(), om, 0, s));
+    std::swap(U, tU);
+    std::swap(V, tV);
+    // eq. singular_value
+    BAMG_TRY(spmm_block<T>(L.n, ld, L.B.r(), L.B.c(), L.B.vals<T>(), V.as<T>(), BV.as<T>(), s));
+    mu = U.as<T>();
+    nv = V.as<T>();
+    if (!L.M.empty()) {
+      BAMG_TRY(spmm_block<T>(L.n, ld, L.M.r(), L.M.c(), L.M.vals<T>(), U.as<T>(), MU.as<T>(), s));
+      mu = MU.as<T>();
+    }
+    if (!L.N.empty()) {
+      BAMG_TRY(spmm_block<T>(L.n, ld, L.N.r(), L.N.c(), L.N.vals<T>(), V.as<T>(), NV.as<T>(), s));
+      nv = NV.as<T>();
+    }
+    BAMG_TRY(col_dots<T>(L.n, ld, 3, U.as<T>(), BV.as<T>(), U.as<T>(), mu, V.as<T>(), nv, sums.as<double>(), s));
+    BAMG_TRY(rayleigh_finalize<T>(sums.as<double>(), ld, r, sig.as<T>(), sig64.as<double>(), s));
+  }
+  return BAMG_OK;
+}
+
+template <typename T>
+static bamg_status run_setup(bamg_hierarchy* h, cudaStream_t s) {
+  const bamg_params& p = h->p;
+  const int ld = h->ld, r = p.r;
+  std::vector<DevMem> U(1), V(1);
+  int n0 = h->lv[0].n;
+  BAMG_TRY(U[0].alloc(sizeof(T) * (size_t)n0 * ld, s));
+  BAMG_TRY(V[0].alloc(sizeof(T) * (size_t)n0 * ld, s));
+  BAMG_TRY(init_vectors<T>(n0, ld, r, p.seed, U[0].as<T>(), V[0].as<T>(), s));
+  DevMem scale, norms, rkd, sig, sig64;
+  BAMG_TRY(scale.alloc(sizeof(T) * ld, s));
+  BAMG_TRY(norms.alloc(sizeof(double) * ld, s));
+  BAMG_TRY(rkd.alloc(sizeof(int), s));
+  BAMG_TRY(sig.alloc(sizeof(T) * ld, s));
+  BAMG_TRY(sig64.alloc(sizeof(double) * ld, s));
+  BAMG_CUDA(cudaMemsetAsync(rkd.p, 0, sizeof(int), s));
+  int l = 0;
+  while (!is_coarsest(h, h->lv[l], l)) {
+    DevMem tU, tV;
+    size_t bytes = sizeof(T) * (size_t)h->lv[l].n * ld;
+    BAMG_TRY(tU.alloc(bytes, s));
+    BAMG_TRY(tV.alloc(bytes, s));
+    U.emplace_back();
+    V.emplace_back();
+    BAMG_TRY(coarsen_level<T>(h, l, U[l], V[l], U[l + 1], V[l + 1], tU, tV, scale, norms, rkd, s));
+    ++l;
+  }
+  // coarsest level: eq. generalized_eigenvalue and the pseudo-inverse
+  Level& LL = h->lv[l];
+  int nL = LL.n;
+  h->nL = nL;
+  int rr = r < nL ? r : nL;
+  DevMem Bd, Md, Nd, sg, Ud, Vd;
+  size_t nn = (size_t)nL * nL;
+  BAMG_TRY(Bd.alloc(sizeof(double) * nn, s));
+  BAMG_TRY(Md.alloc(sizeof(double) * nn, s));
+  BAMG_TRY(Nd.alloc(sizeof(double) * nn, s));
+  BAMG_TRY(sg.alloc(sizeof(double) * r, s));
+  BAMG_TRY(Ud.alloc(sizeof(double) * (size_t)nL * r, s));
+  BAMG_TRY(Vd.alloc(sizeof(double) * (size_t)nL * r, s));
+  BAMG_CUDA(cudaMemsetAsync(sg.p, 0, sizeof(double) * r, s));
+  BAMG_CUDA(cudaMemsetAsync(Ud.p, 0, sizeof(double) * (size_t)nL * r, s));
+  BAMG_CUDA(cudaMemsetAsync(Vd.p, 0, sizeof(double) * (size_t)nL * r, s));
+  BAMG_TRY(csr_to_dense(nL, LL.B.r(), LL.B.c(), LL.B.v(), Bd.as<double>(), s));
+  if (LL.M.empty()) {
+    std::vector<double> I(nn, 0.0);
+    for (int i = 0; i < nL; ++i) I[(size_t)i * nL + i] = 1.0;
+    BAMG_CUDA(cudaMemcpyAsync(Md.p, I.data(), sizeof(double) * nn, cudaMemcpyHostToDevice, s));
+    BAMG_CUDA(cudaMemcpyAsync(Nd.p, I.data(), sizeof(double) * nn, cudaMemcpyHostToDevice, s));
+    BAMG_CUDA(cudaStreamSynchronize(s));
+  } else {
+    BAMG_TRY(csr_to_dense(nL, LL.M.r(), LL.M.c(), LL.M.v(), Md.as<double>(), s));
+    BAMG_TRY(csr_to_dense(nL, LL.N.r(), LL.N.c(), LL.N.v(), Nd.as<double>(), s));
+  }
+  BAMG_TRY(h->Bpinv.alloc(sizeof(double) * nn, s));
+  // Ud/Vd are nL x rr row-major (rr <= r)
+  BAMG_TRY(coarsest_solve(h->mixed ? 1 : 0, nL, rr, Bd.as<double>(), Md.as<double>(), Nd.as<double>(),
+                          sg.as<double>(), Ud.as<double>(), Vd.as<double>(), h->Bpinv.as<double>(), s));
+  if (h->mixed) {
+    BAMG_TRY(h->Bpinv32.alloc(sizeof(float) * nn, s));
+    BAMG_TRY(convert<double, float>(nn, h->Bpinv.as<double>(), h->Bpinv32.as<float>(), s));
+  }
+  // triplets into padded blocks
+  BAMG_TRY(U[l].alloc(sizeof(T) * (size_t)nL * ld, s));
+  BAMG_TRY(V[l].alloc(sizeof(T) * (size_t)nL * ld, s));
+  unsigned g = cdiv((long long)nL * ld, 256);
+  float* f32 = nullptr;
+  double* f64 = nullptr;
+  if (sizeof(T) == 4) f32 = (float*)U[l].p; else f64 = (double*)U[l].p;
+  BAMG_TRY(launch(pad_block_kernel, dim3(g), dim3(256), 0, s, nL, rr, ld, (const double*)Ud.as<double>(), f32, f64));
+  if (sizeof(T) == 4) f32 = (float*)V[l].p; else f64 = (double*)V[l].p;
+  BAMG_TRY(launch(pad_block_kernel, dim3(g), dim3(256), 0, s, nL, rr, ld, (const double*)Vd.as<double>(), f32, f64));
+  {
+    unsigned g1 = cdiv(ld, 256);
+    if (sizeof(T) == 4) { f32 = (float*)sig.p; f64 = nullptr; } else { f64 = (double*)sig.p; f32 = nullptr; }
+    BAMG_TRY(launch(pad_block_kernel, dim3(g1), dim3(256), 0, s, 1, rr, ld, (const double*)sg.as<double>(), f32, f64));
+    BAMG_TRY(launch(pad_block_kernel, dim3(g1), dim3(256), 0, s, 1, rr, ld, (const double*)sg.as<double>(),
+                    (float*)nullptr, sig64.as<double>()));
+  }
+  // bottom-up: interpolate and relax (Algorithm 1, last loop)
+  for (int k = l - 1; k >= 0; --k) {
+    Level& L = h->lv[k];
+    BAMG_TRY(spmm_block<T>(L.n, ld, L.Qt.r(), L.Qt.c(), L.Qt.vals<T>(), U[k + 1].as<T>(), U[k].as<T>(), s));
+    BAMG_TRY(spmm_block<T>(L.n, ld, L.P.r(), L.P.c(), L.P.vals<T>(), V[k + 1].as<T>(), V[k].as<T>(), s));
+    BAMG_TRY(relax_triplets<T>(h, k, U[k], V[k], sig, sig64, s));
+    U[k + 1].release();
+    V[k + 1].release();
+  }
+  // finest triplets, x^(0) = v of the smallest |sigma|
+  h->sigma.assign(ld, 0.0);
+  BAMG_CUDA(cudaMemcpyAsync(h->sigma.data(), sig64.p, sizeof(double) * ld, cudaMemcpyDeviceToHost, s));
+  BAMG_TRY(h->U64.alloc(sizeof(double) * (size_t)n0 * ld, s));
+  BAMG_TRY(h->V64.alloc(sizeof(double) * (size_t)n0 * ld, s));
+  BAMG_TRY(convert<T, double>((size_t)n0 * ld, U[0].as<T>(), h->U64.as<double>(), s));
+  BAMG_TRY(convert<T, double>((size_t)n0 * ld, V[0].as<T>(), h->V64.as<double>(), s));
+  int hr = 0;
+  BAMG_CUDA(cudaMemcpyAsync(&hr, rkd.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BAMG_CUDA(cudaStreamSynchronize(s));
+  h->rankdef = hr;
+  h->sigma.resize(r);
+  int kmin = 0;
+  for (int k = 1; k < rr; ++k)
+    if (std::fabs(h->sigma[k]) < std::fabs(h->sigma[kmin])) kmin = k;
+  BAMG_TRY(h->x0.alloc(sizeof(double) * n0, s));
+  BAMG_TRY(launch(column_kernel, dim3(cdiv(n0, 256)), dim3(256), 0, s, n0, ld, kmin,
+                  (const double*)h->V64.as<double>(), h->x0.as<double>()));
+  BAMG_TRY(orient_normalise(n0, h->x0.as<double>(), s));
+  // complexities (eq. operator_complexity_def; Section 7)
+  double nnz_sum = 0, n_sum = 0;
+  for (auto& L : h->lv) { nnz_sum += L.B.nnz; n_sum += L.n; }
+  h->op_cplx = nnz_sum / h->lv[0].B.nnz;
+  h->grid_cplx = n_sum / h->lv[0].n;
+  return BAMG_OK;
+}
+
+template bamg_status run_setup<double>(bamg_hierarchy*, cudaStream_t);
+template bamg_status run_setup<float>(bamg_hierarchy*, cudaStream_t);
+
+// --------------------------------------------------------------- level 0
+bamg_status setup_finest(bamg_hierarchy* h, const bamg_csr* A, cudaStream_t s) {
+  int n = (int)A->n;
+  int nnz = (int)A->nnz;
+  DevMem arp, aci, ava;
+  const int32_t *rp = A->row_ptr, *ci = A->col_idx;
+  const double* va = A->val;
+  if (!A->on_device) {
+    BAMG_TRY(arp.alloc(sizeof(int32_t) * (n + 1), s));
+    BAMG_TRY(aci.alloc(sizeof(int32_t) * (nnz > 0 ? nnz : 1), s));
+    BAMG_TRY(ava.alloc(sizeof(double) * (nnz > 0 ? nnz : 1), s));
+    BAMG_CUDA(cudaMemcpyAsync(arp.p, rp, sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s));
+    BAMG_CUDA(cudaMemcpyAsync(aci.p, ci, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, s));
+    BAMG_CUDA(cudaMemcpyAsync(ava.p, va, sizeof(double) * nnz, cudaMemcpyHostToDevice, s));
+    rp = arp.as<int32_t>(); ci = aci.as<int32_t>(); va = ava.as<double>();
+  }
+  BAMG_TRY(check_rowptr(n, rp, nnz, s));
+  int64_t bad = 0;
+  BAMG_TRY(check_stochastic(n, rp, ci, va, h->p.stochastic_tol, &bad, s));
+  if (bad) {
+    set_error("A is not column stochastic: %lld offending entries or columns", (long long)bad);
+    return BAMG_ERR_NOT_STOCHASTIC;
+  }
+  h->lv.emplace_back();
+  Level& L = h->lv[0];
+  DevMem cnt;
+  BAMG_TRY(cnt.alloc(sizeof(int32_t) * (n + 1), s));
+  BAMG_TRY(build_B_count(n, rp, ci, cnt.as<int32_t>(), s));
+  DevMem brp;
+  BAMG_TRY(brp.alloc(sizeof(int32_t) * (n + 1), s));
+  int64_t nnzB = 0;
+  BAMG_TRY(scan_counts(cnt.as<int32_t>(), brp.as<int32_t>(), n, s, &nnzB));
+  L.B.rows = L.B.cols = n;
+  L.B.nnz = (int)nnzB;
+  L.B.rp = std::move(brp);
+  BAMG_TRY(L.B.ci.alloc(sizeof(int32_t) * nnzB, s));
+  BAMG_TRY(L.B.va.alloc(sizeof(double) * nnzB, s));
+  BAMG_TRY(build_B_fill(n, rp, ci, va, L.B.r(), L.B.ci.as<int32_t>(), L.B.va.as<double>(), s));
+  L.nx = A->nx;
+  L.ny = A->ny;
+  BAMG_TRY(finish_level(h, L, 0, s));
+  BAMG_CUDA(cudaStreamSynchronize(s));  // A's copies are released on return
+  return BAMG_OK;
+}
+
+}  // namespace bamg

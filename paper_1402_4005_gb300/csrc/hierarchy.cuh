@@ -1,0 +1,75 @@
+// The multigrid hierarchy owned by a bamg_hierarchy handle.
+#pragma once
+
+#include <vector>
+
+#include "internal.cuh"
+
+namespace bamg {
+
+struct Csr {
+  int rows = 0, cols = 0, nnz = 0;
+  DevMem rp, ci, va, va32;  // va32: float copy of the values (mixed precision)
+  const int32_t* r() const { return rp.as<int32_t>(); }
+  const int32_t* c() const { return ci.as<int32_t>(); }
+  const double* v() const { return va.as<double>(); }
+  template <typename T> const T* vals() const;
+  bamg_status alloc(int rows_, int cols_, int nnz_, cudaStream_t s) {
+    rows = rows_; cols = cols_; nnz = nnz_;
+    BAMG_TRY(rp.alloc(sizeof(int32_t) * (rows + 1), s));
+    BAMG_TRY(ci.alloc(sizeof(int32_t) * (nnz > 0 ? nnz : 1), s));
+    return va.alloc(sizeof(double) * (nnz > 0 ? nnz : 1), s);
+  }
+  bamg_status make32(cudaStream_t s) {
+    BAMG_TRY(va32.alloc(sizeof(float) * (nnz > 0 ? nnz : 1), s));
+    return convert<double, float>((size_t)nnz, v(), va32.as<float>(), s);
+  }
+  bool empty() const { return rows == 0; }
+};
+template <> inline const double* Csr::vals<double>() const { return va.as<double>(); }
+template <> inline const float* Csr::vals<float>() const { return va32.as<float>(); }
+
+struct Level {
+  int n = 0;
+  int nx = 0, ny = 0;
+  int nc = 0;             // coarse size (0 on the coarsest level)
+  int vec_g = 4;          // lanes per row in the vector kernels (chosen from nnz/row)
+  Csr B, Bt, M, N, P, Qt, Q, Pt;
+  DevMem dinv, dinv32;
+  DevMem cf, cmap, cpt, Jrp, Jci;
+  DevMem s, t;            // sqrt LS weights (double[ld])
+  // V-cycle vectors in the V-cycle precision
+  DevMem vb, vz, vt, vr;
+};
+
+}  // namespace bamg
+
+struct bamg_hierarchy {
+  bamg_params p;
+  int ld = 8;             // block stride (power of two >= r)
+  int mixed = 0;
+  int device = 0;
+  cudaStream_t cap_stream = nullptr;   // private stream for graph capture
+  std::vector<bamg::Level> lv;
+  int nL = 0;
+  bamg::DevMem Bpinv, Bpinv32;
+  std::vector<double> sigma;            // setup triplets (finest level)
+  bamg::DevMem U64, V64, x0;            // n x ld, n x ld, n
+  bamg::DevMem io_in, io_out;           // V-cycle entry/exit (double)
+  cudaGraph_t vgraph = nullptr;
+  cudaGraphExec_t vexec = nullptr;
+  uint64_t vgraph_kernels = 0;          // kernels per V-cycle graph launch
+  double setup_ms = 0.0;
+  double op_cplx = 0.0, grid_cplx = 0.0;
+  int rankdef = 0;
+};
+
+namespace bamg {
+template <typename T> bamg_status vcycle_body(bamg_hierarchy* h, cudaStream_t s);
+bamg_status vcycle_prepare(bamg_hierarchy* h, cudaStream_t s);
+bamg_status vcycle_run(bamg_hierarchy* h, cudaStream_t s);
+bamg_status fgmres(bamg_hierarchy* h, double* x, const bamg_solve_params* sp, bamg_solve_info* info,
+                   cudaStream_t s);
+bamg_status setup_finest(bamg_hierarchy* h, const bamg_csr* A, cudaStream_t s);
+template <typename T> bamg_status run_setup(bamg_hierarchy* h, cudaStream_t s);
+}  // namespace bamg

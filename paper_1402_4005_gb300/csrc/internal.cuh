@@ -1,0 +1,89 @@
+// Host-side launchers shared between the translation units of libbamg.
+#pragma once
+
+#include "common.cuh"
+
+namespace bamg {
+
+enum VecModeHost { VEC_JACOBI = 0, VEC_JACOBI_ZERO = 1, VEC_RESID = 2, VEC_SPMV = 3, VEC_SPMV_ADD = 4 };
+
+// sparse.cu
+bamg_status check_rowptr(int n, const int32_t* rp, int64_t nnz, cudaStream_t s);
+bamg_status transpose_csr(int rows, int cols, int nnz, const int32_t* rp, const int32_t* ci,
+                          const double* va, int32_t* trp, int32_t* tci, double* tva, cudaStream_t s);
+bamg_status build_B_count(int n, const int32_t* rp, const int32_t* ci, int32_t* cnt, cudaStream_t s);
+bamg_status build_B_fill(int n, const int32_t* rp, const int32_t* ci, const double* va,
+                         const int32_t* brp, int32_t* bci, double* bva, cudaStream_t s);
+bamg_status check_stochastic(int n, const int32_t* rp, const int32_t* ci, const double* va, double tol,
+                             int64_t* bad_host, cudaStream_t s);
+
+// spgemm.cu
+bamg_status spgemm_symbolic(int m, const int32_t* arp, const int32_t* aci, const int32_t* brp,
+                            const int32_t* bci, int32_t* crp, int64_t* nnz_host, cudaStream_t s);
+bamg_status spgemm_numeric(int m, const int32_t* arp, const int32_t* aci, const double* ava,
+                           const int32_t* brp, const int32_t* bci, const double* bva,
+                           const int32_t* crp, int32_t* cci, double* cva, cudaStream_t s);
+
+// blockops.cu
+template <typename T>
+bamg_status relax_block(int n, int ld, const int32_t* rp, const int32_t* ci, const T* va, const T* dinv,
+                        const T* X, T* Y, const T* R, const T* sig, T omega, int keep0, cudaStream_t s);
+template <typename T>
+bamg_status spmm_block(int rows, int ld, const int32_t* rp, const int32_t* ci, const T* va, const T* X,
+                       T* Y, cudaStream_t s);
+template <typename T>
+bamg_status norms_weights(int n, int ld, int r, const int32_t* rp, const int32_t* ci, const T* va, T* X,
+                          int normalise, int skip0, T* scale, double* w, double* norms, cudaStream_t s);
+template <typename T>
+bamg_status col_dots(int n, int ld, int npairs, const T* A0, const T* B0, const T* A1, const T* B1,
+                     const T* A2, const T* B2, double* sums, cudaStream_t s);
+template <typename T>
+bamg_status rayleigh_finalize(const double* sums, int ld, int r, T* sig, double* sig64, cudaStream_t s);
+template <typename T>
+bamg_status init_vectors(int n, int ld, int r, uint64_t seed, T* U, T* V, cudaStream_t s);
+template <typename T>
+bamg_status inject(int nc, int ld, const int32_t* cpt, const T* X, T* Xc, cudaStream_t s);
+template <typename T>
+bamg_status csr_vec(int mode, int n, int G, const int32_t* rp, const int32_t* ci, const T* va, const T* dinv,
+                    T omega, const T* x, const T* b, T* y, cudaStream_t s);
+template <typename T>
+bamg_status dense_gemv(int n, const T* A, const T* x, T* y, cudaStream_t s);
+template <typename S, typename D>
+bamg_status convert(size_t n, const S* a, D* b, cudaStream_t s);
+template <typename T>
+bamg_status diag_inv(int n, const int32_t* rp, const int32_t* ci, const double* va, T* dinv, int* bad_row,
+                     cudaStream_t s);
+
+// hierarchy.cu: out[0] = sum x, out[1] = sum |x|
+bamg_status abs_sums(int n, const double* x, double* out, cudaStream_t s);
+bamg_status orient_normalise(int n, double* x, cudaStream_t s);
+
+// coarsen.cu
+bamg_status coarsen_geometric(int nx, int ny, int8_t* cf, int32_t* cmap, int32_t* J_rp, int32_t* J_ci,
+                              int* nc_host, cudaStream_t s);
+bamg_status coarsen_mis(int n, const int32_t* brp, const int32_t* bci, const int32_t* trp,
+                        const int32_t* tci, uint64_t seed, int level, int8_t* cf, int32_t* cmap,
+                        int* nc_host, cudaStream_t s);
+bamg_status graph_sets(int n, const int32_t* brp, const int32_t* bci, const double* bva,
+                       const int32_t* trp, const int32_t* tci, const double* tva, const int8_t* cf,
+                       int c_min, int c_max, int32_t* J_rp, int32_t* J_ci, cudaStream_t s);
+bamg_status coarse_points(int n, const int8_t* cf, const int32_t* cmap, int32_t* cpt, cudaStream_t s);
+bamg_status transfer_pattern(int n, const int8_t* cf, const int32_t* cmap, const int32_t* J_rp,
+                             const int32_t* J_ci, int32_t* P_rp, int32_t* P_ci, double* P_val,
+                             cudaStream_t s);
+bamg_status scatter_fits(int n, const int8_t* cf, const int32_t* J_rp, const double* fit,
+                         const int32_t* P_rp, double* P_val, cudaStream_t s);
+bamg_status average_fits(int n, const int32_t* J_rp, double* fit, cudaStream_t s);
+
+// lsfit.cu
+template <typename T>
+bamg_status ls_fit(int n, int ld, int r, const int32_t* J_rp, const int32_t* J_ci, const T* X,
+                   const double* w, int constrained, double* out, int* rankdef_dev, cudaStream_t s);
+
+// dense.cu
+bamg_status coarsest_solve(int prec, int n, int r, const double* B, const double* M, const double* N,
+                           double* sigma, double* U, double* V, double* Bpinv, cudaStream_t s);
+bamg_status csr_to_dense(int n, const int32_t* rp, const int32_t* ci, const double* va, double* D,
+                         cudaStream_t s);
+
+}  // namespace bamg

@@ -1,0 +1,410 @@
+// Solve phase (Section 6): V-cycle preconditioner and flexible GMRES.
+//
+// V-cycle (Section 3, eq. error_propagator_twogrid): from z = 0, nu_pre
+// weighted-Jacobi sweeps, residual, r_c = Q r, recursion (B_L^+ r_L on the
+// coarsest level), z += P e_c, nu_post sweeps.  It runs in the hierarchy's
+// V-cycle precision (FP64, or FP32 in mixed mode) and is captured once into a
+// CUDA graph that reads a fixed FP64 input buffer and writes a fixed FP64
+// output buffer.
+//
+// GMRES on the residual equation B e = -B x^(0) (eq. residual), written as
+// B x = 0 from x^(0).  The V-cycle is applied on the right (flexible GMRES,
+// which admits a preconditioner computed in lower precision); Arnoldi uses
+// classical Gram-Schmidt with one re-orthogonalisation, Givens rotations and
+// the small triangular solve run on the device in FP64.  The stopping rule
+// is the true ||B x||_1 / ||x||_1, evaluated whenever the 2-norm estimate
+// allows it to hold.
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "hierarchy.cuh"
+
+namespace bamg {
+
+static int lanes_for(const Csr& A) {
+  double avg = A.rows ? (double)A.nnz / A.rows : 1.0;
+  return avg <= 3 ? 2 : avg <= 6 ? 4 : avg <= 12 ? 8 : avg <= 24 ? 16 : 32;
+}
+
+template <typename T> static const T* dinv_t(const Level& L);
+template <> const double* dinv_t<double>(const Level& L) { return L.dinv.as<double>(); }
+template <> const float* dinv_t<float>(const Level& L) { return L.dinv32.as<float>(); }
+template <typename T> static const T* pinv_t(const bamg_hierarchy* h);
+template <> const double* pinv_t<double>(const bamg_hierarchy* h) { return h->Bpinv.as<double>(); }
+template <> const float* pinv_t<float>(const bamg_hierarchy* h) { return h->Bpinv32.as<float>(); }
+
+template <typename T>
+static bamg_status vcycle_level(bamg_hierarchy* h, int l, cudaStream_t s) {
+  Level& L = h->lv[l];
+  T* b = L.vb.as<T>();
+  T* z = L.vz.as<T>();
+  if (l == (int)h->lv.size() - 1) return dense_gemv<T>(L.n, pinv_t<T>(h), b, z, s);
+  const bamg_params& p = h->p;
+  const T om = T(p.omega);
+  const T* dv = dinv_t<T>(L);
+  const T* bv = L.B.vals<T>();
+  T* cur = z;
+  T* alt = L.vt.as<T>();
+  if (p.nu_pre == 0) {
+    BAMG_CUDA(cudaMemsetAsync(cur, 0, sizeof(T) * L.n, s));
+  } else {
+    BAMG_TRY(csr_vec<T>(VEC_JACOBI_ZERO, L.n, L.vec_g, L.B.r(), L.B.c(), bv, dv, om, nullptr, b, cur, s));
+    for (int it = 1; it < p.nu_pre; ++it) {
+      BAMG_TRY(csr_vec<T>(VEC_JACOBI, L.n, L.vec_g, L.B.r(), L.B.c(), bv, dv, om, cur, b, alt, s));
+      std::swap(cur, alt);
+    }
+  }
+  BAMG_TRY(csr_vec<T>(VEC_RESID, L.n, L.vec_g, L.B.r(), L.B.c(), bv, dv, om, cur, b, L.vr.as<T>(), s));
+  Level& C = h->lv[l + 1];
+  BAMG_TRY(csr_vec<T>(VEC_SPMV, L.nc, lanes_for(L.Q), L.Q.r(), L.Q.c(), L.Q.vals<T>(), dv, om, L.vr.as<T>(),
+                      nullptr, C.vb.as<T>(), s));
+  BAMG_TRY(vcycle_level<T>(h, l + 1, s));
+  BAMG_TRY(csr_vec<T>(VEC_SPMV_ADD, L.n, lanes_for(L.P), L.P.r(), L.P.c(), L.P.vals<T>(), dv, om,
+                      C.vz.as<T>(), nullptr, cur, s));
+  for (int it = 0; it < p.nu_post; ++it) {
+    BAMG_TRY(csr_vec<T>(VEC_JACOBI, L.n, L.vec_g, L.B.r(), L.B.c(), bv, dv, om, cur, b, alt, s));
+    std::swap(cur, alt);
+  }
+  if (cur != z) BAMG_CUDA(cudaMemcpyAsync(z, cur, sizeof(T) * L.n, cudaMemcpyDeviceToDevice, s));
+  return BAMG_OK;
+}
+
+__global__ void copy_d_kernel(size_t n, const double* __restrict__ a, double* __restrict__ b) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) b[t] = a[t];
+}
+
+template <typename T>
+bamg_status vcycle_body(bamg_hierarchy* h, cudaStream_t s) {
+  Level& L0 = h->lv[0];
+  size_t n = L0.n;
+  if (sizeof(T) == 4) {
+    BAMG_TRY(convert<double, float>(n, h->io_in.as<double>(), (float*)L0.vb.p, s));
+  } else {
+    BAMG_TRY(launch(copy_d_kernel, dim3(cdiv((long long)n, 256)), dim3(256), 0, s, n,
+                    (const double*)h->io_in.as<double>(), (double*)L0.vb.p));
+  }
+  BAMG_TRY(vcycle_level<T>(h, 0, s));
+  if (sizeof(T) == 4) {
+    BAMG_TRY(convert<float, double>(n, (const float*)L0.vz.p, h->io_out.as<double>(), s));
+  } else {
+    BAMG_TRY(launch(copy_d_kernel, dim3(cdiv((long long)n, 256)), dim3(256), 0, s, n,
+                    (const double*)L0.vz.p, h->io_out.as<double>()));
+  }
+  return BAMG_OK;
+}
+
+// Allocates the V-cycle vectors and captures the V-cycle into a graph.
+bamg_status vcycle_prepare(bamg_hierarchy* h, cudaStream_t s) {
+  if (h->vexec) return BAMG_OK;
+  size_t es = h->mixed ? sizeof(float) : sizeof(double);
+  for (auto& L : h->lv) {
+    BAMG_TRY(L.vb.alloc(es * L.n, s));
+    BAMG_TRY(L.vz.alloc(es * L.n, s));
+    BAMG_TRY(L.vt.alloc(es * L.n, s));
+    BAMG_TRY(L.vr.alloc(es * L.n, s));
+  }
+  BAMG_TRY(h->io_in.alloc(sizeof(double) * h->lv[0].n, s));
+  BAMG_TRY(h->io_out.alloc(sizeof(double) * h->lv[0].n, s));
+  BAMG_CUDA(cudaStreamSynchronize(s));
+  if (!h->cap_stream) BAMG_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  uint64_t before = g_launches.load();
+  BAMG_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  bamg_status st = h->mixed ? vcycle_body<float>(h, h->cap_stream) : vcycle_body<double>(h, h->cap_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+  if (st != BAMG_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  BAMG_CUDA(e);
+  h->vgraph = g;
+  BAMG_CUDA(cudaGraphInstantiate(&h->vexec, g, 0));
+  h->vgraph_kernels = g_launches.load() - before;
+  g_launches.fetch_sub(h->vgraph_kernels);  // counted again at each replay
+  return BAMG_OK;
+}
+
+bamg_status vcycle_run(bamg_hierarchy* h, cudaStream_t s) {
+  BAMG_CUDA(cudaGraphLaunch(h->vexec, s));
+  g_launches.fetch_add(h->vgraph_kernels);
+  return BAMG_OK;
+}
+
+// ------------------------------------------------------------- FGMRES kernels
+constexpr int kRedBlocks = 256;
+
+// part[b * K + k] = sum over block b's chunk of V_k . w
+__global__ void multidot_kernel(int n, int K, const double* __restrict__ V, size_t ldv,
+                                const double* __restrict__ w, double* __restrict__ part) {
+  int k = blockIdx.y;
+  const double* v = V + (size_t)k * ldv;
+  double s = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) s += v[i] * w[i];
+  s = warp_sum(s);
+  __shared__ double sh[8];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
+    part[(size_t)blockIdx.x * K + k] = t;
+  }
+}
+
+// w -= sum_k h[k] V_k
+__global__ void orth_update_kernel(int n, int K, const double* __restrict__ V, size_t ldv,
+                                   const double* __restrict__ h, double* __restrict__ w) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = w[i];
+  for (int k = 0; k < K; ++k) acc -= h[k] * V[(size_t)k * ldv + i];
+  w[i] = acc;
+}
+
+// y = x + sum_k c[k] Z_k
+__global__ void combine_kernel(int n, int K, const double* __restrict__ Z, size_t ldz,
+                               const double* __restrict__ c, const double* __restrict__ x, double* __restrict__ y) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = x[i];
+  for (int k = 0; k < K; ++k) acc += c[k] * Z[(size_t)k * ldz + i];
+  y[i] = acc;
+}
+
+__global__ void scale_by_kernel(int n, const double* __restrict__ a, const double* __restrict__ f, int inv,
+                                double* __restrict__ b) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = inv ? 1.0 / f[0] : f[0];
+  b[i] = a[i] * s;
+}
+
+__global__ void sumsq_kernel(int n, const double* __restrict__ x, double* __restrict__ part) {
+  double s = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) s += x[i] * x[i];
+  s = warp_sum(s);
+  __shared__ double sh[8];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void sqrt_kernel(double* v) { v[0] = sqrt(v[0]); }
+
+// Arnoldi column j: H(:, j) = h1 + h2 (two CGS passes), H(j+1, j) = ||w||.
+// Applies the previous Givens rotations, forms the new one, updates g, and
+// solves R y = g(0..j).  st[0] = |g(j+1)| (residual 2-norm estimate),
+// st[1] = H(j+1, j) before rotation.
+__global__ void givens_kernel(int j, int m, const double* __restrict__ h1, const double* __restrict__ h2,
+                              const double* __restrict__ wnorm, double* __restrict__ R, double* __restrict__ cs,
+                              double* __restrict__ sn, double* __restrict__ g, double* __restrict__ y,
+                              double* __restrict__ st) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double col[65];
+  for (int k = 0; k <= j; ++k) col[k] = h1[k] + h2[k];
+  double hn = wnorm[0];
+  col[j + 1] = hn;
+  for (int k = 0; k < j; ++k) {
+    double t = cs[k] * col[k] + sn[k] * col[k + 1];
+    col[k + 1] = -sn[k] * col[k] + cs[k] * col[k + 1];
+    col[k] = t;
+  }
+  double a = col[j], b = col[j + 1];
+  double d = hypot(a, b);
+  double c = d > 0.0 ? a / d : 1.0, s = d > 0.0 ? b / d : 0.0;
+  cs[j] = c; sn[j] = s;
+  col[j] = d;
+  g[j + 1] = -s * g[j];
+  g[j] = c * g[j];
+  for (int k = 0; k <= j; ++k) R[(size_t)k * m + j] = col[k];
+  for (int k = j; k >= 0; --k) {
+    double acc = g[k];
+    for (int q = k + 1; q <= j; ++q) acc -= R[(size_t)k * m + q] * y[q];
+    double rkk = R[(size_t)k * m + k];
+    y[k] = rkk != 0.0 ? acc / rkk : 0.0;
+  }
+  st[0] = fabs(g[j + 1]);
+  st[1] = hn;
+}
+
+__global__ void init_g_kernel(int m, const double* __restrict__ beta, double* __restrict__ g) {
+  int k = threadIdx.x;
+  if (k <= m) g[k] = k == 0 ? beta[0] : 0.0;
+}
+
+__global__ void min_kernel(int n, const double* __restrict__ x, double* __restrict__ out) {
+  __shared__ double sh[256];
+  double m = INFINITY;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmin(m, x[i]);
+  sh[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] = fmin(sh[threadIdx.x], sh[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = sh[0];
+}
+
+bamg_status orient_normalise(int n, double* x, cudaStream_t s);
+
+struct Gm {
+  int n, m;
+  DevMem V, Z, w, w2, xj, zeros, h1, h2, part, R, cs, sn, g, y, st, scal, sums;
+};
+
+static int red_blocks(int n) {
+  int nb = (int)cdiv(n, 256);
+  return nb < kRedBlocks ? (nb > 0 ? nb : 1) : kRedBlocks;
+}
+
+static bamg_status norm2_dev(Gm& G, const double* x, double* out, cudaStream_t s) {
+  int nb = red_blocks(G.n);
+  BAMG_TRY(launch(sumsq_kernel, dim3(nb), dim3(256), 0, s, G.n, x, G.part.as<double>()));
+  BAMG_TRY(reduce_partials(G.part.as<double>(), nb, 1, out, s));
+  return launch(sqrt_kernel, dim3(1), dim3(1), 0, s, out);
+}
+
+static bamg_status multidot_dev(Gm& G, int K, const double* V, const double* w, double* out, cudaStream_t s) {
+  int nb = red_blocks(G.n);
+  BAMG_TRY(launch(multidot_kernel, dim3(nb, K), dim3(256), 0, s, G.n, K, V, (size_t)G.n, w, G.part.as<double>()));
+  return reduce_partials(G.part.as<double>(), nb, K, out, s);
+}
+
+// rel = ||B x||_1 / ||x||_1 (read back to the host); xn1 = ||x||_1
+static bamg_status true_residual(bamg_hierarchy* h, Gm& G, const double* x, double* rel, double* xn1,
+                                 cudaStream_t s) {
+  Level& L = h->lv[0];
+  BAMG_TRY(csr_vec<double>(VEC_SPMV, L.n, L.vec_g, L.B.r(), L.B.c(), L.B.v(), L.dinv.as<double>(), 1.0, x,
+                           nullptr, G.w2.as<double>(), s));
+  double* sm = G.sums.as<double>();
+  BAMG_TRY(abs_sums(L.n, G.w2.as<double>(), sm, s));
+  BAMG_TRY(abs_sums(L.n, x, sm + 2, s));
+  double hs[4];
+  BAMG_CUDA(cudaMemcpyAsync(hs, sm, sizeof(hs), cudaMemcpyDeviceToHost, s));
+  BAMG_CUDA(cudaStreamSynchronize(s));
+  *xn1 = hs[3];
+  *rel = hs[3] > 0.0 ? hs[1] / hs[3] : INFINITY;
+  return BAMG_OK;
+}
+
+bamg_status fgmres(bamg_hierarchy* h, double* x, const bamg_solve_params* sp, bamg_solve_info* info,
+                   cudaStream_t s) {
+  Level& L = h->lv[0];
+  const int n = L.n, m = sp->restart;
+  Gm G;
+  G.n = n;
+  G.m = m;
+  BAMG_TRY(G.V.alloc(sizeof(double) * (size_t)(m + 1) * n, s));
+  BAMG_TRY(G.Z.alloc(sizeof(double) * (size_t)m * n, s));
+  BAMG_TRY(G.w.alloc(sizeof(double) * n, s));
+  BAMG_TRY(G.w2.alloc(sizeof(double) * n, s));
+  BAMG_TRY(G.xj.alloc(sizeof(double) * n, s));
+  BAMG_TRY(G.zeros.alloc(sizeof(double) * n, s));
+  BAMG_TRY(G.h1.alloc(sizeof(double) * (m + 1), s));
+  BAMG_TRY(G.h2.alloc(sizeof(double) * (m + 1), s));
+  BAMG_TRY(G.part.alloc(sizeof(double) * kRedBlocks * (m + 1), s));
+  BAMG_TRY(G.R.alloc(sizeof(double) * (size_t)(m + 1) * m, s));
+  BAMG_TRY(G.cs.alloc(sizeof(double) * m, s));
+  BAMG_TRY(G.sn.alloc(sizeof(double) * m, s));
+  BAMG_TRY(G.g.alloc(sizeof(double) * (m + 1), s));
+  BAMG_TRY(G.y.alloc(sizeof(double) * m, s));
+  BAMG_TRY(G.st.alloc(sizeof(double) * 2, s));
+  BAMG_TRY(G.scal.alloc(sizeof(double) * 2, s));
+  BAMG_TRY(G.sums.alloc(sizeof(double) * 4, s));
+  BAMG_CUDA(cudaMemsetAsync(G.zeros.p, 0, sizeof(double) * n, s));
+  BAMG_CUDA(cudaMemcpyAsync(x, h->x0.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+
+  double rel = 0.0, xn1 = 1.0;
+  BAMG_TRY(true_residual(h, G, x, &rel, &xn1, s));
+  const double xn1_0 = xn1;
+  double xn2_0 = 0.0;
+  BAMG_TRY(norm2_dev(G, x, G.scal.as<double>() + 1, s));
+  BAMG_CUDA(cudaMemcpyAsync(&xn2_0, G.scal.as<double>() + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+  BAMG_CUDA(cudaStreamSynchronize(s));
+  int its = 0, it7 = -1;
+  bool done = rel <= sp->tol;
+  bool breakdown = false;
+  double* V = G.V.as<double>();
+  double* Z = G.Z.as<double>();
+  const unsigned gv = cdiv(n, 256);
+  while (!done && its < sp->max_iter) {
+    // r = -B x, beta = ||r||, v_0 = r / beta, g = beta e_1
+    BAMG_TRY(csr_vec<double>(VEC_RESID, n, L.vec_g, L.B.r(), L.B.c(), L.B.v(), L.dinv.as<double>(), 1.0, x,
+                             G.zeros.as<double>(), G.w.as<double>(), s));
+    BAMG_TRY(norm2_dev(G, G.w.as<double>(), G.scal.as<double>(), s));
+    BAMG_TRY(launch(scale_by_kernel, dim3(gv), dim3(256), 0, s, n, (const double*)G.w.as<double>(),
+                    (const double*)G.scal.as<double>(), 1, V));
+    BAMG_TRY(launch(init_g_kernel, dim3(1), dim3(128), 0, s, m, (const double*)G.scal.as<double>(),
+                    G.g.as<double>()));
+    for (int j = 0; j < m && !done; ++j) {
+      double* vj = V + (size_t)j * n;
+      double* zj = Z + (size_t)j * n;
+      // z_j = C v_j (V-cycle graph), w = B z_j
+      BAMG_CUDA(cudaMemcpyAsync(h->io_in.p, vj, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      BAMG_TRY(vcycle_run(h, s));
+      BAMG_CUDA(cudaMemcpyAsync(zj, h->io_out.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      BAMG_TRY(csr_vec<double>(VEC_SPMV, n, L.vec_g, L.B.r(), L.B.c(), L.B.v(), L.dinv.as<double>(), 1.0, zj,
+                               nullptr, G.w.as<double>(), s));
+      // classical Gram-Schmidt, twice
+      int K = j + 1;
+      BAMG_TRY(multidot_dev(G, K, V, G.w.as<double>(), G.h1.as<double>(), s));
+      BAMG_TRY(launch(orth_update_kernel, dim3(gv), dim3(256), 0, s, n, K, (const double*)V, (size_t)n,
+                      (const double*)G.h1.as<double>(), G.w.as<double>()));
+      BAMG_TRY(multidot_dev(G, K, V, G.w.as<double>(), G.h2.as<double>(), s));
+      BAMG_TRY(launch(orth_update_kernel, dim3(gv), dim3(256), 0, s, n, K, (const double*)V, (size_t)n,
+                      (const double*)G.h2.as<double>(), G.w.as<double>()));
+      BAMG_TRY(norm2_dev(G, G.w.as<double>(), G.scal.as<double>(), s));
+      BAMG_TRY(launch(givens_kernel, dim3(1), dim3(32), 0, s, j, m, (const double*)G.h1.as<double>(),
+                      (const double*)G.h2.as<double>(), (const double*)G.scal.as<double>(), G.R.as<double>(),
+                      G.cs.as<double>(), G.sn.as<double>(), G.g.as<double>(), G.y.as<double>(),
+                      G.st.as<double>()));
+      double st[2];
+      BAMG_CUDA(cudaMemcpyAsync(st, G.st.p, sizeof(st), cudaMemcpyDeviceToHost, s));
+      BAMG_CUDA(cudaStreamSynchronize(s));
+      ++its;
+      if (it7 < 0 && st[0] <= 1e-7 * xn2_0) it7 = its;
+      breakdown = !(st[1] > 0.0);
+      bool last = (j == m - 1) || its >= sp->max_iter || breakdown;
+      if (st[0] <= 2.0 * sp->tol * xn1_0 || last) {
+        BAMG_TRY(launch(combine_kernel, dim3(gv), dim3(256), 0, s, n, K, (const double*)Z, (size_t)n,
+                        (const double*)G.y.as<double>(), (const double*)x, G.xj.as<double>()));
+        BAMG_TRY(true_residual(h, G, G.xj.as<double>(), &rel, &xn1, s));
+        if (rel <= sp->tol || last) {
+          BAMG_CUDA(cudaMemcpyAsync(x, G.xj.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+          done = rel <= sp->tol;
+          break;
+        }
+      }
+      BAMG_TRY(launch(scale_by_kernel, dim3(gv), dim3(256), 0, s, n, (const double*)G.w.as<double>(),
+                      (const double*)G.scal.as<double>(), 1, V + (size_t)(j + 1) * n));
+    }
+    if (breakdown && !done) break;
+  }
+  BAMG_TRY(orient_normalise(n, x, s));
+  double fin[2] = {0, 0};
+  BAMG_TRY(launch(min_kernel, dim3(1), dim3(256), 0, s, n, (const double*)x, G.scal.as<double>()));
+  BAMG_CUDA(cudaMemcpyAsync(fin, G.scal.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  BAMG_TRY(true_residual(h, G, x, &rel, &xn1, s));
+  if (info) {
+    info->iterations = its;
+    info->iters_to_1e7 = it7;
+    info->rel_res_1 = rel;
+    info->min_x = fin[0];
+  }
+  if (!done) {
+    set_error("GMRES stopped after %d iterations at ||Bx||_1/||x||_1 = %.3e", its, rel);
+    return breakdown ? BAMG_ERR_BREAKDOWN : BAMG_ERR_NOT_CONVERGED;
+  }
+  return BAMG_OK;
+}
+
+template bamg_status vcycle_body<double>(bamg_hierarchy*, cudaStream_t);
+template bamg_status vcycle_body<float>(bamg_hierarchy*, cudaStream_t);
+
+}  // namespace bamg

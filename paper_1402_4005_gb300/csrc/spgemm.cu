@@ -1,0 +1,270 @@
+// Two-phase sparse matrix product C = A B by expand-sort-compress.
+//
+// Row i of C is built by one group of threads (a warp, or a whole block for
+// long rows): the products a_ik b_kj of row i are expanded into shared memory
+// with key (j << 32 | sequence number), sorted by a bitonic network, and
+// compressed.  The symbolic pass counts distinct j; the numeric pass sums each
+// run of equal j in sequence order, so results do not depend on scheduling.
+// Every structural product keeps its slot (no cancellation drops), which is
+// the pattern convention of the Petrov-Galerkin products Q B P, Q M Q^T and
+// P^T N P (Section 3, Algorithm 1).
+#include "internal.cuh"
+
+namespace bamg {
+
+constexpr int kWarpCap = 512;      // products per row handled by one warp
+constexpr int kBlockCap = 8192;    // products per row handled by one block
+constexpr int kWarpsPerBlock = 4;
+constexpr int kBigThreads = 256;
+
+__global__ void count_products_kernel(int m, const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
+                                      const int32_t* __restrict__ brp, int32_t* __restrict__ prod,
+                                      int* __restrict__ maxprod) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  long long c = 0;
+  for (int p = arp[i]; p < arp[i + 1]; ++p) {
+    int k = aci[p];
+    c += brp[k + 1] - brp[k];
+  }
+  int ci = c > INT32_MAX ? INT32_MAX : (int)c;
+  prod[i] = ci;
+  atomicMax(maxprod, ci);
+}
+
+template <int G>
+__device__ inline void gsync() {
+  if constexpr (G == 32) __syncwarp(); else __syncthreads();
+}
+
+// Bitonic sort of m (power of two) keys with attached values by G threads.
+template <int G, bool VALS>
+__device__ void group_sort(unsigned long long* key, double* val, int m, int lane) {
+  for (int k = 2; k <= m; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < m; i += G) {
+        int ixj = i ^ j;
+        if (ixj > i) {
+          bool up = (i & k) == 0;
+          unsigned long long a = key[i], b = key[ixj];
+          if ((a > b) == up) {
+            key[i] = b; key[ixj] = a;
+            if (VALS) { double t = val[i]; val[i] = val[ixj]; val[ixj] = t; }
+          }
+        }
+      }
+      gsync<G>();
+    }
+  }
+}
+
+// Expand the products of row i into key/val (count entries), pad to pow2.
+template <int G, bool VALS>
+__device__ int expand_row(int i, const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
+                          const double* __restrict__ ava, const int32_t* __restrict__ brp,
+                          const int32_t* __restrict__ bci, const double* __restrict__ bva,
+                          int count, unsigned long long* key, double* val, int lane) {
+  // sequential enumeration split across lanes: lane handles A entries
+  // p = a0 + lane, a0 + lane + G, ...; the sequence number of a product is
+  // its position in the row-major enumeration (A order, then B order).
+  int a0 = arp[i], a1 = arp[i + 1];
+  // prefix of B-row lengths over A entries, computed redundantly per entry
+  for (int p = a0 + lane; p < a1; p += G) {
+    int k = aci[p];
+    int off = 0;
+    for (int q = a0; q < p; ++q) {
+      int kk = aci[q];
+      off += brp[kk + 1] - brp[kk];
+    }
+    double av = VALS ? ava[p] : 0.0;
+    for (int t = brp[k]; t < brp[k + 1]; ++t, ++off) {
+      key[off] = ((unsigned long long)(unsigned)bci[t] << 32) | (unsigned)off;
+      if (VALS) val[off] = av * bva[t];
+    }
+  }
+  int mp = 1;
+  while (mp < count) mp <<= 1;
+  for (int t = count + lane; t < mp; t += G) key[t] = ~0ull;
+  gsync<G>();
+  return mp;
+}
+
+// Symbolic: distinct columns of row i.  Numeric: write sorted columns and
+// run sums.  Rows whose product count is outside (lo, hi] are skipped.
+template <int G, bool NUMERIC>
+__device__ void row_product(int i, int lo, int hi, const int32_t* __restrict__ prod,
+                            const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
+                            const double* __restrict__ ava, const int32_t* __restrict__ brp,
+                            const int32_t* __restrict__ bci, const double* __restrict__ bva,
+                            int32_t* __restrict__ ccount, const int32_t* __restrict__ crp,
+                            int32_t* __restrict__ cci, double* __restrict__ cva,
+                            unsigned long long* key, double* val, int* flag, int lane) {
+  int count = prod[i];
+  if (count <= lo || count > hi) return;
+  int mp = expand_row<G, NUMERIC>(i, arp, aci, ava, brp, bci, bva, count, key, val, lane);
+  group_sort<G, NUMERIC>(key, val, mp, lane);
+  // segment starts
+  for (int t = lane; t < count; t += G) {
+    unsigned c = (unsigned)(key[t] >> 32);
+    flag[t] = (t == 0 || (unsigned)(key[t - 1] >> 32) != c) ? 1 : 0;
+  }
+  gsync<G>();
+  if (!NUMERIC) {
+    int s = 0;
+    for (int t = lane; t < count; t += G) s += flag[t];
+    // reduce within the group
+    if constexpr (G == 32) {
+      s = warp_sum(s);
+      if (lane == 0) ccount[i] = s;
+    } else {
+      s = warp_sum(s);
+      __shared__ int red[32];
+      if ((lane & 31) == 0) red[lane >> 5] = s;
+      __syncthreads();
+      if (lane == 0) {
+        int tot = 0;
+        for (int w = 0; w < G / 32; ++w) tot += red[w];
+        ccount[i] = tot;
+      }
+      __syncthreads();
+    }
+    gsync<G>();
+    return;
+  }
+  // exclusive prefix of flags, sequential chunks per lane
+  int chunk = (count + G - 1) / G;
+  int b = lane * chunk, e = min(count, b + chunk);
+  int local = 0;
+  for (int t = b; t < e; ++t) local += flag[t];
+  int incl = local;
+  if constexpr (G == 32) {
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+  } else {
+    __shared__ int sc[kBigThreads];
+    sc[lane] = local;
+    __syncthreads();
+    if (lane == 0) {
+      int run = 0;
+      for (int w = 0; w < G; ++w) { run += sc[w]; sc[w] = run; }
+    }
+    __syncthreads();
+    incl = sc[lane];
+    __syncthreads();
+  }
+  int pos = incl - local;
+  int base = crp[i];
+  for (int t = b; t < e; ++t) {
+    if (flag[t]) {
+      unsigned c = (unsigned)(key[t] >> 32);
+      double sum = 0.0;
+      for (int u = t; u < count && (unsigned)(key[u] >> 32) == c; ++u) sum += val[u];
+      cci[base + pos] = (int32_t)c;
+      cva[base + pos] = sum;
+      ++pos;
+    }
+  }
+  gsync<G>();
+}
+
+template <bool NUMERIC>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+spgemm_warp_kernel(int m, const int32_t* __restrict__ prod, const int32_t* __restrict__ arp,
+                   const int32_t* __restrict__ aci, const double* __restrict__ ava,
+                   const int32_t* __restrict__ brp, const int32_t* __restrict__ bci,
+                   const double* __restrict__ bva, int32_t* __restrict__ ccount,
+                   const int32_t* __restrict__ crp, int32_t* __restrict__ cci, double* __restrict__ cva) {
+  __shared__ unsigned long long skey[kWarpsPerBlock][kWarpCap];
+  __shared__ double sval[kWarpsPerBlock][NUMERIC ? kWarpCap : 1];
+  __shared__ int sflag[kWarpsPerBlock][kWarpCap];
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int i = blockIdx.x * kWarpsPerBlock + w;
+  if (i >= m) return;
+  row_product<32, NUMERIC>(i, -1, kWarpCap, prod, arp, aci, ava, brp, bci, bva, ccount, crp, cci,
+                           cva, skey[w], sval[w], sflag[w], lane);
+}
+
+template <bool NUMERIC>
+__global__ void __launch_bounds__(kBigThreads)
+spgemm_block_kernel(int m, const int32_t* __restrict__ prod, const int32_t* __restrict__ arp,
+                    const int32_t* __restrict__ aci, const double* __restrict__ ava,
+                    const int32_t* __restrict__ brp, const int32_t* __restrict__ bci,
+                    const double* __restrict__ bva, int32_t* __restrict__ ccount,
+                    const int32_t* __restrict__ crp, int32_t* __restrict__ cci, double* __restrict__ cva) {
+  extern __shared__ unsigned char dyn[];
+  unsigned long long* key = reinterpret_cast<unsigned long long*>(dyn);
+  double* val = reinterpret_cast<double*>(key + kBlockCap);
+  int* flag = reinterpret_cast<int*>(val + (NUMERIC ? kBlockCap : 1));
+  int i = blockIdx.x;
+  if (prod[i] <= kWarpCap) return;
+  row_product<kBigThreads, NUMERIC>(i, kWarpCap, kBlockCap, prod, arp, aci, ava, brp, bci, bva,
+                                    ccount, crp, cci, cva, key, val, flag, threadIdx.x);
+}
+
+struct SpgemmPlan {
+  DevMem prod, maxp;
+  int maxprod = 0;
+};
+
+static bamg_status plan_products(int m, const int32_t* arp, const int32_t* aci, const int32_t* brp,
+                                 SpgemmPlan& pl, cudaStream_t s) {
+  BAMG_TRY(pl.prod.alloc(sizeof(int32_t) * (m + 1), s));
+  BAMG_TRY(pl.maxp.alloc(sizeof(int), s));
+  BAMG_CUDA(cudaMemsetAsync(pl.maxp.p, 0, sizeof(int), s));
+  BAMG_TRY(launch(count_products_kernel, dim3(cdiv(m, 256)), dim3(256), 0, s, m, arp, aci, brp,
+                  pl.prod.as<int32_t>(), pl.maxp.as<int>()));
+  BAMG_CUDA(cudaMemcpyAsync(&pl.maxprod, pl.maxp.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BAMG_CUDA(cudaStreamSynchronize(s));
+  if (pl.maxprod > kBlockCap) {
+    set_error("sparse product row with %d products exceeds the %d limit", pl.maxprod, kBlockCap);
+    return BAMG_ERR_NUMERIC;
+  }
+  return BAMG_OK;
+}
+
+static size_t big_smem(bool numeric) {
+  return sizeof(unsigned long long) * kBlockCap + sizeof(double) * (numeric ? kBlockCap : 1) +
+         sizeof(int) * kBlockCap;
+}
+
+template <bool NUMERIC>
+static bamg_status run_rows(int m, const SpgemmPlan& pl, const int32_t* arp, const int32_t* aci,
+                            const double* ava, const int32_t* brp, const int32_t* bci,
+                            const double* bva, int32_t* ccount, const int32_t* crp, int32_t* cci,
+                            double* cva, cudaStream_t s) {
+  BAMG_TRY(launch(spgemm_warp_kernel<NUMERIC>, dim3(cdiv(m, kWarpsPerBlock)), dim3(kWarpsPerBlock * 32),
+                  0, s, m, (const int32_t*)pl.prod.as<int32_t>(), arp, aci, ava, brp, bci, bva, ccount,
+                  crp, cci, cva));
+  if (pl.maxprod > kWarpCap) {
+    size_t sm = big_smem(NUMERIC);
+    BAMG_CUDA(cudaFuncSetAttribute(spgemm_block_kernel<NUMERIC>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    BAMG_TRY(launch(spgemm_block_kernel<NUMERIC>, dim3(m), dim3(kBigThreads), sm, s, m,
+                    (const int32_t*)pl.prod.as<int32_t>(), arp, aci, ava, brp, bci, bva, ccount, crp,
+                    cci, cva));
+  }
+  return BAMG_OK;
+}
+
+bamg_status spgemm_symbolic(int m, const int32_t* arp, const int32_t* aci, const int32_t* brp,
+                            const int32_t* bci, int32_t* crp, int64_t* nnz_host, cudaStream_t s) {
+  SpgemmPlan pl;
+  BAMG_TRY(plan_products(m, arp, aci, brp, pl, s));
+  DevMem cnt;
+  BAMG_TRY(cnt.alloc(sizeof(int32_t) * (m + 1), s));
+  BAMG_TRY(run_rows<false>(m, pl, arp, aci, nullptr, brp, bci, nullptr, cnt.as<int32_t>(), nullptr,
+                           nullptr, nullptr, s));
+  return scan_counts(cnt.as<int32_t>(), crp, m, s, nnz_host);
+}
+
+bamg_status spgemm_numeric(int m, const int32_t* arp, const int32_t* aci, const double* ava,
+                           const int32_t* brp, const int32_t* bci, const double* bva,
+                           const int32_t* crp, int32_t* cci, double* cva, cudaStream_t s) {
+  SpgemmPlan pl;
+  BAMG_TRY(plan_products(m, arp, aci, brp, pl, s));
+  return run_rows<true>(m, pl, arp, aci, ava, brp, bci, bva, nullptr, crp, cci, cva, s);
+}
+
+}  // namespace bamg

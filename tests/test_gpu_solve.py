@@ -1,0 +1,175 @@
+"""End-to-end parity of setup, V-cycle and solve against the oracle.
+
+Integer structure of geometric hierarchies (C/F split, patterns of P, Q and
+Q B P) is compared bit for bit.  The hierarchy values, the triplets and the
+V-cycle are compared at tolerances that account for the amplification of
+rounding through the least-squares fits (1e-8 relative in FP64).  The
+stationary vector must reach ||Bx||_1/||x||_1 <= 1e-10 and agree with the
+oracle and, where one exists, the closed form to 1e-8 in the 1-norm.
+"""
+import numpy as np
+import pytest
+
+import chaingen as cg
+from oracle import setup as S
+from oracle import solve as So
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1402_4005_gb300 import api as a
+    return a
+
+
+def gpu_setup(api, ch, **kw):
+    p = api.bamg_params_default(**kw)
+    return api.bamg_setup(torch.from_numpy(ch.row_ptr).cuda(), torch.from_numpy(ch.col).cuda(),
+                          torch.from_numpy(ch.val).cuda(), ch.n, p, nx=ch.nx, ny=ch.ny)
+
+
+def oracle_setup(ch, **kw):
+    return S.bamg_setup(ch.csr(), S.Params(**kw), grid=(ch.nx, ch.ny) if ch.nx else None)
+
+
+def csr_np(d):
+    return (d["row_ptr"].cpu().numpy(), d["col"].cpu().numpy(), d["val"].cpu().numpy())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_hierarchy_structure_and_values(api, prec):
+    ch = cg.tandem(64)
+    kw = dict(r=16, max_levels=4, coarse_min=1, seed=2)
+    h = gpu_setup(api, ch, precision=prec, **kw)
+    H = oracle_setup(ch, **kw)
+    assert h.num_levels == len(H.levels)
+    vtol = 1e-8 if prec == "fp64" else 2e-3
+    for l, lev in enumerate(H.levels):
+        g = h.level(l)
+        assert g["n"] == lev.n
+        names = [("B", lev.B)]
+        if l < len(H.levels) - 1:
+            names += [("P", lev.P), ("Qt", lev.Qt), ("Q", lev.Q)]
+            assert np.array_equal(g["cf"].cpu().numpy().astype(bool), lev.cf)
+        if l > 0:
+            names += [("M", lev.M), ("N", lev.N)]
+        for nm, M in names:
+            rp, ci, va = csr_np(g[nm])
+            assert np.array_equal(rp, M.indptr), (l, nm)
+            assert np.array_equal(ci, M.indices), (l, nm)
+            err = np.abs(va - M.data).max() / np.abs(M.data).max()
+            assert err <= vtol, (l, nm, err)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_config1_lattice_32(api, prec):
+    """Weighted 32x32 lattice, r = 8, 2 levels, GMRES(20): closed form x ~ wdeg."""
+    ch = cg.lattice2d(32, seed=1)
+    kw = dict(r=8, max_levels=2, coarse_min=1, seed=1)
+    h = gpu_setup(api, ch, precision=prec, **kw)
+    x, info = api.bamg_solve(h, restart=20, tol=1e-10)
+    x = x.cpu().numpy()
+    xs = ch.meta["wdeg"] / ch.meta["wdeg"].sum()
+    assert info["rel_res_1"] <= 1e-10
+    B = S.operators.build_B(ch.csr())
+    assert So.rel_res_1(B, x) <= 1e-10
+    assert np.abs(x - xs).sum() <= 1e-8
+    assert x.min() > 0
+    H = oracle_setup(ch, **kw)
+    xo, its, _ = So.bamg_solve(H, tol=1e-10, restart=20)
+    assert np.abs(x - xo).sum() <= 1e-8
+    if prec == "fp64":
+        assert abs(info["iterations"] - its) <= 2, (info["iterations"], its)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_vcycle_matches_oracle(api, prec):
+    ch = cg.tandem(48)
+    kw = dict(r=8, max_levels=3, coarse_min=1, seed=3)
+    h = gpu_setup(api, ch, precision=prec, **kw)
+    H = oracle_setup(ch, **kw)
+    B = H.levels[0].B
+    b = B @ rng_vec(ch.n, 5)                           # consistent right-hand side
+    z = h.vcycle(torch.from_numpy(b).cuda()).cpu().numpy()
+    zo = So.vcycle(H, b)
+    tol = 1e-7 if prec == "fp64" else 1e-3
+    assert np.abs(z - zo).max() <= tol * np.abs(zo).max()
+
+
+def rng_vec(n, seed):
+    from oracle import rng
+    return rng.uniform_pm1(seed, 0, n)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_tandem_64_multilevel(api, prec):
+    ch = cg.tandem(64)
+    kw = dict(r=16, max_levels=3, coarse_min=1, seed=2)
+    h = gpu_setup(api, ch, precision=prec, **kw)
+    x, info = api.bamg_solve(h, restart=20, tol=1e-10)
+    x = x.cpu().numpy()
+    H = oracle_setup(ch, **kw)
+    xo, its, _ = So.bamg_solve(H, tol=1e-12, restart=20)
+    assert info["rel_res_1"] <= 1e-10
+    assert np.abs(x - xo).sum() <= 1e-8
+
+
+def test_delaunay_mis_hierarchy(api):
+    ch = cg.delaunay_walk(4096, seed=3)
+    kw = dict(r=8, coarse_min=200, coarsening="mis", c_min=2, c_max=4, nu_pre=5, nu_post=5, seed=3)
+    h = gpu_setup(api, ch, **kw)
+    x, info = api.bamg_solve(h, restart=30, tol=1e-10)
+    x = x.cpu().numpy()
+    xs = ch.meta["deg"] / ch.meta["deg"].sum()
+    assert info["rel_res_1"] <= 1e-10
+    assert np.abs(x - xs).sum() <= 1e-8
+    okw = dict(kw); okw["coarsening"] = "mis"
+    H = S.bamg_setup(ch.csr(), S.Params(**okw))
+    assert h.num_levels == len(H.levels)
+    for l in range(len(H.levels) - 1):
+        g = h.level(l)
+        assert np.array_equal(g["cf"].cpu().numpy().astype(bool), H.levels[l].cf), l
+
+
+def test_host_buffer_path(api):
+    ch = cg.lattice2d(24, seed=6)
+    p = api.bamg_params_default(r=8, max_levels=2, coarse_min=1)
+    x, info = api.bamg_solve_host(ch.row_ptr, ch.col, ch.val, ch.n, p, nx=24, ny=24)
+    xs = ch.meta["wdeg"] / ch.meta["wdeg"].sum()
+    assert np.abs(x - xs).sum() <= 1e-8 and info["rel_res_1"] <= 1e-10
+
+
+def test_errors_are_reported(api):
+    from paper_1402_4005_gb300._lib import BamgError
+    ch = cg.tandem(8)
+    bad = ch.val.copy()
+    bad[3] += 0.01
+    with pytest.raises(BamgError) as e:
+        api.bamg_setup(ch.row_ptr, ch.col, bad, ch.n, api.bamg_params_default(), nx=8, ny=8)
+    assert e.value.status == 2
+    with pytest.raises(BamgError) as e:
+        api.bamg_setup(ch.row_ptr, ch.col, ch.val, ch.n, api.bamg_params_default(r=40), nx=8, ny=8)
+    assert e.value.status == 1
+    with pytest.raises(BamgError) as e:                 # geometric needs nx * ny == n
+        api.bamg_setup(ch.row_ptr, ch.col, ch.val, ch.n, api.bamg_params_default(), nx=5, ny=8)
+    assert e.value.status == 1
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_config2_tandem_256_full_size(api, prec):
+    """Tandem queue 256 x 256 (65,536 states), r = 16, 5 levels: the bench workload."""
+    ch = cg.tandem(256)
+    kw = dict(r=16, max_levels=5, coarse_min=1, seed=2)
+    h = gpu_setup(api, ch, precision=prec, **kw)
+    assert h.num_levels == 5
+    x, info = api.bamg_solve(h, restart=20, tol=1e-10)
+    x = x.cpu().numpy()
+    B = S.operators.build_B(ch.csr())
+    assert So.rel_res_1(B, x) <= 1e-10
+    H = oracle_setup(ch, **kw)
+    xo, _, _ = So.bamg_solve(H, tol=1e-12, restart=20, max_iter=400)
+    assert np.abs(x - xo).sum() <= 1e-8
