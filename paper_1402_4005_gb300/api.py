@@ -122,16 +122,20 @@ class Hierarchy:
         return _copy_dev(ptr.value, nL.value * nL.value, torch.float64).view(nL.value, nL.value)
 
 
+class _DeviceArray:
+    """A read-only device buffer described by __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, count: int, dtype):
+        typestr = {torch.int8: "|i1", torch.int32: "<i4", torch.float64: "<f8", torch.float32: "<f4"}[dtype]
+        self.__cuda_array_interface__ = {"shape": (count,), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
 def _copy_dev(ptr: int, count: int, dtype) -> torch.Tensor:
-    """Copy `count` elements at a device address into a new tensor."""
-    out = torch.empty(count, dtype=dtype, device="cuda")
-    if count:
-        cudart = torch.cuda.cudart()
-        nbytes = count * out.element_size()
-        res = cudart.cudaMemcpy(out.data_ptr(), ptr, nbytes, 3)  # cudaMemcpyDeviceToDevice
-        if int(res) != 0:
-            raise RuntimeError(f"cudaMemcpy failed ({res})")
-    return out
+    """Copy `count` elements at a library-owned device address into a new tensor."""
+    if not count:
+        return torch.empty(0, dtype=dtype, device="cuda")
+    return torch.as_tensor(_DeviceArray(ptr, count, dtype), device="cuda").clone()
 
 
 def _csr_from_view(cv) -> dict:

@@ -81,7 +81,7 @@ static bamg_status check_params(const bamg_csr* A, const bamg_params* p) {
   BAMG_CHECK_ARG(A->n >= 1 && A->n <= INT32_MAX - 1 && A->nnz >= 0 && A->nnz <= INT32_MAX);
   BAMG_CHECK_ARG(A->row_ptr && (A->nnz == 0 || (A->col_idx && A->val)));
   BAMG_CHECK_ARG(p->r >= 1 && p->r <= 32);
-  BAMG_CHECK_ARG(p->max_levels >= 1 && p->coarse_min >= 1);
+  BAMG_CHECK_ARG(p->max_levels >= 1 && p->max_levels <= 64 && p->coarse_min >= 1);
   BAMG_CHECK_ARG(p->nu_setup >= 0 && p->nu_pre >= 0 && p->nu_post >= 0);
   BAMG_CHECK_ARG(p->omega > 0.0 && p->omega < 2.0);
   BAMG_CHECK_ARG(p->coarsening == BAMG_COARSEN_GEOMETRIC || p->coarsening == BAMG_COARSEN_MIS);
