@@ -73,6 +73,23 @@ bamg_status bamg_step_norms_weights(int prec, int n, int ld, int r, const int32_
                                     int normalise, int skip_col0, double* norm_host,
                                     double* w_host, void* stream);
 
+/* bamg_step_norms_weights without any device allocation (the paper has no
+ * counterpart; this is a service for callers).  For callers that must not
+ * allocate device memory once running - for example a service whose device
+ * memory is planned up front by its own allocator or a fixed budget, where a
+ * cudaMalloc or cudaMallocAsync mid-run could fail, stall or fragment that
+ * plan.  Arguments, results and tolerances are those of
+ * bamg_step_norms_weights; scratch lives in a fixed ~0.8 MB device array
+ * that each GPU loading the library keeps until the process exits.  The
+ * first call on a device looks up that array's address (make it before any
+ * stream capture).  ld must be 4, 8, 16 or 32 and r <= ld, else
+ * BAMG_ERR_ARG.  All calls share the array: calls that overlap on the GPU
+ * race and must be serialised by the caller. */
+bamg_status bamg_step_norms_weights_noalloc(int prec, int n, int ld, int r, const int32_t* rp,
+                                            const int32_t* ci, const void* val, void* X,
+                                            int normalise, int skip_col0, double* norm_host,
+                                            double* w_host, void* stream);
+
 /* Geometric C/F splitting (Section 7): coarse = (i even, j even) on an
  * nx x ny grid.  cf[n] int8 (1 = C), cmap[n] int32 coarse index or -1,
  * and the interpolation sets J_i (C points of the 3x3 box, ascending) as a

@@ -277,6 +277,17 @@ def bamg_step_norms_weights(rp, ci, val, X, r: int, normalise=True, skip_col0=Fa
     return np.array(nrm[:]), np.array(w[:])
 
 
+def bamg_step_norms_weights_noalloc(rp, ci, val, X, r: int, normalise=True, skip_col0=False, stream=None):
+    """bamg_step_norms_weights with fixed scratch (no device allocation inside)."""
+    prec = 1 if X.dtype == torch.float32 else 0
+    n, ld = X.shape
+    nrm = (C.c_double * r)()
+    w = (C.c_double * r)()
+    check(lib().bamg_step_norms_weights_noalloc(prec, n, ld, r, _p(rp), _p(ci), _p(val), _p(X), int(normalise),
+                                                int(skip_col0), nrm, w, _stream(stream)), "norms_weights_noalloc")
+    return np.array(nrm[:]), np.array(w[:])
+
+
 def bamg_step_coarsen_geometric(nx: int, ny: int, stream=None):
     n = nx * ny
     cf = torch.empty(n, dtype=torch.int8, device="cuda")

@@ -361,6 +361,35 @@ bamg_status norms_weights(int n, int ld, int r, const int32_t* rp, const int32_t
   BAMG_LD_DISPATCH(ld, return (norms_ld<T, LDC>(n, r, rp, ci, va, X, normalise, skip0, scale, w, norms, s)));
 }
 
+// Same launches as norms_ld, with every buffer supplied by the caller:
+// part[max_blocks * 3 * LD], sums[3 * LD], scale[LD], w[LD], norms[LD].
+template <typename T, int LD>
+static bamg_status norms_ws_ld(int n, int r, const int32_t* rp, const int32_t* ci, const T* va, T* X,
+                               int normalise, int skip0, double* part, int max_blocks, double* sums, T* scale,
+                               double* w, double* norms, cudaStream_t s) {
+  using C = Blk<T, LD>;
+  int nb = reduce_blocks(n, 8 * C::RPW);
+  if (nb > max_blocks) nb = max_blocks;
+  BAMG_TRY(launch(coldot_kernel<T, LD, 0>, dim3(nb), dim3(256), 0, s, n, rp, ci, va, (const T*)X,
+                  (const T*)nullptr, (const T*)nullptr, (const T*)nullptr, (const T*)nullptr,
+                  (const T*)nullptr, (const T*)nullptr, 0, part));
+  BAMG_TRY(reduce_partials(part, nb, 3 * LD, sums, s));
+  BAMG_TRY(launch(weights_finalize_kernel<T, LD>, dim3(1), dim3(32), 0, s, (const double*)sums, r, skip0,
+                  scale, w, norms));
+  if (normalise)
+    BAMG_TRY(launch(scale_cols_kernel<T, LD>, dim3(cdiv((long long)n * LD, 256)), dim3(256), 0, s, n, X,
+                    (const T*)scale));
+  return BAMG_OK;
+}
+
+template <typename T>
+bamg_status norms_weights_ws(int n, int ld, int r, const int32_t* rp, const int32_t* ci, const T* va, T* X,
+                             int normalise, int skip0, double* part, int max_blocks, double* sums, T* scale,
+                             double* w, double* norms, cudaStream_t s) {
+  BAMG_LD_DISPATCH(ld, return (norms_ws_ld<T, LDC>(n, r, rp, ci, va, X, normalise, skip0, part, max_blocks,
+                                                   sums, scale, w, norms, s)));
+}
+
 template <typename T, int LD>
 static bamg_status dots_ld(int n, int npairs, const T* A0, const T* B0, const T* A1, const T* B1,
                            const T* A2, const T* B2, double* sums, cudaStream_t s) {
@@ -458,6 +487,12 @@ bamg_status diag_inv(int n, const int32_t* rp, const int32_t* ci, const double* 
 
 BAMG_INST(float)
 BAMG_INST(double)
+template bamg_status norms_weights_ws<float>(int, int, int, const int32_t*, const int32_t*, const float*, float*,
+                                             int, int, double*, int, double*, float*, double*, double*,
+                                             cudaStream_t);
+template bamg_status norms_weights_ws<double>(int, int, int, const int32_t*, const int32_t*, const double*,
+                                              double*, int, int, double*, int, double*, double*, double*, double*,
+                                              cudaStream_t);
 template bamg_status convert<double, float>(size_t, const double*, float*, cudaStream_t);
 template bamg_status convert<float, double>(size_t, const float*, double*, cudaStream_t);
 template bamg_status convert<double, double>(size_t, const double*, double*, cudaStream_t);

@@ -35,6 +35,10 @@ template <typename T>
 bamg_status norms_weights(int n, int ld, int r, const int32_t* rp, const int32_t* ci, const T* va, T* X,
                           int normalise, int skip0, T* scale, double* w, double* norms, cudaStream_t s);
 template <typename T>
+bamg_status norms_weights_ws(int n, int ld, int r, const int32_t* rp, const int32_t* ci, const T* va, T* X,
+                             int normalise, int skip0, double* part, int max_blocks, double* sums, T* scale,
+                             double* w, double* norms, cudaStream_t s);
+template <typename T>
 bamg_status col_dots(int n, int ld, int npairs, const T* A0, const T* B0, const T* A1, const T* B1,
                      const T* A2, const T* B2, double* sums, cudaStream_t s);
 template <typename T>
