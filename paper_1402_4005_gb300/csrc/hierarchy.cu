@@ -11,11 +11,28 @@
 // host; all arithmetic runs in the kernels.
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "hierarchy.cuh"
 
 namespace bamg {
+
+// Optional phase timing (BAMG_TRACE set): synchronises the stream at each
+// mark and prints the elapsed host time to stderr.
+struct Trace {
+  bool on = std::getenv("BAMG_TRACE") != nullptr;
+  std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
+  void mark(cudaStream_t s, const char* what, int level) {
+    if (!on) return;
+    cudaStreamSynchronize(s);
+    auto now = std::chrono::steady_clock::now();
+    fprintf(stderr, "[bamg] L%d %-18s %8.3f ms\n", level, what,
+            std::chrono::duration<double, std::milli>(now - t).count());
+    t = now;
+  }
+};
 
 // ------------------------------------------------------------ small kernels
 __global__ void pad_block_kernel(int n, int r, int ld, const double* __restrict__ src, float* __restrict__ d32,
@@ -150,6 +167,7 @@ static bamg_status coarsen_level(bamg_hierarchy* h, int l, DevMem& U, DevMem& V,
   const T* Bv = L.B.vals<T>();
   const T* Btv = L.Bt.vals<T>();
   const T* dv = dinv_of<T>(L);
+  Trace tr;
   // Algorithm 1, first smoothing loop: relax V with B and U with B^T
   for (int it = 0; it < p.nu_setup; ++it) {
     BAMG_TRY(relax_block<T>(L.n, ld, L.B.r(), L.B.c(), Bv, dv, V.as<T>(), tmpV.as<T>(), nullptr, nullptr, om,
@@ -159,6 +177,7 @@ static bamg_status coarsen_level(bamg_hierarchy* h, int l, DevMem& U, DevMem& V,
                             om, 1, s));
     std::swap(U, tmpU);
   }
+  tr.mark(s, "relax", l);
   // eq. ls_weights with unit vectors
   BAMG_TRY(L.s.alloc(sizeof(double) * ld, s));
   BAMG_TRY(L.t.alloc(sizeof(double) * ld, s));
@@ -166,6 +185,7 @@ static bamg_status coarsen_level(bamg_hierarchy* h, int l, DevMem& U, DevMem& V,
                             L.s.as<double>(), norms.as<double>(), s));
   BAMG_TRY(norms_weights<T>(L.n, ld, r, L.Bt.r(), L.Bt.c(), Btv, U.as<T>(), 1, 1, scale.as<T>(),
                             L.t.as<double>(), norms.as<double>(), s));
+  tr.mark(s, "weights", l);
   // C/F splitting and interpolation sets
   BAMG_TRY(L.cf.alloc(L.n, s));
   BAMG_TRY(L.cmap.alloc(sizeof(int32_t) * L.n, s));
@@ -195,6 +215,7 @@ static bamg_status coarsen_level(bamg_hierarchy* h, int l, DevMem& U, DevMem& V,
   int32_t njz = 0;
   BAMG_CUDA(cudaMemcpyAsync(&njz, L.Jrp.as<int32_t>() + L.n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   BAMG_CUDA(cudaStreamSynchronize(s));
+  tr.mark(s, "split+sets", l);
   // P rows and Q columns (eq. ls_interpolation; Section 5)
   DevMem fitP, fitQ;
   BAMG_TRY(fitP.alloc(sizeof(double) * (njz > 0 ? njz : 1), s));
@@ -217,8 +238,10 @@ static bamg_status coarsen_level(bamg_hierarchy* h, int l, DevMem& U, DevMem& V,
                         L.P.va.as<double>(), s));
   BAMG_TRY(scatter_fits(L.n, L.cf.as<int8_t>(), L.Jrp.as<int32_t>(), fitQ.as<double>(), L.Qt.r(),
                         L.Qt.va.as<double>(), s));
+  tr.mark(s, "ls fits", l);
   BAMG_TRY(csr_transpose(L.Qt, L.Q, s));
   BAMG_TRY(csr_transpose(L.P, L.Pt, s));
+  tr.mark(s, "transposes", l);
   // Petrov-Galerkin operators (Section 3; Algorithm 1)
   h->lv.emplace_back();
   Level& Lc = h->lv[l + 1];
@@ -242,9 +265,11 @@ static bamg_status coarsen_level(bamg_hierarchy* h, int l, DevMem& U, DevMem& V,
     BAMG_TRY(csr_product(Lf.N, Lf.P, NP, s));
     BAMG_TRY(csr_product(Lf.Pt, NP, Lc.N, s));
   }
+  tr.mark(s, "galerkin spgemm", l);
   Lc.nx = cgx;
   Lc.ny = cgy;
   BAMG_TRY(finish_level(h, Lc, l + 1, s));
+  tr.mark(s, "finish coarse", l);
   if (h->mixed) {
     BAMG_TRY(Lf.P.make32(s));
     BAMG_TRY(Lf.Qt.make32(s));
@@ -255,6 +280,7 @@ static bamg_status coarsen_level(bamg_hierarchy* h, int l, DevMem& U, DevMem& V,
   BAMG_TRY(Vc.alloc(sizeof(T) * (size_t)nc * ld, s));
   BAMG_TRY(inject<T>(nc, ld, Lf.cpt.as<int32_t>(), U.as<T>(), Uc.as<T>(), s));
   BAMG_TRY(inject<T>(nc, ld, Lf.cpt.as<int32_t>(), V.as<T>(), Vc.as<T>(), s));
+  tr.mark(s, "inject", l);
   return BAMG_OK;
 }
 
@@ -339,6 +365,7 @@ static bamg_status run_setup(bamg_hierarchy* h, cudaStream_t s) {
     ++l;
   }
   // coarsest level: eq. generalized_eigenvalue and the pseudo-inverse
+  Trace tr;
   Level& LL = h->lv[l];
   int nL = LL.n;
   h->nL = nL;
@@ -373,6 +400,7 @@ static bamg_status run_setup(bamg_hierarchy* h, cudaStream_t s) {
     BAMG_TRY(h->Bpinv32.alloc(sizeof(float) * nn, s));
     BAMG_TRY(convert<double, float>(nn, h->Bpinv.as<double>(), h->Bpinv32.as<float>(), s));
   }
+  tr.mark(s, "coarsest solve", l);
   // triplets into padded blocks
   BAMG_TRY(U[l].alloc(sizeof(T) * (size_t)nL * ld, s));
   BAMG_TRY(V[l].alloc(sizeof(T) * (size_t)nL * ld, s));
@@ -396,6 +424,7 @@ static bamg_status run_setup(bamg_hierarchy* h, cudaStream_t s) {
     BAMG_TRY(spmm_block<T>(L.n, ld, L.Qt.r(), L.Qt.c(), L.Qt.vals<T>(), U[k + 1].as<T>(), U[k].as<T>(), s));
     BAMG_TRY(spmm_block<T>(L.n, ld, L.P.r(), L.P.c(), L.P.vals<T>(), V[k + 1].as<T>(), V[k].as<T>(), s));
     BAMG_TRY(relax_triplets<T>(h, k, U[k], V[k], sig, sig64, s));
+    tr.mark(s, "bottom-up relax", k);
     U[k + 1].release();
     V[k + 1].release();
   }
