@@ -21,6 +21,8 @@
  *  - device pointers are CUDA device addresses of the current device;
  *  - `stream` is a cudaStream_t (NULL = legacy default stream); work is
  *    stream-ordered and a hierarchy must be used from one stream at a time;
+ *    the hierarchy returns its memory on the stream given to bamg_setup, so
+ *    that stream must stay valid until bamg_destroy;
  *  - the caller owns A and every vector passed in; the library owns the
  *    hierarchy until bamg_destroy();
  *  - on error the outputs are unspecified and no memory is leaked.
@@ -141,6 +143,34 @@ const char* bamg_last_error(void);
 
 /* Number of kernels this library has launched in the process so far. */
 uint64_t bamg_launch_count(void);
+
+/* -------------------------------------------------------------- batches --
+ * Many independent chains solved together.  Each chain gets its own bootstrap
+ * setup (run concurrently on `host_threads` host threads, 0 = 16, each with
+ * its own stream); the hierarchies are then joined level by level into
+ * block-diagonal operators so that one V-cycle (captured as a CUDA graph)
+ * and one flexible GMRES run serve all chains, with per-chain dot products,
+ * Givens rotations and convergence tests (Section 6).  Vectors are the
+ * concatenation of the chains' vectors in input order (offsets from
+ * bamg_batch_offsets).  Every chain must satisfy the conditions of
+ * bamg_setup. */
+typedef struct bamg_batch bamg_batch;
+
+bamg_status bamg_setup_batched(const bamg_csr* As, int nchains, const bamg_params* p, int host_threads,
+                               void* stream, bamg_batch** out);
+/* x_dev: concatenated device vector (sum of n_c doubles) receiving every
+ * chain's x > 0 with ||x_c||_1 = 1; infos: nchains entries or NULL. */
+bamg_status bamg_solve_batched(bamg_batch* b, double* x_dev, const bamg_solve_params* sp,
+                               bamg_solve_info* infos, void* stream);
+/* z = C r for every chain at once (one batched V-cycle). */
+bamg_status bamg_vcycle_batched(bamg_batch* b, const double* r_dev, double* z_dev, void* stream);
+/* offsets_host[nchains + 1]: start of chain c in the concatenated vectors. */
+bamg_status bamg_batch_offsets(const bamg_batch* b, int64_t* offsets_host);
+/* Lanes per row chosen by the autotuner for the batched B, P and Q of a level. */
+bamg_status bamg_batch_lanes(const bamg_batch* b, int level, int* lanes_B, int* lanes_P, int* lanes_Q);
+/* The hierarchy of chain c (owned by the batch; do not destroy it). */
+bamg_hierarchy* bamg_batch_chain(const bamg_batch* b, int c);
+void bamg_destroy_batched(bamg_batch* b);
 
 /* ---------------------------------------------------------------- views --
  * Read-only views of the device arrays of a hierarchy, valid until

@@ -72,6 +72,13 @@ SIGNATURES = {
     "bamg_status_string": (C.c_char_p, [i32]),
     "bamg_last_error": (C.c_char_p, []),
     "bamg_launch_count": (u64, []),
+    "bamg_setup_batched": (i32, [C.POINTER(Csr), i32, C.POINTER(Params), i32, vp, C.POINTER(vp)]),
+    "bamg_solve_batched": (i32, [vp, vp, C.POINTER(SolveParams), vp, vp]),
+    "bamg_vcycle_batched": (i32, [vp, vp, vp, vp]),
+    "bamg_batch_offsets": (i32, [vp, i64p]),
+    "bamg_batch_lanes": (i32, [vp, i32, ip, ip, ip]),
+    "bamg_batch_chain": (vp, [vp, i32]),
+    "bamg_destroy_batched": (None, [vp]),
     "bamg_num_levels": (i32, [vp]),
     "bamg_level": (i32, [vp, i32, C.POINTER(LevelView)]),
     "bamg_triplets": (i32, [vp, dp, ip, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]),

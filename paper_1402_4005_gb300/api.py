@@ -63,19 +63,21 @@ def launch_count() -> int:
 
 
 class Hierarchy:
-    """Owner of a bamg_hierarchy handle (destroyed with the object)."""
+    """A bamg_hierarchy handle; destroyed with the object when owned."""
 
-    def __init__(self, handle: int, n: int, keep=()):
+    def __init__(self, handle: int, n: int, keep=(), owned: bool = True):
         self.handle = handle
         self.n = n
         self._keep = keep
+        self._owned = owned
 
     def __del__(self):
         self.destroy()
 
     def destroy(self):
         if getattr(self, "handle", None):
-            lib().bamg_destroy(C.c_void_p(self.handle))
+            if self._owned:
+                lib().bamg_destroy(C.c_void_p(self.handle))
             self.handle = None
 
     def vcycle(self, r: torch.Tensor, stream=None) -> torch.Tensor:
@@ -217,6 +219,73 @@ def bamg_solve_host(row_ptr, col, val, n: int, params=None, nx: int = 0, ny: int
                                 x.ctypes.data_as(C.POINTER(C.c_double)), C.byref(info), _stream(stream)),
           "bamg_solve_host")
     return x, info.as_dict()
+
+
+# ------------------------------------------------------------------- batches
+class Batch:
+    """Owner of a bamg_batch handle: many chains, one batched V-cycle and GMRES."""
+
+    def __init__(self, handle: int, nchains: int, offsets: np.ndarray, keep=()):
+        self.handle = handle
+        self.nchains = nchains
+        self.offsets = offsets
+        self.n = int(offsets[-1])
+        self._keep = keep
+
+    def __del__(self):
+        self.destroy()
+
+    def destroy(self):
+        if getattr(self, "handle", None):
+            lib().bamg_destroy_batched(C.c_void_p(self.handle))
+            self.handle = None
+
+    def chain(self, c: int) -> Hierarchy:
+        h = lib().bamg_batch_chain(C.c_void_p(self.handle), c)
+        n = int(self.offsets[c + 1] - self.offsets[c])
+        return Hierarchy(h, n, owned=False)
+
+    def lanes(self, level: int):
+        b, p, q = C.c_int(), C.c_int(), C.c_int()
+        check(lib().bamg_batch_lanes(C.c_void_p(self.handle), level, C.byref(b), C.byref(p), C.byref(q)),
+              "bamg_batch_lanes")
+        return b.value, p.value, q.value
+
+
+def bamg_setup_batched(chains, params=None, host_threads: int = 0, stream=None) -> Batch:
+    """chains: sequence of (row_ptr, col, val, n, nx, ny) host arrays."""
+    p = params if params is not None else bamg_params_default()
+    arr = (_lib.Csr * len(chains))()
+    keep = []
+    for k, (rp, ci, va, n, nx, ny) in enumerate(chains):
+        rp = np.ascontiguousarray(rp, dtype=np.int32)
+        ci = np.ascontiguousarray(ci, dtype=np.int32)
+        va = np.ascontiguousarray(va, dtype=np.float64)
+        keep += [rp, ci, va]
+        arr[k] = _csr_struct(rp, ci, va, n, nx, ny, on_device=False)
+    h = C.c_void_p()
+    check(lib().bamg_setup_batched(arr, len(chains), C.byref(p), host_threads, _stream(stream), C.byref(h)),
+          "bamg_setup_batched")
+    off = np.zeros(len(chains) + 1, dtype=np.int64)
+    check(lib().bamg_batch_offsets(h, off.ctypes.data_as(C.POINTER(C.c_int64))), "bamg_batch_offsets")
+    return Batch(h.value, len(chains), off)
+
+
+def bamg_solve_batched(b: Batch, restart: int = 20, max_iter: int = 500, tol: float = 1e-10, stream=None):
+    """Returns (x concatenated in input order, list of per-chain info dicts)."""
+    x = torch.empty(b.n, dtype=torch.float64, device="cuda")
+    sp = bamg_solve_params_default(restart=restart, max_iter=max_iter, tol=tol)
+    infos = (_lib.SolveInfo * b.nchains)()
+    check(lib().bamg_solve_batched(C.c_void_p(b.handle), _p(x), C.byref(sp), C.cast(infos, C.c_void_p),
+                                   _stream(stream)), "bamg_solve_batched")
+    return x, [infos[k].as_dict() for k in range(b.nchains)]
+
+
+def bamg_vcycle_batched(b: Batch, r: torch.Tensor, stream=None) -> torch.Tensor:
+    r = _dev(r, torch.float64)
+    z = torch.empty_like(r)
+    check(lib().bamg_vcycle_batched(C.c_void_p(b.handle), _p(r), _p(z), _stream(stream)), "bamg_vcycle_batched")
+    return z
 
 
 # --------------------------------------------------------------------- steps

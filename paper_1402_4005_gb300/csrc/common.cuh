@@ -16,6 +16,8 @@ namespace bamg {
 // ------------------------------------------------------------ status plumbing
 void set_error(const char* fmt, ...);
 extern std::atomic<uint64_t> g_launches;
+// launches issued by the calling thread (used to size captured graphs)
+extern thread_local uint64_t t_launches;
 
 #define BAMG_TRY(...)                                    \
   do {                                                   \
@@ -48,6 +50,7 @@ inline bamg_status launch(void (*k)(KArgs...), dim3 grid, dim3 block, size_t sme
   if (grid.x == 0 || grid.y == 0 || grid.z == 0) return BAMG_OK;
   k<<<grid, block, smem, s>>>(std::forward<Args>(args)...);
   g_launches.fetch_add(1, std::memory_order_relaxed);
+  ++t_launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error("kernel launch failed: %s", cudaGetErrorString(e));

@@ -812,9 +812,11 @@ static bamg_status coarsest_t(int n, int r, const double* B, const double* M, co
   a.cval = cv.as<T>(); a.cidx = ci.as<int>(); a.pcol = pc.as<int>();
   a.d = de.as<T>(); a.e = a.d + n; a.taup = a.e + n;
   a.sig = sg.as<T>(); a.vb = vb.as<T>(); a.z = z.as<T>(); a.unull = un.as<T>(); a.ctl = ctl.as<DenseCtl>();
+  // at most 2 * 1024 doubles: below the default dynamic shared memory limit,
+  // so no per-call attribute (a per-function setting would race between
+  // threads that set up different chains concurrently)
   size_t smem = sizeof(T) * 2 * (size_t)n + 64;
   auto kern = coarsest_kernel<T>;
-  BAMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   BAMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];

@@ -109,7 +109,7 @@ bamg_status vcycle_prepare(bamg_hierarchy* h, cudaStream_t s) {
   BAMG_TRY(h->io_out.alloc(sizeof(double) * h->lv[0].n, s));
   BAMG_CUDA(cudaStreamSynchronize(s));
   if (!h->cap_stream) BAMG_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-  uint64_t before = g_launches.load();
+  uint64_t before = t_launches;
   BAMG_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
   bamg_status st = h->mixed ? vcycle_body<float>(h, h->cap_stream) : vcycle_body<double>(h, h->cap_stream);
   cudaGraph_t g = nullptr;
@@ -121,7 +121,7 @@ bamg_status vcycle_prepare(bamg_hierarchy* h, cudaStream_t s) {
   BAMG_CUDA(e);
   h->vgraph = g;
   BAMG_CUDA(cudaGraphInstantiate(&h->vexec, g, 0));
-  h->vgraph_kernels = g_launches.load() - before;
+  h->vgraph_kernels = t_launches - before;
   g_launches.fetch_sub(h->vgraph_kernels);  // counted again at each replay
   return BAMG_OK;
 }

@@ -12,7 +12,7 @@ def declared_functions():
     names = set()
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         src = open(h).read()
-        names |= set(re.findall(r"^\s*(?:bamg_status|void|const char\*|uint64_t|int)\s+(bamg_\w+)\s*\(",
+        names |= set(re.findall(r"^\s*(?:bamg_status|void|const char\*|uint64_t|int|bamg_hierarchy\*)\s+(bamg_\w+)\s*\(",
                                 src, re.M))
     return names
 

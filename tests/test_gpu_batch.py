@@ -1,0 +1,84 @@
+"""Batched solves of many chains (block-diagonal hierarchies, one V-cycle graph,
+lock-step flexible GMRES) against the per-chain path and closed forms."""
+import numpy as np
+import pytest
+
+import chaingen as cg
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1402_4005_gb300 import api as a
+    return a
+
+
+def spec(ch):
+    return (ch.row_ptr, ch.col, ch.val, ch.n, ch.nx, ch.ny)
+
+
+def closed_form(ch):
+    if "wdeg" in ch.meta:
+        return ch.meta["wdeg"] / ch.meta["wdeg"].sum()
+    if "deg" in ch.meta:
+        return ch.meta["deg"] / ch.meta["deg"].sum()
+    return None
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_geometric_batch_matches_single_chain_solves(api, prec):
+    chains = [cg.lattice2d(24, seed=3), cg.tandem(20), cg.lattice2d(32, seed=7), cg.tandem(33),
+              cg.lattice2d(48, seed=9), cg.tandem(64)]
+    p = api.bamg_params_default(r=16, max_levels=3, coarse_min=1, seed=2, precision=prec)
+    b = api.bamg_setup_batched([spec(c) for c in chains], p, host_threads=4)
+    x, infos = api.bamg_solve_batched(b, restart=20, tol=1e-10)
+    x = x.cpu().numpy()
+    for k, ch in enumerate(chains):
+        xk = x[b.offsets[k]:b.offsets[k + 1]]
+        assert infos[k]["rel_res_1"] <= 1e-10, (k, infos[k])
+        assert xk.min() > 0 and abs(xk.sum() - 1) < 1e-12
+        h = api.bamg_setup(ch.row_ptr, ch.col, ch.val, ch.n, p, nx=ch.nx, ny=ch.ny)
+        xs, _ = api.bamg_solve(h, restart=20, tol=1e-10)
+        assert np.abs(xk - xs.cpu().numpy()).sum() <= 1e-8, k
+        cf = closed_form(ch)
+        if cf is not None:
+            assert np.abs(xk - cf).sum() <= 1e-8, k
+
+
+def test_batched_vcycle_equals_per_chain_vcycles(api):
+    chains = [cg.lattice2d(20, seed=1), cg.tandem(24), cg.lattice2d(12, seed=2)]
+    p = api.bamg_params_default(r=16, max_levels=3, coarse_min=1, seed=5)
+    b = api.bamg_setup_batched([spec(c) for c in chains], p, host_threads=2)
+    from oracle import rng
+    r = torch.from_numpy(rng.uniform_pm1(3, 0, b.n)).cuda()
+    # consistent right-hand side per chain: subtract the mean of each segment
+    for k in range(len(chains)):
+        s = slice(int(b.offsets[k]), int(b.offsets[k + 1]))
+        r[s] -= r[s].mean()
+    z = api.bamg_vcycle_batched(b, r).cpu().numpy()
+    for k in range(len(chains)):
+        s = slice(int(b.offsets[k]), int(b.offsets[k + 1]))
+        zk = b.chain(k).vcycle(r[s].contiguous()).cpu().numpy()
+        assert np.abs(z[s] - zk).max() <= 1e-12 * max(1.0, np.abs(zk).max()), k
+    for l in range(3):
+        assert all(g in (2, 4, 8, 16, 32) for g in b.lanes(l))
+
+
+def test_mis_batch_of_mixed_chains(api):
+    chains = [cg.delaunay_walk(900, seed=4), cg.lattice2d(30, seed=5), cg.delaunay_walk(2500, seed=6),
+              cg.tandem(28), cg.delaunay_walk(400, seed=8)]
+    p = api.bamg_params_default(r=16, coarse_min=150, coarsening="mis", c_min=2, c_max=4, nu_pre=5, nu_post=5,
+                                seed=3, precision="mixed")
+    b = api.bamg_setup_batched([spec(c) for c in chains], p)
+    x, infos = api.bamg_solve_batched(b, restart=30, tol=1e-10)
+    x = x.cpu().numpy()
+    for k, ch in enumerate(chains):
+        xk = x[b.offsets[k]:b.offsets[k + 1]]
+        assert infos[k]["rel_res_1"] <= 1e-10
+        cf = closed_form(ch)
+        if cf is not None:
+            assert np.abs(xk - cf).sum() <= 1e-8, k
