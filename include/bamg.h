@@ -53,6 +53,7 @@ typedef enum {
 enum { BAMG_COARSEN_GEOMETRIC = 0, BAMG_COARSEN_MIS = 1 };
 enum { BAMG_PREC_FP64 = 0, BAMG_PREC_MIXED = 1 };
 enum { BAMG_RESTRICT_LS = 0, BAMG_RESTRICT_AVERAGE = 1 };
+enum { BAMG_INTERP_LS = 0, BAMG_INTERP_MLP = 1 };
 
 /* CSR of the column-stochastic A (row i = probabilities of entering state i).
  * row_ptr[n+1], col_idx[nnz] (ascending within each row, 0 <= col < n),
@@ -87,6 +88,13 @@ typedef struct {
   uint64_t seed;     /* SplitMix64 seed of test vectors and MIS priorities     */
   double stochastic_tol; /* |column sum - 1| allowed at validation (1e-12)     */
   int max_coarse_dense;  /* largest coarsest level solved densely (<= 1024)    */
+  int interp;        /* BAMG_INTERP_LS (eq. ls_interpolation, Section 5) or
+                        BAMG_INTERP_MLP: P and Q weights proposed by the
+                        interpolation network (geometric coarsening only); the
+                        setup then relaxes no test-vector blocks and carries
+                        only x^(0) up from the coarsest level               */
+  const float* mlp_params; /* device, bamg_mlp_num_params() floats, read during
+                        bamg_setup when interp = BAMG_INTERP_MLP              */
 } bamg_params;
 
 typedef struct {
@@ -172,6 +180,62 @@ bamg_status bamg_batch_lanes(const bamg_batch* b, int level, int* lanes_B, int* 
 bamg_hierarchy* bamg_batch_chain(const bamg_batch* b, int c);
 void bamg_destroy_batched(bamg_batch* b);
 
+/* ------------------------------------------------ learned interpolation --
+ * Not in the paper: a small network proposes the weights that the
+ * least-squares fits (eq. ls_interpolation; Section 5) compute, from the
+ * local stencil of B.  The LS setup provides its training targets and stays
+ * the fallback.
+ *
+ * Features of a fine point i of a geometric level (64 bf16 per point):
+ * [0,25) b_{i,i+o}/b_ii and [25,50) b_{i+o,i}/b_ii over the 25 offsets o of
+ * the 5x5 box (row-major, grid state s = gx*ny + gy, 0 outside the grid),
+ * [50,58) 1 where the k-th neighbour of the 3x3 box (row-major, centre
+ * skipped) is a coarse point, [58] = 1, [59,64) = 0.  Outputs (16 floats per
+ * point): [0,8) P weights and [8,16) Q weights in the same 8 neighbour slots;
+ * at setup the Q weights of a point are shifted by a common amount so that
+ * they sum to one over J_i (the constraint of Section 5).
+ * Network: 64 -> 64 -> 64 -> 16, ReLU after the two hidden layers.
+ * Parameter vector (float, bamg_mlp_num_params() = 9360 entries):
+ * W1[64][64], b1[64], W2[64][64], b2[64], W3[16][64], b3[16]; W[out][in].
+ * Products run on the tensor cores with bf16 operands (weights, inputs and
+ * hidden activations rounded to bf16) and fp32 accumulation. */
+int bamg_mlp_num_params(void);
+/* He-uniform weights from SplitMix64(seed, stream 8192), zero biases. */
+bamg_status bamg_mlp_init(float* params_dev, uint64_t seed, void* stream);
+/* Y[M][16] = network(X[M][64]); device arrays, X in bf16. */
+bamg_status bamg_mlp_forward(const float* params_dev, int M, const void* X_bf16, float* Y, void* stream);
+/* Loss = sum(mask * (Y - T)^2) / sum(mask) over the M rows and its gradient:
+ * grad[9360] (device, overwritten), *loss_dev (device float, overwritten). */
+bamg_status bamg_mlp_grad(const float* params_dev, int M, const void* X_bf16, const float* T,
+                          const float* mask, float* grad, float* loss_dev, void* stream);
+/* Adam (beta 0.9, 0.999, eps 1e-8) on minibatches of `batch` consecutive
+ * rows for `epochs` passes; params updated in place; loss_host[epochs] (may
+ * be NULL) receives the mean minibatch loss of each pass. */
+bamg_status bamg_mlp_train(float* params_dev, int M, const void* X_bf16, const float* T, const float* mask,
+                           int epochs, int batch, float lr, float* loss_host, void* stream);
+/* Training rows of level `level` of an LS hierarchy (geometric): features X,
+ * targets T (the LS weights of P and Q in the 8 slots) and mask (1 on the
+ * slots of J_i), one row per fine point in ascending state order.  With
+ * X_bf16 = NULL only *count (the number of fine points) is returned; else
+ * capacity >= *count rows are required. */
+bamg_status bamg_mlp_harvest(const bamg_hierarchy* h, int level, void* X_bf16, float* T, float* mask,
+                             int capacity, int* count, void* stream);
+
+/* Judge: asymptotic convergence factor of the stationary iteration
+ * x <- x + C(-B x) with the hierarchy's V-cycle C, from `iters` (>= 2)
+ * iterations started at x_i = 1 + 0.5 u_i (u from SplitMix64(seed, stream
+ * 8193)): the geometric mean of the residual 1-norm ratios over the second
+ * half of the run. */
+bamg_status bamg_vcycle_factor(bamg_hierarchy* h, int iters, uint64_t seed, double* factor, void* stream);
+/* Learned setup judged against a bound, with the LS setup as fallback:
+ * builds the hierarchy with interp = BAMG_INTERP_MLP; if that fails
+ * numerically or its V-cycle factor (bamg_vcycle_factor, 12 iterations)
+ * exceeds max_factor, builds the LS hierarchy instead.  *used_ls = 1 when
+ * the fallback was taken; *factor = the factor of the hierarchy returned
+ * (measured for the learned one, -1 when the LS one was not judged). */
+bamg_status bamg_setup_judged(const bamg_csr* A, const bamg_params* p, double max_factor, void* stream,
+                              bamg_hierarchy** out, double* factor, int* used_ls);
+
 /* ---------------------------------------------------------------- views --
  * Read-only views of the device arrays of a hierarchy, valid until
  * bamg_destroy.  Level 0 is the finest.  CSR arrays are int32 row_ptr[rows+1],
@@ -197,7 +261,9 @@ int bamg_num_levels(const bamg_hierarchy* h);
 bamg_status bamg_level(const bamg_hierarchy* h, int l, bamg_level_view* out);
 
 /* Setup triplets on the finest level: sigma (host, r doubles), and device
- * views of U, V (n x ld row-major, ld = block stride >= r) and x^(0). */
+ * views of U, V (n x ld row-major, ld = block stride >= r) and x^(0).  A
+ * hierarchy built with network fits carries no test vectors: U and V are
+ * NULL and sigma holds the coarsest level's values. */
 bamg_status bamg_triplets(const bamg_hierarchy* h, double* sigma_host, int* ld,
                           const double** U_dev, const double** V_dev,
                           const double** x0_dev);

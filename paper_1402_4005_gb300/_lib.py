@@ -34,7 +34,8 @@ class Params(C.Structure):
     _fields_ = [("r", i32), ("max_levels", i32), ("coarse_min", i32), ("nu_setup", i32),
                 ("nu_pre", i32), ("nu_post", i32), ("c_min", i32), ("c_max", i32),
                 ("omega", f64), ("coarsening", i32), ("precision", i32), ("restriction", i32),
-                ("seed", u64), ("stochastic_tol", f64), ("max_coarse_dense", i32)]
+                ("seed", u64), ("stochastic_tol", f64), ("max_coarse_dense", i32),
+                ("interp", i32), ("mlp_params", vp)]
 
 
 class SolveParams(C.Structure):
@@ -79,6 +80,14 @@ SIGNATURES = {
     "bamg_batch_lanes": (i32, [vp, i32, ip, ip, ip]),
     "bamg_batch_chain": (vp, [vp, i32]),
     "bamg_destroy_batched": (None, [vp]),
+    "bamg_mlp_num_params": (i32, []),
+    "bamg_mlp_init": (i32, [vp, u64, vp]),
+    "bamg_mlp_forward": (i32, [vp, i32, vp, vp, vp]),
+    "bamg_mlp_grad": (i32, [vp, i32, vp, vp, vp, vp, vp, vp]),
+    "bamg_mlp_train": (i32, [vp, i32, vp, vp, vp, i32, i32, C.c_float, C.POINTER(C.c_float), vp]),
+    "bamg_mlp_harvest": (i32, [vp, i32, vp, vp, vp, i32, ip, vp]),
+    "bamg_vcycle_factor": (i32, [vp, i32, u64, dp, vp]),
+    "bamg_setup_judged": (i32, [C.POINTER(Csr), C.POINTER(Params), f64, vp, C.POINTER(vp), dp, ip]),
     "bamg_num_levels": (i32, [vp]),
     "bamg_level": (i32, [vp, i32, C.POINTER(LevelView)]),
     "bamg_triplets": (i32, [vp, dp, ip, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]),

@@ -42,10 +42,16 @@ def bamg_params_default(**overrides) -> _lib.Params:
     check(lib().bamg_params_default(C.byref(p)), "bamg_params_default")
     names = {"coarsening": {"geometric": 0, "mis": 1},
              "precision": {"fp64": 0, "mixed": 1},
-             "restriction": {"ls": 0, "average": 1}}
+             "restriction": {"ls": 0, "average": 1},
+             "interp": {"ls": 0, "mlp": 1}}
     for k, v in overrides.items():
         if k in names and isinstance(v, str):
             v = names[k][v]
+        if k == "mlp_params" and isinstance(v, torch.Tensor):
+            # the caller keeps the tensor alive until bamg_setup returns
+            if v.dtype != torch.float32 or not v.is_cuda or v.numel() != bamg_mlp_num_params():
+                raise ValueError("mlp_params must be a CUDA float32 tensor of bamg_mlp_num_params() entries")
+            v = v.data_ptr()
         setattr(p, k, v)
     return p
 
@@ -425,3 +431,90 @@ def bamg_step_coarsest(B, M, N, r: int, prec: str = "fp64", pinv=True, stream=No
     check(lib().bamg_step_coarsest(PREC[prec], n, r, _p(B), _p(M), _p(N), _p(sig), _p(U), _p(V), _p(P),
                                    _stream(stream)), "coarsest")
     return sig, U, V, P
+
+
+# ------------------------------------------------------ learned interpolation
+def bamg_mlp_num_params() -> int:
+    return int(lib().bamg_mlp_num_params())
+
+
+def bamg_mlp_init(seed: int = 5, stream=None) -> torch.Tensor:
+    """Fresh network parameters (float32 vector on the GPU)."""
+    p = torch.empty(bamg_mlp_num_params(), dtype=torch.float32, device="cuda")
+    check(lib().bamg_mlp_init(_p(p), C.c_uint64(seed), _stream(stream)), "bamg_mlp_init")
+    return p
+
+
+def _bf16_rows(X) -> torch.Tensor:
+    X = X if isinstance(X, torch.Tensor) else torch.as_tensor(np.asarray(X, dtype=np.float32))
+    X = X.to(device="cuda", dtype=torch.bfloat16).contiguous()
+    if X.dim() != 2 or X.shape[1] != 64:
+        raise ValueError("features must be an M x 64 array")
+    return X
+
+
+def bamg_mlp_forward(params: torch.Tensor, X, stream=None) -> torch.Tensor:
+    X = _bf16_rows(X)
+    Y = torch.empty(X.shape[0], 16, dtype=torch.float32, device="cuda")
+    check(lib().bamg_mlp_forward(_p(params), X.shape[0], _p(X), _p(Y), _stream(stream)), "bamg_mlp_forward")
+    return Y
+
+
+def bamg_mlp_grad(params: torch.Tensor, X, T, mask, stream=None):
+    """(loss, gradient) of the masked mean squared error."""
+    X = _bf16_rows(X)
+    T = _dev(T, torch.float32)
+    mask = _dev(mask, torch.float32)
+    g = torch.empty_like(params)
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    check(lib().bamg_mlp_grad(_p(params), X.shape[0], _p(X), _p(T), _p(mask), _p(g), _p(loss),
+                              _stream(stream)), "bamg_mlp_grad")
+    return float(loss.item()), g
+
+
+def bamg_mlp_train(params: torch.Tensor, X, T, mask, epochs: int = 10, batch: int = 4096, lr: float = 1e-3,
+                   stream=None) -> list:
+    """Adam on the network in place; returns the mean loss of each epoch."""
+    X = _bf16_rows(X)
+    T = _dev(T, torch.float32)
+    mask = _dev(mask, torch.float32)
+    losses = (C.c_float * epochs)()
+    check(lib().bamg_mlp_train(_p(params), X.shape[0], _p(X), _p(T), _p(mask), epochs, batch, C.c_float(lr),
+                               losses, _stream(stream)), "bamg_mlp_train")
+    return list(losses)
+
+
+def bamg_mlp_harvest(h: Hierarchy, level: int, stream=None):
+    """(X bf16 [nF, 64], T [nF, 16], mask [nF, 16]) of a level of an LS hierarchy."""
+    cnt = C.c_int(0)
+    check(lib().bamg_mlp_harvest(C.c_void_p(h.handle), level, None, None, None, 0, C.byref(cnt),
+                                 _stream(stream)), "bamg_mlp_harvest")
+    nf = cnt.value
+    X = torch.empty(max(nf, 1), 64, dtype=torch.bfloat16, device="cuda")
+    T = torch.empty(max(nf, 1), 16, dtype=torch.float32, device="cuda")
+    M = torch.empty(max(nf, 1), 16, dtype=torch.float32, device="cuda")
+    check(lib().bamg_mlp_harvest(C.c_void_p(h.handle), level, _p(X), _p(T), _p(M), max(nf, 1), C.byref(cnt),
+                                 _stream(stream)), "bamg_mlp_harvest")
+    return X[:nf], T[:nf], M[:nf]
+
+
+def bamg_vcycle_factor(h: Hierarchy, iters: int = 12, seed: int = 1, stream=None) -> float:
+    f = C.c_double(0.0)
+    check(lib().bamg_vcycle_factor(C.c_void_p(h.handle), iters, C.c_uint64(seed), C.byref(f), _stream(stream)),
+          "bamg_vcycle_factor")
+    return f.value
+
+
+def bamg_setup_judged(row_ptr, col, val, n: int, params: _lib.Params, max_factor: float, nx: int = 0,
+                      ny: int = 0, stream=None):
+    """Learned setup with the LS fallback: (Hierarchy, factor, used_ls)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col, dtype=np.int32)
+    va = np.ascontiguousarray(val, dtype=np.float64)
+    A = _csr_struct(rp, ci, va, n, nx, ny, on_device=False)
+    h = C.c_void_p()
+    f = C.c_double(0.0)
+    used = C.c_int(0)
+    check(lib().bamg_setup_judged(C.byref(A), C.byref(params), C.c_double(max_factor), _stream(stream),
+                                  C.byref(h), C.byref(f), C.byref(used)), "bamg_setup_judged")
+    return Hierarchy(h.value, n), f.value, bool(used.value)

@@ -92,6 +92,14 @@ static bamg_status check_params(const bamg_csr* A, const bamg_params* p) {
   BAMG_CHECK_ARG(p->max_coarse_dense >= 1 && p->max_coarse_dense <= 1024);
   if (p->coarsening == BAMG_COARSEN_GEOMETRIC)
     BAMG_CHECK_ARG(A->nx >= 1 && A->ny >= 1 && (int64_t)A->nx * A->ny == A->n);
+  BAMG_CHECK_ARG(p->interp == BAMG_INTERP_LS || p->interp == BAMG_INTERP_MLP);
+  if (p->interp == BAMG_INTERP_MLP) {
+    BAMG_CHECK_ARG(p->mlp_params != nullptr);
+    if (p->coarsening != BAMG_COARSEN_GEOMETRIC) {
+      set_error("network fits need geometric coarsening (grid-offset features)");
+      return BAMG_ERR_UNSUPPORTED;
+    }
+  }
   return BAMG_OK;
 }
 
@@ -111,6 +119,17 @@ bamg_status bamg_setup(const bamg_csr* A, const bamg_params* p, void* stream, ba
   do {
     if (cudaGetDevice(&h->device) != cudaSuccess) { st = BAMG_ERR_CUDA; break; }
     configure_pool(h->device);
+    if (p->interp == BAMG_INTERP_MLP) {
+      h->learned = 1;
+      size_t bytes = sizeof(float) * mlp_num_params();
+      st = h->mlp.alloc(bytes, s);
+      if (st != BAMG_OK) break;
+      if (cudaMemcpyAsync(h->mlp.p, p->mlp_params, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+        set_error("copy of the network parameters failed");
+        st = BAMG_ERR_CUDA;
+        break;
+      }
+    }
     st = setup_finest(h, A, s);
     if (st != BAMG_OK) break;
     st = h->mixed ? run_setup<float>(h, s) : run_setup<double>(h, s);
@@ -142,6 +161,41 @@ bamg_status bamg_vcycle(bamg_hierarchy* h, const double* r_dev, double* z_dev, v
   BAMG_TRY(vcycle_run(h, s));
   BAMG_CUDA(cudaMemcpyAsync(z_dev, h->io_out.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   return BAMG_OK;
+}
+
+bamg_status bamg_vcycle_factor(bamg_hierarchy* h, int iters, uint64_t seed, double* factor, void* stream) {
+  BAMG_CHECK_ARG(h && factor && iters >= 2 && iters <= 10000);
+  return vcycle_factor(h, iters, seed, factor, S(stream));
+}
+
+bamg_status bamg_setup_judged(const bamg_csr* A, const bamg_params* p, double max_factor, void* stream,
+                              bamg_hierarchy** out, double* factor, int* used_ls) {
+  BAMG_CHECK_ARG(out && p && factor && used_ls && p->interp == BAMG_INTERP_MLP);
+  *out = nullptr;
+  *used_ls = 0;
+  *factor = -1.0;
+  bamg_hierarchy* h = nullptr;
+  bamg_status st = bamg_setup(A, p, stream, &h);
+  if (st == BAMG_OK) {
+    double f = 0.0;
+    st = vcycle_factor(h, 12, p->seed, &f, S(stream));
+    if (st == BAMG_OK && f <= max_factor) {
+      *out = h;
+      *factor = f;
+      return BAMG_OK;
+    }
+    bamg_destroy(h);
+    if (st != BAMG_OK) return st;
+  } else if (st != BAMG_ERR_NUMERIC) {
+    return st;
+  }
+  // fallback: the least-squares fits
+  bamg_params q = *p;
+  q.interp = BAMG_INTERP_LS;
+  q.mlp_params = nullptr;
+  st = bamg_setup(A, &q, stream, out);
+  if (st == BAMG_OK) *used_ls = 1;
+  return st;
 }
 
 bamg_status bamg_solve(bamg_hierarchy* h, double* x_dev, const bamg_solve_params* sp, bamg_solve_info* info,

@@ -168,8 +168,10 @@ static bamg_status coarsen_level(bamg_hierarchy* h, int l, DevMem& U, DevMem& V,
   const T* Btv = L.Bt.vals<T>();
   const T* dv = dinv_of<T>(L);
   Trace tr;
+  const bool learned = h->learned != 0;
   // Algorithm 1, first smoothing loop: relax V with B and U with B^T
-  for (int it = 0; it < p.nu_setup; ++it) {
+  // (not needed when the network proposes the fits)
+  for (int it = 0; !learned && it < p.nu_setup; ++it) {
     BAMG_TRY(relax_block<T>(L.n, ld, L.B.r(), L.B.c(), Bv, dv, V.as<T>(), tmpV.as<T>(), nullptr, nullptr, om,
                             0, s));
     std::swap(V, tmpV);
@@ -179,13 +181,15 @@ static bamg_status coarsen_level(bamg_hierarchy* h, int l, DevMem& U, DevMem& V,
   }
   tr.mark(s, "relax", l);
   // eq. ls_weights with unit vectors
-  BAMG_TRY(L.s.alloc(sizeof(double) * ld, s));
-  BAMG_TRY(L.t.alloc(sizeof(double) * ld, s));
-  BAMG_TRY(norms_weights<T>(L.n, ld, r, L.B.r(), L.B.c(), Bv, V.as<T>(), 1, 0, scale.as<T>(),
-                            L.s.as<double>(), norms.as<double>(), s));
-  BAMG_TRY(norms_weights<T>(L.n, ld, r, L.Bt.r(), L.Bt.c(), Btv, U.as<T>(), 1, 1, scale.as<T>(),
-                            L.t.as<double>(), norms.as<double>(), s));
-  tr.mark(s, "weights", l);
+  if (!learned) {
+    BAMG_TRY(L.s.alloc(sizeof(double) * ld, s));
+    BAMG_TRY(L.t.alloc(sizeof(double) * ld, s));
+    BAMG_TRY(norms_weights<T>(L.n, ld, r, L.B.r(), L.B.c(), Bv, V.as<T>(), 1, 0, scale.as<T>(),
+                              L.s.as<double>(), norms.as<double>(), s));
+    BAMG_TRY(norms_weights<T>(L.n, ld, r, L.Bt.r(), L.Bt.c(), Btv, U.as<T>(), 1, 1, scale.as<T>(),
+                              L.t.as<double>(), norms.as<double>(), s));
+    tr.mark(s, "weights", l);
+  }
   // C/F splitting and interpolation sets
   BAMG_TRY(L.cf.alloc(L.n, s));
   BAMG_TRY(L.cmap.alloc(sizeof(int32_t) * L.n, s));
@@ -220,13 +224,18 @@ static bamg_status coarsen_level(bamg_hierarchy* h, int l, DevMem& U, DevMem& V,
   DevMem fitP, fitQ;
   BAMG_TRY(fitP.alloc(sizeof(double) * (njz > 0 ? njz : 1), s));
   BAMG_TRY(fitQ.alloc(sizeof(double) * (njz > 0 ? njz : 1), s));
-  BAMG_TRY(ls_fit<T>(L.n, ld, r, L.Jrp.as<int32_t>(), L.Jci.as<int32_t>(), V.as<T>(), L.s.as<double>(), 0,
-                     fitP.as<double>(), rkd.as<int>(), s));
-  if (p.restriction == BAMG_RESTRICT_AVERAGE)
-    BAMG_TRY(average_fits(L.n, L.Jrp.as<int32_t>(), fitQ.as<double>(), s));
-  else
-    BAMG_TRY(ls_fit<T>(L.n, ld, r, L.Jrp.as<int32_t>(), L.Jci.as<int32_t>(), U.as<T>(), L.t.as<double>(), 1,
-                       fitQ.as<double>(), rkd.as<int>(), s));
+  if (learned) {
+    BAMG_TRY(mlp_fits(L, h->mlp.as<float>(), fitP.as<double>(), fitQ.as<double>(), s));
+    if (p.restriction == BAMG_RESTRICT_AVERAGE) BAMG_TRY(average_fits(L.n, L.Jrp.as<int32_t>(), fitQ.as<double>(), s));
+  } else {
+    BAMG_TRY(ls_fit<T>(L.n, ld, r, L.Jrp.as<int32_t>(), L.Jci.as<int32_t>(), V.as<T>(), L.s.as<double>(), 0,
+                       fitP.as<double>(), rkd.as<int>(), s));
+    if (p.restriction == BAMG_RESTRICT_AVERAGE)
+      BAMG_TRY(average_fits(L.n, L.Jrp.as<int32_t>(), fitQ.as<double>(), s));
+    else
+      BAMG_TRY(ls_fit<T>(L.n, ld, r, L.Jrp.as<int32_t>(), L.Jci.as<int32_t>(), U.as<T>(), L.t.as<double>(), 1,
+                         fitQ.as<double>(), rkd.as<int>(), s));
+  }
   int nnzP = njz + nc;
   for (Csr* X : {&L.P, &L.Qt}) {
     BAMG_TRY(X->alloc(L.n, nc, nnzP, s));
@@ -275,6 +284,7 @@ static bamg_status coarsen_level(bamg_hierarchy* h, int l, DevMem& U, DevMem& V,
     BAMG_TRY(Lf.Qt.make32(s));
     BAMG_TRY(Lf.Q.make32(s));
   }
+  if (learned) return BAMG_OK;
   // injection of the test vectors
   BAMG_TRY(Uc.alloc(sizeof(T) * (size_t)nc * ld, s));
   BAMG_TRY(Vc.alloc(sizeof(T) * (size_t)nc * ld, s));
@@ -337,15 +347,66 @@ static bamg_status relax_triplets(bamg_hierarchy* h, int l, DevMem& U, DevMem& V
   return BAMG_OK;
 }
 
+static void complexities(bamg_hierarchy* h) {
+  // eq. operator_complexity_def; Section 7
+  double nnz_sum = 0, n_sum = 0;
+  for (auto& L : h->lv) { nnz_sum += L.B.nnz; n_sum += L.n; }
+  h->op_cplx = nnz_sum / h->lv[0].B.nnz;
+  h->grid_cplx = n_sum / h->lv[0].n;
+}
+
+// Setup with network fits: no test vectors to carry up, so only the right
+// singular vector of the smallest coarsest |sigma| is interpolated (v <- P v)
+// and smoothed towards B v = 0 on each level on the way up (the sigma = 0
+// case of the inhomogeneous relaxation); it becomes x^(0).
+static bamg_status learned_unwind(bamg_hierarchy* h, int l, int rr, const double* Vd, const double* sg,
+                                  cudaStream_t s) {
+  std::vector<double> sig(rr);
+  BAMG_CUDA(cudaMemcpyAsync(sig.data(), sg, sizeof(double) * rr, cudaMemcpyDeviceToHost, s));
+  BAMG_CUDA(cudaStreamSynchronize(s));
+  int kmin = 0;
+  for (int k = 1; k < rr; ++k)
+    if (std::fabs(sig[k]) < std::fabs(sig[kmin])) kmin = k;
+  h->sigma = sig;
+  h->sigma.resize(h->p.r, 0.0);
+  const int nL = h->lv[l].n;
+  DevMem x, y, zero;
+  BAMG_TRY(x.alloc(sizeof(double) * nL, s));
+  BAMG_TRY(launch(column_kernel, dim3(cdiv(nL, 256)), dim3(256), 0, s, nL, rr, kmin, Vd, x.as<double>()));
+  for (int k = l - 1; k >= 0; --k) {
+    Level& L = h->lv[k];
+    BAMG_TRY(y.alloc(sizeof(double) * L.n, s));
+    BAMG_TRY(zero.alloc(sizeof(double) * L.n, s));
+    BAMG_CUDA(cudaMemsetAsync(zero.p, 0, sizeof(double) * L.n, s));
+    int gp = (L.P.rows && L.P.nnz / L.P.rows > 2) ? 4 : 2;
+    BAMG_TRY(csr_vec<double>(VEC_SPMV, L.n, gp, L.P.r(), L.P.c(), L.P.v(), nullptr, 0.0, x.as<double>(), nullptr,
+                             y.as<double>(), s));
+    std::swap(x, y);
+    BAMG_TRY(y.alloc(sizeof(double) * L.n, s));
+    for (int it = 0; it < h->p.nu_setup; ++it) {
+      BAMG_TRY(csr_vec<double>(VEC_JACOBI, L.n, L.vec_g, L.B.r(), L.B.c(), L.B.v(), L.dinv.as<double>(),
+                               h->p.omega, x.as<double>(), zero.as<double>(), y.as<double>(), s));
+      std::swap(x, y);
+    }
+  }
+  h->x0 = std::move(x);
+  BAMG_TRY(orient_normalise(h->lv[0].n, h->x0.as<double>(), s));
+  complexities(h);
+  return BAMG_OK;
+}
+
 template <typename T>
 static bamg_status run_setup(bamg_hierarchy* h, cudaStream_t s) {
   const bamg_params& p = h->p;
   const int ld = h->ld, r = p.r;
+  const bool learned = h->learned != 0;
   std::vector<DevMem> U(1), V(1);
   int n0 = h->lv[0].n;
-  BAMG_TRY(U[0].alloc(sizeof(T) * (size_t)n0 * ld, s));
-  BAMG_TRY(V[0].alloc(sizeof(T) * (size_t)n0 * ld, s));
-  BAMG_TRY(init_vectors<T>(n0, ld, r, p.seed, U[0].as<T>(), V[0].as<T>(), s));
+  if (!learned) {
+    BAMG_TRY(U[0].alloc(sizeof(T) * (size_t)n0 * ld, s));
+    BAMG_TRY(V[0].alloc(sizeof(T) * (size_t)n0 * ld, s));
+    BAMG_TRY(init_vectors<T>(n0, ld, r, p.seed, U[0].as<T>(), V[0].as<T>(), s));
+  }
   DevMem scale, norms, rkd, sig, sig64;
   BAMG_TRY(scale.alloc(sizeof(T) * ld, s));
   BAMG_TRY(norms.alloc(sizeof(double) * ld, s));
@@ -357,8 +418,10 @@ static bamg_status run_setup(bamg_hierarchy* h, cudaStream_t s) {
   while (!is_coarsest(h, h->lv[l], l)) {
     DevMem tU, tV;
     size_t bytes = sizeof(T) * (size_t)h->lv[l].n * ld;
-    BAMG_TRY(tU.alloc(bytes, s));
-    BAMG_TRY(tV.alloc(bytes, s));
+    if (!learned) {
+      BAMG_TRY(tU.alloc(bytes, s));
+      BAMG_TRY(tV.alloc(bytes, s));
+    }
     U.emplace_back();
     V.emplace_back();
     BAMG_TRY(coarsen_level<T>(h, l, U[l], V[l], U[l + 1], V[l + 1], tU, tV, scale, norms, rkd, s));
@@ -401,6 +464,7 @@ static bamg_status run_setup(bamg_hierarchy* h, cudaStream_t s) {
     BAMG_TRY(convert<double, float>(nn, h->Bpinv.as<double>(), h->Bpinv32.as<float>(), s));
   }
   tr.mark(s, "coarsest solve", l);
+  if (learned) return learned_unwind(h, l, rr, Vd.as<double>(), sg.as<double>(), s);
   // triplets into padded blocks
   BAMG_TRY(U[l].alloc(sizeof(T) * (size_t)nL * ld, s));
   BAMG_TRY(V[l].alloc(sizeof(T) * (size_t)nL * ld, s));
@@ -447,11 +511,7 @@ static bamg_status run_setup(bamg_hierarchy* h, cudaStream_t s) {
   BAMG_TRY(launch(column_kernel, dim3(cdiv(n0, 256)), dim3(256), 0, s, n0, ld, kmin,
                   (const double*)h->V64.as<double>(), h->x0.as<double>()));
   BAMG_TRY(orient_normalise(n0, h->x0.as<double>(), s));
-  // complexities (eq. operator_complexity_def; Section 7)
-  double nnz_sum = 0, n_sum = 0;
-  for (auto& L : h->lv) { nnz_sum += L.B.nnz; n_sum += L.n; }
-  h->op_cplx = nnz_sum / h->lv[0].B.nnz;
-  h->grid_cplx = n_sum / h->lv[0].n;
+  complexities(h);
   return BAMG_OK;
 }
 

@@ -62,6 +62,8 @@ struct bamg_hierarchy {
   double setup_ms = 0.0;
   double op_cplx = 0.0, grid_cplx = 0.0;
   int rankdef = 0;
+  int learned = 0;                      // fits from the interpolation network
+  bamg::DevMem mlp;                     // its parameters (float, copied at setup)
 };
 
 namespace bamg {
@@ -72,4 +74,9 @@ bamg_status fgmres(bamg_hierarchy* h, double* x, const bamg_solve_params* sp, ba
                    cudaStream_t s);
 bamg_status setup_finest(bamg_hierarchy* h, const bamg_csr* A, cudaStream_t s);
 template <typename T> bamg_status run_setup(bamg_hierarchy* h, cudaStream_t s);
+// mlp.cu: P rows and Q columns of a geometric level from the network
+int mlp_num_params();
+bamg_status mlp_fits(const Level& L, const float* params, double* fitP, double* fitQ, cudaStream_t s);
+// solve.cu: asymptotic factor of the stationary iteration x <- x - C B x
+bamg_status vcycle_factor(bamg_hierarchy* h, int iters, uint64_t seed, double* factor, cudaStream_t s);
 }  // namespace bamg

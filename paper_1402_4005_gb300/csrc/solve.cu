@@ -404,6 +404,56 @@ bamg_status fgmres(bamg_hierarchy* h, double* x, const bamg_solve_params* sp, ba
   return BAMG_OK;
 }
 
+// ------------------------------------------------- V-cycle convergence factor
+// x_i = 1 + 0.5 * u_i with u_i uniform in [-1, 1) (SplitMix64 stream 8193)
+__global__ void factor_start_kernel(int n, uint64_t seed, double* __restrict__ x) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = 1.0 + 0.5 * splitmix_pm1(seed, 8193, (uint64_t)i);
+}
+
+__global__ void add_kernel(int n, const double* __restrict__ z, double* __restrict__ x) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] += z[i];
+}
+
+// Stationary iteration x <- x + C(0 - B x) with the V-cycle C: the residual
+// obeys r <- (I - B C) r (eq. error_propagator_twogrid moved to the residual
+// side), so the ratio of its 1-norms over the second half of the run
+// estimates the asymptotic convergence factor on the range of B.
+bamg_status vcycle_factor(bamg_hierarchy* h, int iters, uint64_t seed, double* factor, cudaStream_t s) {
+  Level& L = h->lv[0];
+  const int n = L.n;
+  DevMem x, r, zero, sums;
+  BAMG_TRY(x.alloc(sizeof(double) * n, s));
+  BAMG_TRY(r.alloc(sizeof(double) * n, s));
+  BAMG_TRY(zero.alloc(sizeof(double) * n, s));
+  BAMG_TRY(sums.alloc(sizeof(double) * 2 * (iters + 1), s));
+  BAMG_CUDA(cudaMemsetAsync(zero.p, 0, sizeof(double) * n, s));
+  unsigned g = cdiv(n, 256);
+  BAMG_TRY(launch(factor_start_kernel, dim3(g), dim3(256), 0, s, n, seed, x.as<double>()));
+  const int G = lanes_for(L.B);
+  for (int k = 0; k <= iters; ++k) {
+    BAMG_TRY(csr_vec<double>(VEC_RESID, n, G, L.B.r(), L.B.c(), L.B.v(), nullptr, 0.0, x.as<double>(),
+                             zero.as<double>(), r.as<double>(), s));
+    BAMG_TRY(abs_sums(n, r.as<double>(), sums.as<double>() + 2 * k, s));
+    if (k == iters) break;
+    BAMG_CUDA(cudaMemcpyAsync(h->io_in.p, r.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    BAMG_TRY(vcycle_run(h, s));
+    BAMG_TRY(launch(add_kernel, dim3(g), dim3(256), 0, s, n, (const double*)h->io_out.as<double>(), x.as<double>()));
+  }
+  std::vector<double> hs(2 * (iters + 1));
+  BAMG_CUDA(cudaMemcpyAsync(hs.data(), sums.p, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, s));
+  BAMG_CUDA(cudaStreamSynchronize(s));
+  const int k0 = iters / 2;
+  double a = hs[2 * k0 + 1], b = hs[2 * iters + 1];
+  if (!(a > 0.0) || !std::isfinite(b)) {
+    *factor = std::isfinite(b) ? 0.0 : INFINITY;
+    return BAMG_OK;
+  }
+  *factor = std::pow(b / a, 1.0 / (iters - k0));
+  return BAMG_OK;
+}
+
 template bamg_status vcycle_body<double>(bamg_hierarchy*, cudaStream_t);
 template bamg_status vcycle_body<float>(bamg_hierarchy*, cudaStream_t);
 
