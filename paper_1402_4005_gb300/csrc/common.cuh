@@ -179,4 +179,10 @@ bamg_status reduce_partials(const double* partial, int nb, int K, double* out,
 
 int num_sms();
 
+// Raises the dynamic shared-memory limit of kernel fn to the device's opt-in
+// maximum (less its static shared memory) once per device: setups may run
+// concurrently on several host threads, so the attribute is set under a lock
+// and never changed afterwards.  *max_dyn receives the usable bytes.
+bamg_status allow_max_smem(const void* fn, std::atomic<uint64_t>& done, int* max_dyn);
+
 }  // namespace bamg

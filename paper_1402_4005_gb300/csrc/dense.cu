@@ -19,15 +19,23 @@
 // (right), B^+ = (B + e w^T)^{-1} - w e^T; the inverse is Gauss-Jordan
 // elimination with partial pivoting.
 //
-// Mapping: one cluster of up to 16 blocks.  Every n x n matrix is row-major
-// and its rows are owned cyclically (row i by block i mod NB); a block only
-// writes its own rows, so they stay in its L1.  The sequential algorithms
-// (Cholesky, triangular solves, bidiagonalization, Gauss-Jordan) advance one
-// index per step: the owner of the next pivot row publishes the vector all
-// blocks need, then a hardware cluster barrier, then every block updates its
-// own rows.  Published vectors are read through L2 (__ldcg).
+// Mapping: one cluster of up to 16 blocks.  Rows of every n x n matrix are
+// owned cyclically (row i by block i mod NB) and only their owner writes
+// them.  The sequential algorithms (Cholesky, triangular solves,
+// bidiagonalization, Gauss-Jordan) advance one index per step: the owner of
+// the next pivot row publishes the vector all blocks need, a hardware
+// cluster barrier follows, then every block updates its own rows.
+//
+// Two storage policies share this code.  Shared (SM = true, when the own
+// rows of all matrices fit): each block keeps its own rows, its published
+// vectors and its partial sums in shared memory, and the other blocks read
+// them through distributed shared memory, so a step costs a barrier and one
+// remote read.  Global (SM = false, larger n): the same arrays live in global
+// memory and remote reads go through L2 (__ldcg).  Reductions over the NB
+// blocks load the NB partials in parallel (unrolled to the cluster limit).
 #include <cooperative_groups.h>
 
+#include <atomic>
 #include <cfloat>
 #include <cstdio>
 #include <cstdlib>
@@ -60,23 +68,23 @@ template <typename T> struct Eps;
 template <> struct Eps<float> { static constexpr double v = FLT_EPSILON; static constexpr double tiny = FLT_MIN; };
 template <> struct Eps<double> { static constexpr double v = DBL_EPSILON; static constexpr double tiny = DBL_MIN; };
 
+// Row-owned arrays (LM ... pcol) are, under the shared policy, the compact
+// own rows of the block (local row i / NB); under the global policy, the
+// full arrays.  The remaining arrays are global under both policies.
 template <typename T>
 struct DenseArgs {
-  int n, r;
+  int n, r, NB, RP;      // size, triplets, cluster blocks, own rows per block
   const double *B, *M, *N;
   double *sigma, *U, *V, *Bpinv;
-  T *LM, *LN;      // n x n: Cholesky factor L below the diagonal, L^T above
-  T *X;            // n x n work (L_M^{-1} B, then its transpose solved with L_N)
-  T *C;            // n x n: C = L_M^{-1} B L_N^{-T}
-  T *W;            // n x n: bidiagonalization work
-  T *Pr;           // n x n: right Householder vectors (row k = reflector k)
-  T *G;            // n x 2n: Gauss-Jordan tableau
+  T *LM, *LN;      // Cholesky factor L below the diagonal, L^T above
+  T *S1;           // X = L_M^{-1} B, then C = L_M^{-1} B L_N^{-T}
+  T *S2;           // W: C^T during the solves, then C for the bidiagonalization
+  T *S3;           // right Householder vectors (row k = reflector k)
+                   // S2 and S3 are adjacent: Gauss-Jordan tableau G (2n per row)
   T *R;            // n x 2r: right-hand sides of the triplet solves
-  T *pub;          // 4 slots of 2n: published vectors (double buffered)
-  T *part;         // kMaxNB x (n + 2 kMaxR + 2): per-block partial sums
-  T *cval;         // kMaxNB: pivot candidates (value)
-  int *cidx;       // kMaxNB: pivot candidates (row)
-  int *pcol;       // n: pivot column assigned to each row (-1 = none yet)
+  T *pub;          // published vectors: 4 slots of 2n (+ 64)
+  T *part;         // partial sums of a block: part_stride(n) entries
+  int *pcol;       // pivot column assigned to each row (-1 = none yet)
   T *d, *e, *taup; // bidiagonal and right reflector scalars
   T *sig;          // r selected singular values
   T *vb;           // r x n: right vectors of the bidiagonal, then of C
@@ -85,9 +93,65 @@ struct DenseArgs {
   DenseCtl* ctl;
 };
 
+// partial sums: [0, n) vector, n.. scalars and per-value slots, 2 pivot slots
+__host__ __device__ inline int part_stride(int n) { return n + 2 * kMaxR + 4; }
+
 __device__ inline void csync() { cg::this_cluster().sync(); }
 
-template <typename T> __device__ inline T ldcg(const T* p) { return __ldcg(p); }
+template <bool SM, typename T> __device__ inline T rd(const T* p) {
+  if constexpr (SM) return *p;
+  else return __ldcg(p);
+}
+
+// blocks of the cluster: a compile-time 16 under the shared policy (index
+// arithmetic by shifts), the launched cluster size otherwise
+template <bool SM, typename T> __device__ inline int nblocks(const DenseArgs<T>& A) {
+  if constexpr (SM) return kMaxNB;
+  else return A.NB;
+}
+
+// own row i of a row-owned array with row length ld
+template <bool SM, typename T>
+__device__ inline T* own(const DenseArgs<T>& A, T* base, int i, int ld) {
+  if constexpr (SM) return base + (size_t)(i / kMaxNB) * ld;
+  else return base + (size_t)i * ld;
+}
+// row i of a row-owned array, possibly owned by another block
+template <bool SM, typename T>
+__device__ inline const T* any(const DenseArgs<T>& A, T* base, int i, int ld) {
+  if constexpr (SM) return cg::this_cluster().map_shared_rank(base + (size_t)(i / kMaxNB) * ld, i % kMaxNB);
+  else return base + (size_t)i * ld;
+}
+template <bool SM, typename T>
+__device__ inline int* own_pcol(const DenseArgs<T>& A, int i) {
+  if constexpr (SM) return A.pcol + i / kMaxNB;
+  else return A.pcol + i;
+}
+// publication buffer: written by its owner, read by everyone
+template <bool SM, typename T> __device__ inline T* pub_w(const DenseArgs<T>& A) { return A.pub; }
+template <bool SM, typename T> __device__ inline const T* pub_r(const DenseArgs<T>& A, int owner) {
+  if constexpr (SM) return cg::this_cluster().map_shared_rank(A.pub, owner);
+  else return A.pub;
+}
+template <bool SM, typename T> __device__ inline T* part_w(const DenseArgs<T>& A) {
+  if constexpr (SM) return A.part;
+  else return A.part + (size_t)blockIdx.x * part_stride(A.n);
+}
+template <bool SM, typename T> __device__ inline const T* part_r(const DenseArgs<T>& A, int q) {
+  if constexpr (SM) return cg::this_cluster().map_shared_rank(A.part, q);
+  else return A.part + (size_t)q * part_stride(A.n);
+}
+// sum over the blocks of partial slot k (the loads are issued together)
+template <bool SM, typename T>
+__device__ inline T part_sum(const DenseArgs<T>& A, int k) {
+  T v[kMaxNB];
+#pragma unroll
+  for (int q = 0; q < kMaxNB; ++q) v[q] = q < nblocks<SM>(A) ? rd<SM>(part_r<SM>(A, q) + k) : T(0);
+  T s = 0;
+#pragma unroll
+  for (int q = 0; q < kMaxNB; ++q) s += v[q];
+  return s;
+}
 
 // first index i >= from owned by block b (i mod NB == b)
 __device__ inline int first_own(int b, int NB, int from) {
@@ -113,81 +177,91 @@ __device__ T block_sum(T a, T* red) {
 // publishes column k of L (row k of the trailing matrix over sqrt(a_kk));
 // every block subtracts l l^T from its own rows.  On exit the lower triangle
 // holds L and the upper triangle L^T.
-template <typename T>
+template <bool SM, typename T>
 __device__ void chol_publish(const DenseArgs<T>& A, int m) {
   const int n = A.n;
   for (int f = 0; f < 2; ++f) {
-    const T* L = f ? A.LN : A.LM;
-    T* pb = A.pub + (size_t)(2 * f + (m & 1)) * n;
-    T a = L[(size_t)m * n + m];
+    const T* L = own<SM>(A, f ? A.LN : A.LM, m, n);
+    T* pb = pub_w<SM>(A) + (size_t)(2 * f + (m & 1)) * n;
+    T a = L[m];
     T l = a > T(0) ? sqrt(a) : a;
     T inv = a > T(0) ? T(1) / l : T(0);
-    for (int j = m + 1 + threadIdx.x; j < n; j += blockDim.x) pb[j] = L[(size_t)m * n + j] * inv;
+    for (int j = m + 1 + threadIdx.x; j < n; j += blockDim.x) pb[j] = L[j] * inv;
     if (threadIdx.x == 0) pb[m] = l;
   }
 }
 
-template <typename T>
-__device__ bool cholesky_rows(const DenseArgs<T>& A, int NB, T* sv) {
-  const int n = A.n, b = blockIdx.x;
-  for (int i = b; i < n; i += NB)
+template <bool SM, typename T>
+__device__ bool cholesky_rows(const DenseArgs<T>& A, T* sv) {
+  const int n = A.n, NB = nblocks<SM>(A), b = blockIdx.x;
+  for (int i = b; i < n; i += NB) {
+    T* lm = own<SM>(A, A.LM, i, n);
+    T* ln = own<SM>(A, A.LN, i, n);
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      A.LM[(size_t)i * n + j] = T(A.M[(size_t)i * n + j]);
-      A.LN[(size_t)i * n + j] = T(A.N[(size_t)i * n + j]);
+      lm[j] = T(A.M[(size_t)i * n + j]);
+      ln[j] = T(A.N[(size_t)i * n + j]);
     }
+  }
   __syncthreads();
-  if (b == 0) chol_publish(A, 0);
+  if (b == 0) chol_publish<SM>(A, 0);
   csync();
   T* sm = sv;
   T* sn = sv + n;
   for (int k = 0; k < n; ++k) {
-    const T* pm = A.pub + (size_t)(k & 1) * n;
-    const T* pn = A.pub + (size_t)(2 + (k & 1)) * n;
+    const T* pb = pub_r<SM>(A, k % NB);
+    const T* pm = pb + (size_t)(k & 1) * n;
+    const T* pn = pb + (size_t)(2 + (k & 1)) * n;
     for (int j = k + threadIdx.x; j < n; j += blockDim.x) {
-      sm[j] = ldcg(pm + j);
-      sn[j] = ldcg(pn + j);
+      sm[j] = rd<SM>(pm + j);
+      sn[j] = rd<SM>(pn + j);
     }
     __syncthreads();
     if (!(sm[k] > T(0)) || !(sn[k] > T(0))) {
       if (b == 0 && threadIdx.x == 0) A.ctl->err = 2;
-      return false;  // every block reads the same pivots and leaves here
+      csync();       // every block reads the same pivots and leaves here,
+      return false;  // after the others have read its published vector
     }
-    if (k % NB == b)
+    if (k % NB == b) {
+      T* lm = own<SM>(A, A.LM, k, n);
+      T* ln = own<SM>(A, A.LN, k, n);
       for (int j = k + threadIdx.x; j < n; j += blockDim.x) {
-        A.LM[(size_t)k * n + j] = sm[j];
-        A.LN[(size_t)k * n + j] = sn[j];
+        lm[j] = sm[j];
+        ln[j] = sn[j];
       }
+    }
     for (int i = first_own(b, NB, k + 1); i < n; i += NB) {
+      T* lmi = own<SM>(A, A.LM, i, n);
+      T* lni = own<SM>(A, A.LN, i, n);
       const T lm = sm[i], ln = sn[i];
       for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
-        A.LM[(size_t)i * n + j] -= lm * sm[j];
-        A.LN[(size_t)i * n + j] -= ln * sn[j];
+        lmi[j] -= lm * sm[j];
+        lni[j] -= ln * sn[j];
       }
       if (threadIdx.x == 0) {
-        A.LM[(size_t)i * n + k] = lm;
-        A.LN[(size_t)i * n + k] = ln;
+        lmi[k] = lm;
+        lni[k] = ln;
       }
     }
     __syncthreads();
-    if (k + 1 < n && (k + 1) % NB == b) chol_publish(A, k + 1);
+    if (k + 1 < n && (k + 1) % NB == b) chol_publish<SM>(A, k + 1);
     csync();
   }
   return true;
 }
 
 // ------------------------------------------------ row triangular solves
-// F holds L below and L^T above the diagonal.  X (n x ncol, row stride ld,
-// own rows) is overwritten by L^{-1} X (FORWARD) or L^{-T} X (backward).  A
-// second factor F2 may serve the columns from split on (F2 = nullptr: none).
-template <typename T, bool FORWARD>
-__device__ void row_solve(const DenseArgs<T>& A, int NB, const T* F, const T* F2, int split, T* X, int ld,
-                          int ncol, T* sv) {
-  const int n = A.n, b = blockIdx.x;
+// F holds L below and L^T above the diagonal (row-owned, length n).  X
+// (row-owned, row length ld, ncol used) is overwritten by L^{-1} X (FORWARD)
+// or L^{-T} X (backward).  A second factor F2 may serve the columns from
+// split on (F2 = nullptr: none).
+template <bool SM, bool FORWARD, typename T>
+__device__ void row_solve(const DenseArgs<T>& A, T* F, T* F2, int split, T* X, int ld, int ncol, T* sv) {
+  const int n = A.n, NB = nblocks<SM>(A), b = blockIdx.x;
   auto pivot_row = [&](int m) {
-    T* pb = A.pub + (size_t)(m & 1) * 2 * n;
-    T* xm = X + (size_t)m * ld;
-    const T d1 = F[(size_t)m * n + m];
-    const T d2 = F2 ? F2[(size_t)m * n + m] : d1;
+    T* pb = pub_w<SM>(A) + (size_t)(m & 1) * 2 * n;
+    T* xm = own<SM>(A, X, m, ld);
+    const T d1 = own<SM>(A, F, m, n)[m];
+    const T d2 = F2 ? own<SM>(A, F2, m, n)[m] : d1;
     for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
       T v = xm[c] / (c < split ? d1 : d2);
       xm[c] = v;
@@ -198,15 +272,15 @@ __device__ void row_solve(const DenseArgs<T>& A, int NB, const T* F, const T* F2
   if (m % NB == b) pivot_row(m);
   csync();
   for (int s = 0; s < n; ++s, m += FORWARD ? 1 : -1) {
-    const T* pb = A.pub + (size_t)(m & 1) * 2 * n;
-    for (int c = threadIdx.x; c < ncol; c += blockDim.x) sv[c] = ldcg(pb + c);
+    const T* pb = pub_r<SM>(A, m % NB) + (size_t)(m & 1) * 2 * n;
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) sv[c] = rd<SM>(pb + c);
     __syncthreads();
     int i0 = FORWARD ? first_own(b, NB, m + 1) : b;
     for (int i = i0; FORWARD ? i < n : i < m; i += NB) {
       // forward: L[i][m] (below diagonal of row i); backward: L^T[i][m] (above)
-      const T f1 = F[(size_t)i * n + m];
-      const T f2 = F2 ? F2[(size_t)i * n + m] : f1;
-      T* xi = X + (size_t)i * ld;
+      const T f1 = own<SM>(A, F, i, n)[m];
+      const T f2 = F2 ? own<SM>(A, F2, i, n)[m] : f1;
+      T* xi = own<SM>(A, X, i, ld);
       for (int c = threadIdx.x; c < ncol; c += blockDim.x) xi[c] -= (c < split ? f1 : f2) * sv[c];
     }
     __syncthreads();
@@ -216,23 +290,34 @@ __device__ void row_solve(const DenseArgs<T>& A, int NB, const T* F, const T* F2
   }
 }
 
-// C = L_M^{-1} B L_N^{-T}; W = C for the bidiagonalization.
-template <typename T>
-__device__ void form_C(const DenseArgs<T>& A, int NB, T* sv) {
-  const int n = A.n, b = blockIdx.x;
-  for (int i = b; i < n; i += NB)
-    for (int j = threadIdx.x; j < n; j += blockDim.x) A.X[(size_t)i * n + j] = T(A.B[(size_t)i * n + j]);
+// C = L_M^{-1} B L_N^{-T} in S1; W = C in S2 for the bidiagonalization.
+template <bool SM, typename T>
+__device__ void form_C(const DenseArgs<T>& A, T* sv) {
+  const int n = A.n, NB = nblocks<SM>(A), b = blockIdx.x;
+  for (int i = b; i < n; i += NB) {
+    T* x = own<SM>(A, A.S1, i, n);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) x[j] = T(A.B[(size_t)i * n + j]);
+  }
   __syncthreads();
-  row_solve<T, true>(A, NB, A.LM, (const T*)nullptr, n, A.X, n, n, sv);   // X = L_M^{-1} B
-  for (int i = b; i < n; i += NB)                                        // W = X^T (own rows)
-    for (int j = threadIdx.x; j < n; j += blockDim.x) A.W[(size_t)i * n + j] = ldcg(A.X + (size_t)j * n + i);
+  row_solve<SM, true>(A, A.LM, (T*)nullptr, n, A.S1, n, n, sv);        // X = L_M^{-1} B
+  for (int i = b; i < n; i += NB) {                                     // W = X^T (own rows)
+    T* w = own<SM>(A, A.S2, i, n);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) w[j] = rd<SM>(any<SM>(A, A.S1, j, n) + i);
+  }
   __syncthreads();
-  row_solve<T, true>(A, NB, A.LN, (const T*)nullptr, n, A.W, n, n, sv);   // W = C^T
-  for (int i = b; i < n; i += NB)                                        // C = W^T
-    for (int j = threadIdx.x; j < n; j += blockDim.x) A.C[(size_t)i * n + j] = ldcg(A.W + (size_t)j * n + i);
+  // the barriers of this solve also order every block's reads of X before
+  // the writes of C into the same rows below
+  row_solve<SM, true>(A, A.LN, (T*)nullptr, n, A.S2, n, n, sv);        // W = C^T
+  for (int i = b; i < n; i += NB) {                                     // C = W^T
+    T* c = own<SM>(A, A.S1, i, n);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) c[j] = rd<SM>(any<SM>(A, A.S2, j, n) + i);
+  }
   csync();  // all of W read before any block overwrites its rows
-  for (int i = b; i < n; i += NB)
-    for (int j = threadIdx.x; j < n; j += blockDim.x) A.W[(size_t)i * n + j] = A.C[(size_t)i * n + j];
+  for (int i = b; i < n; i += NB) {
+    T* w = own<SM>(A, A.S2, i, n);
+    const T* c = own<SM>(A, A.S1, i, n);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) w[j] = c[j];
+  }
   csync();
 }
 
@@ -247,77 +332,80 @@ __device__ void householder(T alpha, T s2, T& beta, T& tau, T& scale) {
   }
 }
 
-
 // ------------------------------------------------- Householder bidiagonalization
 // W = Q_B D P_B^T, d[k] on the diagonal and e[k] above it; right reflectors
-// I - taup[k] p_k p_k^T (p_k[k+1] = 1, support k+1..n-1) kept in row k of Pr
+// I - taup[k] p_k p_k^T (p_k[k+1] = 1, support k+1..n-1) kept in row k of S3
 // (the left ones are not needed).  Left reflector of column k: each block
 // sums x_i W[i][j] and x_i^2 over its own rows i > k into partials; after the
 // barrier every block forms s_j = tau (W[k][j] + scale * sum_b partial_b[j])
 // and updates its rows.  Right reflector of row k: built and published by
 // the owner of row k, applied by every block to its own rows.
-template <typename T>
-__device__ void bidiag_partials(const DenseArgs<T>& A, int NB, int k) {
-  const int n = A.n, b = blockIdx.x;
-  const int stride = n + 2 * kMaxR + 2;
-  T* part = A.part + (size_t)b * stride;
+template <bool SM, typename T>
+__device__ void bidiag_partials(const DenseArgs<T>& A, int k) {
+  const int n = A.n, NB = nblocks<SM>(A), b = blockIdx.x;
+  T* part = part_w<SM>(A);
   const int i0 = first_own(b, NB, k + 1);
   for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
     T t = 0;
-    for (int i = i0; i < n; i += NB) t += A.W[(size_t)i * n + k] * A.W[(size_t)i * n + j];
+    for (int i = i0; i < n; i += NB) {
+      const T* wi = own<SM>(A, A.S2, i, n);
+      t += wi[k] * wi[j];
+    }
     part[j] = t;
   }
   if (threadIdx.x == 0) {
     T s2 = 0;
-    for (int i = i0; i < n; i += NB) s2 += A.W[(size_t)i * n + k] * A.W[(size_t)i * n + k];
+    for (int i = i0; i < n; i += NB) {
+      const T x = own<SM>(A, A.S2, i, n)[k];
+      s2 += x * x;
+    }
     part[n] = s2;
   }
   if (k % NB == b) {                       // publish row k for the other blocks
-    T* rowk = A.pub;
-    for (int j = k + threadIdx.x; j < n; j += blockDim.x) rowk[j] = A.W[(size_t)k * n + j];
+    T* rowk = pub_w<SM>(A);
+    const T* wk = own<SM>(A, A.S2, k, n);
+    for (int j = k + threadIdx.x; j < n; j += blockDim.x) rowk[j] = wk[j];
   }
 }
 
-template <typename T>
-__device__ void bidiagonalize(const DenseArgs<T>& A, int NB, T* sv, T* red) {
-  const int n = A.n, b = blockIdx.x;
+template <bool SM, typename T>
+__device__ void bidiagonalize(const DenseArgs<T>& A, T* sv, T* red) {
+  const int n = A.n, NB = nblocks<SM>(A), b = blockIdx.x;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int stride = n + 2 * kMaxR + 2;
   T* s_vec = sv;          // n: s_j of the left reflector
   T* p_vec = sv + n;      // n: right reflector
   __shared__ T sc[4];
-  bidiag_partials(A, NB, 0);
+  bidiag_partials<SM>(A, 0);
   csync();
   for (int k = 0; k < n; ++k) {
+    const T* rowk = pub_r<SM>(A, k % NB);
     // left reflector of column k
     if (threadIdx.x == 0) {
-      T s2 = 0;
-      for (int q = 0; q < NB; ++q) s2 += ldcg(A.part + (size_t)q * stride + n);
+      T s2 = part_sum<SM>(A, n);
       T beta, tau, scale;
-      householder(ldcg(A.pub + k), s2, beta, tau, scale);
+      householder(rd<SM>(rowk + k), s2, beta, tau, scale);
       sc[0] = tau; sc[1] = scale;
       if (b == 0) A.d[k] = beta;
     }
     __syncthreads();
     const T tau = sc[0], scale = sc[1];
-    for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
-      T t = 0;
-      for (int q = 0; q < NB; ++q) t += ldcg(A.part + (size_t)q * stride + j);
-      s_vec[j] = tau * (ldcg(A.pub + j) + scale * t);
-    }
+    for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x)
+      s_vec[j] = tau * (rd<SM>(rowk + j) + scale * part_sum<SM>(A, j));
     __syncthreads();
     if (tau != T(0)) {
       for (int i = first_own(b, NB, k); i < n; i += NB) {
-        const T vi = (i == k) ? T(1) : A.W[(size_t)i * n + k] * scale;
-        for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) A.W[(size_t)i * n + j] -= vi * s_vec[j];
+        T* wi = own<SM>(A, A.S2, i, n);
+        const T vi = (i == k) ? T(1) : wi[k] * scale;
+        for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) wi[j] -= vi * s_vec[j];
       }
     }
     __syncthreads();
     if (k == n - 1) break;
     // right reflector of row k (owner builds and publishes it)
-    T* pub_p = A.pub + 2 * n;
     if (k % NB == b) {
-      const T* wk = A.W + (size_t)k * n;
+      T* pw = pub_w<SM>(A) + 2 * n;
+      const T* wk = own<SM>(A, A.S2, k, n);
+      T* pk = own<SM>(A, A.S3, k, n);
       T s2 = 0;
       for (int j = k + 2 + threadIdx.x; j < n; j += blockDim.x) s2 += wk[j] * wk[j];
       s2 = block_sum(s2, red);
@@ -325,23 +413,24 @@ __device__ void bidiagonalize(const DenseArgs<T>& A, int NB, T* sv, T* red) {
       householder(wk[k + 1], s2, beta, taup, scp);
       for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
         T pj = (j == k + 1) ? T(1) : wk[j] * scp;
-        pub_p[j] = pj;
-        A.Pr[(size_t)k * n + j] = pj;
+        pw[j] = pj;
+        pk[j] = pj;
       }
-      for (int j = threadIdx.x; j <= k; j += blockDim.x) A.Pr[(size_t)k * n + j] = T(0);
+      for (int j = threadIdx.x; j <= k; j += blockDim.x) pk[j] = T(0);
       if (threadIdx.x == 0) {
-        pub_p[n] = taup;
+        pw[n] = taup;
         A.e[k] = beta;
         A.taup[k] = taup;
       }
     }
     csync();
-    const T taup = ldcg(pub_p + n);
-    for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) p_vec[j] = ldcg(pub_p + j);
+    const T* pp = pub_r<SM>(A, k % NB) + 2 * n;
+    const T taup = rd<SM>(pp + n);
+    for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) p_vec[j] = rd<SM>(pp + j);
     __syncthreads();
     if (taup != T(0)) {
       for (int i = first_own(b, NB, k + 1) + NB * w; i < n; i += NB * kWarps) {   // one warp per row
-        T* wi = A.W + (size_t)i * n;
+        T* wi = own<SM>(A, A.S2, i, n);
         T sdot = 0;
         for (int j = k + 1 + lane; j < n; j += 32) sdot += wi[j] * p_vec[j];
         sdot = warp_sum(sdot) * taup;
@@ -349,7 +438,7 @@ __device__ void bidiagonalize(const DenseArgs<T>& A, int NB, T* sv, T* red) {
       }
     }
     __syncthreads();
-    bidiag_partials(A, NB, k + 1);
+    bidiag_partials<SM>(A, k + 1);
     csync();
   }
   csync();
@@ -417,7 +506,6 @@ __device__ T gk_sigma(const T* d, const T* e, int n, int a, T gmax, T pivmin) {
   return T(0.5) * (lo + hi);
 }
 
-
 // One lane: LU with partial pivoting of the tridiagonal T - sigma I (size m),
 // storing reciprocal pivots for the solves.
 template <typename T>
@@ -475,11 +563,13 @@ __device__ void gk_solve(int m, const T* rdd, const T* du, const T* du2, const T
 // sqrt(eps) * bound form a cluster; one warp per cluster runs inverse
 // iteration on the Golub-Kahan tridiagonal, orthogonalising each member
 // against the earlier ones.
-template <typename T>
+template <bool SM, typename T>
 __device__ void bidiag_triplets(const DenseArgs<T>& A) {
   const int n = A.n, r = A.r, m = 2 * n;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int gw = blockIdx.x * kWarps + w, GW = gridDim.x * kWarps;
+  // consecutive values on different blocks: one warp per SM while r <= NB,
+  // so the per-value work does not share an SM's FP64 units
+  const int gw = w * gridDim.x + blockIdx.x, GW = gridDim.x * kWarps;
   const T gmax = gk_bound(A.d, A.e, n);
   const T pivmin = T(Eps<T>::tiny) * fmax(T(1), gmax * gmax);
   for (int a = gw; a < r; a += GW) {
@@ -491,15 +581,15 @@ __device__ void bidiag_triplets(const DenseArgs<T>& A) {
   const T pert = T(Eps<T>::v) * gmax;
   int c = 0;
   for (int a0 = 0; a0 < r; ++a0) {
-    if (a0 > 0 && ldcg(A.sig + a0) - ldcg(A.sig + a0 - 1) <= ortol) continue;
+    if (a0 > 0 && __ldcg(A.sig + a0) - __ldcg(A.sig + a0 - 1) <= ortol) continue;
     int a1 = a0 + 1;
-    while (a1 < r && ldcg(A.sig + a1) - ldcg(A.sig + a1 - 1) <= ortol) ++a1;
+    while (a1 < r && __ldcg(A.sig + a1) - __ldcg(A.sig + a1 - 1) <= ortol) ++a1;
     if (c++ % GW != gw) continue;
     for (int a = a0; a < a1; ++a) {
       T* base = A.z + (size_t)a * 6 * m;
       T *dd = base, *du = base + m, *du2 = base + 2 * m, *dl = base + 3 * m, *pv = base + 4 * m;
       T* zv = base + 5 * m;
-      if (lane == 0) gk_factor(A.d, A.e, m, ldcg(A.sig + a), pert, dd, du, du2, dl, pv);
+      if (lane == 0) gk_factor(A.d, A.e, m, __ldcg(A.sig + a), pert, dd, du, du2, dl, pv);
       for (int k = lane; k < m; k += 32)
         zv[k] = T(1) + T(0.5) * T((unsigned)(k * 2654435761u) % 1000u) / T(1000) + T(a);
       __syncwarp();
@@ -533,13 +623,13 @@ __device__ void bidiag_triplets(const DenseArgs<T>& A) {
   for (int a = gw; a < r; a += GW) {              // v~ = P_B v_D, last reflector first
     T* y = A.vb + (size_t)a * n;
     for (int k = n - 2; k >= 0; --k) {
-      const T tau = ldcg(A.taup + k);
+      const T tau = __ldcg(A.taup + k);
       if (tau == T(0)) continue;
-      const T* p = A.Pr + (size_t)k * n;
+      const T* p = any<SM>(A, A.S3, k, n);
       T s = 0;
-      for (int j = k + 1 + lane; j < n; j += 32) s += ldcg(p + j) * y[j];
+      for (int j = k + 1 + lane; j < n; j += 32) s += rd<SM>(p + j) * y[j];
       s = warp_sum(s) * tau;
-      for (int j = k + 1 + lane; j < n; j += 32) y[j] -= s * ldcg(p + j);
+      for (int j = k + 1 + lane; j < n; j += 32) y[j] -= s * rd<SM>(p + j);
       __syncwarp();
     }
   }
@@ -552,31 +642,37 @@ __device__ void bidiag_triplets(const DenseArgs<T>& A) {
 // |v_i| positive (lowest index on ties).  For a zero singular value (below
 // n * eps * bound) u = 1 / sqrt(1^T M 1) and v normalised in the 2-norm is the
 // right null vector w of B.
-template <typename T>
-__device__ void triplets(const DenseArgs<T>& A, int NB, T* sv, T* red) {
-  const int n = A.n, r = A.r, r2 = 2 * r, b = blockIdx.x;
-  const int stride = n + 2 * kMaxR + 2;
-  T* part = A.part + (size_t)b * stride;
+template <bool SM, typename T>
+__device__ void triplets(const DenseArgs<T>& A, T* sv, T* red) {
+  const int n = A.n, r = A.r, r2 = 2 * r, NB = nblocks<SM>(A), b = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  T* part = part_w<SM>(A);
   const T gmax = gk_bound(A.d, A.e, n);
   const T null_tol = T(n * Eps<T>::v) * gmax;
-  for (int i = b; i < n; i += NB)
-    for (int c = threadIdx.x; c < r2; c += blockDim.x) {
-      T val;
-      if (c < r) {
-        val = ldcg(A.vb + (size_t)c * n + i);
-      } else {
-        const T* va = A.vb + (size_t)(c - r) * n;
-        const T* ci = A.C + (size_t)i * n;
-        T acc = 0;
-        for (int j = 0; j < n; ++j) acc += ci[j] * ldcg(va + j);
-        val = acc;
-      }
-      A.R[(size_t)i * r2 + c] = val;
+  for (int i = b; i < n; i += NB) {
+    T* ri = own<SM>(A, A.R, i, r2);
+    for (int c = threadIdx.x; c < r; c += blockDim.x) ri[c] = __ldcg(A.vb + (size_t)c * n + i);
+  }
+  {
+    // C v~_a for the own rows: one warp per (row, value) pair
+    const int npair = ((n - b + NB - 1) / NB) * r;
+    for (int q = w; q < npair; q += kWarps) {
+      const int i = b + (q / r) * NB, a = q % r;
+      const T* ci = own<SM>(A, A.S1, i, n);
+      const T* va = A.vb + (size_t)a * n;
+      T acc = 0;
+      for (int j = lane; j < n; j += 32) acc += ci[j] * __ldcg(va + j);
+      acc = warp_sum(acc);
+      if (lane == 0) own<SM>(A, A.R, i, r2)[r + a] = acc;
     }
+  }
   __syncthreads();
   for (int a = threadIdx.x; a < r; a += blockDim.x) {
     T s = 0;
-    for (int i = b; i < n; i += NB) s += A.R[(size_t)i * r2 + r + a] * A.R[(size_t)i * r2 + r + a];
+    for (int i = b; i < n; i += NB) {
+      const T x = own<SM>(A, A.R, i, r2)[r + a];
+      s += x * x;
+    }
     part[a] = s;
   }
   {
@@ -588,20 +684,21 @@ __device__ void triplets(const DenseArgs<T>& A, int NB, T* sv, T* red) {
   }
   csync();
   for (int a = threadIdx.x; a < r; a += blockDim.x) {
-    T s = 0;
-    for (int q = 0; q < NB; ++q) s += ldcg(A.part + (size_t)q * stride + a);
+    T s = part_sum<SM>(A, a);
     sv[a] = s > T(0) ? T(1) / sqrt(s) : T(0);
   }
   __syncthreads();
-  for (int i = b; i < n; i += NB)
-    for (int a = threadIdx.x; a < r; a += blockDim.x) A.R[(size_t)i * r2 + r + a] *= sv[a];
+  for (int i = b; i < n; i += NB) {
+    T* ri = own<SM>(A, A.R, i, r2);
+    for (int a = threadIdx.x; a < r; a += blockDim.x) ri[r + a] *= sv[a];
+  }
   __syncthreads();
-  row_solve<T, false>(A, NB, A.LN, A.LM, r, A.R, r2, r2, sv);
+  row_solve<SM, false>(A, A.LN, A.LM, r, A.R, r2, r2, sv);
   // sign candidates per value and the norm of v_0
   for (int a = threadIdx.x; a < r; a += blockDim.x) {
     T best = -1, bi = T(n), s0 = 0;
     for (int i = b; i < n; i += NB) {
-      T v = A.R[(size_t)i * r2 + a];
+      T v = own<SM>(A, A.R, i, r2)[a];
       if (fabs(v) > best) { best = fabs(v); bi = T(i); }
       if (a == 0) s0 += v * v;
     }
@@ -613,38 +710,38 @@ __device__ void triplets(const DenseArgs<T>& A, int NB, T* sv, T* red) {
   T* sgn = sv;          // r signs
   T* uconst = sv + r;   // 1 / sqrt(1^T M 1) and 1/||v_0||
   for (int a = threadIdx.x; a < r; a += blockDim.x) {
-    T best = -1, bi = T(n);
-    for (int q = 0; q < NB; ++q) {
-      T v = ldcg(A.part + (size_t)q * stride + n + 2 * a);
-      T ix = ldcg(A.part + (size_t)q * stride + n + 2 * a + 1);
-      if (v > best || (v == best && ix < bi)) { best = v; bi = ix; }
+    T vals[kMaxNB], idx[kMaxNB];
+#pragma unroll
+    for (int q = 0; q < kMaxNB; ++q) {
+      vals[q] = q < NB ? rd<SM>(part_r<SM>(A, q) + n + 2 * a) : T(-2);
+      idx[q] = q < NB ? rd<SM>(part_r<SM>(A, q) + n + 2 * a + 1) : T(n);
     }
-    T vv = A.R[(size_t)(int)bi * r2 + a];  // read through L2: row bi may belong to another block
-    vv = ldcg(A.R + (size_t)(int)bi * r2 + a);
+    T best = -1, bi = T(n);
+#pragma unroll
+    for (int q = 0; q < kMaxNB; ++q)
+      if (vals[q] > best || (vals[q] == best && idx[q] < bi)) { best = vals[q]; bi = idx[q]; }
+    const T vv = rd<SM>(any<SM>(A, A.R, (int)bi, r2) + a);
     sgn[a] = vv < T(0) ? T(-1) : T(1);
   }
   if (threadIdx.x == 0) {
-    T s1 = 0, s0 = 0;
-    for (int q = 0; q < NB; ++q) {
-      s1 += ldcg(A.part + (size_t)q * stride + n + r2 + 1);
-      s0 += ldcg(A.part + (size_t)q * stride + n + r2);
-    }
+    const T s1 = part_sum<SM>(A, n + r2 + 1);
+    const T s0 = part_sum<SM>(A, n + r2);
     uconst[0] = T(1) / sqrt(s1);
     uconst[1] = s0 > T(0) ? T(1) / sqrt(s0) : T(0);
   }
   __syncthreads();
-  const bool null0 = ldcg(A.sig) <= null_tol;
+  const bool null0 = __ldcg(A.sig) <= null_tol;
   for (int i = b; i < n; i += NB) {
+    const T* ri = own<SM>(A, A.R, i, r2);
     for (int a = threadIdx.x; a < r; a += blockDim.x) {
-      const bool is_null = ldcg(A.sig + a) <= null_tol;
-      T v = sgn[a] * A.R[(size_t)i * r2 + a];
-      A.V[(size_t)i * r + a] = double(v);
-      A.U[(size_t)i * r + a] = double(is_null ? uconst[0] : sgn[a] * A.R[(size_t)i * r2 + r + a]);
+      const bool is_null = __ldcg(A.sig + a) <= null_tol;
+      A.V[(size_t)i * r + a] = double(sgn[a] * ri[a]);
+      A.U[(size_t)i * r + a] = double(is_null ? uconst[0] : sgn[a] * ri[r + a]);
     }
-    if (threadIdx.x == 0) A.unull[i] = null0 ? sgn[0] * A.R[(size_t)i * r2] * uconst[1] : T(0);
+    if (threadIdx.x == 0) A.unull[i] = null0 ? sgn[0] * ri[0] * uconst[1] : T(0);
   }
   if (b == 0)
-    for (int a = threadIdx.x; a < r; a += blockDim.x) A.sigma[a] = double(ldcg(A.sig + a));
+    for (int a = threadIdx.x; a < r; a += blockDim.x) A.sigma[a] = double(__ldcg(A.sig + a));
   csync();
 }
 
@@ -652,16 +749,17 @@ __device__ void triplets(const DenseArgs<T>& A, int NB, T* sv, T* red) {
 // B^+ = (B + e w^T)^{-1} - w e^T by Gauss-Jordan on [B + e w^T | I] with
 // partial pivoting and no row exchanges: the row chosen for column k keeps
 // its place and records k; at the end row i holds row pcol[i] of the inverse.
-template <typename T>
-__device__ void gj_candidate(const DenseArgs<T>& A, int NB, int k, T* red) {
-  const int n = A.n, n2 = 2 * n, b = blockIdx.x;
+// The tableau G (2n per row) occupies the storage of S2 and S3.
+template <bool SM, typename T>
+__device__ void gj_candidate(const DenseArgs<T>& A, int k) {
+  const int n = A.n, n2 = 2 * n, NB = nblocks<SM>(A), b = blockIdx.x;
   __shared__ T cv[kWarps];
   __shared__ int ci[kWarps];
   T best = -1;
   int bi = n;
   for (int i = b + NB * threadIdx.x; i < n; i += NB * blockDim.x) {
-    if (A.pcol[i] >= 0) continue;
-    T v = fabs(A.G[(size_t)i * n2 + k]);
+    if (*own_pcol<SM>(A, i) >= 0) continue;
+    T v = fabs(own<SM>(A, A.S2, i, n2)[k]);
     if (v > best) { best = v; bi = i; }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -675,57 +773,66 @@ __device__ void gj_candidate(const DenseArgs<T>& A, int NB, int k, T* red) {
   if (threadIdx.x == 0) {
     for (int q = 1; q < kWarps; ++q)
       if (cv[q] > best || (cv[q] == best && ci[q] < bi)) { best = cv[q]; bi = ci[q]; }
-    A.cval[b] = best;
-    A.cidx[b] = bi;
+    T* part = part_w<SM>(A);
+    part[n + 2 * kMaxR + 2] = best;
+    part[n + 2 * kMaxR + 3] = T(bi);
   }
-  (void)red;
 }
 
-template <typename T>
-__device__ void pseudo_inverse(const DenseArgs<T>& A, int NB, T* sv, T* red) {
-  const int n = A.n, n2 = 2 * n, b = blockIdx.x;
+template <bool SM, typename T>
+__device__ void pseudo_inverse(const DenseArgs<T>& A, T* sv) {
+  const int n = A.n, n2 = 2 * n, NB = nblocks<SM>(A), b = blockIdx.x;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const T e = T(1) / sqrt(T(n));
+  T* G = A.S2;
   for (int i = b; i < n; i += NB) {
+    T* gi = own<SM>(A, G, i, n2);
     for (int j = threadIdx.x; j < n2; j += blockDim.x)
-      A.G[(size_t)i * n2 + j] = j < n ? T(A.B[(size_t)i * n + j]) + e * ldcg(A.unull + j) : (j - n == i ? T(1) : T(0));
-    if (threadIdx.x == 0) A.pcol[i] = -1;
+      gi[j] = j < n ? T(A.B[(size_t)i * n + j]) + e * __ldcg(A.unull + j) : (j - n == i ? T(1) : T(0));
+    if (threadIdx.x == 0) *own_pcol<SM>(A, i) = -1;
   }
   __syncthreads();
-  gj_candidate(A, NB, 0, red);
+  gj_candidate<SM>(A, 0);
   csync();
   __shared__ int sp;
   T* prow = sv;
   for (int k = 0; k < n; ++k) {
-    if (threadIdx.x == 0) {
+    if (w == 0) {                               // best candidate over the blocks
       T best = -1;
       int bi = n;
-      for (int q = 0; q < NB; ++q) {
-        T v = ldcg(A.cval + q);
-        int ix = __ldcg(A.cidx + q);
-        if (v > best || (v == best && ix < bi)) { best = v; bi = ix; }
+      if (lane < NB) {
+        const T* pq = part_r<SM>(A, lane);
+        best = rd<SM>(pq + n + 2 * kMaxR + 2);
+        bi = (int)rd<SM>(pq + n + 2 * kMaxR + 3);
       }
-      sp = bi;
+      for (int o = 16; o > 0; o >>= 1) {
+        T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) sp = bi;
     }
     __syncthreads();
     const int p = sp;
     if (p % NB == b) {                          // normalise and publish the pivot row
-      T* gp = A.G + (size_t)p * n2;
+      T* gp = own<SM>(A, G, p, n2);
+      T* pw = pub_w<SM>(A);
       const T inv = T(1) / gp[k];
       __syncthreads();
       for (int j = k + threadIdx.x; j < n2; j += blockDim.x) {
         T v = gp[j] * inv;
         gp[j] = v;
-        A.pub[j] = v;
+        pw[j] = v;
       }
-      if (threadIdx.x == 0) A.pcol[p] = k;
+      if (threadIdx.x == 0) *own_pcol<SM>(A, p) = k;
     }
     csync();
-    for (int j = k + threadIdx.x; j < n2; j += blockDim.x) prow[j] = ldcg(A.pub + j);
+    const T* pr = pub_r<SM>(A, p % NB);
+    for (int j = k + threadIdx.x; j < n2; j += blockDim.x) prow[j] = rd<SM>(pr + j);
     __syncthreads();
     for (int i = b + NB * w; i < n; i += NB * kWarps) {   // one warp per own row
       if (i == p) continue;
-      T* gi = A.G + (size_t)i * n2;
+      T* gi = own<SM>(A, G, i, n2);
       const T f = gi[k];
       __syncwarp();
       if (f != T(0))
@@ -733,36 +840,57 @@ __device__ void pseudo_inverse(const DenseArgs<T>& A, int NB, T* sv, T* red) {
       __syncwarp();
     }
     __syncthreads();
-    if (k + 1 < n) gj_candidate(A, NB, k + 1, red);
+    if (k + 1 < n) gj_candidate<SM>(A, k + 1);
     csync();
   }
   for (int i = b; i < n; i += NB) {
-    const int c = A.pcol[i];
+    const int c = *own_pcol<SM>(A, i);
+    const T* gi = own<SM>(A, G, i, n2);
     for (int j = threadIdx.x; j < n; j += blockDim.x)
-      A.Bpinv[(size_t)c * n + j] = double(A.G[(size_t)i * n2 + n + j] - ldcg(A.unull + c) * e);
+      A.Bpinv[(size_t)c * n + j] = double(gi[n + j] - __ldcg(A.unull + c) * e);
   }
 }
 
-template <typename T>
+// Shared-policy layout of one block's dynamic shared memory, in elements of
+// T after the 2n scratch vector: pub, part, LM, LN, S1, S2, S3, R, then pcol.
+__host__ __device__ inline size_t smem_elems(int n, int r, int RP) {
+  return (size_t)2 * n + (size_t)8 * n + 64 + part_stride(n) + (size_t)5 * RP * n + (size_t)RP * 2 * r;
+}
+
+template <typename T, bool SM>
 __global__ void __launch_bounds__(kDenseThreads, 1) coarsest_kernel(DenseArgs<T> A) {
-  extern __shared__ unsigned char dyn[];
+  extern __shared__ __align__(16) unsigned char dyn[];
   T* sv = reinterpret_cast<T*>(dyn);
   __shared__ T red[kWarps];
-  const int NB = gridDim.x;
+  const int n = A.n;
+  A.NB = gridDim.x;
+  if constexpr (SM) {
+    T* p = sv + 2 * n;
+    A.pub = p;  p += 8 * n + 64;
+    A.part = p; p += part_stride(n);
+    A.LM = p;   p += (size_t)A.RP * n;
+    A.LN = p;   p += (size_t)A.RP * n;
+    A.S1 = p;   p += (size_t)A.RP * n;
+    A.S2 = p;   p += (size_t)A.RP * n;
+    A.S3 = p;   p += (size_t)A.RP * n;
+    A.R = p;    p += (size_t)A.RP * 2 * A.r;
+    A.pcol = reinterpret_cast<int*>(p);
+  }
   const bool b0 = blockIdx.x == 0 && threadIdx.x == 0;
   if (b0) A.ctl->tp[0] = gtimer();
-  if (!cholesky_rows(A, NB, sv)) return;
+  if (!cholesky_rows<SM>(A, sv)) return;
   if (b0) A.ctl->tp[1] = gtimer();
-  form_C(A, NB, sv);
+  form_C<SM>(A, sv);
   if (b0) A.ctl->tp[2] = gtimer();
-  bidiagonalize(A, NB, sv, red);
+  bidiagonalize<SM>(A, sv, red);
   if (b0) A.ctl->tp[3] = gtimer();
-  bidiag_triplets(A);
+  bidiag_triplets<SM>(A);
   if (b0) A.ctl->tp[4] = gtimer();
-  triplets(A, NB, sv, red);
+  triplets<SM>(A, sv, red);
   if (b0) A.ctl->tp[5] = gtimer();
-  if (A.Bpinv) pseudo_inverse(A, NB, sv, red);
+  if (A.Bpinv) pseudo_inverse<SM>(A, sv);
   if (b0) A.ctl->tp[6] = gtimer();
+  csync();   // no block leaves while another may still read its shared memory
 }
 
 __global__ void csr_to_dense_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
@@ -777,24 +905,67 @@ bamg_status csr_to_dense(int n, const int32_t* rp, const int32_t* ci, const doub
   return launch(csr_to_dense_kernel, dim3(n), dim3(64), 0, s, n, rp, ci, va, D);
 }
 
+template <typename T> struct SmemAttr { static std::atomic<uint64_t> done; };
+template <typename T> std::atomic<uint64_t> SmemAttr<T>::done{0};
+
+static int max_cluster(const void* kern, cudaLaunchConfig_t cfg, int want) {
+  int maxc = 0;
+  cfg.gridDim = dim3(want);
+  cfg.numAttrs = 0;
+  if (cudaOccupancyMaxPotentialClusterSize(&maxc, kern, &cfg) != cudaSuccess) maxc = 0;
+  cudaGetLastError();
+  return maxc < want ? maxc : want;
+}
+
 template <typename T>
 static bamg_status coarsest_t(int n, int r, const double* B, const double* M, const double* N, double* sigma,
                               double* U, double* V, double* Bpinv, cudaStream_t s) {
-  DevMem lm, ln, x, c, w, pr, g, rr, pub, part, cv, ci, pc, de, sg, vb, z, un, ctl;
-  size_t nn = (size_t)n * n;
-  BAMG_TRY(lm.alloc(sizeof(T) * nn, s));
-  BAMG_TRY(ln.alloc(sizeof(T) * nn, s));
-  BAMG_TRY(x.alloc(sizeof(T) * nn, s));
-  BAMG_TRY(c.alloc(sizeof(T) * nn, s));
-  BAMG_TRY(w.alloc(sizeof(T) * nn, s));
-  BAMG_TRY(pr.alloc(sizeof(T) * nn, s));
-  BAMG_TRY(g.alloc(Bpinv ? sizeof(T) * 2 * nn : 16, s));
-  BAMG_TRY(rr.alloc(sizeof(T) * (size_t)n * 2 * r, s));
-  BAMG_TRY(pub.alloc(sizeof(T) * 8 * (size_t)n + 64, s));
-  BAMG_TRY(part.alloc(sizeof(T) * kMaxNB * (size_t)(n + 2 * kMaxR + 2), s));
-  BAMG_TRY(cv.alloc(sizeof(T) * kMaxNB, s));
-  BAMG_TRY(ci.alloc(sizeof(int) * kMaxNB, s));
-  BAMG_TRY(pc.alloc(sizeof(int) * n, s));
+  DenseArgs<T> a = {};
+  a.n = n; a.r = r; a.B = B; a.M = M; a.N = N;
+  a.sigma = sigma; a.U = U; a.V = V; a.Bpinv = Bpinv;
+  // policy: own rows in shared memory when a 16-block cluster holds them
+  auto ksm = coarsest_kernel<T, true>;
+  auto kgl = coarsest_kernel<T, false>;
+  int max_dyn = 0;
+  BAMG_TRY(allow_max_smem((const void*)ksm, SmemAttr<T>::done, &max_dyn));
+  BAMG_CUDA(cudaFuncSetAttribute(ksm, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  BAMG_CUDA(cudaFuncSetAttribute(kgl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(kDenseThreads);
+  cfg.stream = s;
+  const int rp16 = (n + kMaxNB - 1) / kMaxNB;
+  const size_t smem16 = sizeof(T) * smem_elems(n, r, rp16) + sizeof(int) * rp16;
+  bool use_sm = false;
+  int csize = 0;
+  if (smem16 <= (size_t)max_dyn) {
+    cfg.dynamicSmemBytes = smem16;
+    csize = max_cluster((const void*)ksm, cfg, kMaxNB);
+    use_sm = csize == kMaxNB;
+  }
+  DevMem big, de, sg, vb, z, un, ctl, glob;
+  if (use_sm) {
+    a.RP = rp16;
+  } else {
+    // global policy: full matrices in device memory
+    size_t nn = (size_t)n * n;
+    size_t elems = 5 * nn + (size_t)n * 2 * r + 8 * (size_t)n + 64 + kMaxNB * (size_t)part_stride(n);
+    BAMG_TRY(big.alloc(sizeof(T) * elems, s));
+    BAMG_TRY(glob.alloc(sizeof(int) * n, s));
+    T* p = big.as<T>();
+    a.LM = p; p += nn;
+    a.LN = p; p += nn;
+    a.S1 = p; p += nn;
+    a.S2 = p; p += nn;
+    a.S3 = p; p += nn;
+    a.R = p; p += (size_t)n * 2 * r;
+    a.pub = p; p += 8 * (size_t)n + 64;
+    a.part = p;
+    a.pcol = glob.as<int>();
+    cfg.dynamicSmemBytes = sizeof(T) * 2 * (size_t)n + 64;
+    csize = max_cluster((const void*)kgl, cfg, kMaxNB);
+    if (csize < 1) csize = 1;
+    a.RP = (n + csize - 1) / csize;
+  }
   BAMG_TRY(de.alloc(sizeof(T) * 3 * n, s));
   BAMG_TRY(sg.alloc(sizeof(T) * r, s));
   BAMG_TRY(vb.alloc(sizeof(T) * (size_t)r * n, s));
@@ -804,34 +975,10 @@ static bamg_status coarsest_t(int n, int r, const double* B, const double* M, co
   BAMG_CUDA(cudaMemsetAsync(ctl.p, 0, sizeof(DenseCtl), s));
   BAMG_CUDA(cudaMemsetAsync(un.p, 0, sizeof(T) * n, s));
   BAMG_CUDA(cudaMemsetAsync(de.p, 0, sizeof(T) * 3 * n, s));
-  DenseArgs<T> a;
-  a.n = n; a.r = r; a.B = B; a.M = M; a.N = N;
-  a.sigma = sigma; a.U = U; a.V = V; a.Bpinv = Bpinv;
-  a.LM = lm.as<T>(); a.LN = ln.as<T>(); a.X = x.as<T>(); a.C = c.as<T>(); a.W = w.as<T>(); a.Pr = pr.as<T>();
-  a.G = g.as<T>(); a.R = rr.as<T>(); a.pub = pub.as<T>(); a.part = part.as<T>();
-  a.cval = cv.as<T>(); a.cidx = ci.as<int>(); a.pcol = pc.as<int>();
   a.d = de.as<T>(); a.e = a.d + n; a.taup = a.e + n;
   a.sig = sg.as<T>(); a.vb = vb.as<T>(); a.z = z.as<T>(); a.unull = un.as<T>(); a.ctl = ctl.as<DenseCtl>();
-  // at most 2 * 1024 doubles: below the default dynamic shared memory limit,
-  // so no per-call attribute (a per-function setting would race between
-  // threads that set up different chains concurrently)
-  size_t smem = sizeof(T) * 2 * (size_t)n + 64;
-  auto kern = coarsest_kernel<T>;
-  BAMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-  cudaLaunchConfig_t cfg = {};
+  a.NB = csize;
   cudaLaunchAttribute attr[1];
-  cfg.blockDim = dim3(kDenseThreads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cfg.gridDim = dim3(kMaxNB);
-  int csize = 8;
-  {
-    int maxc = 0;
-    cfg.numAttrs = 0;
-    if (cudaOccupancyMaxPotentialClusterSize(&maxc, (void*)kern, &cfg) == cudaSuccess && maxc >= 1)
-      csize = maxc < kMaxNB ? maxc : kMaxNB;
-    cudaGetLastError();
-  }
   cfg.gridDim = dim3(csize);
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = csize;
@@ -839,14 +986,17 @@ static bamg_status coarsest_t(int n, int r, const double* B, const double* M, co
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  BAMG_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
+  if (use_sm) BAMG_CUDA(cudaLaunchKernelEx(&cfg, ksm, a));
+  else BAMG_CUDA(cudaLaunchKernelEx(&cfg, kgl, a));
   g_launches.fetch_add(1, std::memory_order_relaxed);
+  ++t_launches;
   DenseCtl h;
   BAMG_CUDA(cudaMemcpyAsync(&h, ctl.p, sizeof(DenseCtl), cudaMemcpyDeviceToHost, s));
   BAMG_CUDA(cudaStreamSynchronize(s));
   if (std::getenv("BAMG_TRACE")) {
     const char* nm[6] = {"cholesky", "form_C", "bidiag", "bidiag_svd", "triplets", "pinv"};
-    fprintf(stderr, "[bamg] coarsest n=%d prec=%s cluster=%d:", n, sizeof(T) == 4 ? "f32" : "f64", csize);
+    fprintf(stderr, "[bamg] coarsest n=%d prec=%s cluster=%d %s:", n, sizeof(T) == 4 ? "f32" : "f64", csize,
+            use_sm ? "smem" : "global");
     for (int k = 0; k < 6; ++k)
       if (h.tp[k + 1] >= h.tp[k] && h.tp[k + 1]) fprintf(stderr, " %s=%.1fus", nm[k], (h.tp[k + 1] - h.tp[k]) / 1e3);
     fprintf(stderr, "\n");

@@ -323,4 +323,22 @@ bamg_status check_stochastic(int n, const int32_t* rp, const int32_t* ci, const 
   return BAMG_OK;
 }
 
+bamg_status allow_max_smem(const void* fn, std::atomic<uint64_t>& done, int* max_dyn) {
+  int dev = 0, optin = 0;
+  BAMG_CUDA(cudaGetDevice(&dev));
+  BAMG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa;
+  BAMG_CUDA(cudaFuncGetAttributes(&fa, fn));
+  const int avail = optin - (int)fa.sharedSizeBytes;
+  *max_dyn = avail;
+  const uint64_t bit = 1ull << (dev & 63);
+  if (done.load() & bit) return BAMG_OK;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.load() & bit) return BAMG_OK;
+  BAMG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, avail));
+  done.fetch_or(bit);
+  return BAMG_OK;
+}
+
 }  // namespace bamg

@@ -295,10 +295,12 @@ def _coarse_problem(n_side=12):
     return L.B.toarray(), L.M.toarray(), L.N.toarray()
 
 
+# sizes: 144 (own rows in shared memory), 289 (FP64 rows in global memory),
+# 441 (both precisions in global memory), 9 (fewer rows than cluster blocks)
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_coarsest_triplets_and_pinv(api, prec):
-    Bd, Md, Nd = _coarse_problem(12)
-    r = 8
+@pytest.mark.parametrize("side,r", [(12, 8), (17, 16), (21, 8), (3, 8)])
+def test_coarsest_triplets_and_pinv(api, prec, side, r):
+    Bd, Md, Nd = _coarse_problem(side)
     sig, U, V, Pinv = api.bamg_step_coarsest(Bd, Md, Nd, r, prec=prec)
     sig, U, V, Pinv = (t.cpu().numpy() for t in (sig, U, V, Pinv))
     so, Uo, Vo = coarsest.generalized_triplets(Bd, Md, Nd, r)
@@ -317,8 +319,9 @@ def test_coarsest_triplets_and_pinv(api, prec):
     else:
         assert np.allclose(sig[1:], so[1:], rtol=1e-3)
         assert np.abs(Pinv - Xo).max() <= 1e-2 * np.abs(Xo).max()
-    # residuals of the generalized singular equations (any precision)
-    tol = 1e-11 if prec == "fp64" else 1e-4
+    # residuals of the generalized singular equations (any precision); the
+    # FP32 rounding error of the factorizations grows about linearly with n
+    tol = 1e-11 if prec == "fp64" else max(1e-4, 1e-6 * Bd.shape[0])
     for k in range(r):
         assert np.linalg.norm(Bd @ V[:, k] - sig[k] * Md @ U[:, k]) <= tol * scale
         assert np.linalg.norm(Bd.T @ U[:, k] - sig[k] * Nd @ V[:, k]) <= tol * scale
