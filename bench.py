@@ -8,7 +8,17 @@ tandem queueing network with 65,536 states (arrival 10/31, service 11/31 and
 mixed-precision path (FP32 V-cycle and setup relaxation inside FP64 GMRES);
 the plain FP64 GPU path is timed beside it on the same chain.
 
+Beside the headline line the same JSON object reports, on the same GPU:
+  roofline          the dominant kernel of a step (coarsest-level solver),
+                    timed live with CUDA events
+  roofline_sparse   the finest-level block relaxation on a 2048 x 2048
+                    tandem queue (4.2M states, inputs far above L2) vs HBM
+  learned           network fits vs LS fits on the 2048 x 2048 tandem queue
+  batched           256 seeded chains of 1k-65k states, batched vs a loop
+  delaunay          random walk on the Delaunay graph of 2^20 points (MIS)
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--sections all|none|learned,batched,...] [--no-cpu-baseline]
 
 Prints one JSON line.  With --impl reference the CPU oracle is timed on the
 host cores instead (the reference arm of the comparison).
@@ -34,6 +44,8 @@ WORKLOAD = {"workload": "tandem queue 256x256 (65,536 states, nnz(B)=261,121), r
             "setup_relaxations": 5}
 SIDE = 256
 KW = dict(r=16, max_levels=5, coarse_min=1, seed=2)
+SECTIONS = ("learned", "batched", "delaunay", "sparse")
+FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (4 partitions x 32)
 
 
 def env_int(name, default):
@@ -41,6 +53,16 @@ def env_int(name, default):
         return int(os.environ.get(name, default))
     except ValueError:
         return default
+
+
+def load_peaks():
+    """HBM GB/s from MEASURED_PEAKS.json (else the fallback figure)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+        return float(peaks["hbm_gbs"]), "measured", peaks
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback", {}
 
 
 # ---------------------------------------------------------------- clocks
@@ -93,9 +115,25 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-# ---------------------------------------------------------------- GPU arm
+def event_ms(torch, stream, fn, reps=1):
+    """Mean CUDA-event time of fn() on `stream` over reps calls (ms)."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = None
+    for _ in range(reps):
+        out = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps, out
+
+
+def chain_tensors(torch, ch):
+    return tuple(torch.from_numpy(a).cuda() for a in (ch.row_ptr, ch.col, ch.val))
+
+
+# ---------------------------------------------------------------- headline
 def gpu_arm(args, rank: int, world: int):
-    import numpy as np
     import torch
 
     import chaingen as cg
@@ -107,9 +145,7 @@ def gpu_arm(args, rank: int, world: int):
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream()
     ch = cg.tandem(SIDE)
-    rp = torch.from_numpy(ch.row_ptr).cuda()
-    ci = torch.from_numpy(ch.col).cuda()
-    va = torch.from_numpy(ch.val).cuda()
+    rp, ci, va = chain_tensors(torch, ch)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def one_step(prec):
@@ -118,7 +154,7 @@ def gpu_arm(args, rank: int, world: int):
         x, info = api.bamg_solve(h, restart=20, tol=1e-10, stream=stream)
         return h, x, info
 
-    def timed(prec, steps, warmup, count_launches=False):
+    def timed(prec, steps, warmup):
         times, infos = [], []
         with torch.cuda.stream(stream):
             for _ in range(warmup):
@@ -130,13 +166,9 @@ def gpu_arm(args, rank: int, world: int):
             l0 = api.launch_count()
             for _ in range(steps):
                 flush.fill_(1.0)                     # evict the 129 MB L2 between steps
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                h, x, info = one_step(prec)
-                e1.record(stream)
-                e1.synchronize()
-                times.append(e0.elapsed_time(e1))
+                torch.cuda.synchronize()
+                ms, (h, x, info) = event_ms(torch, stream, lambda: one_step(prec))
+                times.append(ms)
                 infos.append(info)
                 last = (h, x)
             torch.cuda.synchronize()
@@ -144,8 +176,8 @@ def gpu_arm(args, rank: int, world: int):
         return times, infos, last, launches
 
     with ClockSampler(dev) as clk:
-        t_mix, i_mix, (h_mix, x_mix), launches = timed("mixed", args.steps, args.warmup, True)
-    t_64, i_64, (h_64, x_64), _ = timed("fp64", max(3, args.steps // 2), 2)
+        t_mix, i_mix, (h_mix, x_mix), launches = timed("mixed", args.steps, args.warmup)
+    t_64, i_64, (h_64, x_64), _ = timed("fp64", max(3, args.steps // 2), 3)
 
     ms = statistics.mean(t_mix)
     if world > 1:
@@ -167,65 +199,282 @@ def gpu_arm(args, rank: int, world: int):
                                         stream=stream)
             if k:
                 e2e.append((time.perf_counter() - t0) * 1e3)
-    h2d = hrp.nbytes + hci.nbytes + hva.nbytes
-    d2h = xh.nbytes
-
-    roof = roofline(api, torch, np, ch, stream, h_mix)
-    return {
+    out = {
         "ms": ms, "t_mix": t_mix, "i_mix": i_mix, "t_64": t_64, "i_64": i_64, "launches": launches,
         "clocks": clk.summary(), "err_vs_fp64": err_vs_fp64, "e2e_ms": statistics.mean(e2e),
-        "h2d": h2d, "d2h": d2h, "roofline": roof,
+        "h2d": hrp.nbytes + hci.nbytes + hva.nbytes, "d2h": xh.nbytes,
+        "roofline": roofline_coarsest(api, torch, stream, h_mix),
     }
+    h_mix.destroy()
+    h_64.destroy()
+    for name, fn in (("sparse", roofline_sparse), ("learned", learned_section),
+                     ("batched", batched_section), ("delaunay", delaunay_section)):
+        if name in args.sections:
+            try:
+                out[name] = fn(api, torch, stream)
+            except Exception as exc:          # a section failure must not lose the headline
+                out[name] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+    return out
 
 
-def roofline(api, torch, np, ch, stream, h):
-    """Live CUDA-event timing of the dominant kernel on the bench's data.
+# ---------------------------------------------------------------- rooflines
+def _dense(torch, lv_csr, n):
+    rp, col, val = lv_csr["row_ptr"].long(), lv_csr["col"].long(), lv_csr["val"]
+    rows = torch.repeat_interleave(torch.arange(n, device="cuda"), rp[1:] - rp[:-1])
+    D = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    D[rows, col] = val
+    return D
 
-    The dominant kernel of a step (by the ncu launch list) is the cooperative
-    coarsest-level solver; it is latency bound.  Its figure is reported
-    against the FP32 ALU peak; the finest-level block relaxation (the hot
-    sparse kernel) is timed too and reported against the HBM peak.
-    """
-    peaks = {}
+
+def _max_sm_mhz():
     try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-        hbm, src = float(peaks["hbm_gbs"]), "measured"
-    except (OSError, KeyError, ValueError):
-        hbm, src = 6800.0, "fallback"
-    # finest-level FP32 block relaxation: n x 16 block, B of the tandem chain
-    lev = h.level(0)
-    B = lev["B"]
-    n, ld = ch.n, 16
-    rp, ci = B["row_ptr"], B["col"]
-    va = B["val"].float()
-    d = torch.zeros(n, dtype=torch.float64, device="cuda")
-    rows = torch.repeat_interleave(torch.arange(n, device="cuda"), (rp[1:] - rp[:-1]).long())
-    diag = (B["col"].long() == rows)
-    d[rows[diag]] = B["val"][diag]
-    dinv = (1.0 / d).float()
-    X = torch.rand((n, ld), device="cuda", dtype=torch.float32)
-    nb = 64   # > L2 in total: cycle through distinct X/Y pairs
-    Xs = [torch.rand((n, ld), device="cuda", dtype=torch.float32) for _ in range(nb)]
+        out = subprocess.run(["nvidia-smi", "-i", "0", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=20)
+        return float(out.stdout.strip().splitlines()[0])
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        return 2070.0
+
+
+def coarsest_flops(n: int) -> float:
+    """Algorithmic flops of one coarsest solve (leading terms): Cholesky of M
+    and N (2 n^3/3), L_M^{-1} B and L_N^{-1} X^T (2 n^3), two-sided
+    Householder bidiagonalization (8 n^3/3), Gauss-Jordan on [B + e w^T | I]
+    (3 n^3); the triplet solves are lower order."""
+    return (2.0 / 3.0 + 2.0 + 8.0 / 3.0 + 3.0) * n ** 3
+
+
+def roofline_coarsest(api, torch, stream, h):
+    """The dominant kernel of a step: the dense coarsest-level solver (one
+    16-block cluster, FP32 on the mixed path), timed with CUDA events on the
+    stream it is launched on, on the bench hierarchy's own coarsest level."""
+    L = h.num_levels - 1
+    lv = h.level(L)
+    n = lv["n"]
+    B, M, N = (_dense(torch, lv[k], n) for k in ("B", "M", "N"))
+    r = KW["r"]
     with torch.cuda.stream(stream):
-        for k in range(5):
-            api.bamg_step_relax_block(rp, ci, va, dinv, Xs[k % nb], stream=stream)
-        reps = 200
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for k in range(reps):
-            api.bamg_step_relax_block(rp, ci, va, dinv, Xs[k % nb], stream=stream)
-        e1.record(stream)
-        e1.synchronize()
-    dur_s = e0.elapsed_time(e1) / reps / 1e3
-    nnz = int(B["nnz"])
-    alg_bytes = nnz * 8 + (n + 1) * 4 + n * 4 + 2 * n * ld * 4
-    achieved = alg_bytes / dur_s / 1e9
-    return {"bound": "hbm", "kernel": "relax_block_kernel<float,16> (finest level)",
-            "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(achieved / hbm, 4), "traffic": None, "peak_source": src,
-            "launch_us": round(dur_s * 1e6, 3), "alg_bytes": alg_bytes}
+        for _ in range(2):
+            api.bamg_step_coarsest(B, M, N, r, prec="mixed", stream=stream)
+        torch.cuda.synchronize()
+        ms, _ = event_ms(torch, stream, lambda: api.bamg_step_coarsest(B, M, N, r, prec="mixed", stream=stream),
+                         reps=5)
+    flops = coarsest_flops(n)
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = _max_sm_mhz()
+    peak = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    achieved = flops / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": f"coarsest_kernel<float> (n={n} dense coarsest level, 16-block cluster, "
+                                      f"rows in shared memory)",
+            "achieved": round(achieved, 4), "peak": round(peak, 1), "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 6), "traffic": None,
+            "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x {mhz:.0f} MHz",
+            "launch_ms": round(ms, 3), "alg_flops": flops,
+            "frac_of_cluster_sms": round(achieved / (peak * 16 / sms), 5)}
+
+
+_CHAIN_CACHE = {}
+
+
+def _tandem(side):
+    import chaingen as cg
+    if side not in _CHAIN_CACHE:
+        _CHAIN_CACHE[side] = cg.tandem(side)
+    return _CHAIN_CACHE[side]
+
+
+def roofline_sparse(api, torch, stream, side=2048, ld=16):
+    """Finest-level FP32 block relaxation (setup hot loop, Algorithm 1) on a
+    2048 x 2048 tandem queue: n = 4,194,304 rows, X and Y blocks of 268 MB
+    (above L2), two alternating input blocks, CUDA events on the stream."""
+    hbm, src, _ = load_peaks()
+    ch = _tandem(side)
+    rp, ci, va = chain_tensors(torch, ch)
+    with torch.cuda.stream(stream):
+        Brp, Bci, Bva = api.bamg_step_build_B(rp, ci, va, stream=stream)
+        n = ch.n
+        rows = torch.repeat_interleave(torch.arange(n, device="cuda"), (Brp[1:] - Brp[:-1]).long())
+        diag = Bci.long() == rows
+        d = torch.zeros(n, dtype=torch.float64, device="cuda")
+        d[rows[diag]] = Bva[diag]
+        dinv = (1.0 / d).float()
+        va32 = Bva.float()
+        Xs = [torch.rand((n, ld), device="cuda", dtype=torch.float32) for _ in range(2)]
+        for k in range(4):
+            api.bamg_step_relax_block(Brp, Bci, va32, dinv, Xs[k % 2], stream=stream)
+        torch.cuda.synchronize()
+        reps = 20
+        state = {"k": 0}
+
+        def one():
+            state["k"] += 1
+            return api.bamg_step_relax_block(Brp, Bci, va32, dinv, Xs[state["k"] % 2], stream=stream)
+        ms, _ = event_ms(torch, stream, one, reps=reps)
+    nnz = int(Bci.numel())
+    alg = nnz * (4 + 4) + 4 * (n + 1) + 2 * n * ld * 4 + n * 4
+    achieved = alg / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": "relax_block_kernel<float,16> (finest level, r=16)",
+            "workload": f"tandem queue {side}x{side} (n={n}, nnz(B)={nnz})",
+            "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+            "traffic": None, "peak_source": src, "launch_us": round(ms * 1e3, 2), "alg_bytes": alg}
+
+
+# ---------------------------------------------------------------- learned (config 5)
+def learned_section(api, torch, stream, eval_side=2048):
+    """Network fits against LS fits on a 2048 x 2048 tandem queue.  The
+    network is trained first, on LS setups of 8 seeded chains (tandem queues
+    and weighted lattices, sides 64-512)."""
+    import numpy as np
+    import chaingen as cg
+    t0 = time.perf_counter()
+    train = [cg.tandem(s) for s in (64, 128, 256, 512)] + [cg.lattice2d(s, seed=s + 5) for s in (64, 128, 256, 512)]
+    Xs, Ts, Ms = [], [], []
+    with torch.cuda.stream(stream):
+        for ch in train:
+            p = api.bamg_params_default(r=16, seed=5, precision="mixed")
+            h = api.bamg_setup(*chain_tensors(torch, ch), ch.n, p, nx=ch.nx, ny=ch.ny, stream=stream)
+            for l in range(h.num_levels - 1):
+                X, T, M = api.bamg_mlp_harvest(h, l, stream=stream)
+                Xs.append(X); Ts.append(T); Ms.append(M)
+            h.destroy()
+        X, T, M = torch.cat(Xs), torch.cat(Ts), torch.cat(Ms)
+        perm = torch.from_numpy(np.random.default_rng(6).permutation(X.shape[0])).cuda()
+        X, T, M = X[perm].contiguous(), T[perm].contiguous(), M[perm].contiguous()
+        t_h = time.perf_counter()
+        params = api.bamg_mlp_init(seed=5, stream=stream)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        losses = api.bamg_mlp_train(params, X, T, M, epochs=40, batch=4096, lr=2e-3, stream=stream)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t1
+    ch = _tandem(eval_side)
+    rp, ci, va = chain_tensors(torch, ch)
+    res = {"train_rows": int(X.shape[0]), "train_chains": len(train), "harvest_s": round(t_h - t0, 2),
+           "train_s": round(t_train, 2), "epochs": 40, "loss_first": losses[0], "loss_last": losses[-1],
+           "workload": f"tandem queue {eval_side}x{eval_side} ({ch.n} states)"}
+    # default depth (8 levels down to 16 x 16) for both fits, and an LS
+    # hierarchy tuned to converge at this size (7 levels, r = 32, 20 setup
+    # relaxations: with the defaults its deepest levels get b_ii <= 0)
+    variants = (("ls_mixed", dict(precision="mixed", r=16)),
+                ("learned_mixed", dict(precision="mixed", r=16, interp="mlp")),
+                ("learned_fp64", dict(precision="fp64", r=16, interp="mlp")),
+                ("ls_tuned_mixed", dict(precision="mixed", r=32, max_levels=7, nu_setup=20)))
+    xs = {}
+    for name, kw in variants:
+        rows = []
+        with torch.cuda.stream(stream):
+            for k in range(3):
+                p = api.bamg_params_default(seed=2, mlp_params=params, **kw)
+                torch.cuda.synchronize()
+                ms, (h, x, info) = event_ms(torch, stream, lambda: (lambda hh: (hh, *api.bamg_solve(
+                    hh, restart=20, tol=1e-10, max_iter=400, stream=stream, allow_not_converged=True)))(
+                        api.bamg_setup(rp, ci, va, ch.n, p, nx=eval_side, ny=eval_side, stream=stream)))
+                if k:
+                    rows.append((ms, info))
+                if k < 2:
+                    h.destroy()
+            f = api.bamg_vcycle_factor(h, iters=12, stream=stream)
+        xs[name] = x
+        h.destroy()
+        info = rows[-1][1]
+        res[name] = {"ms_per_step": round(statistics.mean(m for m, _ in rows), 2),
+                     "setup_ms": round(statistics.mean(i["setup_ms"] for _, i in rows), 2),
+                     "solve_ms": round(statistics.mean(i["solve_ms"] for _, i in rows), 2),
+                     "iterations": info["iterations"], "levels": info["levels"],
+                     "rel_res_1": info["rel_res_1"], "converged": info["rel_res_1"] <= 1e-10,
+                     "vcycle_factor": round(f, 4), "params": {k: v for k, v in kw.items()}}
+    ref = xs["ls_tuned_mixed"]
+    for name in xs:
+        res[name]["err_l1_vs_ls_tuned"] = float((xs[name] - ref).abs().sum().item())
+    return res
+
+
+# ---------------------------------------------------------------- batched (config 4)
+def batched_section(api, torch, stream, count=256):
+    """256 seeded chains (weighted lattices and tandem queues of side 32-256,
+    Delaunay walks of 1k-64k states): one batched setup + lock-step FGMRES
+    against a loop of per-chain setups and solves, FP32 V-cycle."""
+    import chaingen as cg
+    t0 = time.perf_counter()
+    chains = cg.chain_mix(count, seed=4)
+    t_gen = time.perf_counter() - t0
+    p = api.bamg_params_default(r=16, coarse_min=150, coarsening="mis", c_min=1, c_max=3, nu_pre=5, nu_post=5,
+                                seed=3, precision="mixed")
+    specs = [(c.row_ptr, c.col, c.val, c.n, c.nx, c.ny) for c in chains]
+    res = {"chains": count, "states": int(sum(c.n for c in chains)), "generate_s": round(t_gen, 1)}
+    with torch.cuda.stream(stream):
+        b = api.bamg_setup_batched(specs[:8], p, host_threads=16, stream=stream)    # warm-up
+        api.bamg_solve_batched(b, restart=30, tol=1e-10, stream=stream)
+        b.destroy()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        b = api.bamg_setup_batched(specs, p, host_threads=16, stream=stream)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        x, infos = api.bamg_solve_batched(b, restart=30, tol=1e-10, stream=stream)
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        b.destroy()
+        loop_setup = loop_solve = 0.0
+        its = []
+        for c in chains:
+            s0 = time.perf_counter()
+            h = api.bamg_setup(c.row_ptr, c.col, c.val, c.n, p, nx=c.nx, ny=c.ny, stream=stream)
+            torch.cuda.synchronize()
+            s1 = time.perf_counter()
+            _, info = api.bamg_solve(h, restart=30, tol=1e-10, stream=stream)
+            torch.cuda.synchronize()
+            s2 = time.perf_counter()
+            loop_setup += s1 - s0
+            loop_solve += s2 - s1
+            its.append(info["iterations"])
+            h.destroy()
+    bt = (t3 - t1) * 1e3
+    lt = (loop_setup + loop_solve) * 1e3
+    res.update({"batched_ms": round(bt, 1), "batched_setup_ms": round((t2 - t1) * 1e3, 1),
+                "batched_solve_ms": round((t3 - t2) * 1e3, 1), "loop_ms": round(lt, 1),
+                "loop_setup_ms": round(loop_setup * 1e3, 1), "loop_solve_ms": round(loop_solve * 1e3, 1),
+                "speedup": round(lt / bt, 2), "max_rel_res_1": max(i["rel_res_1"] for i in infos),
+                "iterations_max": max(i["iterations"] for i in infos),
+                "loop_iterations_max": max(its)})
+    return res
+
+
+# ---------------------------------------------------------------- Delaunay (config 3)
+def delaunay_section(api, torch, stream, npts=1 << 20):
+    """Random walk on the Delaunay graph of 2^20 uniform points: MIS
+    coarsening, up to 3 interpolation points (the paper's planar-graph
+    setting; sets of 3-8 points give coarse operators with b_ii <= 0 at this
+    size and GMRES stalls), r = 16, 5+5 sweeps, coarse_min 500."""
+    import chaingen as cg
+    t0 = time.perf_counter()
+    ch = cg.delaunay_walk(npts, seed=3)
+    t_gen = time.perf_counter() - t0
+    deg = torch.from_numpy(ch.meta["deg"]).cuda()
+    xstar = deg / deg.sum()
+    rp, ci, va = chain_tensors(torch, ch)
+    res = {"workload": f"Delaunay walk, {npts} points (nnz(A)={ch.nnz})", "generate_s": round(t_gen, 1)}
+    for name, prec, reps in (("mixed", "mixed", 2), ("fp64", "fp64", 1)):
+        p = api.bamg_params_default(r=16, coarsening="mis", c_min=1, c_max=3, nu_pre=5, nu_post=5, coarse_min=500,
+                                    seed=3, precision=prec)
+        rows = []
+        with torch.cuda.stream(stream):
+            for k in range(reps + 1):
+                torch.cuda.synchronize()
+                ms, (h, x, info) = event_ms(torch, stream, lambda: (lambda hh: (hh, *api.bamg_solve(
+                    hh, restart=30, tol=1e-10, stream=stream)))(api.bamg_setup(rp, ci, va, ch.n, p, stream=stream)))
+                if k:
+                    rows.append((ms, info))
+                h.destroy()
+        info = rows[-1][1]
+        res[name] = {"ms_per_step": round(statistics.mean(m for m, _ in rows), 2),
+                     "setup_ms": round(statistics.mean(i["setup_ms"] for _, i in rows), 2),
+                     "solve_ms": round(statistics.mean(i["solve_ms"] for _, i in rows), 2),
+                     "iterations": info["iterations"], "levels": info["levels"], "rel_res_1": info["rel_res_1"],
+                     "op_cplx": round(info["op_cplx"], 3), "grid_cplx": round(info["grid_cplx"], 3),
+                     "err_l1_vs_closed_form": float((x - xstar).abs().sum().item())}
+    return res
 
 
 # ---------------------------------------------------------------- CPU baseline
@@ -259,9 +508,13 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--sections", default="all",
+                    help="comma list of " + ",".join(SECTIONS) + ", or all / none")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    args.sections = (set(SECTIONS) if args.sections == "all" else set() if args.sections == "none"
+                     else set(args.sections.split(",")))
     rank = env_int("RANK", 0)
     world = env_int("WORLD_SIZE", 1)
 
@@ -288,6 +541,8 @@ def main():
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
+    if rank != 0:
+        args.sections = set()               # replicas time the headline only
     r = gpu_arm(args, rank, world)
     if rank != 0:
         return
@@ -321,6 +576,9 @@ def main():
         "cpu_baseline": cpu,
         "clocks": r["clocks"],
     }
+    for k in ("sparse", "learned", "batched", "delaunay"):
+        if k in r:
+            line["roofline_sparse" if k == "sparse" else k] = r[k]
     print(json.dumps(line))
 
 

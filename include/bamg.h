@@ -44,7 +44,7 @@ typedef enum {
   BAMG_ERR_OOM = 4,            /* device allocation failed                      */
   BAMG_ERR_NOT_CONVERGED = 5,  /* max_iter reached above the tolerance          */
   BAMG_ERR_BREAKDOWN = 6,      /* GMRES breakdown before convergence            */
-  BAMG_ERR_NUMERIC = 7,        /* non-positive coarse diagonal, non-SPD M_l/N_l,
+  BAMG_ERR_NUMERIC = 7,        /* zero row and column in a coarse B, non-SPD M_l/N_l,
                                   singular fit, or a row beyond kernel limits   */
   BAMG_ERR_TIMEOUT = 8,        /* a bounded device-side wait gave up            */
   BAMG_ERR_UNSUPPORTED = 9     /* valid request outside this build's limits     */
@@ -80,7 +80,9 @@ typedef struct {
   int nu_setup;      /* Jacobi sweeps per level in each setup relaxation phase */
   int nu_pre, nu_post; /* V-cycle pre/post Jacobi sweeps                       */
   int c_min, c_max;  /* interpolation set size bounds (graph coarsening)       */
-  double omega;      /* Jacobi weight: x <- x + omega D^{-1}(b - B x)          */
+  double omega;      /* Jacobi weight: x <- x + omega D^{-1}(b - B x); a coarse
+                        row with b_ii <= 0 takes for d_i the larger l1 norm of
+                        row i and column i of B                               */
   int coarsening;    /* BAMG_COARSEN_GEOMETRIC (needs nx, ny) or _MIS          */
   int precision;     /* BAMG_PREC_FP64 or BAMG_PREC_MIXED (FP32 V-cycle and
                         setup relaxation inside FP64 GMRES)                    */
@@ -95,6 +97,10 @@ typedef struct {
                         only x^(0) up from the coarsest level               */
   const float* mlp_params; /* device, bamg_mlp_num_params() floats, read during
                         bamg_setup when interp = BAMG_INTERP_MLP              */
+  int setup_cycles;  /* bootstrap setup cycles, 1..8 (2 = the BAMG^2 variant of
+                        Section 7): each later cycle rebuilds the hierarchy from
+                        the previous cycle's finest triplets; must be 1 with
+                        network fits                                          */
 } bamg_params;
 
 typedef struct {
@@ -255,6 +261,7 @@ typedef struct {
   const int32_t* cmap;              /* coarse index or -1                      */
   const double* s;                  /* sqrt LS weights of V (r)                */
   const double* t;                  /* sqrt LS weights of U (r, t[0] = 0)      */
+  int jacobi_l1_rows;               /* rows with b_ii <= 0 (l1 Jacobi divisor)  */
 } bamg_level_view;
 
 int bamg_num_levels(const bamg_hierarchy* h);

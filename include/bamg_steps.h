@@ -58,6 +58,17 @@ bamg_status bamg_step_relax_block(int prec, int n, int ld, const int32_t* rp,
                                   const void* sigma, double omega, int keep_col0,
                                   void* stream);
 
+/* Reciprocal Jacobi divisors (Section 3, weighted Jacobi): dinv[i] = 1/b_ii
+ * where b_ii > 0; where b_ii <= 0 (possible on coarse Petrov-Galerkin levels,
+ * which the paper does not treat) 1/max(||row i||_1, ||column i||_1).  B and
+ * its transpose (trp, tva: CSR of B^T) are device CSR arrays of an n x n
+ * matrix; dinv: device, n doubles; *nsafe_host receives the number of rows
+ * that took the l1 divisor.  BAMG_ERR_NUMERIC when a row and its column are
+ * both zero. */
+bamg_status bamg_step_jacobi_divisor(int n, const int32_t* rp, const int32_t* ci, const double* val,
+                                     const int32_t* trp, const double* tval, double* dinv,
+                                     int* nsafe_host, void* stream);
+
 /* Y = A X for a rows x cols CSR A and a cols x ld block X (Y rows x ld). */
 bamg_status bamg_step_spmm_block(int prec, int rows, int ld, const int32_t* rp,
                                  const int32_t* ci, const void* val, const void* X,

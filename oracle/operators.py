@@ -39,6 +39,23 @@ def diag(B: sp.csr_matrix) -> np.ndarray:
     return B.diagonal().copy()
 
 
+def jacobi_divisor(B: sp.csr_matrix) -> np.ndarray:
+    """Divisors d of the weighted Jacobi step x + omega D^{-1}(b - B x)
+    (Section 3).  d_i = b_ii where b_ii > 0.  The paper does not treat a
+    coarse operator Q B P with b_ii <= 0, where its step is undefined; there
+    d_i is the larger of the l1 norms of row i and of column i of B (an
+    l1-Jacobi row that serves the relaxations with B and with B^T).  A row
+    and column that are both zero make the level unusable (ValueError)."""
+    d = B.diagonal().copy()
+    A = abs(B).tocsr()
+    l1 = np.maximum(np.asarray(A.sum(axis=1)).ravel(), np.asarray(A.sum(axis=0)).ravel())
+    bad = ~(d > 0)
+    if np.any(bad & ~(l1 > 0)):
+        raise ValueError("a row and column of B are zero")
+    d[bad] = l1[bad]
+    return d
+
+
 def transpose(X: sp.csr_matrix) -> sp.csr_matrix:
     T = X.T.tocsr()
     T.sort_indices()

@@ -17,6 +17,12 @@ B_l v = sigma M_l u and B_l^T u = sigma N_l v, both from the previous
 iterates, then updates sigma by the generalized Rayleigh quotient
 (eq. singular_value).
 
+Subsequent cycles (Section 4, after Algorithm 1; the BAMG^2 rows of the
+tables in Section 7) rebuild the hierarchy from the finest level with the
+previous cycle's finest triplets as test vectors; their first smoothing on
+every level is the inhomogeneous one with the sigma update, instead of the
+homogeneous one.
+
 Readings where the paper is silent: 5 setup relaxations per level and phase
 (with 3, the r = 8 fits over-fit rough vectors and the first hierarchy can
 diverge as a stationary method); the inner loop runs once (mu = 1);
@@ -46,6 +52,7 @@ class Params:
     c_max: int = 4
     seed: int = 1
     restriction: str = "ls"           # or "average" (Section 5 comparison)
+    cycles: int = 1                   # bootstrap setup cycles (2 = BAMG^2)
 
 
 @dataclass
@@ -133,7 +140,7 @@ def split(lev: Level, l: int, p: Params):
 
 
 def make_level(B: sp.csr_matrix, M=None, N=None, grid=None) -> Level:
-    return Level(n=B.shape[0], B=B, Bt=operators.transpose(B), d=operators.diag(B),
+    return Level(n=B.shape[0], B=B, Bt=operators.transpose(B), d=operators.jacobi_divisor(B),
                  M=M, N=N, grid=grid)
 
 
@@ -145,8 +152,9 @@ def is_coarsest(lev: Level, l: int, p: Params) -> bool:
     return False
 
 
-def bamg_mle(H: Hierarchy, l: int, U: np.ndarray, V: np.ndarray):
-    """Algorithm 1 on level l; returns (sigma, U_l, V_l)."""
+def bamg_mle(H: Hierarchy, l: int, U: np.ndarray, V: np.ndarray, sig=None):
+    """Algorithm 1 on level l; returns (sigma, U_l, V_l).  With sig given
+    (a subsequent cycle) the first smoothing is the inhomogeneous one."""
     p = H.params
     lev = H.levels[l]
     if is_coarsest(lev, l, p):
@@ -155,7 +163,10 @@ def bamg_mle(H: Hierarchy, l: int, U: np.ndarray, V: np.ndarray):
         Nd = np.eye(lev.n) if lev.N is None else lev.N.toarray()
         H.Bpinv = coarsest.pinv_drop_smallest(Bd)
         return coarsest.generalized_triplets(Bd, Md, Nd, p.r)
-    U, V = relax_homogeneous(lev, U, V, p)
+    if sig is None:
+        U, V = relax_homogeneous(lev, U, V, p)
+    else:
+        sig, U, V = relax_inhomogeneous(lev, sig, U, V, p)
     r = V.shape[1]
     V = interp.normalise(V)
     U = interp.normalise(U, range(1, r))
@@ -176,7 +187,7 @@ def bamg_mle(H: Hierarchy, l: int, U: np.ndarray, V: np.ndarray):
     Nc = operators.spmatmul(Pt, lev.P if lev.N is None
                             else operators.spmatmul(lev.N, lev.P))
     H.levels.append(make_level(Bc, Mc, Nc, cgrid))
-    sig, Uc, Vc = bamg_mle(H, l + 1, U[cf], V[cf])
+    sig, Uc, Vc = bamg_mle(H, l + 1, U[cf], V[cf], sig)
     U = lev.Qt @ Uc
     V = lev.P @ Vc
     return relax_inhomogeneous(lev, sig, U, V, p)
@@ -191,7 +202,7 @@ def initial_x(sig: np.ndarray, V: np.ndarray) -> np.ndarray:
 
 
 def bamg_setup(A: sp.csr_matrix, p: Params, grid=None, U0=None, V0=None) -> Hierarchy:
-    """Build B = I - A and run one bootstrap cycle (Algorithm 1)."""
+    """Build B = I - A and run p.cycles bootstrap cycles (Algorithm 1)."""
     A = sp.csr_matrix(A)
     operators.validate_stochastic(A)
     B = operators.build_B(A)
@@ -200,6 +211,9 @@ def bamg_setup(A: sp.csr_matrix, p: Params, grid=None, U0=None, V0=None) -> Hier
     if U0 is None or V0 is None:
         U0, V0 = rng.initial_test_vectors(p.seed, B.shape[0], p.r)
     sig, U, V = bamg_mle(H, 0, U0.copy(), V0.copy())
+    for _ in range(1, p.cycles):
+        del H.levels[1:]                       # rebuild below the finest level
+        sig, U, V = bamg_mle(H, 0, U, V, sig)
     H.sigma, H.U, H.V = sig, U, V
     H.x0 = initial_x(sig, V)
     return H

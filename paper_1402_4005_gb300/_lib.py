@@ -35,7 +35,7 @@ class Params(C.Structure):
                 ("nu_pre", i32), ("nu_post", i32), ("c_min", i32), ("c_max", i32),
                 ("omega", f64), ("coarsening", i32), ("precision", i32), ("restriction", i32),
                 ("seed", u64), ("stochastic_tol", f64), ("max_coarse_dense", i32),
-                ("interp", i32), ("mlp_params", vp)]
+                ("interp", i32), ("mlp_params", vp), ("setup_cycles", i32)]
 
 
 class SolveParams(C.Structure):
@@ -57,7 +57,8 @@ class CsrView(C.Structure):
 
 class LevelView(C.Structure):
     _fields_ = [("n", i32), ("B", CsrView), ("M", CsrView), ("N", CsrView), ("P", CsrView),
-                ("Qt", CsrView), ("Q", CsrView), ("cf", vp), ("cmap", vp), ("s", vp), ("t", vp)]
+                ("Qt", CsrView), ("Q", CsrView), ("cf", vp), ("cmap", vp), ("s", vp), ("t", vp),
+                ("jacobi_l1_rows", i32)]
 
 
 # name -> (restype, argtypes)
@@ -98,6 +99,7 @@ SIGNATURES = {
     "bamg_step_transpose": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]),
     "bamg_step_relax_block": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, f64, i32, vp]),
     "bamg_step_spmm_block": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp]),
+    "bamg_step_jacobi_divisor": (i32, [i32, vp, vp, vp, vp, vp, vp, ip, vp]),
     "bamg_step_norms_weights": (i32, [i32, i32, i32, i32, vp, vp, vp, vp, i32, i32, dp, dp, vp]),
     "bamg_step_norms_weights_noalloc": (i32, [i32, i32, i32, i32, vp, vp, vp, vp, i32, i32, dp, dp, vp]),
     "bamg_step_coarsen_geometric": (i32, [i32, i32, vp, vp, vp, vp, ip, vp]),

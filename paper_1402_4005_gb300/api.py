@@ -101,7 +101,7 @@ class Hierarchy:
         v = _lib.LevelView()
         check(lib().bamg_level(C.c_void_p(self.handle), l, C.byref(v)), "bamg_level")
         torch.cuda.synchronize()
-        out = {"n": v.n}
+        out = {"n": v.n, "jacobi_l1_rows": v.jacobi_l1_rows}
         for name in ("B", "M", "N", "P", "Qt", "Q"):
             cv = getattr(v, name)
             out[name] = None if cv.rows == 0 else _csr_from_view(cv)
@@ -331,6 +331,16 @@ def bamg_step_relax_block(rp, ci, val, dinv, X, R=None, sigma=None, omega=0.7, k
     check(lib().bamg_step_relax_block(prec, n, ld, _p(rp), _p(ci), _p(val), _p(dinv), _p(X), _p(Y), _p(R),
                                       _p(sigma), omega, int(keep_col0), _stream(stream)), "relax_block")
     return Y
+
+
+def bamg_step_jacobi_divisor(rp, ci, val, trp, tval, stream=None):
+    """(dinv, number of rows that took the l1 divisor) of a square CSR B."""
+    n = rp.shape[0] - 1
+    dinv = torch.empty(n, dtype=torch.float64, device="cuda")
+    ns = C.c_int(0)
+    check(lib().bamg_step_jacobi_divisor(n, _p(rp), _p(ci), _p(val), _p(trp), _p(tval), _p(dinv), C.byref(ns),
+                                         _stream(stream)), "jacobi_divisor")
+    return dinv, ns.value
 
 
 def bamg_step_spmm_block(rp, ci, val, X, rows: int, stream=None):

@@ -45,6 +45,7 @@ bamg_status bamg_params_default(bamg_params* p) {
   p->seed = 1;
   p->stochastic_tol = 1e-12;
   p->max_coarse_dense = 1024;
+  p->setup_cycles = 1;
   return BAMG_OK;
 }
 
@@ -93,6 +94,8 @@ static bamg_status check_params(const bamg_csr* A, const bamg_params* p) {
   if (p->coarsening == BAMG_COARSEN_GEOMETRIC)
     BAMG_CHECK_ARG(A->nx >= 1 && A->ny >= 1 && (int64_t)A->nx * A->ny == A->n);
   BAMG_CHECK_ARG(p->interp == BAMG_INTERP_LS || p->interp == BAMG_INTERP_MLP);
+  BAMG_CHECK_ARG(p->setup_cycles >= 1 && p->setup_cycles <= 8);
+  BAMG_CHECK_ARG(p->interp == BAMG_INTERP_LS || p->setup_cycles == 1);
   if (p->interp == BAMG_INTERP_MLP) {
     BAMG_CHECK_ARG(p->mlp_params != nullptr);
     if (p->coarsening != BAMG_COARSEN_GEOMETRIC) {
@@ -276,6 +279,7 @@ bamg_status bamg_level(const bamg_hierarchy* h, int l, bamg_level_view* out) {
   out->cmap = L.cmap.as<int32_t>();
   out->s = L.s.as<double>();
   out->t = L.t.as<double>();
+  out->jacobi_l1_rows = L.nsafe;
   return BAMG_OK;
 }
 
@@ -341,6 +345,27 @@ bamg_status bamg_step_relax_block(int prec, int n, int ld, const int32_t* rp, co
                               (const float*)R, (const float*)sigma, (float)omega, keep_col0, S(stream));
   return relax_block<double>(n, ld, rp, ci, (const double*)val, (const double*)dinv, (const double*)X,
                              (double*)Y, (const double*)R, (const double*)sigma, omega, keep_col0, S(stream));
+}
+
+bamg_status bamg_step_jacobi_divisor(int n, const int32_t* rp, const int32_t* ci, const double* val,
+                                     const int32_t* trp, const double* tval, double* dinv, int* nsafe_host,
+                                     void* stream) {
+  BAMG_CHECK_ARG(n >= 1 && rp && ci && val && trp && tval && dinv && nsafe_host);
+  cudaStream_t s = S(stream);
+  DevMem flags;
+  BAMG_TRY(flags.alloc(2 * sizeof(int), s));
+  int init[2] = {INT32_MAX, 0};
+  BAMG_CUDA(cudaMemcpyAsync(flags.p, init, sizeof(init), cudaMemcpyHostToDevice, s));
+  BAMG_TRY(diag_inv<double>(n, rp, ci, val, trp, tval, dinv, flags.as<int>(), flags.as<int>() + 1, s));
+  int hf[2] = {0, 0};
+  BAMG_CUDA(cudaMemcpyAsync(hf, flags.p, sizeof(hf), cudaMemcpyDeviceToHost, s));
+  BAMG_CUDA(cudaStreamSynchronize(s));
+  *nsafe_host = hf[1];
+  if (hf[0] != INT32_MAX) {
+    set_error("row and column %d are zero", hf[0]);
+    return BAMG_ERR_NUMERIC;
+  }
+  return BAMG_OK;
 }
 
 bamg_status bamg_step_spmm_block(int prec, int rows, int ld, const int32_t* rp, const int32_t* ci,

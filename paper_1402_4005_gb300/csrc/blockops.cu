@@ -276,17 +276,38 @@ __global__ void convert_kernel(size_t n, const S* __restrict__ a, D* __restrict_
   if (t < n) b[t] = D(a[t]);
 }
 
+// Jacobi divisor of row i (Section 3: x <- x + omega D^{-1} (b - B x)).
+// d_i = b_ii when b_ii > 0.  A coarse Petrov-Galerkin operator Q B P may have
+// b_ii <= 0, where that step is undefined; there d_i is the larger of the l1
+// norms of row i and of column i of B (an l1-Jacobi row, usable for the
+// relaxations with B and with B^T alike) and the row is counted in *nsafe.
+// A row whose row and column are both zero is reported in *bad_row.
 template <typename T>
 __global__ void diag_inv_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                const double* __restrict__ va, T* __restrict__ dinv,
-                                int* __restrict__ bad_row) {
+                                const double* __restrict__ va, const int32_t* __restrict__ trp,
+                                const double* __restrict__ tva, T* __restrict__ dinv,
+                                int* __restrict__ bad_row, int* __restrict__ nsafe) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double d = 0.0;
-  for (int p = rp[i]; p < rp[i + 1]; ++p)
+  double d = 0.0, l1r = 0.0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
     if (ci[p] == i) d = va[p];
-  if (!(d > 0.0)) atomicMin(bad_row, i);
-  dinv[i] = T(1.0 / d);
+    l1r += fabs(va[p]);
+  }
+  if (d > 0.0) {
+    dinv[i] = T(1.0 / d);
+    return;
+  }
+  double l1c = 0.0;
+  for (int p = trp[i]; p < trp[i + 1]; ++p) l1c += fabs(tva[p]);
+  const double m = fmax(l1r, l1c);
+  if (m > 0.0) {
+    dinv[i] = T(1.0 / m);
+    atomicAdd(nsafe, 1);
+  } else {
+    dinv[i] = T(0);
+    atomicMin(bad_row, i);
+  }
 }
 
 // =================================================================== host
@@ -462,9 +483,10 @@ bamg_status convert(size_t n, const S* a, D* b, cudaStream_t s) {
 }
 
 template <typename T>
-bamg_status diag_inv(int n, const int32_t* rp, const int32_t* ci, const double* va, T* dinv, int* bad_row,
-                     cudaStream_t s) {
-  return launch(diag_inv_kernel<T>, dim3(cdiv(n, 256)), dim3(256), 0, s, n, rp, ci, va, dinv, bad_row);
+bamg_status diag_inv(int n, const int32_t* rp, const int32_t* ci, const double* va, const int32_t* trp,
+                     const double* tva, T* dinv, int* bad_row, int* nsafe, cudaStream_t s) {
+  return launch(diag_inv_kernel<T>, dim3(cdiv(n, 256)), dim3(256), 0, s, n, rp, ci, va, trp, tva, dinv, bad_row,
+                nsafe);
 }
 
 #define BAMG_INST(T)                                                                                       \
@@ -482,8 +504,8 @@ bamg_status diag_inv(int n, const int32_t* rp, const int32_t* ci, const double* 
   template bamg_status csr_vec<T>(int, int, int, const int32_t*, const int32_t*, const T*, const T*, T,   \
                                   const T*, const T*, T*, cudaStream_t);                                \
   template bamg_status dense_gemv<T>(int, const T*, const T*, T*, cudaStream_t);                         \
-  template bamg_status diag_inv<T>(int, const int32_t*, const int32_t*, const double*, T*, int*,         \
-                                   cudaStream_t);
+  template bamg_status diag_inv<T>(int, const int32_t*, const int32_t*, const double*, const int32_t*,  \
+                                   const double*, T*, int*, int*, cudaStream_t);
 
 BAMG_INST(float)
 BAMG_INST(double)

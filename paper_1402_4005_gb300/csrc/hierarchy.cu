@@ -119,18 +119,20 @@ static bamg_status finish_level(bamg_hierarchy* h, Level& L, int l, cudaStream_t
   L.n = L.B.rows;
   BAMG_TRY(csr_transpose(L.B, L.Bt, s));
   BAMG_TRY(L.dinv.alloc(sizeof(double) * L.n, s));
-  DevMem bad;
-  BAMG_TRY(bad.alloc(sizeof(int), s));
-  int big = INT32_MAX;
-  BAMG_CUDA(cudaMemcpyAsync(bad.p, &big, sizeof(int), cudaMemcpyHostToDevice, s));
-  BAMG_TRY(diag_inv<double>(L.n, L.B.r(), L.B.c(), L.B.v(), L.dinv.as<double>(), bad.as<int>(), s));
-  int hb = 0;
-  BAMG_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DevMem flags;
+  BAMG_TRY(flags.alloc(2 * sizeof(int), s));
+  int init[2] = {INT32_MAX, 0};
+  BAMG_CUDA(cudaMemcpyAsync(flags.p, init, sizeof(init), cudaMemcpyHostToDevice, s));
+  BAMG_TRY(diag_inv<double>(L.n, L.B.r(), L.B.c(), L.B.v(), L.Bt.r(), L.Bt.v(), L.dinv.as<double>(),
+                            flags.as<int>(), flags.as<int>() + 1, s));
+  int hf[2] = {0, 0};
+  BAMG_CUDA(cudaMemcpyAsync(hf, flags.p, sizeof(hf), cudaMemcpyDeviceToHost, s));
   BAMG_CUDA(cudaStreamSynchronize(s));
-  if (hb != INT32_MAX) {
-    set_error("level %d: non-positive diagonal of B at row %d", l, hb);
+  if (hf[0] != INT32_MAX) {
+    set_error("level %d: row and column %d of B are zero", l, hf[0]);
     return BAMG_ERR_NUMERIC;
   }
+  L.nsafe = hf[1];
   double avg = L.n ? (double)L.B.nnz / L.n : 1.0;
   L.vec_g = avg <= 3 ? 2 : avg <= 6 ? 4 : avg <= 12 ? 8 : avg <= 24 ? 16 : 32;
   if (h->mixed) {
@@ -155,11 +157,18 @@ static bool is_coarsest(const bamg_hierarchy* h, const Level& L, int l) {
   return false;
 }
 
+template <typename T>
+static bamg_status relax_triplets(bamg_hierarchy* h, int l, DevMem& U, DevMem& V, DevMem& sig, DevMem& sig64,
+                                  cudaStream_t s);
+
 // ------------------------------------------------------------ one level down
+// inhomog: a subsequent bootstrap cycle, whose first smoothing is the
+// inhomogeneous one with the sigma update (the smoothing of the last loop
+// of Algorithm 1) on the carried triplets.
 template <typename T>
 static bamg_status coarsen_level(bamg_hierarchy* h, int l, DevMem& U, DevMem& V, DevMem& Uc, DevMem& Vc,
                                  DevMem& tmpU, DevMem& tmpV, DevMem& scale, DevMem& norms, DevMem& rkd,
-                                 cudaStream_t s) {
+                                 DevMem& sig, DevMem& sig64, bool inhomog, cudaStream_t s) {
   const bamg_params& p = h->p;
   const int ld = h->ld, r = p.r;
   Level& L = h->lv[l];
@@ -171,7 +180,8 @@ static bamg_status coarsen_level(bamg_hierarchy* h, int l, DevMem& U, DevMem& V,
   const bool learned = h->learned != 0;
   // Algorithm 1, first smoothing loop: relax V with B and U with B^T
   // (not needed when the network proposes the fits)
-  for (int it = 0; !learned && it < p.nu_setup; ++it) {
+  if (inhomog && !learned) BAMG_TRY(relax_triplets<T>(h, l, U, V, sig, sig64, s));
+  for (int it = 0; !learned && !inhomog && it < p.nu_setup; ++it) {
     BAMG_TRY(relax_block<T>(L.n, ld, L.B.r(), L.B.c(), Bv, dv, V.as<T>(), tmpV.as<T>(), nullptr, nullptr, om,
                             0, s));
     std::swap(V, tmpV);
@@ -414,83 +424,95 @@ static bamg_status run_setup(bamg_hierarchy* h, cudaStream_t s) {
   BAMG_TRY(sig.alloc(sizeof(T) * ld, s));
   BAMG_TRY(sig64.alloc(sizeof(double) * ld, s));
   BAMG_CUDA(cudaMemsetAsync(rkd.p, 0, sizeof(int), s));
-  int l = 0;
-  while (!is_coarsest(h, h->lv[l], l)) {
-    DevMem tU, tV;
-    size_t bytes = sizeof(T) * (size_t)h->lv[l].n * ld;
-    if (!learned) {
-      BAMG_TRY(tU.alloc(bytes, s));
-      BAMG_TRY(tV.alloc(bytes, s));
+  // bootstrap cycles: each later cycle rebuilds the hierarchy below the
+  // finest level from the previous cycle's finest triplets (Section 4)
+  const int cycles = learned ? 1 : p.setup_cycles;
+  int rr = r;   // triplets the coarsest level provides (min(r, n_L))
+  for (int cyc = 0; cyc < cycles; ++cyc) {
+    if (cyc > 0) {
+      h->lv.resize(1);
+      U.resize(1);
+      V.resize(1);
     }
-    U.emplace_back();
-    V.emplace_back();
-    BAMG_TRY(coarsen_level<T>(h, l, U[l], V[l], U[l + 1], V[l + 1], tU, tV, scale, norms, rkd, s));
-    ++l;
-  }
-  // coarsest level: eq. generalized_eigenvalue and the pseudo-inverse
-  Trace tr;
-  Level& LL = h->lv[l];
-  int nL = LL.n;
-  h->nL = nL;
-  int rr = r < nL ? r : nL;
-  DevMem Bd, Md, Nd, sg, Ud, Vd;
-  size_t nn = (size_t)nL * nL;
-  BAMG_TRY(Bd.alloc(sizeof(double) * nn, s));
-  BAMG_TRY(Md.alloc(sizeof(double) * nn, s));
-  BAMG_TRY(Nd.alloc(sizeof(double) * nn, s));
-  BAMG_TRY(sg.alloc(sizeof(double) * r, s));
-  BAMG_TRY(Ud.alloc(sizeof(double) * (size_t)nL * r, s));
-  BAMG_TRY(Vd.alloc(sizeof(double) * (size_t)nL * r, s));
-  BAMG_CUDA(cudaMemsetAsync(sg.p, 0, sizeof(double) * r, s));
-  BAMG_CUDA(cudaMemsetAsync(Ud.p, 0, sizeof(double) * (size_t)nL * r, s));
-  BAMG_CUDA(cudaMemsetAsync(Vd.p, 0, sizeof(double) * (size_t)nL * r, s));
-  BAMG_TRY(csr_to_dense(nL, LL.B.r(), LL.B.c(), LL.B.v(), Bd.as<double>(), s));
-  if (LL.M.empty()) {
-    std::vector<double> I(nn, 0.0);
-    for (int i = 0; i < nL; ++i) I[(size_t)i * nL + i] = 1.0;
-    BAMG_CUDA(cudaMemcpyAsync(Md.p, I.data(), sizeof(double) * nn, cudaMemcpyHostToDevice, s));
-    BAMG_CUDA(cudaMemcpyAsync(Nd.p, I.data(), sizeof(double) * nn, cudaMemcpyHostToDevice, s));
-    BAMG_CUDA(cudaStreamSynchronize(s));
-  } else {
-    BAMG_TRY(csr_to_dense(nL, LL.M.r(), LL.M.c(), LL.M.v(), Md.as<double>(), s));
-    BAMG_TRY(csr_to_dense(nL, LL.N.r(), LL.N.c(), LL.N.v(), Nd.as<double>(), s));
-  }
-  BAMG_TRY(h->Bpinv.alloc(sizeof(double) * nn, s));
-  // Ud/Vd are nL x rr row-major (rr <= r)
-  BAMG_TRY(coarsest_solve(h->mixed ? 1 : 0, nL, rr, Bd.as<double>(), Md.as<double>(), Nd.as<double>(),
-                          sg.as<double>(), Ud.as<double>(), Vd.as<double>(), h->Bpinv.as<double>(), s));
-  if (h->mixed) {
-    BAMG_TRY(h->Bpinv32.alloc(sizeof(float) * nn, s));
-    BAMG_TRY(convert<double, float>(nn, h->Bpinv.as<double>(), h->Bpinv32.as<float>(), s));
-  }
-  tr.mark(s, "coarsest solve", l);
-  if (learned) return learned_unwind(h, l, rr, Vd.as<double>(), sg.as<double>(), s);
-  // triplets into padded blocks
-  BAMG_TRY(U[l].alloc(sizeof(T) * (size_t)nL * ld, s));
-  BAMG_TRY(V[l].alloc(sizeof(T) * (size_t)nL * ld, s));
-  unsigned g = cdiv((long long)nL * ld, 256);
-  float* f32 = nullptr;
-  double* f64 = nullptr;
-  if (sizeof(T) == 4) f32 = (float*)U[l].p; else f64 = (double*)U[l].p;
-  BAMG_TRY(launch(pad_block_kernel, dim3(g), dim3(256), 0, s, nL, rr, ld, (const double*)Ud.as<double>(), f32, f64));
-  if (sizeof(T) == 4) f32 = (float*)V[l].p; else f64 = (double*)V[l].p;
-  BAMG_TRY(launch(pad_block_kernel, dim3(g), dim3(256), 0, s, nL, rr, ld, (const double*)Vd.as<double>(), f32, f64));
-  {
-    unsigned g1 = cdiv(ld, 256);
-    if (sizeof(T) == 4) { f32 = (float*)sig.p; f64 = nullptr; } else { f64 = (double*)sig.p; f32 = nullptr; }
-    BAMG_TRY(launch(pad_block_kernel, dim3(g1), dim3(256), 0, s, 1, rr, ld, (const double*)sg.as<double>(), f32, f64));
-    BAMG_TRY(launch(pad_block_kernel, dim3(g1), dim3(256), 0, s, 1, rr, ld, (const double*)sg.as<double>(),
-                    (float*)nullptr, sig64.as<double>()));
-  }
-  // bottom-up: interpolate and relax (Algorithm 1, last loop)
-  for (int k = l - 1; k >= 0; --k) {
-    Level& L = h->lv[k];
-    BAMG_TRY(spmm_block<T>(L.n, ld, L.Qt.r(), L.Qt.c(), L.Qt.vals<T>(), U[k + 1].as<T>(), U[k].as<T>(), s));
-    BAMG_TRY(spmm_block<T>(L.n, ld, L.P.r(), L.P.c(), L.P.vals<T>(), V[k + 1].as<T>(), V[k].as<T>(), s));
-    BAMG_TRY(relax_triplets<T>(h, k, U[k], V[k], sig, sig64, s));
-    tr.mark(s, "bottom-up relax", k);
-    U[k + 1].release();
-    V[k + 1].release();
+    int l = 0;
+    while (!is_coarsest(h, h->lv[l], l)) {
+      DevMem tU, tV;
+      size_t bytes = sizeof(T) * (size_t)h->lv[l].n * ld;
+      if (!learned) {
+        BAMG_TRY(tU.alloc(bytes, s));
+        BAMG_TRY(tV.alloc(bytes, s));
+      }
+      U.emplace_back();
+      V.emplace_back();
+      BAMG_TRY(coarsen_level<T>(h, l, U[l], V[l], U[l + 1], V[l + 1], tU, tV, scale, norms, rkd, sig, sig64,
+                                cyc > 0, s));
+      ++l;
+    }
+    // coarsest level: eq. generalized_eigenvalue and the pseudo-inverse
+    Trace tr;
+    Level& LL = h->lv[l];
+    int nL = LL.n;
+    h->nL = nL;
+    rr = r < nL ? r : nL;
+    DevMem Bd, Md, Nd, sg, Ud, Vd;
+    size_t nn = (size_t)nL * nL;
+    BAMG_TRY(Bd.alloc(sizeof(double) * nn, s));
+    BAMG_TRY(Md.alloc(sizeof(double) * nn, s));
+    BAMG_TRY(Nd.alloc(sizeof(double) * nn, s));
+    BAMG_TRY(sg.alloc(sizeof(double) * r, s));
+    BAMG_TRY(Ud.alloc(sizeof(double) * (size_t)nL * r, s));
+    BAMG_TRY(Vd.alloc(sizeof(double) * (size_t)nL * r, s));
+    BAMG_CUDA(cudaMemsetAsync(sg.p, 0, sizeof(double) * r, s));
+    BAMG_CUDA(cudaMemsetAsync(Ud.p, 0, sizeof(double) * (size_t)nL * r, s));
+    BAMG_CUDA(cudaMemsetAsync(Vd.p, 0, sizeof(double) * (size_t)nL * r, s));
+    BAMG_TRY(csr_to_dense(nL, LL.B.r(), LL.B.c(), LL.B.v(), Bd.as<double>(), s));
+    if (LL.M.empty()) {
+      std::vector<double> I(nn, 0.0);
+      for (int i = 0; i < nL; ++i) I[(size_t)i * nL + i] = 1.0;
+      BAMG_CUDA(cudaMemcpyAsync(Md.p, I.data(), sizeof(double) * nn, cudaMemcpyHostToDevice, s));
+      BAMG_CUDA(cudaMemcpyAsync(Nd.p, I.data(), sizeof(double) * nn, cudaMemcpyHostToDevice, s));
+      BAMG_CUDA(cudaStreamSynchronize(s));
+    } else {
+      BAMG_TRY(csr_to_dense(nL, LL.M.r(), LL.M.c(), LL.M.v(), Md.as<double>(), s));
+      BAMG_TRY(csr_to_dense(nL, LL.N.r(), LL.N.c(), LL.N.v(), Nd.as<double>(), s));
+    }
+    BAMG_TRY(h->Bpinv.alloc(sizeof(double) * nn, s));
+    // Ud/Vd are nL x rr row-major (rr <= r)
+    BAMG_TRY(coarsest_solve(h->mixed ? 1 : 0, nL, rr, Bd.as<double>(), Md.as<double>(), Nd.as<double>(),
+                            sg.as<double>(), Ud.as<double>(), Vd.as<double>(), h->Bpinv.as<double>(), s));
+    if (h->mixed) {
+      BAMG_TRY(h->Bpinv32.alloc(sizeof(float) * nn, s));
+      BAMG_TRY(convert<double, float>(nn, h->Bpinv.as<double>(), h->Bpinv32.as<float>(), s));
+    }
+    tr.mark(s, "coarsest solve", l);
+    if (learned) return learned_unwind(h, l, rr, Vd.as<double>(), sg.as<double>(), s);
+    // triplets into padded blocks
+    BAMG_TRY(U[l].alloc(sizeof(T) * (size_t)nL * ld, s));
+    BAMG_TRY(V[l].alloc(sizeof(T) * (size_t)nL * ld, s));
+    unsigned g = cdiv((long long)nL * ld, 256);
+    float* f32 = nullptr;
+    double* f64 = nullptr;
+    if (sizeof(T) == 4) f32 = (float*)U[l].p; else f64 = (double*)U[l].p;
+    BAMG_TRY(launch(pad_block_kernel, dim3(g), dim3(256), 0, s, nL, rr, ld, (const double*)Ud.as<double>(), f32, f64));
+    if (sizeof(T) == 4) f32 = (float*)V[l].p; else f64 = (double*)V[l].p;
+    BAMG_TRY(launch(pad_block_kernel, dim3(g), dim3(256), 0, s, nL, rr, ld, (const double*)Vd.as<double>(), f32, f64));
+    {
+      unsigned g1 = cdiv(ld, 256);
+      if (sizeof(T) == 4) { f32 = (float*)sig.p; f64 = nullptr; } else { f64 = (double*)sig.p; f32 = nullptr; }
+      BAMG_TRY(launch(pad_block_kernel, dim3(g1), dim3(256), 0, s, 1, rr, ld, (const double*)sg.as<double>(), f32, f64));
+      BAMG_TRY(launch(pad_block_kernel, dim3(g1), dim3(256), 0, s, 1, rr, ld, (const double*)sg.as<double>(),
+                      (float*)nullptr, sig64.as<double>()));
+    }
+    // bottom-up: interpolate and relax (Algorithm 1, last loop)
+    for (int k = l - 1; k >= 0; --k) {
+      Level& L = h->lv[k];
+      BAMG_TRY(spmm_block<T>(L.n, ld, L.Qt.r(), L.Qt.c(), L.Qt.vals<T>(), U[k + 1].as<T>(), U[k].as<T>(), s));
+      BAMG_TRY(spmm_block<T>(L.n, ld, L.P.r(), L.P.c(), L.P.vals<T>(), V[k + 1].as<T>(), V[k].as<T>(), s));
+      BAMG_TRY(relax_triplets<T>(h, k, U[k], V[k], sig, sig64, s));
+      tr.mark(s, "bottom-up relax", k);
+      U[k + 1].release();
+      V[k + 1].release();
+    }
   }
   // finest triplets, x^(0) = v of the smallest |sigma|
   h->sigma.assign(ld, 0.0);

@@ -34,6 +34,7 @@ struct Level {
   int nx = 0, ny = 0;
   int nc = 0;             // coarse size (0 on the coarsest level)
   int vec_g = 4;          // lanes per row in the vector kernels (chosen from nnz/row)
+  int nsafe = 0;          // rows with b_ii <= 0 whose Jacobi divisor is an l1 norm
   Csr B, Bt, M, N, P, Qt, Q, Pt;
   DevMem dinv, dinv32;
   DevMem cf, cmap, cpt, Jrp, Jci;

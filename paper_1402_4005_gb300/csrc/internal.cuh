@@ -55,8 +55,8 @@ bamg_status dense_gemv(int n, const T* A, const T* x, T* y, cudaStream_t s);
 template <typename S, typename D>
 bamg_status convert(size_t n, const S* a, D* b, cudaStream_t s);
 template <typename T>
-bamg_status diag_inv(int n, const int32_t* rp, const int32_t* ci, const double* va, T* dinv, int* bad_row,
-                     cudaStream_t s);
+bamg_status diag_inv(int n, const int32_t* rp, const int32_t* ci, const double* va, const int32_t* trp,
+                     const double* tva, T* dinv, int* bad_row, int* nsafe, cudaStream_t s);
 
 // hierarchy.cu: out[0] = sum x, out[1] = sum |x|
 bamg_status abs_sums(int n, const double* x, double* out, cudaStream_t s);

@@ -144,17 +144,28 @@ bamg_status scan_counts(const int32_t* counts, int32_t* out, int n, cudaStream_t
   return BAMG_OK;
 }
 
-__global__ void reduce_partials_kernel(const double* __restrict__ part, int nb, int K,
-                                       double* __restrict__ out) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
+// One block per output: each thread sums a strided subset of the nb
+// partials, then a fixed-order tree over the block, so the result is the
+// same on every run (the order depends on nb only).
+constexpr int kReduceThreads = 256;
+__global__ void __launch_bounds__(kReduceThreads) reduce_partials_kernel(const double* __restrict__ part, int nb,
+                                                                         int K, double* __restrict__ out) {
+  __shared__ double sh[kReduceThreads / 32];
+  const int k = blockIdx.x;
   double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += part[(size_t)b * K + k];
-  out[k] = s;
+  for (int b = threadIdx.x; b < nb; b += kReduceThreads) s += part[(size_t)b * K + k];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kReduceThreads / 32; ++w) t += sh[w];
+    out[k] = t;
+  }
 }
 
 bamg_status reduce_partials(const double* partial, int nb, int K, double* out, cudaStream_t s) {
-  return launch(reduce_partials_kernel, dim3(cdiv(K, 128)), dim3(128), 0, s, partial, nb, K, out);
+  return launch(reduce_partials_kernel, dim3(K), dim3(kReduceThreads), 0, s, partial, nb, K, out);
 }
 
 // ------------------------------------------------------------- B = I - A

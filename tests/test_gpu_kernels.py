@@ -286,6 +286,24 @@ def test_spgemm_exact_cancellation_keeps_slot(api):
     assert cva.cpu().tolist() == [0.0, 0.0]
 
 
+def test_jacobi_divisor_matches_oracle(api):
+    rng_ = np.random.default_rng(9)
+    n = 700
+    M = sp.random(n, n, density=0.01, random_state=11, format="csr")
+    M.data = rng_.uniform(-1, 1, M.nnz)
+    M = (M + sp.diags(rng_.uniform(-1, 2, n))).tocsr()      # about a third of the diagonal <= 0
+    M.sort_indices()
+    T = M.T.tocsr()
+    T.sort_indices()
+    want = 1.0 / operators.jacobi_divisor(M)
+    dev = lambda a, t: torch.from_numpy(np.ascontiguousarray(a)).to("cuda", t)
+    dinv, ns = api.bamg_step_jacobi_divisor(dev(M.indptr, torch.int32), dev(M.indices, torch.int32),
+                                            dev(M.data, torch.float64), dev(T.indptr, torch.int32),
+                                            dev(T.data, torch.float64))
+    assert ns == int((M.diagonal() <= 0).sum()) > 0
+    assert np.allclose(dinv.cpu().numpy(), want, rtol=1e-15, atol=0)
+
+
 # ------------------------------------------------------------------ A12
 def _coarse_problem(n_side=12):
     from oracle import setup as S

@@ -65,6 +65,31 @@ def test_hierarchy_structure_and_values(api, prec):
             assert err <= vtol, (l, nm, err)
 
 
+def test_second_setup_cycle_matches_oracle(api):
+    """Two bootstrap cycles (BAMG^2): the second rebuilds P, Q and the
+    coarse levels from the first cycle's finest triplets, with the
+    inhomogeneous first smoothing; same C/F structure, values at 1e-8."""
+    ch = cg.tandem(32)
+    kw = dict(r=8, max_levels=3, coarse_min=1, seed=2)
+    h = gpu_setup(api, ch, setup_cycles=2, **kw)
+    H = oracle_setup(ch, cycles=2, **kw)
+    assert h.num_levels == len(H.levels)
+    for l, lev in enumerate(H.levels):
+        g = h.level(l)
+        names = [("B", lev.B)]
+        if l < len(H.levels) - 1:
+            names += [("P", lev.P), ("Qt", lev.Qt)]
+        for nm, M in names:
+            rp, ci, va = csr_np(g[nm])
+            assert np.array_equal(rp, M.indptr) and np.array_equal(ci, M.indices), (l, nm)
+            err = np.abs(va - M.data).max() / np.abs(M.data).max()
+            assert err <= 1e-8, (l, nm, err)
+    x, info = api.bamg_solve(h, restart=20, tol=1e-10)
+    assert info["rel_res_1"] <= 1e-10
+    xo, _, _ = So.bamg_solve(H, tol=1e-10, restart=20)
+    assert np.abs(x.cpu().numpy() - xo).sum() <= 1e-8
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_config1_lattice_32(api, prec):
     """Weighted 32x32 lattice, r = 8, 2 levels, GMRES(20): closed form x ~ wdeg."""
@@ -173,3 +198,23 @@ def test_config2_tandem_256_full_size(api, prec):
     H = oracle_setup(ch, **kw)
     xo, _, _ = So.bamg_solve(H, tol=1e-12, restart=20, max_iter=400)
     assert np.abs(x - xo).sum() <= 1e-8
+
+
+def test_deep_tandem_hierarchy_uses_l1_divisor_rows(api):
+    """Tandem 1024 x 1024 with the default depth: a deep coarse level has
+    b_ii <= 0 rows; they take the l1 Jacobi divisor and the solve still
+    reaches the tolerance, FP32 and FP64 V-cycles agreeing to 1e-8."""
+    ch = cg.tandem(1024)
+    xs = {}
+    for prec in ("mixed", "fp64"):
+        h = gpu_setup(api, ch, r=16, seed=2, precision=prec)
+        rows = [h.level(l)["jacobi_l1_rows"] for l in range(h.num_levels)]
+        assert rows[0] == 0 and sum(rows) > 0, rows
+        x, info = api.bamg_solve(h, restart=20, tol=1e-10)
+        assert info["rel_res_1"] <= 1e-10
+        xs[prec] = x.cpu().numpy()
+        # x_(i,j) decays like (10/11)^i, far below the 1e-10 accuracy at the
+        # far edge: entries there may come out <= 0, within the 1e-8 1-norm
+        # accuracy of the whole vector (||x||_1 = 1)
+        assert np.abs(np.minimum(xs[prec], 0.0)).sum() <= 1e-8
+    assert np.abs(xs["mixed"] - xs["fp64"]).sum() <= 1e-8

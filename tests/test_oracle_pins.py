@@ -77,6 +77,22 @@ def test_jacobi_fixes_stationary_vector():
     assert np.abs(out - x).max() <= 1e-16
 
 
+def test_jacobi_divisor_is_the_diagonal_where_positive():
+    ch = cg.tandem(12)
+    B = operators.build_B(ch.csr())
+    assert np.array_equal(operators.jacobi_divisor(B), B.diagonal())
+
+
+def test_jacobi_divisor_l1_rows_by_hand():
+    # row 0: b_00 < 0, ||row||_1 = 0.7, ||col||_1 = 0.8; row 1: b_11 = 0,
+    # ||row||_1 = 0.4, ||col||_1 = 0.2; row 2: b_22 = 2 > 0 is kept
+    B = sp.csr_matrix(np.array([[-0.5, 0.2, 0.0], [0.3, 0.0, -0.1], [0.0, 0.0, 2.0]]))
+    assert np.allclose(operators.jacobi_divisor(B), [0.8, 0.4, 2.0], rtol=0, atol=1e-15)
+    Z = sp.csr_matrix(np.array([[1.0, 0.0], [0.0, 0.0]]))
+    with pytest.raises(ValueError):
+        operators.jacobi_divisor(Z)
+
+
 def test_multicolour_jacobi_equals_natural_and_gs_orders_converge():
     """Jacobi is order independent; both GS orders are valid smoothers."""
     ch = cg.tandem(9)
