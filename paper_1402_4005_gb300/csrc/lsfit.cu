@@ -8,8 +8,12 @@
 //
 // GPU mapping: one segment of LD lanes per fine point, lane k = test vector
 // k, so the r x c system lives one row per lane and every gather of x_j is a
-// coalesced LD-element row read.  Householder QR in FP64 with segment
-// shuffles, then back substitution.  The constraint is removed by the
+// coalesced LD-element row read.  Householder QR with segment shuffles, then
+// back substitution.  FP64 test vectors are fitted in FP64.  FP32 test
+// vectors (mixed precision) are fitted in FP32 first; a point whose
+// triangular factor has min |r_jj| < 1e-3 max |r_jj| (an ill-conditioned
+// neighbourhood) is flagged and fitted again in FP64 by a second launch that
+// skips every other point.  The constraint is removed by the
 // null-space method: p = 1/c + Z y with Z the last c-1 columns of the
 // Householder reflector H = I - 2 h h^T / h^T h, h = 1 + sqrt(c) e_1, which
 // maps the ones vector to a multiple of e_1 (so those columns are an
@@ -20,59 +24,62 @@ namespace bamg {
 
 constexpr int kCMax = 8;
 
-template <int S>
-__device__ inline double seg_sum(double v) {
+template <int S, typename R>
+__device__ inline R seg_sum(R v) {
 #pragma unroll
   for (int o = S / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-template <int S>
-__device__ inline double seg_get(double v, int src) {
+template <int S, typename R>
+__device__ inline R seg_get(R v, int src) {
   return __shfl_sync(0xffffffffu, v, src, S);
 }
 
-template <typename T, int S, bool CONSTR>
+// R: arithmetic type.  only != nullptr: fit just the points with only[i] != 0.
+// flag != nullptr: set flag[i] = 1 where min |r_jj| < cond_tol * max |r_jj|.
+template <typename T, typename R, int S, bool CONSTR>
 __global__ void __launch_bounds__(256)
 ls_fit_kernel(int n, int r, const int32_t* __restrict__ jrp, const int32_t* __restrict__ jci,
               const T* __restrict__ X, const double* __restrict__ w, double* __restrict__ out,
-              int* __restrict__ rankdef) {
+              int* __restrict__ rankdef, const int8_t* __restrict__ only, int8_t* __restrict__ flag,
+              R cond_tol) {
   constexpr int PPW = 32 / S;
   int lane = threadIdx.x & 31;
   int gw = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   int i = gw * PPW + lane / S;
   int k = lane % S;
-  bool valid = i < n;
+  bool valid = i < n && (only == nullptr || only[i] != 0);
   int c = valid ? jrp[i + 1] - jrp[i] : 0;
   int base = valid ? jrp[i] : 0;
   if (__reduce_max_sync(0xffffffffu, c) == 0) return;  // warp-uniform exit
 
   bool row_on = valid && c > 0 && k < r && !(CONSTR && k == 0);
-  double wk = row_on ? w[k] : 0.0;
-  double y = row_on ? wk * (double)X[(size_t)i * S + k] : 0.0;
-  double a[kCMax];
+  R wk = row_on ? R(w[k]) : R(0);
+  R y = row_on ? wk * R(X[(size_t)i * S + k]) : R(0);
+  R a[kCMax];
 #pragma unroll
   for (int m = 0; m < kCMax; ++m)
-    a[m] = (row_on && m < c) ? wk * (double)X[(size_t)jci[base + m] * S + k] : 0.0;
+    a[m] = (row_on && m < c) ? wk * R(X[(size_t)jci[base + m] * S + k]) : R(0);
 
   // Section 5 constraint: substitute p = 1/c + Z y~
   int cc = c;
-  double sqc = 0.0, hh = 1.0;
+  R sqc = 0, hh = 1;
   if (CONSTR && c >= 2) {
-    sqc = sqrt((double)c);
-    hh = 2.0 * c + 2.0 * sqc;
-    double inv_c = 1.0 / c;
-    double t = (1.0 + sqc) * a[0];
-    double sa = a[0];
+    sqc = sqrt(R(c));
+    hh = R(2) * R(c) + R(2) * sqc;
+    R inv_c = R(1) / R(c);
+    R t = (R(1) + sqc) * a[0];
+    R sa = a[0];
 #pragma unroll
     for (int m = 1; m < kCMax; ++m) {
       if (m < c) { t += a[m]; sa += a[m]; }
     }
     y -= sa * inv_c;
-    double g = 2.0 * t / hh;
+    R g = R(2) * t / hh;
 #pragma unroll
-    for (int m = 0; m < kCMax - 1; ++m) a[m] = (m < c - 1) ? a[m + 1] - g : 0.0;
-    a[kCMax - 1] = 0.0;
+    for (int m = 0; m < kCMax - 1; ++m) a[m] = (m < c - 1) ? a[m + 1] - g : R(0);
+    a[kCMax - 1] = R(0);
     cc = c - 1;
   } else if (CONSTR) {
     cc = 0;  // c == 1: p = 1
@@ -80,84 +87,108 @@ ls_fit_kernel(int n, int r, const int32_t* __restrict__ jrp, const int32_t* __re
   int ccw = __reduce_max_sync(0xffffffffu, cc);
 
   // Householder QR of the S x cc system, right-hand side y.
-  double rdiag[kCMax];
-  double rmax = 0.0;
+  R rdiag[kCMax];
+  R rmax = 0, rmin = R(1e30);
 #pragma unroll
   for (int j = 0; j < kCMax; ++j) {
-    rdiag[j] = 0.0;
+    rdiag[j] = R(0);
     if (j < ccw) {
       bool act = j < cc;
-      double xj = (k >= j) ? a[j] : 0.0;
-      double s2 = seg_sum<S>(xj * xj);
-      double ajj = seg_get<S>(a[j], j);
-      double nrm = sqrt(s2);
-      double alpha = ajj > 0.0 ? -nrm : nrm;
-      double v = (k == j) ? ajj - alpha : xj;
-      double vtv = 2.0 * nrm * (nrm + fabs(ajj));
-      bool go = act && nrm > 0.0;
-      double inv = go ? 2.0 / vtv : 0.0;
+      R xj = (k >= j) ? a[j] : R(0);
+      R s2 = seg_sum<S>(xj * xj);
+      R ajj = seg_get<S>(a[j], j);
+      R nrm = sqrt(s2);
+      R alpha = ajj > R(0) ? -nrm : nrm;
+      R v = (k == j) ? ajj - alpha : xj;
+      R vtv = R(2) * nrm * (nrm + fabs(ajj));
+      bool go = act && nrm > R(0);
+      R inv = go ? R(2) / vtv : R(0);
 #pragma unroll
       for (int m = j + 1; m < kCMax; ++m) {
         if (m < ccw) {
-          double d = seg_sum<S>(v * a[m]);
+          R d = seg_sum<S>(v * a[m]);
           if (go) a[m] -= v * (d * inv);
         }
       }
-      double dy = seg_sum<S>(v * y);
+      R dy = seg_sum<S>(v * y);
       if (go) y -= v * (dy * inv);
-      if (go) a[j] = (k == j) ? alpha : (k > j ? 0.0 : a[j]);
-      rdiag[j] = go ? alpha : 0.0;
+      if (go) a[j] = (k == j) ? alpha : (k > j ? R(0) : a[j]);
+      rdiag[j] = go ? alpha : R(0);
       rmax = fmax(rmax, fabs(rdiag[j]));
+      if (act) rmin = fmin(rmin, fabs(rdiag[j]));
     }
   }
   // back substitution; pivots below 1e-13 relative are dropped
-  double p[kCMax];
+  R p[kCMax];
   int dropped = 0;
 #pragma unroll
   for (int j = kCMax - 1; j >= 0; --j) {
-    p[j] = 0.0;
+    p[j] = R(0);
     if (j < ccw) {
-      double num = y;
+      R num = y;
 #pragma unroll
       for (int m = j + 1; m < kCMax; ++m) num -= a[m] * p[m];
-      bool keep = j < cc && fabs(rdiag[j]) > 1e-13 * rmax;
+      bool keep = j < cc && fabs(rdiag[j]) > R(1e-13) * rmax;
       if (j < cc && !keep) dropped = 1;
-      double pj = (k == j && keep) ? num / a[j] : 0.0;
+      R pj = (k == j && keep) ? num / a[j] : R(0);
       p[j] = seg_get<S>(pj, j);
     }
   }
   if (!valid || c == 0) return;
+  if (flag != nullptr && k == 0 && cc > 0 && rmin < cond_tol * rmax) flag[i] = 1;
+  // the constrained weights are assembled in FP64 from the null-space
+  // coordinates, so they sum to one to FP64 rounding in either precision
   double val;
   if (CONSTR) {
     if (c == 1) {
       val = 1.0;
     } else {
+      const double sq = sqrt((double)c), h2 = 2.0 * c + 2.0 * sq;
       double sy = 0.0;
 #pragma unroll
-      for (int m = 0; m < kCMax - 1; ++m) sy += (m < c - 1) ? p[m] : 0.0;
-      double g = 2.0 * sy / hh;
+      for (int m = 0; m < kCMax - 1; ++m) sy += (m < c - 1) ? (double)p[m] : 0.0;
+      double g = 2.0 * sy / h2;
       double ym = 0.0;
 #pragma unroll
-      for (int m = 1; m < kCMax; ++m) if (m == k) ym = p[m - 1];
-      val = 1.0 / c + (k == 0 ? -(1.0 + sqc) * g : ym - g);
+      for (int m = 1; m < kCMax; ++m) if (m == k) ym = (double)p[m - 1];
+      val = 1.0 / c + (k == 0 ? -(1.0 + sq) * g : ym - g);
     }
   } else {
     val = 0.0;
 #pragma unroll
-    for (int m = 0; m < kCMax; ++m) if (m == k) val = p[m];
+    for (int m = 0; m < kCMax; ++m) if (m == k) val = (double)p[m];
   }
   if (k < c) out[base + k] = val;
   if (k == 0 && dropped) atomicAdd(rankdef, 1);
 }
 
+template <typename T, typename R, int S>
+static bamg_status ls_fit_launch(int n, int r, const int32_t* J_rp, const int32_t* J_ci, const T* X,
+                                 const double* w, int constrained, double* out, int* rankdef, const int8_t* only,
+                                 int8_t* flag, cudaStream_t s) {
+  constexpr int PPW = 32 / S;
+  unsigned grid = cdiv(n, 8 * PPW);
+  const R tol = R(1e-3);
+  if (constrained)
+    return launch(ls_fit_kernel<T, R, S, true>, dim3(grid), dim3(256), 0, s, n, r, J_rp, J_ci, X, w, out, rankdef,
+                  only, flag, tol);
+  return launch(ls_fit_kernel<T, R, S, false>, dim3(grid), dim3(256), 0, s, n, r, J_rp, J_ci, X, w, out, rankdef,
+                only, flag, tol);
+}
+
 template <typename T, int S>
 static bamg_status ls_fit_s(int n, int r, const int32_t* J_rp, const int32_t* J_ci, const T* X,
                             const double* w, int constrained, double* out, int* rankdef, cudaStream_t s) {
-  constexpr int PPW = 32 / S;
-  unsigned grid = cdiv(n, 8 * PPW);
-  if (constrained)
-    return launch(ls_fit_kernel<T, S, true>, dim3(grid), dim3(256), 0, s, n, r, J_rp, J_ci, X, w, out, rankdef);
-  return launch(ls_fit_kernel<T, S, false>, dim3(grid), dim3(256), 0, s, n, r, J_rp, J_ci, X, w, out, rankdef);
+  if (sizeof(T) == 8)
+    return ls_fit_launch<T, double, S>(n, r, J_rp, J_ci, X, w, constrained, out, rankdef, nullptr, nullptr, s);
+  // FP32 pass, then FP64 on the flagged (ill-conditioned) points only
+  DevMem flag;
+  BAMG_TRY(flag.alloc((size_t)n, s));
+  BAMG_CUDA(cudaMemsetAsync(flag.p, 0, (size_t)n, s));
+  BAMG_TRY(ls_fit_launch<T, float, S>(n, r, J_rp, J_ci, X, w, constrained, out, rankdef, nullptr,
+                                      flag.as<int8_t>(), s));
+  return ls_fit_launch<T, double, S>(n, r, J_rp, J_ci, X, w, constrained, out, rankdef,
+                                     (const int8_t*)flag.as<int8_t>(), nullptr, s);
 }
 
 template <typename T>

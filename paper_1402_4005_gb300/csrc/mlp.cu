@@ -22,7 +22,6 @@
 
 #include <algorithm>
 #include <atomic>
-#include <mutex>
 #include <cmath>
 #include <vector>
 
@@ -449,20 +448,6 @@ __global__ void cf_count_kernel(int n, const int8_t* __restrict__ cf, int32_t* _
 // ============================================================ host side
 static size_t fwd_smem() { return sizeof(MlpSmem) + kMlpWarps * sizeof(WarpTile); }
 
-// The dynamic shared-memory limit of a kernel is raised once per device
-// (setups may run concurrently on several host threads).
-static bamg_status raise_smem(const void* fn, size_t bytes, std::atomic<uint64_t>& done) {
-  int dev = 0;
-  BAMG_CUDA(cudaGetDevice(&dev));
-  uint64_t bit = 1ull << (dev & 63);
-  if (done.load() & bit) return BAMG_OK;
-  static std::mutex mu;
-  std::lock_guard<std::mutex> lock(mu);
-  if (done.load() & bit) return BAMG_OK;
-  BAMG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  done.fetch_or(bit);
-  return BAMG_OK;
-}
 static std::atomic<uint64_t> g_fwd_attr{0}, g_grad_attr{0};
 static size_t grad_smem() {
   return sizeof(MlpSmem) + sizeof(GradSmem) + kMlpWarps * (sizeof(WarpTile) + sizeof(BackTile));
@@ -471,7 +456,8 @@ static size_t grad_smem() {
 bamg_status mlp_forward(int M, const float* P, const void* X, float* Y, cudaStream_t s) {
   if (M <= 0) return BAMG_OK;
   size_t sm = fwd_smem();
-  BAMG_TRY(raise_smem((const void*)mlp_forward_kernel, sm, g_fwd_attr));
+  int max_dyn = 0;
+  BAMG_TRY(allow_max_smem((const void*)mlp_forward_kernel, g_fwd_attr, &max_dyn));
   int tiles = (M + 15) / 16;
   int grid = (int)cdiv(tiles, kMlpWarps);
   if (grid > 8 * num_sms()) grid = 8 * num_sms();
@@ -483,7 +469,8 @@ bamg_status mlp_grad(int M, float inv_count, const float* P, const void* X, cons
                      float* G, float* loss, cudaStream_t s) {
   if (M <= 0) return BAMG_OK;
   size_t sm = grad_smem();
-  BAMG_TRY(raise_smem((const void*)mlp_grad_kernel, sm, g_grad_attr));
+  int max_dyn = 0;
+  BAMG_TRY(allow_max_smem((const void*)mlp_grad_kernel, g_grad_attr, &max_dyn));
   int tiles = (M + 15) / 16;
   int grid = (int)cdiv(tiles, kMlpWarps * 4);   // each warp takes a few tiles: fewer global gradient adds
   if (grid > 2 * num_sms()) grid = 2 * num_sms();

@@ -239,8 +239,9 @@ static bamg_status run_rows(int m, const SpgemmPlan& pl, const int32_t* arp, con
                   crp, cci, cva));
   if (pl.maxprod > kWarpCap) {
     size_t sm = big_smem(NUMERIC);
-    BAMG_CUDA(cudaFuncSetAttribute(spgemm_block_kernel<NUMERIC>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    static std::atomic<uint64_t> attr_done{0};
+    int max_dyn = 0;
+    BAMG_TRY(allow_max_smem((const void*)spgemm_block_kernel<NUMERIC>, attr_done, &max_dyn));
     BAMG_TRY(launch(spgemm_block_kernel<NUMERIC>, dim3(m), dim3(kBigThreads), sm, s, m,
                     (const int32_t*)pl.prod.as<int32_t>(), arp, aci, ava, brp, bci, bva, ccount, crp,
                     cci, cva));
