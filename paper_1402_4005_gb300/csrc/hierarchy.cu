@@ -102,16 +102,10 @@ static bamg_status csr_transpose(const Csr& A, Csr& T, cudaStream_t s) {
 }
 
 static bamg_status csr_product(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
-  DevMem rp;
-  BAMG_TRY(rp.alloc(sizeof(int32_t) * (A.rows + 1), s));
   int64_t nnz = 0;
-  BAMG_TRY(spgemm_symbolic(A.rows, A.r(), A.c(), B.r(), B.c(), rp.as<int32_t>(), &nnz, s));
+  BAMG_TRY(spgemm(A.rows, A.r(), A.c(), A.v(), B.r(), B.c(), B.v(), C.rp, C.ci, C.va, &nnz, s));
   C.rows = A.rows; C.cols = B.cols; C.nnz = (int)nnz;
-  C.rp = std::move(rp);
-  BAMG_TRY(C.ci.alloc(sizeof(int32_t) * (nnz > 0 ? nnz : 1), s));
-  BAMG_TRY(C.va.alloc(sizeof(double) * (nnz > 0 ? nnz : 1), s));
-  return spgemm_numeric(A.rows, A.r(), A.c(), A.v(), B.r(), B.c(), B.v(), C.r(), C.ci.as<int32_t>(),
-                        C.va.as<double>(), s);
+  return BAMG_OK;
 }
 
 // B^T, 1/diag(B) (Jacobi needs b_ii > 0: Section 3 / coarse levels), lanes.

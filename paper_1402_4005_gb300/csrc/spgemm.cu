@@ -8,6 +8,9 @@
 // Every structural product keeps its slot (no cancellation drops), which is
 // the pattern convention of the Petrov-Galerkin products Q B P, Q M Q^T and
 // P^T N P (Section 3, Algorithm 1).
+#include <atomic>
+#include <cstring>
+
 #include "internal.cuh"
 
 namespace bamg {
@@ -17,9 +20,10 @@ constexpr int kBlockCap = 8192;    // products per row handled by one block
 constexpr int kWarpsPerBlock = 4;
 constexpr int kBigThreads = 256;
 
+// stats[0] = largest row product count, stats[1..2] = 64-bit total
 __global__ void count_products_kernel(int m, const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
                                       const int32_t* __restrict__ brp, int32_t* __restrict__ prod,
-                                      int* __restrict__ maxprod) {
+                                      int* __restrict__ stats) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
   long long c = 0;
@@ -29,7 +33,8 @@ __global__ void count_products_kernel(int m, const int32_t* __restrict__ arp, co
   }
   int ci = c > INT32_MAX ? INT32_MAX : (int)c;
   prod[i] = ci;
-  atomicMax(maxprod, ci);
+  atomicMax(stats, ci);
+  atomicAdd(reinterpret_cast<unsigned long long*>(stats + 2), (unsigned long long)c);
 }
 
 template <int G>
@@ -152,7 +157,12 @@ __device__ void row_product(int i, int lo, int hi, const int32_t* __restrict__ p
     }
     __syncthreads();
     incl = sc[lane];
+    if (ccount != nullptr && lane == 0) ccount[i] = sc[G - 1];
     __syncthreads();
+  }
+  if constexpr (G == 32) {
+    const int tot = __shfl_sync(0xffffffffu, incl, 31);
+    if (ccount != nullptr && lane == 0) ccount[i] = tot;
   }
   int pos = incl - local;
   int base = crp[i];
@@ -204,22 +214,32 @@ spgemm_block_kernel(int m, const int32_t* __restrict__ prod, const int32_t* __re
 }
 
 struct SpgemmPlan {
-  DevMem prod, maxp;
+  DevMem prod, stats;
   int maxprod = 0;
+  long long total = 0;
 };
 
 static bamg_status plan_products(int m, const int32_t* arp, const int32_t* aci, const int32_t* brp,
                                  SpgemmPlan& pl, cudaStream_t s) {
   BAMG_TRY(pl.prod.alloc(sizeof(int32_t) * (m + 1), s));
-  BAMG_TRY(pl.maxp.alloc(sizeof(int), s));
-  BAMG_CUDA(cudaMemsetAsync(pl.maxp.p, 0, sizeof(int), s));
+  BAMG_TRY(pl.stats.alloc(4 * sizeof(int), s));
+  BAMG_CUDA(cudaMemsetAsync(pl.stats.p, 0, 4 * sizeof(int), s));
   BAMG_TRY(launch(count_products_kernel, dim3(cdiv(m, 256)), dim3(256), 0, s, m, arp, aci, brp,
-                  pl.prod.as<int32_t>(), pl.maxp.as<int>()));
-  BAMG_CUDA(cudaMemcpyAsync(&pl.maxprod, pl.maxp.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+                  pl.prod.as<int32_t>(), pl.stats.as<int>()));
+  int h[4];
+  BAMG_CUDA(cudaMemcpyAsync(h, pl.stats.p, sizeof(h), cudaMemcpyDeviceToHost, s));
   BAMG_CUDA(cudaStreamSynchronize(s));
+  pl.maxprod = h[0];
+  unsigned long long t = 0;
+  std::memcpy(&t, h + 2, sizeof(t));
+  pl.total = (long long)t;
   if (pl.maxprod > kBlockCap) {
     set_error("sparse product row with %d products exceeds the %d limit", pl.maxprod, kBlockCap);
     return BAMG_ERR_NUMERIC;
+  }
+  if (pl.total > INT32_MAX) {
+    set_error("sparse product with %lld products exceeds the int32 index range", pl.total);
+    return BAMG_ERR_UNSUPPORTED;
   }
   return BAMG_OK;
 }
@@ -258,6 +278,47 @@ bamg_status spgemm_symbolic(int m, const int32_t* arp, const int32_t* aci, const
   BAMG_TRY(run_rows<false>(m, pl, arp, aci, nullptr, brp, bci, nullptr, cnt.as<int32_t>(), nullptr,
                            nullptr, nullptr, s));
   return scan_counts(cnt.as<int32_t>(), crp, m, s, nnz_host);
+}
+
+__global__ void compact_rows_kernel(int m, const int32_t* __restrict__ src_rp, const int32_t* __restrict__ cnt,
+                                    const int32_t* __restrict__ scol, const double* __restrict__ sval,
+                                    const int32_t* __restrict__ crp, int32_t* __restrict__ cci,
+                                    double* __restrict__ cva) {
+  const int lane = threadIdx.x & 31;
+  const int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (i >= m) return;
+  const int a = src_rp[i], b = crp[i], c = cnt[i];
+  for (int t = lane; t < c; t += 32) {
+    cci[b + t] = scol[a + t];
+    cva[b + t] = sval[a + t];
+  }
+}
+
+// One expansion pass: each row's sorted, summed entries go to a scratch
+// slot of its product count, then the rows are packed into C.  Two host
+// reads: the product statistics (buffer sizes) and nnz(C).
+bamg_status spgemm(int m, const int32_t* arp, const int32_t* aci, const double* ava, const int32_t* brp,
+                   const int32_t* bci, const double* bva, DevMem& crp, DevMem& cci, DevMem& cva, int64_t* nnz_host,
+                   cudaStream_t s) {
+  SpgemmPlan pl;
+  BAMG_TRY(plan_products(m, arp, aci, brp, pl, s));
+  DevMem off, cnt, scol, sval;
+  BAMG_TRY(off.alloc(sizeof(int32_t) * (m + 1), s));
+  BAMG_TRY(scan_counts(pl.prod.as<int32_t>(), off.as<int32_t>(), m, s, nullptr));
+  BAMG_TRY(cnt.alloc(sizeof(int32_t) * (m + 1), s));
+  BAMG_TRY(scol.alloc(sizeof(int32_t) * (pl.total > 0 ? pl.total : 1), s));
+  BAMG_TRY(sval.alloc(sizeof(double) * (pl.total > 0 ? pl.total : 1), s));
+  BAMG_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * (m + 1), s));
+  BAMG_TRY(run_rows<true>(m, pl, arp, aci, ava, brp, bci, bva, cnt.as<int32_t>(), off.as<int32_t>(),
+                          scol.as<int32_t>(), sval.as<double>(), s));
+  BAMG_TRY(crp.alloc(sizeof(int32_t) * (m + 1), s));
+  BAMG_TRY(scan_counts(cnt.as<int32_t>(), crp.as<int32_t>(), m, s, nnz_host));
+  BAMG_TRY(cci.alloc(sizeof(int32_t) * (*nnz_host > 0 ? *nnz_host : 1), s));
+  BAMG_TRY(cva.alloc(sizeof(double) * (*nnz_host > 0 ? *nnz_host : 1), s));
+  return launch(compact_rows_kernel, dim3(cdiv((long long)m * 32, 256)), dim3(256), 0, s, m,
+                (const int32_t*)off.as<int32_t>(), (const int32_t*)cnt.as<int32_t>(),
+                (const int32_t*)scol.as<int32_t>(), (const double*)sval.as<double>(),
+                (const int32_t*)crp.as<int32_t>(), cci.as<int32_t>(), cva.as<double>());
 }
 
 bamg_status spgemm_numeric(int m, const int32_t* arp, const int32_t* aci, const double* ava,
