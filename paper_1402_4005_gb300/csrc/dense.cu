@@ -290,29 +290,80 @@ __device__ void row_solve(const DenseArgs<T>& A, T* F, T* F2, int split, T* X, i
   }
 }
 
+// Solves in place, for the block's own vectors z_c (c = b mod NB, c in
+// [c_lo, c_hi), stored as the own rows c of the row-owned array Z, length
+// n), L z = z (UPPER = false: forward substitution) or L^T z = z (UPPER:
+// backward), with L lower triangular stored in the rows of F (row t holds
+// L[t][0..t] and L^T[t][t..n-1]).  Rows of F are read in chunks of kStage
+// rows into the shared staging buffer (any block's rows); then every vector
+// advances with no cluster barrier: a group of g lanes per vector forms the
+// dot product and its leader divides by L[t][t].
+constexpr int kStage = 8;
+template <bool SM, bool UPPER, typename T>
+__device__ void local_solve(const DenseArgs<T>& A, T* F, T* Z, int c_lo, int c_hi, T* stage) {
+  const int n = A.n, NB = nblocks<SM>(A), b = blockIdx.x;
+  const int v0 = c_lo <= b ? 0 : (c_lo - b + NB - 1) / NB;        // first own c >= c_lo
+  const int nvec = b < c_hi ? max(0, (c_hi - b + NB - 1) / NB - v0) : 0;
+  int g = 32;                                     // lanes per vector (power of two)
+  while (g > 1 && nvec * g > (int)blockDim.x) g >>= 1;
+  const int grp = threadIdx.x / g, gl = threadIdx.x % g;
+  const int ngrp = blockDim.x / g;
+  const int vmax = ((nvec + ngrp - 1) / ngrp) * ngrp;
+  for (int k0 = 0; k0 < n; k0 += kStage) {
+    const int rows = min(kStage, n - k0);
+    const int c0 = UPPER ? n - k0 - rows : k0;     // first row of the chunk
+    for (int e = threadIdx.x; e < rows * n; e += blockDim.x) {
+      const int t = c0 + e / n, q = e % n;
+      if (UPPER ? q >= t : q <= t) stage[e] = rd<SM>(any<SM>(A, F, t, n) + q);
+    }
+    __syncthreads();
+    for (int step = 0; step < rows; ++step) {
+      const int t = UPPER ? c0 + rows - 1 - step : c0 + step;
+      const T* lt = stage + (size_t)(t - c0) * n;
+      for (int v = grp; v < vmax; v += ngrp) {
+        const bool act = v < nvec;
+        T* z = act ? own<SM>(A, Z, b + (v0 + v) * NB, n) : nullptr;
+        T acc = 0;
+        if (act) {
+          if (UPPER)
+            for (int q = t + 1 + gl; q < n; q += g) acc += lt[q] * z[q];
+          else
+            for (int q = gl; q < t; q += g) acc += lt[q] * z[q];
+        }
+        for (int o = g / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, g);
+        if (act && gl == 0) z[t] = (z[t] - acc) / lt[t];
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // C = L_M^{-1} B L_N^{-T} in S1; W = C in S2 for the bidiagonalization.
+// X = L_M^{-1} B column by column (block b solves the columns j = b mod NB,
+// kept as the own rows j of S2 = X^T), then X's rows gathered into S1, then
+// each row of C solves L_N c^T = x^T: two local solves, two barriers.
 template <bool SM, typename T>
 __device__ void form_C(const DenseArgs<T>& A, T* sv) {
   const int n = A.n, NB = nblocks<SM>(A), b = blockIdx.x;
-  for (int i = b; i < n; i += NB) {
+  // staging rows: the block's own publication buffer under the shared policy
+  // (no block publishes during the local solves), its dynamic shared memory
+  // after the 3n scratch otherwise (the global publication buffer is common)
+  T* stage = SM ? A.pub : sv + 3 * n;
+  for (int j = b; j < n; j += NB) {                 // own rows j of S2: column j of B
+    T* x = own<SM>(A, A.S2, j, n);
+    for (int t = threadIdx.x; t < n; t += blockDim.x) x[t] = T(A.B[(size_t)t * n + j]);
+  }
+  __syncthreads();
+  local_solve<SM, false>(A, A.LM, A.S2, 0, n, stage);   // S2 rows: columns of X
+  csync();
+  for (int i = b; i < n; i += NB) {                 // X rows into S1
     T* x = own<SM>(A, A.S1, i, n);
-    for (int j = threadIdx.x; j < n; j += blockDim.x) x[j] = T(A.B[(size_t)i * n + j]);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) x[j] = rd<SM>(any<SM>(A, A.S2, j, n) + i);
   }
   __syncthreads();
-  row_solve<SM, true>(A, A.LM, (T*)nullptr, n, A.S1, n, n, sv);        // X = L_M^{-1} B
-  for (int i = b; i < n; i += NB) {                                     // W = X^T (own rows)
-    T* w = own<SM>(A, A.S2, i, n);
-    for (int j = threadIdx.x; j < n; j += blockDim.x) w[j] = rd<SM>(any<SM>(A, A.S1, j, n) + i);
-  }
-  __syncthreads();
-  // the barriers of this solve also order every block's reads of X before
-  // the writes of C into the same rows below
-  row_solve<SM, true>(A, A.LN, (T*)nullptr, n, A.S2, n, n, sv);        // W = C^T
-  for (int i = b; i < n; i += NB) {                                     // C = W^T
-    T* c = own<SM>(A, A.S1, i, n);
-    for (int j = threadIdx.x; j < n; j += blockDim.x) c[j] = rd<SM>(any<SM>(A, A.S2, j, n) + i);
-  }
-  csync();  // all of W read before any block overwrites its rows
+  local_solve<SM, false>(A, A.LN, A.S1, 0, n, stage);   // S1 rows: rows of C
+  csync();  // every block done reading S2 before it becomes W
   for (int i = b; i < n; i += NB) {
     T* w = own<SM>(A, A.S2, i, n);
     const T* c = own<SM>(A, A.S1, i, n);
@@ -564,16 +615,26 @@ __device__ void gk_solve(int m, const T* rdd, const T* du, const T* du2, const T
 // iteration on the Golub-Kahan tridiagonal, orthogonalising each member
 // against the earlier ones.
 template <bool SM, typename T>
-__device__ void bidiag_triplets(const DenseArgs<T>& A) {
+__device__ void bidiag_triplets(const DenseArgs<T>& A, T* sv) {
   const int n = A.n, r = A.r, m = 2 * n;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   // consecutive values on different blocks: one warp per SM while r <= NB,
   // so the per-value work does not share an SM's FP64 units
   const int gw = w * gridDim.x + blockIdx.x, GW = gridDim.x * kWarps;
-  const T gmax = gk_bound(A.d, A.e, n);
+  // the bidiagonal and the reflector scalars, staged in shared memory
+  T* d = sv;
+  T* e = sv + n;
+  T* taup = sv + 2 * n;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    d[k] = __ldcg(A.d + k);
+    e[k] = __ldcg(A.e + k);
+    taup[k] = __ldcg(A.taup + k);
+  }
+  __syncthreads();
+  const T gmax = gk_bound(d, e, n);
   const T pivmin = T(Eps<T>::tiny) * fmax(T(1), gmax * gmax);
   for (int a = gw; a < r; a += GW) {
-    T s = gk_sigma(A.d, A.e, n, a, gmax, pivmin);
+    T s = gk_sigma(d, e, n, a, gmax, pivmin);
     if (lane == 0) A.sig[a] = s;
   }
   csync();
@@ -589,7 +650,7 @@ __device__ void bidiag_triplets(const DenseArgs<T>& A) {
       T* base = A.z + (size_t)a * 6 * m;
       T *dd = base, *du = base + m, *du2 = base + 2 * m, *dl = base + 3 * m, *pv = base + 4 * m;
       T* zv = base + 5 * m;
-      if (lane == 0) gk_factor(A.d, A.e, m, __ldcg(A.sig + a), pert, dd, du, du2, dl, pv);
+      if (lane == 0) gk_factor(d, e, m, __ldcg(A.sig + a), pert, dd, du, du2, dl, pv);
       for (int k = lane; k < m; k += 32)
         zv[k] = T(1) + T(0.5) * T((unsigned)(k * 2654435761u) % 1000u) / T(1000) + T(a);
       __syncwarp();
@@ -622,14 +683,31 @@ __device__ void bidiag_triplets(const DenseArgs<T>& A) {
   csync();
   for (int a = gw; a < r; a += GW) {              // v~ = P_B v_D, last reflector first
     T* y = A.vb + (size_t)a * n;
+    constexpr int kReg = 8;                       // reflector entries held per lane
     for (int k = n - 2; k >= 0; --k) {
-      const T tau = __ldcg(A.taup + k);
+      const T tau = taup[k];
       if (tau == T(0)) continue;
       const T* p = any<SM>(A, A.S3, k, n);
+      T pr[kReg];
       T s = 0;
-      for (int j = k + 1 + lane; j < n; j += 32) s += rd<SM>(p + j) * y[j];
+#pragma unroll
+      for (int q = 0; q < kReg; ++q) {            // loads issued together
+        const int j = k + 1 + lane + 32 * q;
+        pr[q] = j < n ? rd<SM>(p + j) : T(0);
+      }
+#pragma unroll
+      for (int q = 0; q < kReg; ++q) {
+        const int j = k + 1 + lane + 32 * q;
+        if (j < n) s += pr[q] * y[j];
+      }
+      for (int j = k + 1 + lane + 32 * kReg; j < n; j += 32) s += rd<SM>(p + j) * y[j];
       s = warp_sum(s) * tau;
-      for (int j = k + 1 + lane; j < n; j += 32) y[j] -= s * rd<SM>(p + j);
+#pragma unroll
+      for (int q = 0; q < kReg; ++q) {
+        const int j = k + 1 + lane + 32 * q;
+        if (j < n) y[j] -= s * pr[q];
+      }
+      for (int j = k + 1 + lane + 32 * kReg; j < n; j += 32) y[j] -= s * rd<SM>(p + j);
       __syncwarp();
     }
   }
@@ -852,9 +930,9 @@ __device__ void pseudo_inverse(const DenseArgs<T>& A, T* sv) {
 }
 
 // Shared-policy layout of one block's dynamic shared memory, in elements of
-// T after the 2n scratch vector: pub, part, LM, LN, S1, S2, S3, R, then pcol.
+// T after the 3n scratch vector: pub, part, LM, LN, S1, S2, S3, R, then pcol.
 __host__ __device__ inline size_t smem_elems(int n, int r, int RP) {
-  return (size_t)2 * n + (size_t)8 * n + 64 + part_stride(n) + (size_t)5 * RP * n + (size_t)RP * 2 * r;
+  return (size_t)3 * n + (size_t)8 * n + 64 + part_stride(n) + (size_t)5 * RP * n + (size_t)RP * 2 * r;
 }
 
 template <typename T, bool SM>
@@ -865,7 +943,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) coarsest_kernel(DenseArgs<T>
   const int n = A.n;
   A.NB = gridDim.x;
   if constexpr (SM) {
-    T* p = sv + 2 * n;
+    T* p = sv + 3 * n;
     A.pub = p;  p += 8 * n + 64;
     A.part = p; p += part_stride(n);
     A.LM = p;   p += (size_t)A.RP * n;
@@ -884,7 +962,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) coarsest_kernel(DenseArgs<T>
   if (b0) A.ctl->tp[2] = gtimer();
   bidiagonalize<SM>(A, sv, red);
   if (b0) A.ctl->tp[3] = gtimer();
-  bidiag_triplets<SM>(A);
+  bidiag_triplets<SM>(A, sv);
   if (b0) A.ctl->tp[4] = gtimer();
   triplets<SM>(A, sv, red);
   if (b0) A.ctl->tp[5] = gtimer();
@@ -961,7 +1039,14 @@ static bamg_status coarsest_t(int n, int r, const double* B, const double* M, co
     a.pub = p; p += 8 * (size_t)n + 64;
     a.part = p;
     a.pcol = glob.as<int>();
-    cfg.dynamicSmemBytes = sizeof(T) * 2 * (size_t)n + 64;
+    cfg.dynamicSmemBytes = sizeof(T) * (3 + kStage) * (size_t)n + 64;
+    static std::atomic<uint64_t> gl_attr{0};
+    int gl_max = 0;
+    BAMG_TRY(allow_max_smem((const void*)kgl, gl_attr, &gl_max));
+    if (cfg.dynamicSmemBytes > (size_t)gl_max) {
+      set_error("coarsest level of %d points needs %zu bytes of shared memory", n, cfg.dynamicSmemBytes);
+      return BAMG_ERR_UNSUPPORTED;
+    }
     csize = max_cluster((const void*)kgl, cfg, kMaxNB);
     if (csize < 1) csize = 1;
     a.RP = (n + csize - 1) / csize;
