@@ -15,9 +15,12 @@
 // makes u proportional to 1 (Section 5).
 //
 // Section 3, eq. coarse_grid_correction: the V-cycle applies the
-// pseudo-inverse of B.  With the unit null vectors e = 1/sqrt(n) (left) and w
-// (right), B^+ = (B + e w^T)^{-1} - w e^T; the inverse is Gauss-Jordan
-// elimination with partial pivoting.
+// pseudo-inverse of B.  With e = 1/sqrt(n) 1 (the unit left null vector,
+// 1^T B = 0) the matrix B + e e^T is nonsingular and X = (B + e e^T)^{-1}
+// satisfies e^T X = e^T and X e = w / (e^T w) for the right null vector w;
+// then B^+ = (I - w w^T) X (I - e e^T) (B B^+ = I - e e^T, B^+ B = I - w w^T).
+// None of this needs the singular triplets, so X (Gauss-Jordan with partial
+// pivoting) runs in a second cluster concurrently with the triplets.
 //
 // Mapping: one cluster of up to 16 blocks.  Rows of every n x n matrix are
 // owned cyclically (row i by block i mod NB) and only their owner writes
@@ -824,10 +827,10 @@ __device__ void triplets(const DenseArgs<T>& A, T* sv, T* red) {
 }
 
 // ------------------------------------------------------------ pseudo-inverse
-// B^+ = (B + e w^T)^{-1} - w e^T by Gauss-Jordan on [B + e w^T | I] with
-// partial pivoting and no row exchanges: the row chosen for column k keeps
-// its place and records k; at the end row i holds row pcol[i] of the inverse.
-// The tableau G (2n per row) occupies the storage of S2 and S3.
+// X = (B + e e^T)^{-1} by Gauss-Jordan on [B + e e^T | I] with partial
+// pivoting and no row exchanges: the row chosen for column k keeps its place
+// and records k; at the end row i holds row pcol[i] of X.  The tableau G
+// (2n per row) is the row-owned array S2.
 template <bool SM, typename T>
 __device__ void gj_candidate(const DenseArgs<T>& A, int k) {
   const int n = A.n, n2 = 2 * n, NB = nblocks<SM>(A), b = blockIdx.x;
@@ -857,16 +860,18 @@ __device__ void gj_candidate(const DenseArgs<T>& A, int k) {
   }
 }
 
+// sv: 2n scratch; A.unull: global n-vector for X e (any values on entry).
 template <bool SM, typename T>
-__device__ void pseudo_inverse(const DenseArgs<T>& A, T* sv) {
+__device__ void pseudo_inverse(const DenseArgs<T>& A, T* sv, T* red) {
   const int n = A.n, n2 = 2 * n, NB = nblocks<SM>(A), b = blockIdx.x;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const T e = T(1) / sqrt(T(n));
+  const T ee = T(1) / T(n);                      // every entry of e e^T
   T* G = A.S2;
   for (int i = b; i < n; i += NB) {
     T* gi = own<SM>(A, G, i, n2);
     for (int j = threadIdx.x; j < n2; j += blockDim.x)
-      gi[j] = j < n ? T(A.B[(size_t)i * n + j]) + e * __ldcg(A.unull + j) : (j - n == i ? T(1) : T(0));
+      gi[j] = j < n ? T(A.B[(size_t)i * n + j]) + ee : (j - n == i ? T(1) : T(0));
     if (threadIdx.x == 0) *own_pcol<SM>(A, i) = -1;
   }
   __syncthreads();
@@ -921,11 +926,45 @@ __device__ void pseudo_inverse(const DenseArgs<T>& A, T* sv) {
     if (k + 1 < n) gj_candidate<SM>(A, k + 1);
     csync();
   }
+  // s = X e (s_c = e * row sum of X's row c), w = s / ||s||
+  T* part = part_w<SM>(A);
+  T* xs = A.unull;
+  T ps2 = 0;
   for (int i = b; i < n; i += NB) {
     const int c = *own_pcol<SM>(A, i);
     const T* gi = own<SM>(A, G, i, n2);
+    T t = 0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) t += gi[n + j];
+    t = block_sum(t, red) * e;
+    if (threadIdx.x == 0) {
+      xs[c] = t;
+      ps2 += t * t;
+    }
+  }
+  if (threadIdx.x == 0) part[n] = ps2;
+  __syncthreads();
+  csync();
+  const T nrm = sqrt(part_sum<SM>(A, n));
+  // partial w^T X over the own rows
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    T t = 0;
+    for (int i = b; i < n; i += NB) {
+      const int c = *own_pcol<SM>(A, i);
+      t += (xs[c] / nrm) * own<SM>(A, G, i, n2)[n + j];
+    }
+    part[j] = t;
+  }
+  csync();
+  T* wtx = sv;                                    // w^T X
+  for (int j = threadIdx.x; j < n; j += blockDim.x) wtx[j] = part_sum<SM>(A, j);
+  __syncthreads();
+  // B^+ = X - w (w^T X) - (X e) e^T + w (w^T X e) e^T, with w^T X e = ||s||
+  for (int i = b; i < n; i += NB) {
+    const int c = *own_pcol<SM>(A, i);
+    const T* gi = own<SM>(A, G, i, n2);
+    const T sc = xs[c], wc = sc / nrm;
     for (int j = threadIdx.x; j < n; j += blockDim.x)
-      A.Bpinv[(size_t)c * n + j] = double(gi[n + j] - __ldcg(A.unull + c) * e);
+      A.Bpinv[(size_t)c * n + j] = double(gi[n + j] - wc * wtx[j] - sc * e + wc * nrm * e);
   }
 }
 
@@ -966,9 +1005,34 @@ __global__ void __launch_bounds__(kDenseThreads, 1) coarsest_kernel(DenseArgs<T>
   if (b0) A.ctl->tp[4] = gtimer();
   triplets<SM>(A, sv, red);
   if (b0) A.ctl->tp[5] = gtimer();
-  if (A.Bpinv) pseudo_inverse<SM>(A, sv);
-  if (b0) A.ctl->tp[6] = gtimer();
   csync();   // no block leaves while another may still read its shared memory
+}
+
+// Shared-policy layout of the pseudo-inverse kernel, in elements of T: 2n
+// scratch, pub (2n + 64), part, the tableau rows (RP x 2n), then pcol.
+__host__ __device__ inline size_t pinv_smem_elems(int n, int RP) {
+  return (size_t)2 * n + (size_t)2 * n + 64 + part_stride(n) + (size_t)RP * 2 * n;
+}
+
+template <typename T, bool SM>
+__global__ void __launch_bounds__(kDenseThreads, 1) pinv_kernel(DenseArgs<T> A) {
+  extern __shared__ __align__(16) unsigned char dyn[];
+  T* sv = reinterpret_cast<T*>(dyn);
+  __shared__ T red[kWarps];
+  const int n = A.n;
+  A.NB = gridDim.x;
+  if constexpr (SM) {
+    T* p = sv + 2 * n;
+    A.pub = p;  p += 2 * n + 64;
+    A.part = p; p += part_stride(n);
+    A.S2 = p;   p += (size_t)A.RP * 2 * n;
+    A.pcol = reinterpret_cast<int*>(p);
+  }
+  const bool b0 = blockIdx.x == 0 && threadIdx.x == 0;
+  if (b0) A.ctl->tp[0] = gtimer();
+  pseudo_inverse<SM>(A, sv, red);
+  if (b0) A.ctl->tp[1] = gtimer();
+  csync();
 }
 
 __global__ void csr_to_dense_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
@@ -983,9 +1047,6 @@ bamg_status csr_to_dense(int n, const int32_t* rp, const int32_t* ci, const doub
   return launch(csr_to_dense_kernel, dim3(n), dim3(64), 0, s, n, rp, ci, va, D);
 }
 
-template <typename T> struct SmemAttr { static std::atomic<uint64_t> done; };
-template <typename T> std::atomic<uint64_t> SmemAttr<T>::done{0};
-
 static int max_cluster(const void* kern, cudaLaunchConfig_t cfg, int want) {
   int maxc = 0;
   cfg.gridDim = dim3(want);
@@ -995,36 +1056,99 @@ static int max_cluster(const void* kern, cudaLaunchConfig_t cfg, int want) {
   return maxc < want ? maxc : want;
 }
 
+// Cluster launch of kern with csize blocks and smem bytes on stream s.
 template <typename T>
-static bamg_status coarsest_t(int n, int r, const double* B, const double* M, const double* N, double* sigma,
-                              double* U, double* V, double* Bpinv, cudaStream_t s) {
-  DenseArgs<T> a = {};
-  a.n = n; a.r = r; a.B = B; a.M = M; a.N = N;
-  a.sigma = sigma; a.U = U; a.V = V; a.Bpinv = Bpinv;
-  // policy: own rows in shared memory when a 16-block cluster holds them
-  auto ksm = coarsest_kernel<T, true>;
-  auto kgl = coarsest_kernel<T, false>;
-  int max_dyn = 0;
-  BAMG_TRY(allow_max_smem((const void*)ksm, SmemAttr<T>::done, &max_dyn));
+static bamg_status cluster_launch(void (*kern)(DenseArgs<T>), int csize, size_t smem, cudaStream_t s,
+                                  const DenseArgs<T>& a) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.blockDim = dim3(kDenseThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.gridDim = dim3(csize);
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  BAMG_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  ++t_launches;
+  return BAMG_OK;
+}
+
+// Storage policy and cluster size for a kernel: shared rows with 16 blocks
+// when smem_sm bytes fit and such a cluster can be placed, else global rows
+// with the largest placeable cluster and smem_gl bytes.
+template <typename T>
+static bamg_status choose_policy(void (*ksm)(DenseArgs<T>), void (*kgl)(DenseArgs<T>), size_t smem_sm,
+                                 size_t smem_gl, std::atomic<uint64_t>& sm_attr, std::atomic<uint64_t>& gl_attr,
+                                 bool* use_sm, int* csize) {
+  int max_sm = 0, max_gl = 0;
+  BAMG_TRY(allow_max_smem((const void*)ksm, sm_attr, &max_sm));
+  BAMG_TRY(allow_max_smem((const void*)kgl, gl_attr, &max_gl));
   BAMG_CUDA(cudaFuncSetAttribute(ksm, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   BAMG_CUDA(cudaFuncSetAttribute(kgl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(kDenseThreads);
-  cfg.stream = s;
+  *use_sm = false;
+  if (smem_sm <= (size_t)max_sm) {
+    cfg.dynamicSmemBytes = smem_sm;
+    *use_sm = max_cluster((const void*)ksm, cfg, kMaxNB) == kMaxNB;
+  }
+  if (*use_sm) {
+    *csize = kMaxNB;
+    return BAMG_OK;
+  }
+  if (smem_gl > (size_t)max_gl) {
+    set_error("dense coarsest kernel needs %zu bytes of shared memory", smem_gl);
+    return BAMG_ERR_UNSUPPORTED;
+  }
+  cfg.dynamicSmemBytes = smem_gl;
+  *csize = max_cluster((const void*)kgl, cfg, kMaxNB);
+  if (*csize < 1) *csize = 1;
+  return BAMG_OK;
+}
+
+template <typename T> struct DenseAttrs {
+  static std::atomic<uint64_t> tsm, tgl, psm, pgl;
+};
+template <typename T> std::atomic<uint64_t> DenseAttrs<T>::tsm{0};
+template <typename T> std::atomic<uint64_t> DenseAttrs<T>::tgl{0};
+template <typename T> std::atomic<uint64_t> DenseAttrs<T>::psm{0};
+template <typename T> std::atomic<uint64_t> DenseAttrs<T>::pgl{0};
+
+// A side stream per host thread and device for the pseudo-inverse cluster.
+static bamg_status side_stream(cudaStream_t* out) {
+  thread_local cudaStream_t streams[64] = {};
+  int dev = 0;
+  BAMG_CUDA(cudaGetDevice(&dev));
+  cudaStream_t& st = streams[dev & 63];
+  if (!st) BAMG_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  *out = st;
+  return BAMG_OK;
+}
+
+template <typename T>
+static bamg_status coarsest_t(int n, int r, const double* B, const double* M, const double* N, double* sigma,
+                              double* U, double* V, double* Bpinv, cudaStream_t s) {
+  // ---- triplets: Cholesky, C, bidiagonalization, SVD, back-transform
+  DenseArgs<T> a = {};
+  a.n = n; a.r = r; a.B = B; a.M = M; a.N = N;
+  a.sigma = sigma; a.U = U; a.V = V; a.Bpinv = nullptr;
+  auto ksm = coarsest_kernel<T, true>;
+  auto kgl = coarsest_kernel<T, false>;
   const int rp16 = (n + kMaxNB - 1) / kMaxNB;
   const size_t smem16 = sizeof(T) * smem_elems(n, r, rp16) + sizeof(int) * rp16;
+  const size_t smemg = sizeof(T) * (3 + kStage) * (size_t)n + 64;
   bool use_sm = false;
   int csize = 0;
-  if (smem16 <= (size_t)max_dyn) {
-    cfg.dynamicSmemBytes = smem16;
-    csize = max_cluster((const void*)ksm, cfg, kMaxNB);
-    use_sm = csize == kMaxNB;
-  }
-  DevMem big, de, sg, vb, z, un, ctl, glob;
+  BAMG_TRY(choose_policy<T>(ksm, kgl, smem16, smemg, DenseAttrs<T>::tsm, DenseAttrs<T>::tgl, &use_sm, &csize));
+  DevMem big, glob, de, sg, vb, z, un, ctl;
   if (use_sm) {
     a.RP = rp16;
   } else {
-    // global policy: full matrices in device memory
     size_t nn = (size_t)n * n;
     size_t elems = 5 * nn + (size_t)n * 2 * r + 8 * (size_t)n + 64 + kMaxNB * (size_t)part_stride(n);
     BAMG_TRY(big.alloc(sizeof(T) * elems, s));
@@ -1039,16 +1163,6 @@ static bamg_status coarsest_t(int n, int r, const double* B, const double* M, co
     a.pub = p; p += 8 * (size_t)n + 64;
     a.part = p;
     a.pcol = glob.as<int>();
-    cfg.dynamicSmemBytes = sizeof(T) * (3 + kStage) * (size_t)n + 64;
-    static std::atomic<uint64_t> gl_attr{0};
-    int gl_max = 0;
-    BAMG_TRY(allow_max_smem((const void*)kgl, gl_attr, &gl_max));
-    if (cfg.dynamicSmemBytes > (size_t)gl_max) {
-      set_error("coarsest level of %d points needs %zu bytes of shared memory", n, cfg.dynamicSmemBytes);
-      return BAMG_ERR_UNSUPPORTED;
-    }
-    csize = max_cluster((const void*)kgl, cfg, kMaxNB);
-    if (csize < 1) csize = 1;
     a.RP = (n + csize - 1) / csize;
   }
   BAMG_TRY(de.alloc(sizeof(T) * 3 * n, s));
@@ -1056,37 +1170,76 @@ static bamg_status coarsest_t(int n, int r, const double* B, const double* M, co
   BAMG_TRY(vb.alloc(sizeof(T) * (size_t)r * n, s));
   BAMG_TRY(z.alloc(sizeof(T) * (size_t)r * 12 * n, s));
   BAMG_TRY(un.alloc(sizeof(T) * n, s));
-  BAMG_TRY(ctl.alloc(sizeof(DenseCtl), s));
-  BAMG_CUDA(cudaMemsetAsync(ctl.p, 0, sizeof(DenseCtl), s));
+  BAMG_TRY(ctl.alloc(2 * sizeof(DenseCtl), s));
+  BAMG_CUDA(cudaMemsetAsync(ctl.p, 0, 2 * sizeof(DenseCtl), s));
   BAMG_CUDA(cudaMemsetAsync(un.p, 0, sizeof(T) * n, s));
   BAMG_CUDA(cudaMemsetAsync(de.p, 0, sizeof(T) * 3 * n, s));
   a.d = de.as<T>(); a.e = a.d + n; a.taup = a.e + n;
   a.sig = sg.as<T>(); a.vb = vb.as<T>(); a.z = z.as<T>(); a.unull = un.as<T>(); a.ctl = ctl.as<DenseCtl>();
   a.NB = csize;
-  cudaLaunchAttribute attr[1];
-  cfg.gridDim = dim3(csize);
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = csize;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  if (use_sm) BAMG_CUDA(cudaLaunchKernelEx(&cfg, ksm, a));
-  else BAMG_CUDA(cudaLaunchKernelEx(&cfg, kgl, a));
-  g_launches.fetch_add(1, std::memory_order_relaxed);
-  ++t_launches;
-  DenseCtl h;
-  BAMG_CUDA(cudaMemcpyAsync(&h, ctl.p, sizeof(DenseCtl), cudaMemcpyDeviceToHost, s));
+
+  // ---- pseudo-inverse (independent of the triplets) on a side stream
+  DenseArgs<T> q = {};
+  bool p_sm = false;
+  int p_csize = 0;
+  DevMem pbig, pglob, pxs;
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  auto psm = pinv_kernel<T, true>;
+  auto pgl = pinv_kernel<T, false>;
+  size_t psmem16 = 0, psmemg = sizeof(T) * 2 * (size_t)n + 64;
+  if (Bpinv) {
+    q.n = n; q.r = r; q.B = B; q.Bpinv = Bpinv;
+    psmem16 = sizeof(T) * pinv_smem_elems(n, rp16) + sizeof(int) * rp16;
+    BAMG_TRY(choose_policy<T>(psm, pgl, psmem16, psmemg, DenseAttrs<T>::psm, DenseAttrs<T>::pgl, &p_sm, &p_csize));
+    if (p_sm) {
+      q.RP = rp16;
+    } else {
+      BAMG_TRY(pbig.alloc(sizeof(T) * ((size_t)2 * n * n + 2 * (size_t)n + 64 + kMaxNB * (size_t)part_stride(n)), s));
+      BAMG_TRY(pglob.alloc(sizeof(int) * n, s));
+      T* p = pbig.as<T>();
+      q.S2 = p; p += (size_t)2 * n * n;
+      q.pub = p; p += 2 * (size_t)n + 64;
+      q.part = p;
+      q.pcol = pglob.as<int>();
+      q.RP = (n + p_csize - 1) / p_csize;
+    }
+    BAMG_TRY(pxs.alloc(sizeof(T) * n, s));
+    q.unull = pxs.as<T>();
+    q.ctl = ctl.as<DenseCtl>() + 1;
+    q.NB = p_csize;
+    BAMG_TRY(side_stream(&s2));
+    BAMG_CUDA(cudaEventCreateWithFlags(&ev0, cudaEventDisableTiming));
+    BAMG_CUDA(cudaEventCreateWithFlags(&ev1, cudaEventDisableTiming));
+    BAMG_CUDA(cudaEventRecord(ev0, s));
+    BAMG_CUDA(cudaStreamWaitEvent(s2, ev0, 0));
+    BAMG_TRY(cluster_launch<T>(p_sm ? psm : pgl, p_csize, p_sm ? psmem16 : psmemg, s2, q));
+    BAMG_CUDA(cudaEventRecord(ev1, s2));
+  }
+  bamg_status st = cluster_launch<T>(use_sm ? ksm : kgl, csize, use_sm ? smem16 : smemg, s, a);
+  if (Bpinv) {
+    // the caller's stream waits for the pseudo-inverse (also before any
+    // buffer of this call is released on it)
+    cudaStreamWaitEvent(s, ev1, 0);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+  }
+  BAMG_TRY(st);
+  DenseCtl h[2];
+  BAMG_CUDA(cudaMemcpyAsync(h, ctl.p, sizeof(h), cudaMemcpyDeviceToHost, s));
   BAMG_CUDA(cudaStreamSynchronize(s));
   if (std::getenv("BAMG_TRACE")) {
-    const char* nm[6] = {"cholesky", "form_C", "bidiag", "bidiag_svd", "triplets", "pinv"};
+    const char* nm[5] = {"cholesky", "form_C", "bidiag", "bidiag_svd", "triplets"};
     fprintf(stderr, "[bamg] coarsest n=%d prec=%s cluster=%d %s:", n, sizeof(T) == 4 ? "f32" : "f64", csize,
             use_sm ? "smem" : "global");
-    for (int k = 0; k < 6; ++k)
-      if (h.tp[k + 1] >= h.tp[k] && h.tp[k + 1]) fprintf(stderr, " %s=%.1fus", nm[k], (h.tp[k + 1] - h.tp[k]) / 1e3);
+    for (int k = 0; k < 5; ++k)
+      if (h[0].tp[k + 1] >= h[0].tp[k] && h[0].tp[k + 1])
+        fprintf(stderr, " %s=%.1fus", nm[k], (h[0].tp[k + 1] - h[0].tp[k]) / 1e3);
+    if (Bpinv && h[1].tp[1] >= h[1].tp[0])
+      fprintf(stderr, " | pinv (%s, concurrent)=%.1fus", p_sm ? "smem" : "global", (h[1].tp[1] - h[1].tp[0]) / 1e3);
     fprintf(stderr, "\n");
   }
-  if (h.err == 2) {
+  if (h[0].err == 2) {
     set_error("coarsest level: M or N is not positive definite");
     return BAMG_ERR_NUMERIC;
   }
