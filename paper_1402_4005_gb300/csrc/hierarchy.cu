@@ -108,6 +108,25 @@ static bamg_status csr_product(const Csr& A, const Csr& B, Csr& C, cudaStream_t 
   return BAMG_OK;
 }
 
+static bamg_status csr_products(const std::vector<std::pair<const Csr*, const Csr*>>& ab,
+                                const std::vector<Csr*>& out, cudaStream_t s) {
+  std::vector<SpgemmJob> jobs(ab.size());
+  for (size_t q = 0; q < ab.size(); ++q) {
+    const Csr& A = *ab[q].first;
+    const Csr& B = *ab[q].second;
+    Csr& C = *out[q];
+    jobs[q] = SpgemmJob{A.rows, A.r(), A.c(), A.v(), B.r(), B.c(), B.v(), &C.rp, &C.ci, &C.va, 0};
+  }
+  BAMG_TRY(spgemm_multi(jobs.data(), (int)jobs.size(), s));
+  for (size_t q = 0; q < ab.size(); ++q) {
+    Csr& C = *out[q];
+    C.rows = ab[q].first->rows;
+    C.cols = ab[q].second->cols;
+    C.nnz = (int)jobs[q].nnz;
+  }
+  return BAMG_OK;
+}
+
 // B^T, 1/diag(B) (Jacobi needs b_ii > 0: Section 3 / coarse levels), lanes.
 static bamg_status finish_level(bamg_hierarchy* h, Level& L, int l, cudaStream_t s) {
   L.n = L.B.rows;
@@ -260,23 +279,23 @@ static bamg_status coarsen_level(bamg_hierarchy* h, int l, DevMem& U, DevMem& V,
   Level& Lc = h->lv[l + 1];
   Level& Lf = h->lv[l];
   {
-    Csr BP;
-    BAMG_TRY(csr_product(Lf.B, Lf.P, BP, s));
-    BAMG_TRY(csr_product(Lf.Q, BP, Lc.B, s));
-  }
-  if (Lf.M.empty()) {
-    BAMG_TRY(csr_product(Lf.Q, Lf.Qt, Lc.M, s));
-  } else {
-    Csr MQt;
-    BAMG_TRY(csr_product(Lf.M, Lf.Qt, MQt, s));
-    BAMG_TRY(csr_product(Lf.Q, MQt, Lc.M, s));
-  }
-  if (Lf.N.empty()) {
-    BAMG_TRY(csr_product(Lf.Pt, Lf.P, Lc.N, s));
-  } else {
-    Csr NP;
-    BAMG_TRY(csr_product(Lf.N, Lf.P, NP, s));
-    BAMG_TRY(csr_product(Lf.Pt, NP, Lc.N, s));
+    // two rounds of independent products: B P, M Q^T (or Q Q^T), N P (or
+    // P^T P); then Q (B P), Q (M Q^T), P^T (N P)
+    Csr BP, MQt, NP;
+    std::vector<std::pair<const Csr*, const Csr*>> ab;
+    std::vector<Csr*> out;
+    ab.push_back({&Lf.B, &Lf.P}); out.push_back(&BP);
+    if (Lf.M.empty()) { ab.push_back({&Lf.Q, &Lf.Qt}); out.push_back(&Lc.M); }
+    else { ab.push_back({&Lf.M, &Lf.Qt}); out.push_back(&MQt); }
+    if (Lf.N.empty()) { ab.push_back({&Lf.Pt, &Lf.P}); out.push_back(&Lc.N); }
+    else { ab.push_back({&Lf.N, &Lf.P}); out.push_back(&NP); }
+    BAMG_TRY(csr_products(ab, out, s));
+    ab.clear();
+    out.clear();
+    ab.push_back({&Lf.Q, &BP}); out.push_back(&Lc.B);
+    if (!Lf.M.empty()) { ab.push_back({&Lf.Q, &MQt}); out.push_back(&Lc.M); }
+    if (!Lf.N.empty()) { ab.push_back({&Lf.Pt, &NP}); out.push_back(&Lc.N); }
+    BAMG_TRY(csr_products(ab, out, s));
   }
   tr.mark(s, "galerkin spgemm", l);
   Lc.nx = cgx;

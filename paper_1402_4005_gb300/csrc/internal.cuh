@@ -23,6 +23,17 @@ bamg_status spgemm_symbolic(int m, const int32_t* arp, const int32_t* aci, const
 bamg_status spgemm_numeric(int m, const int32_t* arp, const int32_t* aci, const double* ava,
                            const int32_t* brp, const int32_t* bci, const double* bva,
                            const int32_t* crp, int32_t* cci, double* cva, cudaStream_t s);
+// Independent products C_q = A_q B_q, two host reads for all of them.
+struct SpgemmJob {
+  int m;
+  const int32_t *arp, *aci;
+  const double* ava;
+  const int32_t *brp, *bci;
+  const double* bva;
+  DevMem *crp, *cci, *cva;   // allocated on the stream
+  int64_t nnz;
+};
+bamg_status spgemm_multi(SpgemmJob* jobs, int k, cudaStream_t s);
 // C = A B in one expansion pass; allocates C's arrays on s, nnz(C) to the host
 bamg_status spgemm(int m, const int32_t* arp, const int32_t* aci, const double* ava, const int32_t* brp,
                    const int32_t* bci, const double* bva, DevMem& crp, DevMem& cci, DevMem& cva, int64_t* nnz_host,

@@ -10,6 +10,7 @@
 // P^T N P (Section 3, Algorithm 1).
 #include <atomic>
 #include <cstring>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -250,20 +251,19 @@ static size_t big_smem(bool numeric) {
 }
 
 template <bool NUMERIC>
-static bamg_status run_rows(int m, const SpgemmPlan& pl, const int32_t* arp, const int32_t* aci,
+static bamg_status run_rows(int m, const int32_t* prod, int maxprod, const int32_t* arp, const int32_t* aci,
                             const double* ava, const int32_t* brp, const int32_t* bci,
                             const double* bva, int32_t* ccount, const int32_t* crp, int32_t* cci,
                             double* cva, cudaStream_t s) {
   BAMG_TRY(launch(spgemm_warp_kernel<NUMERIC>, dim3(cdiv(m, kWarpsPerBlock)), dim3(kWarpsPerBlock * 32),
-                  0, s, m, (const int32_t*)pl.prod.as<int32_t>(), arp, aci, ava, brp, bci, bva, ccount,
-                  crp, cci, cva));
-  if (pl.maxprod > kWarpCap) {
+                  0, s, m, prod, arp, aci, ava, brp, bci, bva, ccount, crp, cci, cva));
+  if (maxprod > kWarpCap) {
     size_t sm = big_smem(NUMERIC);
     static std::atomic<uint64_t> attr_done{0};
     int max_dyn = 0;
     BAMG_TRY(allow_max_smem((const void*)spgemm_block_kernel<NUMERIC>, attr_done, &max_dyn));
     BAMG_TRY(launch(spgemm_block_kernel<NUMERIC>, dim3(m), dim3(kBigThreads), sm, s, m,
-                    (const int32_t*)pl.prod.as<int32_t>(), arp, aci, ava, brp, bci, bva, ccount, crp,
+                    prod, arp, aci, ava, brp, bci, bva, ccount, crp,
                     cci, cva));
   }
   return BAMG_OK;
@@ -275,7 +275,7 @@ bamg_status spgemm_symbolic(int m, const int32_t* arp, const int32_t* aci, const
   BAMG_TRY(plan_products(m, arp, aci, brp, pl, s));
   DevMem cnt;
   BAMG_TRY(cnt.alloc(sizeof(int32_t) * (m + 1), s));
-  BAMG_TRY(run_rows<false>(m, pl, arp, aci, nullptr, brp, bci, nullptr, cnt.as<int32_t>(), nullptr,
+  BAMG_TRY(run_rows<false>(m, pl.prod.as<int32_t>(), pl.maxprod, arp, aci, nullptr, brp, bci, nullptr, cnt.as<int32_t>(), nullptr,
                            nullptr, nullptr, s));
   return scan_counts(cnt.as<int32_t>(), crp, m, s, nnz_host);
 }
@@ -309,7 +309,7 @@ bamg_status spgemm(int m, const int32_t* arp, const int32_t* aci, const double* 
   BAMG_TRY(scol.alloc(sizeof(int32_t) * (pl.total > 0 ? pl.total : 1), s));
   BAMG_TRY(sval.alloc(sizeof(double) * (pl.total > 0 ? pl.total : 1), s));
   BAMG_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * (m + 1), s));
-  BAMG_TRY(run_rows<true>(m, pl, arp, aci, ava, brp, bci, bva, cnt.as<int32_t>(), off.as<int32_t>(),
+  BAMG_TRY(run_rows<true>(m, pl.prod.as<int32_t>(), pl.maxprod, arp, aci, ava, brp, bci, bva, cnt.as<int32_t>(), off.as<int32_t>(),
                           scol.as<int32_t>(), sval.as<double>(), s));
   BAMG_TRY(crp.alloc(sizeof(int32_t) * (m + 1), s));
   BAMG_TRY(scan_counts(cnt.as<int32_t>(), crp.as<int32_t>(), m, s, nnz_host));
@@ -321,12 +321,83 @@ bamg_status spgemm(int m, const int32_t* arp, const int32_t* aci, const double* 
                 (const int32_t*)crp.as<int32_t>(), cci.as<int32_t>(), cva.as<double>());
 }
 
+// Several independent products at once: each phase is issued for every
+// product before the one host read that phase needs (product statistics,
+// then the nnz of every result), so k products cost two host reads.
+bamg_status spgemm_multi(SpgemmJob* jobs, int k, cudaStream_t s) {
+  if (k <= 0) return BAMG_OK;
+  // one int32 buffer for the statistics and the per-row arrays of all jobs
+  // (product counts, their offsets, entry counts), one pair for the scratch
+  std::vector<size_t> ro(k + 1, 0);
+  for (int q = 0; q < k; ++q) ro[q + 1] = ro[q] + 3 * (size_t)(jobs[q].m + 1);
+  DevMem ints;
+  BAMG_TRY(ints.alloc(sizeof(int32_t) * (4 * (size_t)k + ro[k]), s));
+  int* stats = ints.as<int>();
+  int32_t* rows = ints.as<int32_t>() + 4 * k;
+  BAMG_CUDA(cudaMemsetAsync(ints.p, 0, sizeof(int32_t) * (4 * (size_t)k + ro[k]), s));
+  auto prod = [&](int q) { return rows + ro[q]; };
+  auto offs = [&](int q) { return rows + ro[q] + (jobs[q].m + 1); };
+  auto cnts = [&](int q) { return rows + ro[q] + 2 * (size_t)(jobs[q].m + 1); };
+  for (int q = 0; q < k; ++q) {
+    SpgemmJob& J = jobs[q];
+    BAMG_TRY(launch(count_products_kernel, dim3(cdiv(J.m, 256)), dim3(256), 0, s, J.m, J.arp, J.aci, J.brp,
+                    prod(q), stats + 4 * q));
+  }
+  std::vector<int> h(4 * k);
+  BAMG_CUDA(cudaMemcpyAsync(h.data(), stats, sizeof(int) * 4 * k, cudaMemcpyDeviceToHost, s));
+  BAMG_CUDA(cudaStreamSynchronize(s));
+  std::vector<SpgemmPlan> pl(k);
+  std::vector<size_t> so(k + 1, 0);
+  for (int q = 0; q < k; ++q) {
+    pl[q].maxprod = h[4 * q];
+    unsigned long long t = 0;
+    std::memcpy(&t, &h[4 * q + 2], sizeof(t));
+    pl[q].total = (long long)t;
+    if (pl[q].maxprod > kBlockCap) {
+      set_error("sparse product row with %d products exceeds the %d limit", pl[q].maxprod, kBlockCap);
+      return BAMG_ERR_NUMERIC;
+    }
+    if (pl[q].total > INT32_MAX) {
+      set_error("sparse product with %lld products exceeds the int32 index range", pl[q].total);
+      return BAMG_ERR_UNSUPPORTED;
+    }
+    so[q + 1] = so[q] + (size_t)pl[q].total;
+  }
+  DevMem scol, sval;
+  BAMG_TRY(scol.alloc(sizeof(int32_t) * (so[k] > 0 ? so[k] : 1), s));
+  BAMG_TRY(sval.alloc(sizeof(double) * (so[k] > 0 ? so[k] : 1), s));
+  for (int q = 0; q < k; ++q) {
+    SpgemmJob& J = jobs[q];
+    BAMG_TRY(scan_counts(prod(q), offs(q), J.m, s, nullptr));
+    BAMG_TRY(run_rows<true>(J.m, prod(q), pl[q].maxprod, J.arp, J.aci, J.ava, J.brp, J.bci, J.bva, cnts(q),
+                            offs(q), scol.as<int32_t>() + so[q], sval.as<double>() + so[q], s));
+    BAMG_TRY(J.crp->alloc(sizeof(int32_t) * (J.m + 1), s));
+    BAMG_TRY(scan_counts(cnts(q), J.crp->as<int32_t>(), J.m, s, nullptr));
+  }
+  std::vector<int32_t> nz(k);
+  for (int q = 0; q < k; ++q)
+    BAMG_CUDA(cudaMemcpyAsync(&nz[q], jobs[q].crp->as<int32_t>() + jobs[q].m, sizeof(int32_t),
+                              cudaMemcpyDeviceToHost, s));
+  BAMG_CUDA(cudaStreamSynchronize(s));
+  for (int q = 0; q < k; ++q) {
+    SpgemmJob& J = jobs[q];
+    J.nnz = nz[q];
+    BAMG_TRY(J.cci->alloc(sizeof(int32_t) * (J.nnz > 0 ? J.nnz : 1), s));
+    BAMG_TRY(J.cva->alloc(sizeof(double) * (J.nnz > 0 ? J.nnz : 1), s));
+    BAMG_TRY(launch(compact_rows_kernel, dim3(cdiv((long long)J.m * 32, 256)), dim3(256), 0, s, J.m,
+                    (const int32_t*)offs(q), (const int32_t*)cnts(q),
+                    (const int32_t*)scol.as<int32_t>() + so[q], (const double*)sval.as<double>() + so[q],
+                    (const int32_t*)J.crp->as<int32_t>(), J.cci->as<int32_t>(), J.cva->as<double>()));
+  }
+  return BAMG_OK;
+}
+
 bamg_status spgemm_numeric(int m, const int32_t* arp, const int32_t* aci, const double* ava,
                            const int32_t* brp, const int32_t* bci, const double* bva,
                            const int32_t* crp, int32_t* cci, double* cva, cudaStream_t s) {
   SpgemmPlan pl;
   BAMG_TRY(plan_products(m, arp, aci, brp, pl, s));
-  return run_rows<true>(m, pl, arp, aci, ava, brp, bci, bva, nullptr, crp, cci, cva, s);
+  return run_rows<true>(m, pl.prod.as<int32_t>(), pl.maxprod, arp, aci, ava, brp, bci, bva, nullptr, crp, cci, cva, s);
 }
 
 }  // namespace bamg
