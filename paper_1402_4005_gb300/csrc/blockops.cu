@@ -99,15 +99,18 @@ coldot_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__
               const T* __restrict__ A2, const T* __restrict__ B2, int npairs,
               double* __restrict__ part) {
   using C = Blk<T, LD>;
+  // per-thread sums in the block precision (a thread covers a few rows; the
+  // FP64 pipes of GB300 are narrow), block and grid sums in FP64
+  using Acc = T;
   constexpr int K = 3;
   __shared__ double sh[8][K * LD];
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int q = lane % C::LPR;
-  double acc[K][C::VW];
+  Acc acc[K][C::VW];
 #pragma unroll
   for (int k = 0; k < K; ++k)
 #pragma unroll
-    for (int v = 0; v < C::VW; ++v) acc[k][v] = 0.0;
+    for (int v = 0; v < C::VW; ++v) acc[k][v] = Acc(0);
   int rows_per_block = (blockDim.x >> 5) * C::RPW;
   for (int i = blockIdx.x * rows_per_block + w * C::RPW + lane / C::LPR; i < n;
        i += gridDim.x * rows_per_block) {
@@ -127,8 +130,8 @@ coldot_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__
       vload_ro(X + o, xi);
 #pragma unroll
       for (int v = 0; v < C::VW; ++v) {
-        acc[0][v] += (double)xi[v] * (double)xi[v];
-        acc[1][v] += (double)bx[v] * (double)bx[v];
+        acc[0][v] = fma(xi[v], xi[v], acc[0][v]);
+        acc[1][v] = fma(bx[v], bx[v], acc[1][v]);
       }
     } else {
       const T* As[3] = {A0, A1, A2};
@@ -140,7 +143,7 @@ coldot_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__
           vload_ro(As[k] + o, a);
           vload_ro(Bs[k] + o, b);
 #pragma unroll
-          for (int v = 0; v < C::VW; ++v) acc[k][v] += (double)a[v] * (double)b[v];
+          for (int v = 0; v < C::VW; ++v) acc[k][v] = fma(a[v], b[v], acc[k][v]);
         }
       }
     }
@@ -155,7 +158,7 @@ coldot_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__
 #pragma unroll
     for (int k = 0; k < K; ++k)
 #pragma unroll
-      for (int v = 0; v < C::VW; ++v) sh[w][k * LD + lane * C::VW + v] = acc[k][v];
+      for (int v = 0; v < C::VW; ++v) sh[w][k * LD + lane * C::VW + v] = (double)acc[k][v];
   }
   __syncthreads();
   for (int t = threadIdx.x; t < K * LD; t += blockDim.x) {

@@ -201,36 +201,44 @@ __global__ void sqrt_kernel(double* v) { v[0] = sqrt(v[0]); }
 // Applies the previous Givens rotations, forms the new one, updates g, and
 // solves R y = g(0..j).  st[0] = |g(j+1)| (residual 2-norm estimate),
 // st[1] = H(j+1, j) before rotation.
+// Column j of the Hessenberg matrix (h1 + h2 from the two Gram-Schmidt
+// passes, then ||w||) through the previous rotations into R, a new rotation,
+// the rotated right-hand side g; st = {|g_{j+1}|, ||w||}.  One thread; the
+// column is streamed (each rotation only needs the entry carried from the
+// previous one).
 __global__ void givens_kernel(int j, int m, const double* __restrict__ h1, const double* __restrict__ h2,
                               const double* __restrict__ wnorm, double* __restrict__ R, double* __restrict__ cs,
-                              double* __restrict__ sn, double* __restrict__ g, double* __restrict__ y,
-                              double* __restrict__ st) {
+                              double* __restrict__ sn, double* __restrict__ g, double* __restrict__ st) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double col[65];
-  for (int k = 0; k <= j; ++k) col[k] = h1[k] + h2[k];
-  double hn = wnorm[0];
-  col[j + 1] = hn;
+  const double hn = wnorm[0];
+  double carry = h1[0] + h2[0];
   for (int k = 0; k < j; ++k) {
-    double t = cs[k] * col[k] + sn[k] * col[k + 1];
-    col[k + 1] = -sn[k] * col[k] + cs[k] * col[k + 1];
-    col[k] = t;
+    const double next = h1[k + 1] + h2[k + 1];
+    const double c = cs[k], sk = sn[k];
+    R[(size_t)k * m + j] = c * carry + sk * next;
+    carry = -sk * carry + c * next;
   }
-  double a = col[j], b = col[j + 1];
-  double d = hypot(a, b);
-  double c = d > 0.0 ? a / d : 1.0, s = d > 0.0 ? b / d : 0.0;
-  cs[j] = c; sn[j] = s;
-  col[j] = d;
-  g[j + 1] = -s * g[j];
+  const double a = carry, b = hn;
+  const double d = hypot(a, b);
+  const double c = d > 0.0 ? a / d : 1.0, sk = d > 0.0 ? b / d : 0.0;
+  cs[j] = c; sn[j] = sk;
+  R[(size_t)j * m + j] = d;
+  g[j + 1] = -sk * g[j];
   g[j] = c * g[j];
-  for (int k = 0; k <= j; ++k) R[(size_t)k * m + j] = col[k];
+  st[0] = fabs(g[j + 1]);
+  st[1] = hn;
+}
+
+// y = R^{-1} g for the leading (j+1) x (j+1) block (back substitution).
+__global__ void ysolve_kernel(int j, int m, const double* __restrict__ R, const double* __restrict__ g,
+                              double* __restrict__ y) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
   for (int k = j; k >= 0; --k) {
     double acc = g[k];
     for (int q = k + 1; q <= j; ++q) acc -= R[(size_t)k * m + q] * y[q];
-    double rkk = R[(size_t)k * m + k];
+    const double rkk = R[(size_t)k * m + k];
     y[k] = rkk != 0.0 ? acc / rkk : 0.0;
   }
-  st[0] = fabs(g[j + 1]);
-  st[1] = hn;
 }
 
 __global__ void init_g_kernel(int m, const double* __restrict__ beta, double* __restrict__ g) {
@@ -238,17 +246,18 @@ __global__ void init_g_kernel(int m, const double* __restrict__ beta, double* __
   if (k <= m) g[k] = k == 0 ? beta[0] : 0.0;
 }
 
-__global__ void min_kernel(int n, const double* __restrict__ x, double* __restrict__ out) {
+// Smallest entry: per-block minima, then one block over them.
+__global__ void min_part_kernel(int n, const double* __restrict__ x, double* __restrict__ part) {
   __shared__ double sh[256];
   double m = INFINITY;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmin(m, x[i]);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) m = fmin(m, x[i]);
   sh[threadIdx.x] = m;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if ((int)threadIdx.x < o) sh[threadIdx.x] = fmin(sh[threadIdx.x], sh[threadIdx.x + o]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[0] = sh[0];
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
 bamg_status orient_normalise(int n, double* x, cudaStream_t s);
@@ -362,8 +371,7 @@ bamg_status fgmres(bamg_hierarchy* h, double* x, const bamg_solve_params* sp, ba
       BAMG_TRY(norm2_dev(G, G.w.as<double>(), G.scal.as<double>(), s));
       BAMG_TRY(launch(givens_kernel, dim3(1), dim3(32), 0, s, j, m, (const double*)G.h1.as<double>(),
                       (const double*)G.h2.as<double>(), (const double*)G.scal.as<double>(), G.R.as<double>(),
-                      G.cs.as<double>(), G.sn.as<double>(), G.g.as<double>(), G.y.as<double>(),
-                      G.st.as<double>()));
+                      G.cs.as<double>(), G.sn.as<double>(), G.g.as<double>(), G.st.as<double>()));
       double st[2];
       BAMG_CUDA(cudaMemcpyAsync(st, G.st.p, sizeof(st), cudaMemcpyDeviceToHost, s));
       BAMG_CUDA(cudaStreamSynchronize(s));
@@ -372,6 +380,8 @@ bamg_status fgmres(bamg_hierarchy* h, double* x, const bamg_solve_params* sp, ba
       breakdown = !(st[1] > 0.0);
       bool last = (j == m - 1) || its >= sp->max_iter || breakdown;
       if (st[0] <= 2.0 * sp->tol * xn1_0 || last) {
+        BAMG_TRY(launch(ysolve_kernel, dim3(1), dim3(32), 0, s, j, m, (const double*)G.R.as<double>(),
+                        (const double*)G.g.as<double>(), G.y.as<double>()));
         BAMG_TRY(launch(combine_kernel, dim3(gv), dim3(256), 0, s, n, K, (const double*)Z, (size_t)n,
                         (const double*)G.y.as<double>(), (const double*)x, G.xj.as<double>()));
         BAMG_TRY(true_residual(h, G, G.xj.as<double>(), &rel, &xn1, s));
@@ -388,7 +398,12 @@ bamg_status fgmres(bamg_hierarchy* h, double* x, const bamg_solve_params* sp, ba
   }
   BAMG_TRY(orient_normalise(n, x, s));
   double fin[2] = {0, 0};
-  BAMG_TRY(launch(min_kernel, dim3(1), dim3(256), 0, s, n, (const double*)x, G.scal.as<double>()));
+  {
+    const int nb = red_blocks(n);
+    BAMG_TRY(launch(min_part_kernel, dim3(nb), dim3(256), 0, s, n, (const double*)x, G.part.as<double>()));
+    BAMG_TRY(launch(min_part_kernel, dim3(1), dim3(256), 0, s, nb, (const double*)G.part.as<double>(),
+                    G.scal.as<double>()));
+  }
   BAMG_CUDA(cudaMemcpyAsync(fin, G.scal.p, sizeof(double), cudaMemcpyDeviceToHost, s));
   BAMG_TRY(true_residual(h, G, x, &rel, &xn1, s));
   if (info) {
