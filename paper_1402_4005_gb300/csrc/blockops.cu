@@ -17,75 +17,91 @@ struct Blk {
   static_assert(LD % VW == 0 && LPR >= 1 && LPR <= 32, "bad block width");
 };
 
-// Y = X + omega D^{-1} (sigma .* R - B X)   (Algorithm 1 smoothing loops;
-// weighted Jacobi, Section 3).  keep0: column 0 copied unchanged.
+// acc = (A X)_row for the row group's VW columns; the nonzeros are taken
+// four at a time (indices and values first, then the four row gathers) so
+// that more loads are in flight per row group.
 template <typename T, int LD>
-__global__ void __launch_bounds__(256)
-relax_block_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                   const T* __restrict__ va, const T* __restrict__ dinv, const T* __restrict__ X,
-                   T* __restrict__ Y, const T* __restrict__ R, const T* __restrict__ sig, T omega,
-                   int keep0) {
+__device__ inline void row_times_block(int i, int q, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                       const T* __restrict__ va, const T* __restrict__ X, T (&acc)[Blk<T, LD>::VW]) {
   using C = Blk<T, LD>;
-  int lane = threadIdx.x & 31;
-  int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int i = gw * C::RPW + lane / C::LPR;
-  int q = lane % C::LPR;
-  if (i >= n) return;
-  T acc[C::VW];
 #pragma unroll
   for (int v = 0; v < C::VW; ++v) acc[v] = T(0);
-  int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
-  for (int p = p0; p < p1; ++p) {
-    int j = __ldg(ci + p);
-    T a = __ldg(va + p);
+  const int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
+  int p = p0;
+  for (; p + 4 <= p1; p += 4) {
+    int j[4];
+    T a[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      j[u] = __ldg(ci + p + u);
+      a[u] = __ldg(va + p + u);
+    }
+    T xv[4][C::VW];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) vload_ro(X + (size_t)j[u] * LD + q * C::VW, xv[u]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < C::VW; ++v) acc[v] = fma(a[u], xv[u][v], acc[v]);
+  }
+  for (; p < p1; ++p) {
+    const int j = __ldg(ci + p);
+    const T a = __ldg(va + p);
     T xv[C::VW];
     vload_ro(X + (size_t)j * LD + q * C::VW, xv);
 #pragma unroll
     for (int v = 0; v < C::VW; ++v) acc[v] = fma(a, xv[v], acc[v]);
   }
+}
+
+// Y = X + omega D^{-1} (sigma .* R - B X)   (Algorithm 1 smoothing loops;
+// weighted Jacobi, Section 3).  keep0: column 0 copied unchanged.  Two
+// independent jobs (the V and U relaxations) share one launch: blockIdx.y
+// selects the job.
+template <typename T, int LD>
+__global__ void __launch_bounds__(256) relax_block_kernel(RelaxJob<T> j0, RelaxJob<T> j1) {
+  using C = Blk<T, LD>;
+  const RelaxJob<T>& a = blockIdx.y ? j1 : j0;
+  int lane = threadIdx.x & 31;
+  int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int i = gw * C::RPW + lane / C::LPR;
+  int q = lane % C::LPR;
+  if (i >= a.n) return;
+  T acc[C::VW];
+  row_times_block<T, LD>(i, q, a.rp, a.ci, a.va, a.X, acc);
   T xi[C::VW], y[C::VW];
-  vload_ro(X + (size_t)i * LD + q * C::VW, xi);
-  T di = __ldg(dinv + i);
-  if (R) {
+  vload_ro(a.X + (size_t)i * LD + q * C::VW, xi);
+  T di = __ldg(a.dinv + i);
+  if (a.R) {
     T rv[C::VW];
-    vload_ro(R + (size_t)i * LD + q * C::VW, rv);
+    vload_ro(a.R + (size_t)i * LD + q * C::VW, rv);
 #pragma unroll
     for (int v = 0; v < C::VW; ++v) {
-      T s = sig ? __ldg(sig + q * C::VW + v) : T(1);
-      y[v] = xi[v] + (omega * (s * rv[v] - acc[v])) * di;
+      T s = a.sig ? __ldg(a.sig + q * C::VW + v) : T(1);
+      y[v] = xi[v] + (a.omega * (s * rv[v] - acc[v])) * di;
     }
   } else {
 #pragma unroll
-    for (int v = 0; v < C::VW; ++v) y[v] = xi[v] + (omega * (-acc[v])) * di;
+    for (int v = 0; v < C::VW; ++v) y[v] = xi[v] + (a.omega * (-acc[v])) * di;
   }
-  if (keep0 && q == 0) y[0] = xi[0];
-  vstore(Y + (size_t)i * LD + q * C::VW, y);
+  if (a.keep0 && q == 0) y[0] = xi[0];
+  vstore(a.Y + (size_t)i * LD + q * C::VW, y);
 }
 
-// Y = A X  (rows x LD) for a CSR A.
+// Y = A X  (rows x LD) for a CSR A; up to three independent products per
+// launch (blockIdx.y selects one).
 template <typename T, int LD>
-__global__ void __launch_bounds__(256)
-spmm_block_kernel(int rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                  const T* __restrict__ va, const T* __restrict__ X, T* __restrict__ Y) {
+__global__ void __launch_bounds__(256) spmm_block_kernel(SpmmJob<T> j0, SpmmJob<T> j1, SpmmJob<T> j2) {
   using C = Blk<T, LD>;
+  const SpmmJob<T>& a = blockIdx.y == 0 ? j0 : (blockIdx.y == 1 ? j1 : j2);
   int lane = threadIdx.x & 31;
   int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int i = gw * C::RPW + lane / C::LPR;
   int q = lane % C::LPR;
-  if (i >= rows) return;
+  if (i >= a.rows) return;
   T acc[C::VW];
-#pragma unroll
-  for (int v = 0; v < C::VW; ++v) acc[v] = T(0);
-  int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
-  for (int p = p0; p < p1; ++p) {
-    int j = __ldg(ci + p);
-    T a = __ldg(va + p);
-    T xv[C::VW];
-    vload_ro(X + (size_t)j * LD + q * C::VW, xv);
-#pragma unroll
-    for (int v = 0; v < C::VW; ++v) acc[v] = fma(a, xv[v], acc[v]);
-  }
-  vstore(Y + (size_t)i * LD + q * C::VW, acc);
+  row_times_block<T, LD>(i, q, a.rp, a.ci, a.va, a.X, acc);
+  vstore(a.Y + (size_t)i * LD + q * C::VW, acc);
 }
 
 // Per-block column sums of K products, written to part[block][K*LD].
@@ -315,21 +331,20 @@ __global__ void diag_inv_kernel(int n, const int32_t* __restrict__ rp, const int
 
 // =================================================================== host
 template <typename T, int LD>
-static bamg_status relax_ld(int n, const int32_t* rp, const int32_t* ci, const T* va, const T* dinv,
-                            const T* X, T* Y, const T* R, const T* sig, T omega, int keep0,
-                            cudaStream_t s) {
+static bamg_status relax_ld(const RelaxJob<T>& j0, const RelaxJob<T>* j1, cudaStream_t s) {
   using C = Blk<T, LD>;
+  const int n = j1 && j1->n > j0.n ? j1->n : j0.n;
   unsigned blocks = cdiv(n, 8 * C::RPW);
-  return launch(relax_block_kernel<T, LD>, dim3(blocks), dim3(256), 0, s, n, rp, ci, va, dinv, X, Y, R,
-                sig, omega, keep0);
+  return launch(relax_block_kernel<T, LD>, dim3(blocks, j1 ? 2 : 1), dim3(256), 0, s, j0, j1 ? *j1 : j0);
 }
 
 template <typename T, int LD>
-static bamg_status spmm_ld(int rows, const int32_t* rp, const int32_t* ci, const T* va, const T* X, T* Y,
-                           cudaStream_t s) {
+static bamg_status spmm_ld(const SpmmJob<T>* jobs, int k, cudaStream_t s) {
   using C = Blk<T, LD>;
-  return launch(spmm_block_kernel<T, LD>, dim3(cdiv(rows, 8 * C::RPW)), dim3(256), 0, s, rows, rp, ci, va,
-                X, Y);
+  int rows = 0;
+  for (int q = 0; q < k; ++q) rows = jobs[q].rows > rows ? jobs[q].rows : rows;
+  return launch(spmm_block_kernel<T, LD>, dim3(cdiv(rows, 8 * C::RPW), k), dim3(256), 0, s, jobs[0],
+                jobs[k > 1 ? 1 : 0], jobs[k > 2 ? 2 : 0]);
 }
 
 #define BAMG_LD_DISPATCH(ld, CALL)                 \
@@ -344,13 +359,35 @@ static bamg_status spmm_ld(int rows, const int32_t* rp, const int32_t* ci, const
 template <typename T>
 bamg_status relax_block(int n, int ld, const int32_t* rp, const int32_t* ci, const T* va, const T* dinv,
                         const T* X, T* Y, const T* R, const T* sig, T omega, int keep0, cudaStream_t s) {
-  BAMG_LD_DISPATCH(ld, return (relax_ld<T, LDC>(n, rp, ci, va, dinv, X, Y, R, sig, omega, keep0, s)));
+  RelaxJob<T> j{n, rp, ci, va, dinv, X, Y, R, sig, omega, keep0};
+  BAMG_LD_DISPATCH(ld, return (relax_ld<T, LDC>(j, nullptr, s)));
+}
+
+// The V relaxation with B and the U relaxation with B^T in one launch.
+template <typename T>
+bamg_status relax_block2(int n, int ld, const int32_t* rp, const int32_t* ci, const T* va, const int32_t* trp,
+                         const int32_t* tci, const T* tva, const T* dinv, const T* V, T* Vn, const T* U, T* Un,
+                         const T* RV, const T* RU, const T* sig, T omega, int keepU0, cudaStream_t s) {
+  RelaxJob<T> jv{n, rp, ci, va, dinv, V, Vn, RV, sig, omega, 0};
+  RelaxJob<T> ju{n, trp, tci, tva, dinv, U, Un, RU, sig, omega, keepU0};
+  BAMG_LD_DISPATCH(ld, return (relax_ld<T, LDC>(jv, &ju, s)));
 }
 
 template <typename T>
 bamg_status spmm_block(int rows, int ld, const int32_t* rp, const int32_t* ci, const T* va, const T* X,
                        T* Y, cudaStream_t s) {
-  BAMG_LD_DISPATCH(ld, return (spmm_ld<T, LDC>(rows, rp, ci, va, X, Y, s)));
+  SpmmJob<T> j{rows, rp, ci, va, X, Y};
+  BAMG_LD_DISPATCH(ld, return (spmm_ld<T, LDC>(&j, 1, s)));
+}
+
+// Up to three independent products Y_q = A_q X_q in one launch.
+template <typename T>
+bamg_status spmm_block_multi(int ld, const SpmmJob<T>* jobs, int k, cudaStream_t s) {
+  if (k < 1 || k > 3) {
+    set_error("spmm_block_multi takes 1 to 3 products");
+    return BAMG_ERR_ARG;
+  }
+  BAMG_LD_DISPATCH(ld, return (spmm_ld<T, LDC>(jobs, k, s)));
 }
 
 static int reduce_blocks(int n, int rows_per_block) {
@@ -508,7 +545,11 @@ bamg_status diag_inv(int n, const int32_t* rp, const int32_t* ci, const double* 
                                   const T*, const T*, T*, cudaStream_t);                                \
   template bamg_status dense_gemv<T>(int, const T*, const T*, T*, cudaStream_t);                         \
   template bamg_status diag_inv<T>(int, const int32_t*, const int32_t*, const double*, const int32_t*,  \
-                                   const double*, T*, int*, int*, cudaStream_t);
+                                   const double*, T*, int*, int*, cudaStream_t);                        \
+  template bamg_status relax_block2<T>(int, int, const int32_t*, const int32_t*, const T*, const int32_t*, \
+                                       const int32_t*, const T*, const T*, const T*, T*, const T*, T*,    \
+                                       const T*, const T*, const T*, T, int, cudaStream_t);              \
+  template bamg_status spmm_block_multi<T>(int, const SpmmJob<T>*, int, cudaStream_t);
 
 BAMG_INST(float)
 BAMG_INST(double)

@@ -195,11 +195,9 @@ static bamg_status coarsen_level(bamg_hierarchy* h, int l, DevMem& U, DevMem& V,
   // (not needed when the network proposes the fits)
   if (inhomog && !learned) BAMG_TRY(relax_triplets<T>(h, l, U, V, sig, sig64, s));
   for (int it = 0; !learned && !inhomog && it < p.nu_setup; ++it) {
-    BAMG_TRY(relax_block<T>(L.n, ld, L.B.r(), L.B.c(), Bv, dv, V.as<T>(), tmpV.as<T>(), nullptr, nullptr, om,
-                            0, s));
+    BAMG_TRY(relax_block2<T>(L.n, ld, L.B.r(), L.B.c(), Bv, L.Bt.r(), L.Bt.c(), Btv, dv, V.as<T>(), tmpV.as<T>(),
+                             U.as<T>(), tmpU.as<T>(), nullptr, nullptr, nullptr, om, 1, s));
     std::swap(V, tmpV);
-    BAMG_TRY(relax_block<T>(L.n, ld, L.Bt.r(), L.Bt.c(), Btv, dv, U.as<T>(), tmpU.as<T>(), nullptr, nullptr,
-                            om, 1, s));
     std::swap(U, tmpU);
   }
   tr.mark(s, "relax", l);
@@ -334,36 +332,30 @@ static bamg_status relax_triplets(bamg_hierarchy* h, int l, DevMem& U, DevMem& V
   BAMG_TRY(sums.alloc(sizeof(double) * 3 * ld, s));
   const T om = T(p.omega);
   const T* dv = dinv_of<T>(L);
+  const bool hasM = !L.M.empty(), hasN = !L.N.empty();
+  // M U and N V of the current iterates (reused: U and V do not change
+  // between the Rayleigh update of one sweep and the relaxation of the next)
+  auto mass_products = [&](bool withB) -> bamg_status {
+    SpmmJob<T> jobs[3];
+    int k = 0;
+    if (withB) jobs[k++] = SpmmJob<T>{L.n, L.B.r(), L.B.c(), L.B.vals<T>(), V.as<T>(), BV.as<T>()};
+    if (hasM) jobs[k++] = SpmmJob<T>{L.n, L.M.r(), L.M.c(), L.M.vals<T>(), U.as<T>(), MU.as<T>()};
+    if (hasN) jobs[k++] = SpmmJob<T>{L.n, L.N.r(), L.N.c(), L.N.vals<T>(), V.as<T>(), NV.as<T>()};
+    return k ? spmm_block_multi<T>(ld, jobs, k, s) : BAMG_OK;
+  };
+  BAMG_TRY(mass_products(false));
   for (int it = 0; it < p.nu_setup; ++it) {
-    const T* mu = U.as<T>();
-    const T* nv = V.as<T>();
-    if (!L.M.empty()) {
-      BAMG_TRY(spmm_block<T>(L.n, ld, L.M.r(), L.M.c(), L.M.vals<T>(), U.as<T>(), MU.as<T>(), s));
-      mu = MU.as<T>();
-    }
-    if (!L.N.empty()) {
-      BAMG_TRY(spmm_block<T>(L.n, ld, L.N.r(), L.N.c(), L.N.vals<T>(), V.as<T>(), NV.as<T>(), s));
-      nv = NV.as<T>();
-    }
+    const T* mu = hasM ? MU.as<T>() : U.as<T>();
+    const T* nv = hasN ? NV.as<T>() : V.as<T>();
     // both from the previous iterates (Algorithm 1, second smoothing loop)
-    BAMG_TRY(relax_block<T>(L.n, ld, L.B.r(), L.B.c(), L.B.vals<T>(), dv, V.as<T>(), tV.as<T>(), mu,
-                            sig.as<T>(), om, 0, s));
-    BAMG_TRY(relax_block<T>(L.n, ld, L.Bt.r(), L.Bt.c(), L.Bt.vals<T>(), dv, U.as<T>(), tU.as<T>(), nv,
-                            sig.as<T>(), om, 0, s));
+    BAMG_TRY(relax_block2<T>(L.n, ld, L.B.r(), L.B.c(), L.B.vals<T>(), L.Bt.r(), L.Bt.c(), L.Bt.vals<T>(), dv,
+                             V.as<T>(), tV.as<T>(), U.as<T>(), tU.as<T>(), mu, nv, sig.as<T>(), om, 0, s));
     std::swap(U, tU);
     std::swap(V, tV);
     // eq. singular_value
-    BAMG_TRY(spmm_block<T>(L.n, ld, L.B.r(), L.B.c(), L.B.vals<T>(), V.as<T>(), BV.as<T>(), s));
-    mu = U.as<T>();
-    nv = V.as<T>();
-    if (!L.M.empty()) {
-      BAMG_TRY(spmm_block<T>(L.n, ld, L.M.r(), L.M.c(), L.M.vals<T>(), U.as<T>(), MU.as<T>(), s));
-      mu = MU.as<T>();
-    }
-    if (!L.N.empty()) {
-      BAMG_TRY(spmm_block<T>(L.n, ld, L.N.r(), L.N.c(), L.N.vals<T>(), V.as<T>(), NV.as<T>(), s));
-      nv = NV.as<T>();
-    }
+    BAMG_TRY(mass_products(true));
+    mu = hasM ? MU.as<T>() : U.as<T>();
+    nv = hasN ? NV.as<T>() : V.as<T>();
     BAMG_TRY(col_dots<T>(L.n, ld, 3, U.as<T>(), BV.as<T>(), U.as<T>(), mu, V.as<T>(), nv, sums.as<double>(), s));
     BAMG_TRY(rayleigh_finalize<T>(sums.as<double>(), ld, r, sig.as<T>(), sig64.as<double>(), s));
   }

@@ -41,6 +41,29 @@ bamg_status spgemm(int m, const int32_t* arp, const int32_t* aci, const double* 
 
 // blockops.cu
 template <typename T>
+struct RelaxJob {          // Y = X + omega D^{-1}(sig .* R - A X), keep0: column 0 kept
+  int n;
+  const int32_t *rp, *ci;
+  const T *va, *dinv, *X;
+  T* Y;
+  const T *R, *sig;
+  T omega;
+  int keep0;
+};
+template <typename T>
+struct SpmmJob {           // Y = A X for a rows x cols CSR A and a block X
+  int rows;
+  const int32_t *rp, *ci;
+  const T *va, *X;
+  T* Y;
+};
+template <typename T>
+bamg_status relax_block2(int n, int ld, const int32_t* rp, const int32_t* ci, const T* va, const int32_t* trp,
+                         const int32_t* tci, const T* tva, const T* dinv, const T* V, T* Vn, const T* U, T* Un,
+                         const T* RV, const T* RU, const T* sig, T omega, int keepU0, cudaStream_t s);
+template <typename T>
+bamg_status spmm_block_multi(int ld, const SpmmJob<T>* jobs, int k, cudaStream_t s);
+template <typename T>
 bamg_status relax_block(int n, int ld, const int32_t* rp, const int32_t* ci, const T* va, const T* dinv,
                         const T* X, T* Y, const T* R, const T* sig, T omega, int keep0, cudaStream_t s);
 template <typename T>
