@@ -96,8 +96,10 @@ struct DenseArgs {
   DenseCtl* ctl;
 };
 
-// partial sums: [0, n) vector, n.. scalars and per-value slots, 2 pivot slots
-__host__ __device__ inline int part_stride(int n) { return n + 2 * kMaxR + 4; }
+// partial sums of a block: [0, n) a vector, then scalars, per-value slots and
+// two pivot slots; the bidiagonalization double-buffers its column partials
+// (n + 1 entries at offset (k & 1) * (n + 1)), hence the 2n.
+__host__ __device__ inline int part_stride(int n) { return 2 * n + 2 * kMaxR + 8; }
 
 __device__ inline void csync() { cg::this_cluster().sync(); }
 
@@ -394,10 +396,13 @@ __device__ void householder(T alpha, T s2, T& beta, T& tau, T& scale) {
 // barrier every block forms s_j = tau (W[k][j] + scale * sum_b partial_b[j])
 // and updates its rows.  Right reflector of row k: built and published by
 // the owner of row k, applied by every block to its own rows.
+// Partials and published row of step k go to the buffers of parity k & 1:
+// with one cluster barrier per step a block may start writing step k + 1
+// while another still reads step k.
 template <bool SM, typename T>
 __device__ void bidiag_partials(const DenseArgs<T>& A, int k) {
   const int n = A.n, NB = nblocks<SM>(A), b = blockIdx.x;
-  T* part = part_w<SM>(A);
+  T* part = part_w<SM>(A) + (k & 1) * (n + 1);
   const int i0 = first_own(b, NB, k + 1);
   for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
     T t = 0;
@@ -416,7 +421,7 @@ __device__ void bidiag_partials(const DenseArgs<T>& A, int k) {
     part[n] = s2;
   }
   if (k % NB == b) {                       // publish row k for the other blocks
-    T* rowk = pub_w<SM>(A);
+    T* rowk = pub_w<SM>(A) + (k & 1) * n;
     const T* wk = own<SM>(A, A.S2, k, n);
     for (int j = k + threadIdx.x; j < n; j += blockDim.x) rowk[j] = wk[j];
   }
@@ -427,24 +432,27 @@ __device__ void bidiagonalize(const DenseArgs<T>& A, T* sv, T* red) {
   const int n = A.n, NB = nblocks<SM>(A), b = blockIdx.x;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   T* s_vec = sv;          // n: s_j of the left reflector
-  T* p_vec = sv + n;      // n: right reflector
+  T* p_vec = sv + n;      // n: row k after the left reflector, then the right reflector
+  T* rowk = sv + 2 * n;   // n: row k as published at the end of the previous step
   __shared__ T sc[4];
   bidiag_partials<SM>(A, 0);
   csync();
   for (int k = 0; k < n; ++k) {
-    const T* rowk = pub_r<SM>(A, k % NB);
+    const int po = (k & 1) * (n + 1);            // this step's partial buffer
+    const T* pk_pub = pub_r<SM>(A, k % NB) + (k & 1) * n;
+    for (int j = k + threadIdx.x; j < n; j += blockDim.x) rowk[j] = rd<SM>(pk_pub + j);
     // left reflector of column k
     if (threadIdx.x == 0) {
-      T s2 = part_sum<SM>(A, n);
+      T s2 = part_sum<SM>(A, po + n);
       T beta, tau, scale;
-      householder(rd<SM>(rowk + k), s2, beta, tau, scale);
+      householder(rd<SM>(pk_pub + k), s2, beta, tau, scale);
       sc[0] = tau; sc[1] = scale;
       if (b == 0) A.d[k] = beta;
     }
     __syncthreads();
     const T tau = sc[0], scale = sc[1];
     for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x)
-      s_vec[j] = tau * (rd<SM>(rowk + j) + scale * part_sum<SM>(A, j));
+      s_vec[j] = tau * (rowk[j] + scale * part_sum<SM>(A, po + j));
     __syncthreads();
     if (tau != T(0)) {
       for (int i = first_own(b, NB, k); i < n; i += NB) {
@@ -453,34 +461,33 @@ __device__ void bidiagonalize(const DenseArgs<T>& A, T* sv, T* red) {
         for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) wi[j] -= vi * s_vec[j];
       }
     }
-    __syncthreads();
     if (k == n - 1) break;
-    // right reflector of row k (owner builds and publishes it)
-    if (k % NB == b) {
-      T* pw = pub_w<SM>(A) + 2 * n;
-      const T* wk = own<SM>(A, A.S2, k, n);
-      T* pk = own<SM>(A, A.S3, k, n);
-      T s2 = 0;
-      for (int j = k + 2 + threadIdx.x; j < n; j += blockDim.x) s2 += wk[j] * wk[j];
-      s2 = block_sum(s2, red);
-      T beta, taup, scp;
-      householder(wk[k + 1], s2, beta, taup, scp);
-      for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
-        T pj = (j == k + 1) ? T(1) : wk[j] * scp;
-        pw[j] = pj;
-        pk[j] = pj;
-      }
-      for (int j = threadIdx.x; j <= k; j += blockDim.x) pk[j] = T(0);
-      if (threadIdx.x == 0) {
-        pw[n] = taup;
-        A.e[k] = beta;
-        A.taup[k] = taup;
+    // right reflector of row k, formed by every block from the published row
+    // and s (the owner's updated row k is exactly rowk - s)
+    for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x)
+      p_vec[j] = tau != T(0) ? rowk[j] - s_vec[j] : rowk[j];
+    __syncthreads();
+    T s2 = 0;
+    for (int j = k + 2 + threadIdx.x; j < n; j += blockDim.x) s2 += p_vec[j] * p_vec[j];
+    s2 = block_sum(s2, red);
+    T beta, taup, scp;
+    householder(p_vec[k + 1], s2, beta, taup, scp);
+    __syncthreads();
+    const bool owner = k % NB == b;
+    T* pk = owner ? own<SM>(A, A.S3, k, n) : nullptr;   // the owner keeps the reflector
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      if (j > k) {
+        const T pj = (j == k + 1) ? T(1) : p_vec[j] * scp;
+        p_vec[j] = pj;
+        if (owner) pk[j] = pj;
+      } else if (owner) {
+        pk[j] = T(0);
       }
     }
-    csync();
-    const T* pp = pub_r<SM>(A, k % NB) + 2 * n;
-    const T taup = rd<SM>(pp + n);
-    for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) p_vec[j] = rd<SM>(pp + j);
+    if (owner && threadIdx.x == 0) {
+      A.e[k] = beta;
+      A.taup[k] = taup;
+    }
     __syncthreads();
     if (taup != T(0)) {
       for (int i = first_own(b, NB, k + 1) + NB * w; i < n; i += NB * kWarps) {   // one warp per row
