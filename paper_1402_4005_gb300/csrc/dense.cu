@@ -234,19 +234,23 @@ __device__ bool cholesky_rows(const DenseArgs<T>& A, T* sv) {
         ln[j] = sn[j];
       }
     }
-    for (int i = first_own(b, NB, k + 1); i < n; i += NB) {
-      T* lmi = own<SM>(A, A.LM, i, n);
-      T* lni = own<SM>(A, A.LN, i, n);
-      const T lm = sm[i], ln = sn[i];
-      for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
-        lmi[j] -= lm * sm[j];
-        lni[j] -= ln * sn[j];
-      }
-      if (threadIdx.x == 0) {
-        lmi[k] = lm;
-        lni[k] = ln;
+    // column-major sweep: a thread owns column j of every own row, so its
+    // loads are independent (the factors are disjoint from the scratch)
+    for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
+      const T smj = sm[j], snj = sn[j];
+#pragma unroll 4
+      for (int i = first_own(b, NB, k + 1); i < n; i += NB) {
+        T* __restrict__ lmi = own<SM>(A, A.LM, i, n);
+        T* __restrict__ lni = own<SM>(A, A.LN, i, n);
+        lmi[j] -= sm[i] * smj;
+        lni[j] -= sn[i] * snj;
       }
     }
+    if (threadIdx.x == 0)
+      for (int i = first_own(b, NB, k + 1); i < n; i += NB) {
+        own<SM>(A, A.LM, i, n)[k] = sm[i];
+        own<SM>(A, A.LN, i, n)[k] = sn[i];
+      }
     __syncthreads();
     if (k + 1 < n && (k + 1) % NB == b) chol_publish<SM>(A, k + 1);
     csync();
@@ -434,31 +438,38 @@ __device__ void bidiagonalize(const DenseArgs<T>& A, T* sv, T* red) {
   T* s_vec = sv;          // n: s_j of the left reflector
   T* p_vec = sv + n;      // n: row k after the left reflector, then the right reflector
   T* rowk = sv + 2 * n;   // n: row k as published at the end of the previous step
-  __shared__ T sc[4];
+  __shared__ T sc[2];
   bidiag_partials<SM>(A, 0);
   csync();
   for (int k = 0; k < n; ++k) {
     const int po = (k & 1) * (n + 1);            // this step's partial buffer
     const T* pk_pub = pub_r<SM>(A, k % NB) + (k & 1) * n;
-    for (int j = k + threadIdx.x; j < n; j += blockDim.x) rowk[j] = rd<SM>(pk_pub + j);
-    // left reflector of column k
+    // left reflector of column k: thread 0 forms tau while every thread
+    // fetches its entries of row k and of the column sums (s_vec holds the
+    // sums until tau is known)
     if (threadIdx.x == 0) {
-      T s2 = part_sum<SM>(A, po + n);
       T beta, tau, scale;
-      householder(rd<SM>(pk_pub + k), s2, beta, tau, scale);
+      householder(rd<SM>(pk_pub + k), part_sum<SM>(A, po + n), beta, tau, scale);
       sc[0] = tau; sc[1] = scale;
       if (b == 0) A.d[k] = beta;
     }
+    for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
+      rowk[j] = rd<SM>(pk_pub + j);
+      s_vec[j] = part_sum<SM>(A, po + j);
+    }
     __syncthreads();
     const T tau = sc[0], scale = sc[1];
-    for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x)
-      s_vec[j] = tau * (rowk[j] + scale * part_sum<SM>(A, po + j));
+    for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) s_vec[j] = tau * (rowk[j] + scale * s_vec[j]);
     __syncthreads();
     if (tau != T(0)) {
-      for (int i = first_own(b, NB, k); i < n; i += NB) {
-        T* wi = own<SM>(A, A.S2, i, n);
-        const T vi = (i == k) ? T(1) : wi[k] * scale;
-        for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) wi[j] -= vi * s_vec[j];
+      for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
+        const T sj = s_vec[j];
+#pragma unroll 4
+        for (int i = first_own(b, NB, k); i < n; i += NB) {
+          T* __restrict__ wi = own<SM>(A, A.S2, i, n);
+          const T vi = (i == k) ? T(1) : wi[k] * scale;
+          wi[j] -= vi * sj;
+        }
       }
     }
     if (k == n - 1) break;
@@ -467,11 +478,11 @@ __device__ void bidiagonalize(const DenseArgs<T>& A, T* sv, T* red) {
     for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x)
       p_vec[j] = tau != T(0) ? rowk[j] - s_vec[j] : rowk[j];
     __syncthreads();
-    T s2 = 0;
-    for (int j = k + 2 + threadIdx.x; j < n; j += blockDim.x) s2 += p_vec[j] * p_vec[j];
-    s2 = block_sum(s2, red);
-    T beta, taup, scp;
-    householder(p_vec[k + 1], s2, beta, taup, scp);
+    T s2r = 0;
+    for (int j = k + 2 + threadIdx.x; j < n; j += blockDim.x) s2r += p_vec[j] * p_vec[j];
+    s2r = block_sum(s2r, red);
+    T betar, taup, scp;
+    householder(p_vec[k + 1], s2r, betar, taup, scp);
     __syncthreads();
     const bool owner = k % NB == b;
     T* pk = owner ? own<SM>(A, A.S3, k, n) : nullptr;   // the owner keeps the reflector
@@ -485,7 +496,7 @@ __device__ void bidiagonalize(const DenseArgs<T>& A, T* sv, T* red) {
       }
     }
     if (owner && threadIdx.x == 0) {
-      A.e[k] = beta;
+      A.e[k] = betar;
       A.taup[k] = taup;
     }
     __syncthreads();
