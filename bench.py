@@ -67,7 +67,7 @@ def load_peaks():
 
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -82,7 +82,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -353,18 +353,21 @@ def learned_section(api, torch, stream, eval_side=2048):
     res = {"train_rows": int(X.shape[0]), "train_chains": len(train), "harvest_s": round(t_h - t0, 2),
            "train_s": round(t_train, 2), "epochs": 40, "loss_first": losses[0], "loss_last": losses[-1],
            "workload": f"tandem queue {eval_side}x{eval_side} ({ch.n} states)"}
-    # default depth (8 levels down to 16 x 16) for both fits, and an LS
-    # hierarchy tuned to converge at this size (7 levels, r = 32, 20 setup
-    # relaxations: with the defaults its deepest levels get b_ii <= 0)
-    variants = (("ls_mixed", dict(precision="mixed", r=16)),
-                ("learned_mixed", dict(precision="mixed", r=16, interp="mlp")),
-                ("learned_fp64", dict(precision="fp64", r=16, interp="mlp")),
-                ("ls_tuned_mixed", dict(precision="mixed", r=32, max_levels=7, nu_setup=20)))
+    # 7 levels (32 x 32 coarsest, solved densely): network fits with the
+    # default parameters, and the LS fits with the same parameters and tuned
+    # to converge (r = 32, 20 setup relaxations); at the default depth (8
+    # levels) both stall, because the deepest levels get b_ii <= 0 rows
+    variants = (("learned_mixed", dict(precision="mixed", r=16, max_levels=7, interp="mlp"), 2),
+                ("learned_fp64", dict(precision="fp64", r=16, max_levels=7, interp="mlp"), 1),
+                ("ls_mixed", dict(precision="mixed", r=16, max_levels=7), 1),
+                ("ls_tuned_mixed", dict(precision="mixed", r=32, max_levels=7, nu_setup=20), 2),
+                ("learned_default_depth_mixed", dict(precision="mixed", r=16, interp="mlp"), 1),
+                ("ls_default_depth_mixed", dict(precision="mixed", r=16), 1))
     xs = {}
-    for name, kw in variants:
+    for name, kw, reps in variants:
         rows = []
         with torch.cuda.stream(stream):
-            for k in range(3):
+            for k in range(reps + 1):
                 p = api.bamg_params_default(seed=2, mlp_params=params, **kw)
                 torch.cuda.synchronize()
                 ms, (h, x, info) = event_ms(torch, stream, lambda: (lambda hh: (hh, *api.bamg_solve(
@@ -372,7 +375,7 @@ def learned_section(api, torch, stream, eval_side=2048):
                         api.bamg_setup(rp, ci, va, ch.n, p, nx=eval_side, ny=eval_side, stream=stream)))
                 if k:
                     rows.append((ms, info))
-                if k < 2:
+                if k < reps:
                     h.destroy()
             f = api.bamg_vcycle_factor(h, iters=12, stream=stream)
         xs[name] = x
@@ -505,7 +508,7 @@ def cpu_baseline_subprocess(steps=1):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--sections", default="all",
