@@ -245,6 +245,7 @@ bamg_status bamg_solve_host(const bamg_csr* A, const bamg_params* p, const bamg_
 
 void bamg_destroy(bamg_hierarchy* h) {
   if (!h) return;
+  gmres_release(h);
   if (h->vexec) cudaGraphExecDestroy(h->vexec);
   if (h->vgraph) cudaGraphDestroy(h->vgraph);
   if (h->cap_stream) {

@@ -45,6 +45,10 @@ struct Level {
 
 }  // namespace bamg
 
+namespace bamg {
+struct GmresState;   // solve.cu: persistent FGMRES workspace and captured step
+}
+
 struct bamg_hierarchy {
   bamg_params p;
   int ld = 8;             // block stride (power of two >= r)
@@ -63,6 +67,7 @@ struct bamg_hierarchy {
   double setup_ms = 0.0;
   double op_cplx = 0.0, grid_cplx = 0.0;
   int rankdef = 0;
+  bamg::GmresState* gm = nullptr;       // FGMRES workspace (first solve)
   int learned = 0;                      // fits from the interpolation network
   bamg::DevMem mlp;                     // its parameters (float, copied at setup)
 };
@@ -75,6 +80,7 @@ bamg_status fgmres(bamg_hierarchy* h, double* x, const bamg_solve_params* sp, ba
                    cudaStream_t s);
 bamg_status setup_finest(bamg_hierarchy* h, const bamg_csr* A, cudaStream_t s);
 template <typename T> bamg_status run_setup(bamg_hierarchy* h, cudaStream_t s);
+void gmres_release(bamg_hierarchy* h);
 // mlp.cu: P rows and Q columns of a geometric level from the network
 int mlp_num_params();
 bamg_status mlp_fits(const Level& L, const float* params, double* fitP, double* fitQ, cudaStream_t s);

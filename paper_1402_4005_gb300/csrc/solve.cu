@@ -16,6 +16,7 @@
 // allows it to hold.
 #include <chrono>
 #include <cmath>
+#include <new>
 #include <vector>
 
 #include "hierarchy.cuh"
@@ -135,10 +136,15 @@ bamg_status vcycle_run(bamg_hierarchy* h, cudaStream_t s) {
 // ------------------------------------------------------------- FGMRES kernels
 constexpr int kRedBlocks = 256;
 
-// part[b * K + k] = sum over block b's chunk of V_k . w
-__global__ void multidot_kernel(int n, int K, const double* __restrict__ V, size_t ldv,
-                                const double* __restrict__ w, double* __restrict__ part) {
-  int k = blockIdx.y;
+// The Arnoldi step of FGMRES runs as one captured graph; its kernels read
+// the step index j (basis vectors 0..j in use) from device memory, so the
+// same graph serves every step.  Partial sums use the fixed row stride m+1.
+
+// part[b * (m+1) + k] = block b's share of V_k . w for k <= j
+__global__ void multidot_kernel(int n, int m, const int* __restrict__ dj, const double* __restrict__ V,
+                                size_t ldv, const double* __restrict__ w, double* __restrict__ part) {
+  const int k = blockIdx.y;
+  if (k > dj[0]) return;
   const double* v = V + (size_t)k * ldv;
   double s = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) s += v[i] * w[i];
@@ -149,19 +155,58 @@ __global__ void multidot_kernel(int n, int K, const double* __restrict__ V, size
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
-    part[(size_t)blockIdx.x * K + k] = t;
+    part[(size_t)blockIdx.x * (m + 1) + k] = t;
   }
 }
 
-// w -= sum_k h[k] V_k
-__global__ void orth_update_kernel(int n, int K, const double* __restrict__ V, size_t ldv,
+// out[k] = sum over the nb blocks of part[b * (m+1) + k], k <= j (fixed order)
+__global__ void multidot_reduce_kernel(int nb, int m, const int* __restrict__ dj, const double* __restrict__ part,
+                                       double* __restrict__ out) {
+  __shared__ double sh[8];
+  const int k = blockIdx.x;
+  if (k > dj[0]) return;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[(size_t)b * (m + 1) + k];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
+    out[k] = t;
+  }
+}
+
+// w -= sum_{k <= j} h[k] V_k
+__global__ void orth_update_kernel(int n, const int* __restrict__ dj, const double* __restrict__ V, size_t ldv,
                                    const double* __restrict__ h, double* __restrict__ w) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const int K = dj[0] + 1;
   double acc = w[i];
   for (int k = 0; k < K; ++k) acc -= h[k] * V[(size_t)k * ldv + i];
   w[i] = acc;
 }
+
+// out = V_j (get = 1) or V_j = in (get = 0)
+__global__ void column_io_kernel(int n, const int* __restrict__ dj, int get, double* __restrict__ V,
+                                 double* __restrict__ io) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double* v = V + (size_t)dj[0] * n;
+  if (get) io[i] = v[i];
+  else v[i] = io[i];
+}
+
+// V_{j+1} = w / ||w||
+__global__ void next_basis_kernel(int n, const int* __restrict__ dj, const double* __restrict__ w,
+                                  const double* __restrict__ nrm, double* __restrict__ V) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  V[(size_t)(dj[0] + 1) * n + i] = w[i] / nrm[0];
+}
+
+__global__ void step_kernel(int* dj) { dj[0] += 1; }
 
 // y = x + sum_k c[k] Z_k
 __global__ void combine_kernel(int n, int K, const double* __restrict__ Z, size_t ldz,
@@ -206,10 +251,12 @@ __global__ void sqrt_kernel(double* v) { v[0] = sqrt(v[0]); }
 // the rotated right-hand side g; st = {|g_{j+1}|, ||w||}.  One thread; the
 // column is streamed (each rotation only needs the entry carried from the
 // previous one).
-__global__ void givens_kernel(int j, int m, const double* __restrict__ h1, const double* __restrict__ h2,
-                              const double* __restrict__ wnorm, double* __restrict__ R, double* __restrict__ cs,
-                              double* __restrict__ sn, double* __restrict__ g, double* __restrict__ st) {
+__global__ void givens_kernel(const int* __restrict__ dj, int m, const double* __restrict__ h1,
+                              const double* __restrict__ h2, const double* __restrict__ wnorm,
+                              double* __restrict__ R, double* __restrict__ cs, double* __restrict__ sn,
+                              double* __restrict__ g, double* __restrict__ st) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int j = dj[0];
   const double hn = wnorm[0];
   double carry = h1[0] + h2[0];
   for (int k = 0; k < j; ++k) {
@@ -279,11 +326,6 @@ static bamg_status norm2_dev(Gm& G, const double* x, double* out, cudaStream_t s
   return launch(sqrt_kernel, dim3(1), dim3(1), 0, s, out);
 }
 
-static bamg_status multidot_dev(Gm& G, int K, const double* V, const double* w, double* out, cudaStream_t s) {
-  int nb = red_blocks(G.n);
-  BAMG_TRY(launch(multidot_kernel, dim3(nb, K), dim3(256), 0, s, G.n, K, V, (size_t)G.n, w, G.part.as<double>()));
-  return reduce_partials(G.part.as<double>(), nb, K, out, s);
-}
 
 // rel = ||B x||_1 / ||x||_1 (read back to the host); xn1 = ||x||_1
 static bamg_status true_residual(bamg_hierarchy* h, Gm& G, const double* x, double* rel, double* xn1,
@@ -302,31 +344,122 @@ static bamg_status true_residual(bamg_hierarchy* h, Gm& G, const double* x, doub
   return BAMG_OK;
 }
 
+// Persistent FGMRES workspace of a hierarchy and the captured Arnoldi step
+// (rebuilt when the restart length changes).  Buffers live on the
+// hierarchy's private stream, which outlives them.
+struct GmresState {
+  int m = 0;
+  Gm G;
+  DevMem dj;                 // step index j of the current restart cycle
+  double* st_host = nullptr; // pinned: {|g_{j+1}|, ||w||} of the last step
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t kernels = 0;
+  ~GmresState() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (st_host) cudaFreeHost(st_host);
+  }
+};
+
+void gmres_release(bamg_hierarchy* h) {
+  delete h->gm;
+  h->gm = nullptr;
+}
+
+// One Arnoldi step j (read from the device): z_j = C v_j (V-cycle), w = B z_j,
+// two classical Gram-Schmidt passes, ||w||, the Givens update of column j,
+// v_{j+1} = w / ||w||, j <- j + 1, and {|g_{j+1}|, ||w||} to pinned memory.
+static bamg_status arnoldi_body(bamg_hierarchy* h, GmresState& S, cudaStream_t s) {
+  Level& L = h->lv[0];
+  Gm& G = S.G;
+  const int n = G.n, m = G.m;
+  const unsigned gv = cdiv(n, 256);
+  const int nb = red_blocks(n);
+  const int* dj = S.dj.as<int>();
+  double* V = G.V.as<double>();
+  BAMG_TRY(launch(column_io_kernel, dim3(gv), dim3(256), 0, s, n, dj, 1, V, h->io_in.as<double>()));
+  BAMG_TRY(h->mixed ? vcycle_body<float>(h, s) : vcycle_body<double>(h, s));
+  BAMG_TRY(launch(column_io_kernel, dim3(gv), dim3(256), 0, s, n, dj, 0, G.Z.as<double>(), h->io_out.as<double>()));
+  BAMG_TRY(csr_vec<double>(VEC_SPMV, n, L.vec_g, L.B.r(), L.B.c(), L.B.v(), L.dinv.as<double>(), 1.0,
+                           (const double*)h->io_out.as<double>(), nullptr, G.w.as<double>(), s));
+  for (int pass = 0; pass < 2; ++pass) {       // classical Gram-Schmidt, twice
+    double* hc = pass ? G.h2.as<double>() : G.h1.as<double>();
+    BAMG_TRY(launch(multidot_kernel, dim3(nb, m + 1), dim3(256), 0, s, n, m, dj, (const double*)V, (size_t)n,
+                    (const double*)G.w.as<double>(), G.part.as<double>()));
+    BAMG_TRY(launch(multidot_reduce_kernel, dim3(m + 1), dim3(256), 0, s, nb, m, dj,
+                    (const double*)G.part.as<double>(), hc));
+    BAMG_TRY(launch(orth_update_kernel, dim3(gv), dim3(256), 0, s, n, dj, (const double*)V, (size_t)n,
+                    (const double*)hc, G.w.as<double>()));
+  }
+  BAMG_TRY(norm2_dev(G, G.w.as<double>(), G.scal.as<double>(), s));
+  BAMG_TRY(launch(givens_kernel, dim3(1), dim3(32), 0, s, dj, m, (const double*)G.h1.as<double>(),
+                  (const double*)G.h2.as<double>(), (const double*)G.scal.as<double>(), G.R.as<double>(),
+                  G.cs.as<double>(), G.sn.as<double>(), G.g.as<double>(), G.st.as<double>()));
+  BAMG_TRY(launch(next_basis_kernel, dim3(gv), dim3(256), 0, s, n, dj, (const double*)G.w.as<double>(),
+                  (const double*)G.scal.as<double>(), V));
+  BAMG_TRY(launch(step_kernel, dim3(1), dim3(1), 0, s, S.dj.as<int>()));
+  BAMG_CUDA(cudaMemcpyAsync(S.st_host, G.st.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  return BAMG_OK;
+}
+
+static bamg_status gmres_prepare(bamg_hierarchy* h, int m) {
+  if (h->gm && h->gm->m == m) return BAMG_OK;
+  gmres_release(h);
+  cudaStream_t cs = h->cap_stream;
+  GmresState* S = new (std::nothrow) GmresState();
+  if (!S) return BAMG_ERR_OOM;
+  h->gm = S;
+  const int n = h->lv[0].n;
+  Gm& G = S->G;
+  S->m = m;
+  G.n = n;
+  G.m = m;
+  BAMG_TRY(G.V.alloc(sizeof(double) * (size_t)(m + 1) * n, cs));
+  BAMG_TRY(G.Z.alloc(sizeof(double) * (size_t)m * n, cs));
+  BAMG_TRY(G.w.alloc(sizeof(double) * n, cs));
+  BAMG_TRY(G.w2.alloc(sizeof(double) * n, cs));
+  BAMG_TRY(G.xj.alloc(sizeof(double) * n, cs));
+  BAMG_TRY(G.zeros.alloc(sizeof(double) * n, cs));
+  BAMG_TRY(G.h1.alloc(sizeof(double) * (m + 1), cs));
+  BAMG_TRY(G.h2.alloc(sizeof(double) * (m + 1), cs));
+  BAMG_TRY(G.part.alloc(sizeof(double) * kRedBlocks * (m + 1), cs));
+  BAMG_TRY(G.R.alloc(sizeof(double) * (size_t)(m + 1) * m, cs));
+  BAMG_TRY(G.cs.alloc(sizeof(double) * m, cs));
+  BAMG_TRY(G.sn.alloc(sizeof(double) * m, cs));
+  BAMG_TRY(G.g.alloc(sizeof(double) * (m + 1), cs));
+  BAMG_TRY(G.y.alloc(sizeof(double) * m, cs));
+  BAMG_TRY(G.st.alloc(sizeof(double) * 2, cs));
+  BAMG_TRY(G.scal.alloc(sizeof(double) * 2, cs));
+  BAMG_TRY(G.sums.alloc(sizeof(double) * 4, cs));
+  BAMG_TRY(S->dj.alloc(sizeof(int), cs));
+  BAMG_CUDA(cudaMemsetAsync(G.zeros.p, 0, sizeof(double) * n, cs));
+  BAMG_CUDA(cudaHostAlloc(&S->st_host, 2 * sizeof(double), cudaHostAllocDefault));
+  BAMG_CUDA(cudaStreamSynchronize(cs));
+  uint64_t before = t_launches;
+  BAMG_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  bamg_status st = arnoldi_body(h, *S, cs);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &g);
+  if (st != BAMG_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  BAMG_CUDA(e);
+  S->graph = g;
+  BAMG_CUDA(cudaGraphInstantiate(&S->exec, g, 0));
+  S->kernels = t_launches - before;
+  g_launches.fetch_sub(S->kernels);  // counted at each replay
+  return BAMG_OK;
+}
+
 bamg_status fgmres(bamg_hierarchy* h, double* x, const bamg_solve_params* sp, bamg_solve_info* info,
                    cudaStream_t s) {
   Level& L = h->lv[0];
   const int n = L.n, m = sp->restart;
-  Gm G;
-  G.n = n;
-  G.m = m;
-  BAMG_TRY(G.V.alloc(sizeof(double) * (size_t)(m + 1) * n, s));
-  BAMG_TRY(G.Z.alloc(sizeof(double) * (size_t)m * n, s));
-  BAMG_TRY(G.w.alloc(sizeof(double) * n, s));
-  BAMG_TRY(G.w2.alloc(sizeof(double) * n, s));
-  BAMG_TRY(G.xj.alloc(sizeof(double) * n, s));
-  BAMG_TRY(G.zeros.alloc(sizeof(double) * n, s));
-  BAMG_TRY(G.h1.alloc(sizeof(double) * (m + 1), s));
-  BAMG_TRY(G.h2.alloc(sizeof(double) * (m + 1), s));
-  BAMG_TRY(G.part.alloc(sizeof(double) * kRedBlocks * (m + 1), s));
-  BAMG_TRY(G.R.alloc(sizeof(double) * (size_t)(m + 1) * m, s));
-  BAMG_TRY(G.cs.alloc(sizeof(double) * m, s));
-  BAMG_TRY(G.sn.alloc(sizeof(double) * m, s));
-  BAMG_TRY(G.g.alloc(sizeof(double) * (m + 1), s));
-  BAMG_TRY(G.y.alloc(sizeof(double) * m, s));
-  BAMG_TRY(G.st.alloc(sizeof(double) * 2, s));
-  BAMG_TRY(G.scal.alloc(sizeof(double) * 2, s));
-  BAMG_TRY(G.sums.alloc(sizeof(double) * 4, s));
-  BAMG_CUDA(cudaMemsetAsync(G.zeros.p, 0, sizeof(double) * n, s));
+  BAMG_TRY(gmres_prepare(h, m));
+  GmresState& S = *h->gm;
+  Gm& G = S.G;
   BAMG_CUDA(cudaMemcpyAsync(x, h->x0.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
 
   double rel = 0.0, xn1 = 1.0;
@@ -343,7 +476,7 @@ bamg_status fgmres(bamg_hierarchy* h, double* x, const bamg_solve_params* sp, ba
   double* Z = G.Z.as<double>();
   const unsigned gv = cdiv(n, 256);
   while (!done && its < sp->max_iter) {
-    // r = -B x, beta = ||r||, v_0 = r / beta, g = beta e_1
+    // r = -B x, beta = ||r||, v_0 = r / beta, g = beta e_1, j = 0
     BAMG_TRY(csr_vec<double>(VEC_RESID, n, L.vec_g, L.B.r(), L.B.c(), L.B.v(), L.dinv.as<double>(), 1.0, x,
                              G.zeros.as<double>(), G.w.as<double>(), s));
     BAMG_TRY(norm2_dev(G, G.w.as<double>(), G.scal.as<double>(), s));
@@ -351,35 +484,18 @@ bamg_status fgmres(bamg_hierarchy* h, double* x, const bamg_solve_params* sp, ba
                     (const double*)G.scal.as<double>(), 1, V));
     BAMG_TRY(launch(init_g_kernel, dim3(1), dim3(128), 0, s, m, (const double*)G.scal.as<double>(),
                     G.g.as<double>()));
+    BAMG_CUDA(cudaMemsetAsync(S.dj.p, 0, sizeof(int), s));
     for (int j = 0; j < m && !done; ++j) {
-      double* vj = V + (size_t)j * n;
-      double* zj = Z + (size_t)j * n;
-      // z_j = C v_j (V-cycle graph), w = B z_j
-      BAMG_CUDA(cudaMemcpyAsync(h->io_in.p, vj, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-      BAMG_TRY(vcycle_run(h, s));
-      BAMG_CUDA(cudaMemcpyAsync(zj, h->io_out.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-      BAMG_TRY(csr_vec<double>(VEC_SPMV, n, L.vec_g, L.B.r(), L.B.c(), L.B.v(), L.dinv.as<double>(), 1.0, zj,
-                               nullptr, G.w.as<double>(), s));
-      // classical Gram-Schmidt, twice
-      int K = j + 1;
-      BAMG_TRY(multidot_dev(G, K, V, G.w.as<double>(), G.h1.as<double>(), s));
-      BAMG_TRY(launch(orth_update_kernel, dim3(gv), dim3(256), 0, s, n, K, (const double*)V, (size_t)n,
-                      (const double*)G.h1.as<double>(), G.w.as<double>()));
-      BAMG_TRY(multidot_dev(G, K, V, G.w.as<double>(), G.h2.as<double>(), s));
-      BAMG_TRY(launch(orth_update_kernel, dim3(gv), dim3(256), 0, s, n, K, (const double*)V, (size_t)n,
-                      (const double*)G.h2.as<double>(), G.w.as<double>()));
-      BAMG_TRY(norm2_dev(G, G.w.as<double>(), G.scal.as<double>(), s));
-      BAMG_TRY(launch(givens_kernel, dim3(1), dim3(32), 0, s, j, m, (const double*)G.h1.as<double>(),
-                      (const double*)G.h2.as<double>(), (const double*)G.scal.as<double>(), G.R.as<double>(),
-                      G.cs.as<double>(), G.sn.as<double>(), G.g.as<double>(), G.st.as<double>()));
-      double st[2];
-      BAMG_CUDA(cudaMemcpyAsync(st, G.st.p, sizeof(st), cudaMemcpyDeviceToHost, s));
+      BAMG_CUDA(cudaGraphLaunch(S.exec, s));
+      g_launches.fetch_add(S.kernels);
       BAMG_CUDA(cudaStreamSynchronize(s));
+      const double st0 = S.st_host[0], st1 = S.st_host[1];
+      const int K = j + 1;
       ++its;
-      if (it7 < 0 && st[0] <= 1e-7 * xn2_0) it7 = its;
-      breakdown = !(st[1] > 0.0);
+      if (it7 < 0 && st0 <= 1e-7 * xn2_0) it7 = its;
+      breakdown = !(st1 > 0.0);
       bool last = (j == m - 1) || its >= sp->max_iter || breakdown;
-      if (st[0] <= 2.0 * sp->tol * xn1_0 || last) {
+      if (st0 <= 2.0 * sp->tol * xn1_0 || last) {
         BAMG_TRY(launch(ysolve_kernel, dim3(1), dim3(32), 0, s, j, m, (const double*)G.R.as<double>(),
                         (const double*)G.g.as<double>(), G.y.as<double>()));
         BAMG_TRY(launch(combine_kernel, dim3(gv), dim3(256), 0, s, n, K, (const double*)Z, (size_t)n,
@@ -391,8 +507,6 @@ bamg_status fgmres(bamg_hierarchy* h, double* x, const bamg_solve_params* sp, ba
           break;
         }
       }
-      BAMG_TRY(launch(scale_by_kernel, dim3(gv), dim3(256), 0, s, n, (const double*)G.w.as<double>(),
-                      (const double*)G.scal.as<double>(), 1, V + (size_t)(j + 1) * n));
     }
     if (breakdown && !done) break;
   }
