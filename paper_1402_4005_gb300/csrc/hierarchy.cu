@@ -132,20 +132,14 @@ static bamg_status finish_level(bamg_hierarchy* h, Level& L, int l, cudaStream_t
   L.n = L.B.rows;
   BAMG_TRY(csr_transpose(L.B, L.Bt, s));
   BAMG_TRY(L.dinv.alloc(sizeof(double) * L.n, s));
-  DevMem flags;
-  BAMG_TRY(flags.alloc(2 * sizeof(int), s));
-  int init[2] = {INT32_MAX, 0};
-  BAMG_CUDA(cudaMemcpyAsync(flags.p, init, sizeof(init), cudaMemcpyHostToDevice, s));
+  // flags: {first row whose row and column are zero (0x7F7F7F7F = none),
+  // rows with the l1 divisor}; read for all levels at the end of the setup
+  BAMG_TRY(L.dflags.alloc(2 * sizeof(int), s));
+  BAMG_CUDA(cudaMemsetAsync(L.dflags.p, 0x7F, sizeof(int), s));
+  BAMG_CUDA(cudaMemsetAsync(L.dflags.as<int>() + 1, 0, sizeof(int), s));
   BAMG_TRY(diag_inv<double>(L.n, L.B.r(), L.B.c(), L.B.v(), L.Bt.r(), L.Bt.v(), L.dinv.as<double>(),
-                            flags.as<int>(), flags.as<int>() + 1, s));
-  int hf[2] = {0, 0};
-  BAMG_CUDA(cudaMemcpyAsync(hf, flags.p, sizeof(hf), cudaMemcpyDeviceToHost, s));
-  BAMG_CUDA(cudaStreamSynchronize(s));
-  if (hf[0] != INT32_MAX) {
-    set_error("level %d: row and column %d of B are zero", l, hf[0]);
-    return BAMG_ERR_NUMERIC;
-  }
-  L.nsafe = hf[1];
+                            L.dflags.as<int>(), L.dflags.as<int>() + 1, s));
+  (void)l;
   double avg = L.n ? (double)L.B.nnz / L.n : 1.0;
   L.vec_g = avg <= 3 ? 2 : avg <= 6 ? 4 : avg <= 12 ? 8 : avg <= 24 ? 16 : 32;
   if (h->mixed) {
@@ -238,8 +232,17 @@ static bamg_status coarsen_level(bamg_hierarchy* h, int l, DevMem& U, DevMem& V,
   BAMG_TRY(L.cpt.alloc(sizeof(int32_t) * nc, s));
   BAMG_TRY(coarse_points(L.n, L.cf.as<int8_t>(), L.cmap.as<int32_t>(), L.cpt.as<int32_t>(), s));
   int32_t njz = 0;
-  BAMG_CUDA(cudaMemcpyAsync(&njz, L.Jrp.as<int32_t>() + L.n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  BAMG_CUDA(cudaStreamSynchronize(s));
+  if (p.coarsening == BAMG_COARSEN_GEOMETRIC) {
+    // |J_i| summed over the fine points in closed form: per dimension of
+    // size N the odd indices contribute 2 coarse neighbours each, the last
+    // one only 1 when N is even (S_N), and E_N = ceil(N / 2) indices are even
+    auto S = [](int N) { return 2 * (N / 2) - (N % 2 == 0 ? 1 : 0); };
+    auto E = [](int N) { return (N + 1) / 2; };
+    njz = S(L.nx) * E(L.ny) + E(L.nx) * S(L.ny) + S(L.nx) * S(L.ny);
+  } else {
+    BAMG_CUDA(cudaMemcpyAsync(&njz, L.Jrp.as<int32_t>() + L.n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    BAMG_CUDA(cudaStreamSynchronize(s));
+  }
   tr.mark(s, "split+sets", l);
   // P rows and Q columns (eq. ls_interpolation; Section 5)
   DevMem fitP, fitQ;
@@ -362,6 +365,23 @@ static bamg_status relax_triplets(bamg_hierarchy* h, int l, DevMem& U, DevMem& V
   return BAMG_OK;
 }
 
+// The divisor flags of every level in one read: rows with the l1 divisor per
+// level, and an error for a zero row and column.
+static bamg_status check_levels(bamg_hierarchy* h, cudaStream_t s) {
+  std::vector<int> f(2 * h->lv.size(), 0);
+  for (size_t l = 0; l < h->lv.size(); ++l)
+    BAMG_CUDA(cudaMemcpyAsync(&f[2 * l], h->lv[l].dflags.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  BAMG_CUDA(cudaStreamSynchronize(s));
+  for (size_t l = 0; l < h->lv.size(); ++l) {
+    if (f[2 * l] != 0x7F7F7F7F) {
+      set_error("level %zu: row and column %d of B are zero", l, f[2 * l]);
+      return BAMG_ERR_NUMERIC;
+    }
+    h->lv[l].nsafe = f[2 * l + 1];
+  }
+  return BAMG_OK;
+}
+
 static void complexities(bamg_hierarchy* h) {
   // eq. operator_complexity_def; Section 7
   double nnz_sum = 0, n_sum = 0;
@@ -406,6 +426,7 @@ static bamg_status learned_unwind(bamg_hierarchy* h, int l, int rr, const double
   }
   h->x0 = std::move(x);
   BAMG_TRY(orient_normalise(h->lv[0].n, h->x0.as<double>(), s));
+  BAMG_TRY(check_levels(h, s));
   complexities(h);
   return BAMG_OK;
 }
@@ -538,6 +559,7 @@ static bamg_status run_setup(bamg_hierarchy* h, cudaStream_t s) {
   BAMG_TRY(launch(column_kernel, dim3(cdiv(n0, 256)), dim3(256), 0, s, n0, ld, kmin,
                   (const double*)h->V64.as<double>(), h->x0.as<double>()));
   BAMG_TRY(orient_normalise(n0, h->x0.as<double>(), s));
+  BAMG_TRY(check_levels(h, s));
   complexities(h);
   return BAMG_OK;
 }

@@ -36,7 +36,7 @@ struct Level {
   int vec_g = 4;          // lanes per row in the vector kernels (chosen from nnz/row)
   int nsafe = 0;          // rows with b_ii <= 0 whose Jacobi divisor is an l1 norm
   Csr B, Bt, M, N, P, Qt, Q, Pt;
-  DevMem dinv, dinv32;
+  DevMem dinv, dinv32, dflags;
   DevMem cf, cmap, cpt, Jrp, Jci;
   DevMem s, t;            // sqrt LS weights (double[ld])
   // V-cycle vectors in the V-cycle precision
