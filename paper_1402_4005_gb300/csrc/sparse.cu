@@ -121,8 +121,59 @@ __global__ void scan_apply(const int32_t* __restrict__ in, int n, const long lon
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = (int32_t)*total;
 }
 
+// Arrays up to kScanOneBlock entries: one block of 1024 threads, each
+// scanning a contiguous chunk of at most 8 (chunk sums, a block scan of
+// them, then the chunk prefixes), so the scan is a single launch.  Larger
+// arrays take the three-launch tiled scan, which spreads over the SMs.
+constexpr int kScanOneThreads = 1024;
+constexpr int kScanOneBlock = 8 * kScanOneThreads;
+
+__global__ void __launch_bounds__(kScanOneThreads) scan_one_block(const int32_t* __restrict__ in, int n,
+                                                                   int32_t* __restrict__ out) {
+  __shared__ long long sh[kScanOneThreads / 32];
+  const int chunk = (n + kScanOneThreads - 1) / kScanOneThreads;
+  const int b = threadIdx.x * chunk, e = min(n, b + chunk);
+  long long sum = 0;
+  for (int i = b; i < e; ++i) sum += in[i];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  long long x = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    long long t = sh[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      long long y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    sh[lane] = t;
+  }
+  __syncthreads();
+  long long run = (w > 0 ? sh[w - 1] : 0) + x - sum;
+  for (int i = b; i < e; ++i) {
+    out[i] = (int32_t)run;
+    run += in[i];
+  }
+  if (threadIdx.x == kScanOneThreads - 1) out[n] = (int32_t)sh[kScanOneThreads / 32 - 1];
+}
+
 bamg_status scan_counts(const int32_t* counts, int32_t* out, int n, cudaStream_t s,
                         int64_t* total_host) {
+  if (n <= kScanOneBlock) {
+    BAMG_TRY(launch(scan_one_block, dim3(1), dim3(kScanOneThreads), 0, s, counts, n, out));
+    if (total_host) {
+      int32_t t = 0;
+      BAMG_CUDA(cudaMemcpyAsync(&t, out + n, sizeof(t), cudaMemcpyDeviceToHost, s));
+      BAMG_CUDA(cudaStreamSynchronize(s));
+      *total_host = t;
+    }
+    return BAMG_OK;
+  }
   int nb = (int)cdiv(n > 0 ? n : 1, kScanTile);
   DevMem part;
   BAMG_TRY(part.alloc(sizeof(long long) * (nb + 1), s));
