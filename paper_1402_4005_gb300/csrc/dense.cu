@@ -524,18 +524,50 @@ __device__ inline T gk_off(const T* d, const T* e, int k) {
   return (k & 1) ? d[k >> 1] : e[(k >> 1) - 1];
 }
 
-// Number of eigenvalues of the tridiagonal below x (LDL^T Sturm count).
+// Number of eigenvalues of the tridiagonal below x (Sturm count).  In FP64
+// the sign changes of the leading principal minors p_k(x) are counted with
+// the three-term recurrence p_k = -x p_{k-1} - off(k)^2 p_{k-2} (no FP64
+// division, narrow on GB300), rescaled by exact powers of two to stay in
+// range; a ratio p_k / p_{k-1} below pivmin in magnitude is replaced by
+// -pivmin, as in the LDL^T ratio form used in FP32.
+template <typename T> struct GkRange;
+template <> struct GkRange<double> { static constexpr double big = 0x1p+256, small = 0x1p-256; };
+template <> struct GkRange<float> { static constexpr float big = 0x1p+48f, small = 0x1p-48f; };
+
 template <typename T>
 __device__ int gk_count(const T* d, const T* e, int n, T x, T pivmin) {
-  int cnt = 0;
-  T q = -x;
-  if (fabs(q) < pivmin) q = -pivmin;
-  cnt += q < T(0);
-  for (int k = 1; k < 2 * n; ++k) {
-    T o = gk_off(d, e, k);
-    q = -x - o * o / q;
+  if constexpr (sizeof(T) == 4) {
+    // FP32: the LDL^T ratios q_k = -x - off(k)^2 / q_{k-1} (the FP32
+    // division is cheap)
+    int cnt = 0;
+    T q = -x;
     if (fabs(q) < pivmin) q = -pivmin;
     cnt += q < T(0);
+    for (int k = 1; k < 2 * n; ++k) {
+      T o = gk_off(d, e, k);
+      q = -x - o * o / q;
+      if (fabs(q) < pivmin) q = -pivmin;
+      cnt += q < T(0);
+    }
+    return cnt;
+  }
+  T pprev = T(1), p = -x;
+  if (fabs(p) < pivmin) p = -pivmin;
+  int cnt = p < T(0);
+  for (int k = 1; k < 2 * n; ++k) {
+    const T o = gk_off(d, e, k);
+    T pn = -x * p - (o * o) * pprev;
+    if (fabs(pn) < pivmin * fabs(p)) pn = -pivmin * p;
+    cnt += (pn < T(0)) != (p < T(0));
+    pprev = p;
+    p = pn;
+    if (fabs(p) > GkRange<T>::big) {
+      p *= GkRange<T>::small;
+      pprev *= GkRange<T>::small;
+    } else if (fabs(p) < GkRange<T>::small && fabs(pprev) < GkRange<T>::small) {
+      p *= GkRange<T>::big;
+      pprev *= GkRange<T>::big;
+    }
   }
   return cnt;
 }
@@ -578,8 +610,8 @@ __device__ T gk_sigma(const T* d, const T* e, int n, int a, T gmax, T pivmin) {
   return T(0.5) * (lo + hi);
 }
 
-// One lane: LU with partial pivoting of the tridiagonal T - sigma I (size m),
-// storing reciprocal pivots for the solves.
+// One lane: LU with partial pivoting of the tridiagonal T - sigma I (size m);
+// the warp then replaces the pivots by their reciprocals for the solves.
 template <typename T>
 __device__ void gk_factor(const T* d, const T* e, int m, T sigma, T pert, T* dd, T* du, T* du2, T* dl,
                           T* piv) {
@@ -611,7 +643,6 @@ __device__ void gk_factor(const T* d, const T* e, int m, T sigma, T pert, T* dd,
     }
   }
   if (dd[m - 1] == T(0)) dd[m - 1] = pert;
-  for (int k = 0; k < m; ++k) dd[k] = T(1) / dd[k];   // reciprocal pivots
 }
 
 template <typename T>
@@ -672,10 +703,16 @@ __device__ void bidiag_triplets(const DenseArgs<T>& A, T* sv) {
       T *dd = base, *du = base + m, *du2 = base + 2 * m, *dl = base + 3 * m, *pv = base + 4 * m;
       T* zv = base + 5 * m;
       if (lane == 0) gk_factor(d, e, m, __ldcg(A.sig + a), pert, dd, du, du2, dl, pv);
-      for (int k = lane; k < m; k += 32)
-        zv[k] = T(1) + T(0.5) * T((unsigned)(k * 2654435761u) % 1000u) / T(1000) + T(a);
       __syncwarp();
-      for (int it = 0; it < 4; ++it) {
+      for (int k = lane; k < m; k += 32) {
+        dd[k] = T(1) / dd[k];                       // reciprocal pivots
+        zv[k] = T(1) + T(0.5) * T((unsigned)(k * 2654435761u) % 1000u) / T(1000) + T(a);
+      }
+      __syncwarp();
+      // an isolated value converges in two steps from an accurate shift;
+      // members of a cluster take four, with orthogonalisation
+      const int iters = (a1 - a0 > 1) ? 4 : 2;
+      for (int it = 0; it < iters; ++it) {
         if (lane == 0) gk_solve(m, dd, du, du2, dl, pv, zv);
         __syncwarp();
         for (int q = a0; q < a; ++q) {           // orthogonalise within the cluster
