@@ -19,6 +19,7 @@ Beside the headline line the same JSON object reports, on the same GPU:
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                   [--sections all|none|learned,batched,...] [--no-cpu-baseline]
+                  [--no-headline] [--sparse-side S]
 
 Prints one JSON line.  With --impl reference the CPU oracle is timed on the
 host cores instead (the reference arm of the comparison).
@@ -46,6 +47,12 @@ SIDE = 256
 KW = dict(r=16, max_levels=5, coarse_min=1, seed=2)
 SECTIONS = ("learned", "batched", "delaunay", "sparse")
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (4 partitions x 32)
+# DRAM bytes (read + write) of one coarsest_kernel<float> launch of this
+# workload from an ncu capture, valid only while the kernel's source file is
+# byte-identical to the one captured (else the roofline reports null)
+COARSEST_TRAFFIC = {"source": "paper_1402_4005_gb300/csrc/dense.cu",
+                    "sha256": "c513d57d5035aa0b3c4b577d0ebae91759354a7674874ffbf5327476d9b1fe36",
+                    "bytes": 1692672 + 1280}
 
 
 def env_int(name, default):
@@ -144,6 +151,8 @@ def gpu_arm(args, rank: int, world: int):
     dev = int(os.environ.get("LOCAL_RANK", rank))
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream()
+    if args.no_headline:                          # sections alone (profiling runs)
+        return run_sections(args, api, torch, stream, {})
     ch = cg.tandem(SIDE)
     rp, ci, va = chain_tensors(torch, ch)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -207,8 +216,13 @@ def gpu_arm(args, rank: int, world: int):
     }
     h_mix.destroy()
     h_64.destroy()
-    for name, fn in (("sparse", roofline_sparse), ("learned", learned_section),
-                     ("batched", batched_section), ("delaunay", delaunay_section)):
+    return run_sections(args, api, torch, stream, out)
+
+
+def run_sections(args, api, torch, stream, out):
+    for name, fn in (("sparse", lambda *a: roofline_sparse(*a, side=args.sparse_side)),
+                     ("learned", learned_section), ("batched", batched_section),
+                     ("delaunay", delaunay_section)):
         if name in args.sections:
             try:
                 out[name] = fn(api, torch, stream)
@@ -245,6 +259,16 @@ def coarsest_flops(n: int) -> float:
     return (2.0 / 3.0 + 2.0 + 8.0 / 3.0 + 3.0) * n ** 3
 
 
+def captured_traffic(rec):
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            same = hashlib.sha256(f.read()).hexdigest() == rec["sha256"]
+    except OSError:
+        return None
+    return rec["bytes"] if same else None
+
+
 def roofline_coarsest(api, torch, stream, h):
     """The dominant kernel of a step: the dense coarsest-level solver (one
     16-block cluster, FP32 on the mixed path), timed with CUDA events on the
@@ -268,7 +292,7 @@ def roofline_coarsest(api, torch, stream, h):
     return {"bound": "alu", "kernel": f"coarsest_kernel<float> (n={n} dense coarsest level, 16-block cluster, "
                                       f"rows in shared memory)",
             "achieved": round(achieved, 4), "peak": round(peak, 1), "unit": "TFLOP/s",
-            "frac": round(achieved / peak, 6), "traffic": None,
+            "frac": round(achieved / peak, 6), "traffic": captured_traffic(COARSEST_TRAFFIC),
             "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x {mhz:.0f} MHz",
             "launch_ms": round(ms, 3), "alg_flops": flops,
             "frac_of_cluster_sms": round(achieved / (peak * 16 / sms), 5)}
@@ -514,6 +538,10 @@ def main():
     ap.add_argument("--sections", default="all",
                     help="comma list of " + ",".join(SECTIONS) + ", or all / none")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-headline", action="store_true",
+                    help="run the selected sections only and print their JSON (for profiling)")
+    ap.add_argument("--sparse-side", type=int, default=2048,
+                    help="grid side of the tandem queue of the sparse roofline section")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     args.sections = (set(SECTIONS) if args.sections == "all" else set() if args.sections == "none"
@@ -548,6 +576,9 @@ def main():
         args.sections = set()               # replicas time the headline only
     r = gpu_arm(args, rank, world)
     if rank != 0:
+        return
+    if args.no_headline:
+        print(json.dumps({"sections_only": True, **r}))
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
