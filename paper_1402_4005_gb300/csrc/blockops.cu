@@ -17,15 +17,34 @@ struct Blk {
   static_assert(LD % VW == 0 && LPR >= 1 && LPR <= 32, "bad block width");
 };
 
-// acc = (A X)_row for the row group's VW columns; the nonzeros are taken
-// four at a time (indices and values first, then the four row gathers) so
-// that more loads are in flight per row group.
+// Layout of the row kernels (relaxation, block SpMM): rows of 64 bytes or
+// more are split into NV = 2 interleaved 16-byte vectors per lane (lane q of
+// the row group holds vectors q and q + LPR), so a row group has half the
+// lanes, a warp twice the rows, and each gather instruction of the group
+// covers contiguous 32-byte sectors.
+template <typename T, int LD>
+struct RowBlk {
+  static constexpr int VW = Vec16<T>::W;
+  static constexpr int NVR = LD / VW;              // 16-byte vectors per row
+  static constexpr int NV = NVR >= 4 ? 2 : 1;      // vectors per lane
+  static constexpr int LPR = NVR / NV;             // lanes per row
+  static constexpr int RPW = 32 / LPR;             // rows per warp
+  static_assert(LD % VW == 0 && LPR >= 1 && LPR <= 32, "bad block width");
+  __device__ static int col(int q, int v) { return (q + v * LPR) * VW; }
+};
+
+// acc = (A X)_row for the lane's NV vectors; the nonzeros are taken four at
+// a time (indices and values first, then the row gathers) so that more loads
+// are in flight per row group.
 template <typename T, int LD>
 __device__ inline void row_times_block(int i, int q, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                       const T* __restrict__ va, const T* __restrict__ X, T (&acc)[Blk<T, LD>::VW]) {
-  using C = Blk<T, LD>;
+                                       const T* __restrict__ va, const T* __restrict__ X,
+                                       T (&acc)[RowBlk<T, LD>::NV][RowBlk<T, LD>::VW]) {
+  using C = RowBlk<T, LD>;
 #pragma unroll
-  for (int v = 0; v < C::VW; ++v) acc[v] = T(0);
+  for (int v = 0; v < C::NV; ++v)
+#pragma unroll
+    for (int w = 0; w < C::VW; ++w) acc[v][w] = T(0);
   const int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
   int p = p0;
   for (; p + 4 <= p1; p += 4) {
@@ -36,21 +55,28 @@ __device__ inline void row_times_block(int i, int q, const int32_t* __restrict__
       j[u] = __ldg(ci + p + u);
       a[u] = __ldg(va + p + u);
     }
-    T xv[4][C::VW];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) vload_ro(X + (size_t)j[u] * LD + q * C::VW, xv[u]);
+    T xv[4][C::NV][C::VW];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int v = 0; v < C::VW; ++v) acc[v] = fma(a[u], xv[u][v], acc[v]);
+      for (int v = 0; v < C::NV; ++v) vload_ro(X + (size_t)j[u] * LD + C::col(q, v), xv[u][v]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < C::NV; ++v)
+#pragma unroll
+        for (int w = 0; w < C::VW; ++w) acc[v][w] = fma(a[u], xv[u][v][w], acc[v][w]);
   }
   for (; p < p1; ++p) {
     const int j = __ldg(ci + p);
     const T a = __ldg(va + p);
-    T xv[C::VW];
-    vload_ro(X + (size_t)j * LD + q * C::VW, xv);
+    T xv[C::NV][C::VW];
 #pragma unroll
-    for (int v = 0; v < C::VW; ++v) acc[v] = fma(a, xv[v], acc[v]);
+    for (int v = 0; v < C::NV; ++v) vload_ro(X + (size_t)j * LD + C::col(q, v), xv[v]);
+#pragma unroll
+    for (int v = 0; v < C::NV; ++v)
+#pragma unroll
+      for (int w = 0; w < C::VW; ++w) acc[v][w] = fma(a, xv[v][w], acc[v][w]);
   }
 }
 
@@ -59,49 +85,54 @@ __device__ inline void row_times_block(int i, int q, const int32_t* __restrict__
 // independent jobs (the V and U relaxations) share one launch: blockIdx.y
 // selects the job.
 template <typename T, int LD>
-__global__ void __launch_bounds__(256) relax_block_kernel(RelaxJob<T> j0, RelaxJob<T> j1) {
-  using C = Blk<T, LD>;
+__global__ void __launch_bounds__(256, 6) relax_block_kernel(RelaxJob<T> j0, RelaxJob<T> j1) {
+  using C = RowBlk<T, LD>;
   const RelaxJob<T>& a = blockIdx.y ? j1 : j0;
   int lane = threadIdx.x & 31;
   int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int i = gw * C::RPW + lane / C::LPR;
   int q = lane % C::LPR;
   if (i >= a.n) return;
-  T acc[C::VW];
+  T acc[C::NV][C::VW];
   row_times_block<T, LD>(i, q, a.rp, a.ci, a.va, a.X, acc);
-  T xi[C::VW], y[C::VW];
-  vload_ro(a.X + (size_t)i * LD + q * C::VW, xi);
-  T di = __ldg(a.dinv + i);
-  if (a.R) {
-    T rv[C::VW];
-    vload_ro(a.R + (size_t)i * LD + q * C::VW, rv);
+  const T di = __ldg(a.dinv + i);
 #pragma unroll
-    for (int v = 0; v < C::VW; ++v) {
-      T s = a.sig ? __ldg(a.sig + q * C::VW + v) : T(1);
-      y[v] = xi[v] + (a.omega * (s * rv[v] - acc[v])) * di;
+  for (int v = 0; v < C::NV; ++v) {
+    const size_t o = (size_t)i * LD + C::col(q, v);
+    T xi[C::VW], y[C::VW];
+    vload_ro(a.X + o, xi);
+    if (a.R) {
+      T rv[C::VW];
+      vload_ro(a.R + o, rv);
+#pragma unroll
+      for (int w = 0; w < C::VW; ++w) {
+        T s = a.sig ? __ldg(a.sig + C::col(q, v) + w) : T(1);
+        y[w] = xi[w] + (a.omega * (s * rv[w] - acc[v][w])) * di;
+      }
+    } else {
+#pragma unroll
+      for (int w = 0; w < C::VW; ++w) y[w] = xi[w] + (a.omega * (-acc[v][w])) * di;
     }
-  } else {
-#pragma unroll
-    for (int v = 0; v < C::VW; ++v) y[v] = xi[v] + (a.omega * (-acc[v])) * di;
+    if (a.keep0 && q == 0 && v == 0) y[0] = xi[0];
+    vstore(a.Y + o, y);
   }
-  if (a.keep0 && q == 0) y[0] = xi[0];
-  vstore(a.Y + (size_t)i * LD + q * C::VW, y);
 }
 
 // Y = A X  (rows x LD) for a CSR A; up to three independent products per
 // launch (blockIdx.y selects one).
 template <typename T, int LD>
-__global__ void __launch_bounds__(256) spmm_block_kernel(SpmmJob<T> j0, SpmmJob<T> j1, SpmmJob<T> j2) {
-  using C = Blk<T, LD>;
+__global__ void __launch_bounds__(256, 6) spmm_block_kernel(SpmmJob<T> j0, SpmmJob<T> j1, SpmmJob<T> j2) {
+  using C = RowBlk<T, LD>;
   const SpmmJob<T>& a = blockIdx.y == 0 ? j0 : (blockIdx.y == 1 ? j1 : j2);
   int lane = threadIdx.x & 31;
   int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int i = gw * C::RPW + lane / C::LPR;
   int q = lane % C::LPR;
   if (i >= a.rows) return;
-  T acc[C::VW];
+  T acc[C::NV][C::VW];
   row_times_block<T, LD>(i, q, a.rp, a.ci, a.va, a.X, acc);
-  vstore(a.Y + (size_t)i * LD + q * C::VW, acc);
+#pragma unroll
+  for (int v = 0; v < C::NV; ++v) vstore(a.Y + (size_t)i * LD + C::col(q, v), acc[v]);
 }
 
 // Per-block column sums of K products, written to part[block][K*LD].
@@ -332,7 +363,7 @@ __global__ void diag_inv_kernel(int n, const int32_t* __restrict__ rp, const int
 // =================================================================== host
 template <typename T, int LD>
 static bamg_status relax_ld(const RelaxJob<T>& j0, const RelaxJob<T>* j1, cudaStream_t s) {
-  using C = Blk<T, LD>;
+  using C = RowBlk<T, LD>;
   const int n = j1 && j1->n > j0.n ? j1->n : j0.n;
   unsigned blocks = cdiv(n, 8 * C::RPW);
   return launch(relax_block_kernel<T, LD>, dim3(blocks, j1 ? 2 : 1), dim3(256), 0, s, j0, j1 ? *j1 : j0);
@@ -340,7 +371,7 @@ static bamg_status relax_ld(const RelaxJob<T>& j0, const RelaxJob<T>* j1, cudaSt
 
 template <typename T, int LD>
 static bamg_status spmm_ld(const SpmmJob<T>* jobs, int k, cudaStream_t s) {
-  using C = Blk<T, LD>;
+  using C = RowBlk<T, LD>;
   int rows = 0;
   for (int q = 0; q < k; ++q) rows = jobs[q].rows > rows ? jobs[q].rows : rows;
   return launch(spmm_block_kernel<T, LD>, dim3(cdiv(rows, 8 * C::RPW), k), dim3(256), 0, s, jobs[0],
