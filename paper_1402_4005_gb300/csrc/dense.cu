@@ -178,27 +178,26 @@ __device__ T block_sum(T a, T* red) {
 }
 
 // ------------------------------------------------------------ Cholesky x 2
-// Right-looking on the full symmetric trailing matrix.  The owner of row k
-// publishes column k of L (row k of the trailing matrix over sqrt(a_kk));
-// every block subtracts l l^T from its own rows.  On exit the lower triangle
-// holds L and the upper triangle L^T.
-template <bool SM, typename T>
-__device__ void chol_publish(const DenseArgs<T>& A, int m) {
-  const int n = A.n;
-  for (int f = 0; f < 2; ++f) {
-    const T* L = own<SM>(A, f ? A.LN : A.LM, m, n);
-    T* pb = pub_w<SM>(A) + (size_t)(2 * f + (m & 1)) * n;
-    T a = L[m];
-    T l = a > T(0) ? sqrt(a) : a;
-    T inv = a > T(0) ? T(1) / l : T(0);
-    for (int j = m + 1 + threadIdx.x; j < n; j += blockDim.x) pb[j] = L[j] * inv;
-    if (threadIdx.x == 0) pb[m] = l;
-  }
-}
+// Right-looking blocked Cholesky of M and N together, on the full symmetric
+// trailing matrices, kCholK columns per cluster step.  Every block fetches
+// the step's panel rows from their owners, factors the kCholK x kCholK
+// diagonal block and forms the panel rows of L^T itself (the same arithmetic
+// in every block), then subtracts the panel's rank-kCholK product from its
+// own trailing rows.  The owners store the finished panel rows after the
+// step's barrier, when no block reads them any more.  On exit the lower
+// triangle holds L and the upper triangle L^T.
+constexpr int kCholK = 4;
 
 template <bool SM, typename T>
 __device__ bool cholesky_rows(const DenseArgs<T>& A, T* sv) {
   const int n = A.n, NB = nblocks<SM>(A), b = blockIdx.x;
+  // 2 kCholK panel rows of length n (M rows, then N rows): the block's own
+  // publication buffer under the shared policy (no block publishes during
+  // the factorization), its dynamic shared memory after the 3n scratch
+  // otherwise
+  T* stage = SM ? A.pub : sv + 3 * n;
+  __shared__ T pinv[2 * kCholK];
+  __shared__ int bad;
   for (int i = b; i < n; i += NB) {
     T* lm = own<SM>(A, A.LM, i, n);
     T* ln = own<SM>(A, A.LN, i, n);
@@ -207,54 +206,117 @@ __device__ bool cholesky_rows(const DenseArgs<T>& A, T* sv) {
       ln[j] = T(A.N[(size_t)i * n + j]);
     }
   }
-  __syncthreads();
-  if (b == 0) chol_publish<SM>(A, 0);
+  if (threadIdx.x == 0) bad = 0;
   csync();
-  T* sm = sv;
-  T* sn = sv + n;
-  for (int k = 0; k < n; ++k) {
-    const T* pb = pub_r<SM>(A, k % NB);
-    const T* pm = pb + (size_t)(k & 1) * n;
-    const T* pn = pb + (size_t)(2 + (k & 1)) * n;
-    for (int j = k + threadIdx.x; j < n; j += blockDim.x) {
-      sm[j] = rd<SM>(pm + j);
-      sn[j] = rd<SM>(pn + j);
-    }
-    __syncthreads();
-    if (!(sm[k] > T(0)) || !(sn[k] > T(0))) {
-      if (b == 0 && threadIdx.x == 0) A.ctl->err = 2;
-      csync();       // every block reads the same pivots and leaves here,
-      return false;  // after the others have read its published vector
-    }
-    if (k % NB == b) {
-      T* lm = own<SM>(A, A.LM, k, n);
-      T* ln = own<SM>(A, A.LN, k, n);
-      for (int j = k + threadIdx.x; j < n; j += blockDim.x) {
-        lm[j] = sm[j];
-        ln[j] = sn[j];
+  // owner rows of the panel starting at p0 (pk rows) from the staged L^T rows
+  auto store_panel = [&](int p0, int pk) {
+    for (int p = 0; p < pk; ++p) {
+      const int m = p0 + p;
+      if (m % NB != b) continue;
+      T* lm = own<SM>(A, A.LM, m, n);
+      T* ln = own<SM>(A, A.LN, m, n);
+      for (int j = p0 + threadIdx.x; j < n; j += blockDim.x) {
+        // left of the diagonal: L[m][j] = (L^T)[j][m], a staged panel row
+        const int pr = j < m ? j - p0 : p, col = j < m ? m : j;
+        lm[j] = stage[(size_t)pr * n + col];
+        ln[j] = stage[(size_t)(kCholK + pr) * n + col];
       }
     }
-    // column-major sweep: a thread owns column j of every own row, so its
-    // loads are independent (the factors are disjoint from the scratch)
-    for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
-      const T smj = sm[j], snj = sn[j];
-#pragma unroll 4
-      for (int i = first_own(b, NB, k + 1); i < n; i += NB) {
+  };
+  for (int k0 = 0; k0 < n; k0 += kCholK) {
+    const int kk = min(kCholK, n - k0), w = n - k0;
+    if (k0 > 0) {
+      store_panel(k0 - kCholK, kCholK);
+      __syncthreads();
+    }
+    for (int e = threadIdx.x; e < 2 * kk * w; e += blockDim.x) {
+      const int f = e / (kk * w), rem = e - f * kk * w;
+      const int p = rem / w, j = k0 + rem % w;
+      stage[(size_t)(f * kCholK + p) * n + j] = rd<SM>(any<SM>(A, f ? A.LN : A.LM, k0 + p, n) + j);
+    }
+    __syncthreads();
+    // diagonal blocks: thread 0 (M) and thread 32 (N), in place: U = L^T
+    if ((threadIdx.x & 31) == 0 && threadIdx.x < 64) {
+      const int f = threadIdx.x >> 5;
+      T* U = stage + (size_t)f * kCholK * n + k0;
+      for (int p = 0; p < kk; ++p) {
+        T d = U[(size_t)p * n + p];
+        for (int q = 0; q < p; ++q) d -= U[(size_t)q * n + p] * U[(size_t)q * n + p];
+        if (!(d > T(0))) {
+          bad = 1;
+          break;
+        }
+        const T l = sqrt(d), inv = T(1) / l;
+        U[(size_t)p * n + p] = l;
+        pinv[f * kCholK + p] = inv;
+        for (int c = p + 1; c < kk; ++c) {
+          T t = U[(size_t)p * n + c];
+          for (int q = 0; q < p; ++q) t -= U[(size_t)q * n + p] * U[(size_t)q * n + c];
+          U[(size_t)p * n + c] = t * inv;
+        }
+      }
+    }
+    __syncthreads();
+    if (bad) {
+      if (b == 0 && threadIdx.x == 0) A.ctl->err = 2;
+      csync();       // every block reaches the same verdict at the same step
+      return false;
+    }
+    // the panel rows of L^T right of the diagonal block: a thread per column
+    const int w2 = n - k0 - kk;
+    for (int e = threadIdx.x; e < 2 * w2; e += blockDim.x) {
+      const int f = e / w2, j = k0 + kk + (e - f * w2);
+      T* U = stage + (size_t)f * kCholK * n;
+      T u[kCholK];
+#pragma unroll
+      for (int p = 0; p < kCholK; ++p) {
+        if (p < kk) {
+          T t = U[(size_t)p * n + j];
+#pragma unroll
+          for (int q = 0; q < p; ++q) t -= U[(size_t)q * n + k0 + p] * u[q];
+          u[p] = t * pinv[f * kCholK + p];
+          U[(size_t)p * n + j] = u[p];
+        }
+      }
+    }
+    __syncthreads();
+    // own trailing rows: subtract the panel product (column-major sweep, a
+    // thread owns column j of every own row) and store the L entries
+    const int i0 = first_own(b, NB, k0 + kk);
+    for (int j = k0 + kk + threadIdx.x; j < n; j += blockDim.x) {
+      T um[kCholK], un[kCholK];
+#pragma unroll
+      for (int p = 0; p < kCholK; ++p) {
+        um[p] = p < kk ? stage[(size_t)p * n + j] : T(0);
+        un[p] = p < kk ? stage[(size_t)(kCholK + p) * n + j] : T(0);
+      }
+#pragma unroll 2
+      for (int i = i0; i < n; i += NB) {
         T* __restrict__ lmi = own<SM>(A, A.LM, i, n);
         T* __restrict__ lni = own<SM>(A, A.LN, i, n);
-        lmi[j] -= sm[i] * smj;
-        lni[j] -= sn[i] * snj;
+        T xm = lmi[j], xn = lni[j];
+#pragma unroll
+        for (int p = 0; p < kCholK; ++p) {
+          if (p < kk) {                 // rows p >= kk of the stage are stale
+            xm -= stage[(size_t)p * n + i] * um[p];
+            xn -= stage[(size_t)(kCholK + p) * n + i] * un[p];
+          }
+        }
+        lmi[j] = xm;
+        lni[j] = xn;
       }
     }
-    if (threadIdx.x == 0)
-      for (int i = first_own(b, NB, k + 1); i < n; i += NB) {
-        own<SM>(A, A.LM, i, n)[k] = sm[i];
-        own<SM>(A, A.LN, i, n)[k] = sn[i];
+    for (int e = threadIdx.x; e < kCholK * ((n - i0 + NB - 1) / NB); e += blockDim.x) {
+      const int p = e % kCholK, i = i0 + (e / kCholK) * NB;
+      if (p < kk) {
+        own<SM>(A, A.LM, i, n)[k0 + p] = stage[(size_t)p * n + i];
+        own<SM>(A, A.LN, i, n)[k0 + p] = stage[(size_t)(kCholK + p) * n + i];
       }
-    __syncthreads();
-    if (k + 1 < n && (k + 1) % NB == b) chol_publish<SM>(A, k + 1);
+    }
     csync();
   }
+  store_panel(((n - 1) / kCholK) * kCholK, n - ((n - 1) / kCholK) * kCholK);
+  csync();
   return true;
 }
 
@@ -308,6 +370,7 @@ __device__ void row_solve(const DenseArgs<T>& A, T* F, T* F2, int split, T* X, i
 // advances with no cluster barrier: a group of g lanes per vector forms the
 // dot product and its leader divides by L[t][t].
 constexpr int kStage = 8;
+static_assert(2 * kCholK <= kStage, "the Cholesky panels share the staging buffer");
 template <bool SM, bool UPPER, typename T>
 __device__ void local_solve(const DenseArgs<T>& A, T* F, T* Z, int c_lo, int c_hi, T* stage) {
   const int n = A.n, NB = nblocks<SM>(A), b = blockIdx.x;
@@ -777,9 +840,10 @@ __device__ void bidiag_triplets(const DenseArgs<T>& A, T* sv) {
 // back substitutions (L_N^T for v, L_M^T for u) in one sweep; sign: largest
 // |v_i| positive (lowest index on ties).  For a zero singular value (below
 // n * eps * bound) u = 1 / sqrt(1^T M 1) and v normalised in the 2-norm is the
-// right null vector w of B.
+// right null vector w of B.  Row-sweep form (a cluster barrier per row), for
+// the small sizes where the 2r vectors do not fit the rows of S2.
 template <bool SM, typename T>
-__device__ void triplets(const DenseArgs<T>& A, T* sv, T* red) {
+__device__ void triplets_rows(const DenseArgs<T>& A, T* sv, T* red) {
   const int n = A.n, r = A.r, r2 = 2 * r, NB = nblocks<SM>(A), b = blockIdx.x;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   T* part = part_w<SM>(A);
@@ -879,6 +943,131 @@ __device__ void triplets(const DenseArgs<T>& A, T* sv, T* red) {
   if (b == 0)
     for (int a = threadIdx.x; a < r; a += blockDim.x) A.sigma[a] = double(__ldcg(A.sig + a));
   csync();
+}
+
+// The same triplets with the 2r back substitutions as local solves: vector
+// c (c < r: v~_c, else u~_(c-r)) is the own row c of S2 of block c mod NB,
+// solved with no cluster barrier (L_N^T for v, L_M^T for u); the owner of v_a
+// also takes its sign and publishes it for the owner of u_a.
+template <bool SM, typename T>
+__device__ void triplets_local(const DenseArgs<T>& A, T* sv, T* red) {
+  const int n = A.n, r = A.r, r2 = 2 * r, NB = nblocks<SM>(A), b = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  T* part = part_w<SM>(A);
+  const T gmax = gk_bound(A.d, A.e, n);
+  const T null_tol = T(n * Eps<T>::v) * gmax;
+  {
+    // C v~_a for the own rows: one warp per (row, value) pair
+    const int npair = ((n - b + NB - 1) / NB) * r;
+    for (int q = w; q < npair; q += kWarps) {
+      const int i = b + (q / r) * NB, a = q % r;
+      const T* ci = own<SM>(A, A.S1, i, n);
+      const T* va = A.vb + (size_t)a * n;
+      T acc = 0;
+      for (int j = lane; j < n; j += 32) acc += ci[j] * __ldcg(va + j);
+      acc = warp_sum(acc);
+      if (lane == 0) own<SM>(A, A.R, i, r2)[r + a] = acc;
+    }
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < r; a += blockDim.x) {
+    T s = 0;
+    for (int i = b; i < n; i += NB) {
+      const T x = own<SM>(A, A.R, i, r2)[r + a];
+      s += x * x;
+    }
+    part[a] = s;
+  }
+  {
+    T s = 0;                                       // partial 1^T M 1 over own rows
+    for (int i = b; i < n; i += NB)
+      for (int j = threadIdx.x; j < n; j += blockDim.x) s += T(A.M[(size_t)i * n + j]);
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) part[n + r2 + 1] = s;
+  }
+  csync();
+  // own vectors into the rows of S2: v~_a from vb, u~_a gathered from the
+  // rows of R and normalised
+  for (int c = b; c < r2; c += NB) {
+    T* z = own<SM>(A, A.S2, c, n);
+    if (c < r) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) z[i] = __ldcg(A.vb + (size_t)c * n + i);
+    } else {
+      const T s = part_sum<SM>(A, c - r);
+      const T sc = s > T(0) ? T(1) / sqrt(s) : T(0);
+      for (int i = threadIdx.x; i < n; i += blockDim.x) z[i] = rd<SM>(any<SM>(A, A.R, i, r2) + c) * sc;
+    }
+  }
+  __syncthreads();
+  T* stage = SM ? A.pub : sv + 3 * n;
+  local_solve<SM, true>(A, A.LN, A.S2, 0, r, stage);
+  local_solve<SM, true>(A, A.LM, A.S2, r, r2, stage);
+  // signs of the own v_a (largest |v_i| positive, lowest index on ties) and
+  // ||v_0||^2, published in the partial slots n + 2a and n + 2r
+  __shared__ int redi[kWarps];
+  for (int c = b; c < r; c += NB) {
+    const T* z = own<SM>(A, A.S2, c, n);
+    T best = T(-1);
+    int bi = n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const T v = fabs(z[i]);
+      if (v > best) { best = v; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    __syncthreads();
+    if (lane == 0) { red[w] = best; redi[w] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int k = 1; k < kWarps; ++k)
+        if (red[k] > best || (red[k] == best && redi[k] < bi)) { best = red[k]; bi = redi[k]; }
+      part[n + 2 * c] = (bi < n && z[bi] < T(0)) ? T(-1) : T(1);
+    }
+    __syncthreads();
+    if (c == 0) {
+      T s0 = 0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) s0 += z[i] * z[i];
+      s0 = block_sum(s0, red);
+      if (threadIdx.x == 0) part[n + r2] = s0;
+    }
+  }
+  csync();
+  const T uconst = T(1) / sqrt(part_sum<SM>(A, n + r2 + 1));   // 1 / sqrt(1^T M 1)
+  const bool null0 = __ldcg(A.sig) <= null_tol;
+  for (int c = b; c < r2; c += NB) {
+    const T* z = own<SM>(A, A.S2, c, n);
+    const int a = c < r ? c : c - r;
+    const T sg = rd<SM>(part_r<SM>(A, a % NB) + n + 2 * a);
+    if (c < r) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) A.V[(size_t)i * r + a] = double(sg * z[i]);
+      if (a == 0) {
+        const T s0 = part[n + r2];
+        const T inv0 = s0 > T(0) ? T(1) / sqrt(s0) : T(0);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) A.unull[i] = null0 ? sg * z[i] * inv0 : T(0);
+      }
+    } else {
+      const bool is_null = __ldcg(A.sig + a) <= null_tol;
+      for (int i = threadIdx.x; i < n; i += blockDim.x)
+        A.U[(size_t)i * r + a] = double(is_null ? uconst : sg * z[i]);
+    }
+  }
+  if (b == 0)
+    for (int a = threadIdx.x; a < r; a += blockDim.x) A.sigma[a] = double(__ldcg(A.sig + a));
+  csync();
+}
+
+template <bool SM, typename T>
+__device__ void triplets(const DenseArgs<T>& A, T* sv, T* red) {
+  const int NB = nblocks<SM>(A);
+  const bool fits = SM ? (2 * A.r + NB - 1) / NB <= A.RP : 2 * A.r <= A.n;
+  if (fits)
+    triplets_local<SM>(A, sv, red);
+  else
+    triplets_rows<SM>(A, sv, red);
 }
 
 // ------------------------------------------------------------ pseudo-inverse
