@@ -164,6 +164,28 @@ __device__ inline int first_own(int b, int NB, int from) {
   return q <= 0 ? b : b + ((q + NB - 1) / NB) * NB;
 }
 
+// store(e, load(e)) for e in [0, count) over the block's threads, eight
+// loads per thread issued before their stores: loads from another block's
+// shared memory (or L2) then overlap, where a store between them (which the
+// compiler must assume may alias the next load) would serialise them.
+template <typename T, typename Load, typename Store>
+__device__ inline void batched_copy(int count, Load load, Store store) {
+  constexpr int kB = 8;
+  for (int e0 = threadIdx.x; e0 < count; e0 += kB * blockDim.x) {
+    T v[kB];
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      const int e = e0 + u * (int)blockDim.x;
+      v[u] = e < count ? load(e) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      const int e = e0 + u * (int)blockDim.x;
+      if (e < count) store(e, v[u]);
+    }
+  }
+}
+
 template <typename T>
 __device__ T block_sum(T a, T* red) {
   a = warp_sum(a);
@@ -224,37 +246,59 @@ __device__ bool cholesky_rows(const DenseArgs<T>& A, T* sv) {
     }
   };
   for (int k0 = 0; k0 < n; k0 += kCholK) {
-    const int kk = min(kCholK, n - k0), w = n - k0;
+    const int kk = min(kCholK, n - k0);
     if (k0 > 0) {
       store_panel(k0 - kCholK, kCholK);
       __syncthreads();
     }
-    for (int e = threadIdx.x; e < 2 * kk * w; e += blockDim.x) {
-      const int f = e / (kk * w), rem = e - f * kk * w;
-      const int p = rem / w, j = k0 + rem % w;
-      stage[(size_t)(f * kCholK + p) * n + j] = rd<SM>(any<SM>(A, f ? A.LN : A.LM, k0 + p, n) + j);
+    for (int j = k0 + threadIdx.x; j < n; j += blockDim.x) {   // loads batched across the rows
+      T x[2 * kCholK];
+#pragma unroll
+      for (int u = 0; u < 2 * kCholK; ++u) {
+        const int f = u / kCholK, p = u % kCholK;
+        x[u] = p < kk ? rd<SM>(any<SM>(A, f ? A.LN : A.LM, k0 + p, n) + j) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 2 * kCholK; ++u)
+        if (u % kCholK < kk) stage[(size_t)u * n + j] = x[u];
     }
     __syncthreads();
-    // diagonal blocks: thread 0 (M) and thread 32 (N), in place: U = L^T
+    // diagonal blocks: thread 0 (M) and thread 32 (N), in registers, in
+    // place: U = L^T
     if ((threadIdx.x & 31) == 0 && threadIdx.x < 64) {
       const int f = threadIdx.x >> 5;
       T* U = stage + (size_t)f * kCholK * n + k0;
-      for (int p = 0; p < kk; ++p) {
-        T d = U[(size_t)p * n + p];
-        for (int q = 0; q < p; ++q) d -= U[(size_t)q * n + p] * U[(size_t)q * n + p];
-        if (!(d > T(0))) {
-          bad = 1;
-          break;
-        }
-        const T l = sqrt(d), inv = T(1) / l;
-        U[(size_t)p * n + p] = l;
-        pinv[f * kCholK + p] = inv;
-        for (int c = p + 1; c < kk; ++c) {
-          T t = U[(size_t)p * n + c];
-          for (int q = 0; q < p; ++q) t -= U[(size_t)q * n + p] * U[(size_t)q * n + c];
-          U[(size_t)p * n + c] = t * inv;
+      T a[kCholK][kCholK];
+#pragma unroll
+      for (int p = 0; p < kCholK; ++p)
+#pragma unroll
+        for (int c = 0; c < kCholK; ++c) a[p][c] = (c >= p && c < kk) ? U[(size_t)p * n + c] : T(0);
+      bool ok = true;
+#pragma unroll
+      for (int p = 0; p < kCholK; ++p) {
+        if (p < kk) {
+          T d = a[p][p];
+#pragma unroll
+          for (int q = 0; q < p; ++q) d -= a[q][p] * a[q][p];
+          ok = ok && d > T(0);
+          const T l = sqrt(d), inv = T(1) / l;
+          a[p][p] = l;
+          pinv[f * kCholK + p] = inv;
+#pragma unroll
+          for (int c = p + 1; c < kCholK; ++c) {
+            T t = a[p][c];
+#pragma unroll
+            for (int q = 0; q < p; ++q) t -= a[q][p] * a[q][c];
+            a[p][c] = t * inv;
+          }
         }
       }
+#pragma unroll
+      for (int p = 0; p < kCholK; ++p)
+#pragma unroll
+        for (int c = 0; c < kCholK; ++c)
+          if (c >= p && c < kk) U[(size_t)p * n + c] = a[p][c];
+      if (!ok) bad = 1;
     }
     __syncthreads();
     if (bad) {
@@ -365,10 +409,12 @@ __device__ void row_solve(const DenseArgs<T>& A, T* F, T* F2, int split, T* X, i
 // [c_lo, c_hi), stored as the own rows c of the row-owned array Z, length
 // n), L z = z (UPPER = false: forward substitution) or L^T z = z (UPPER:
 // backward), with L lower triangular stored in the rows of F (row t holds
-// L[t][0..t] and L^T[t][t..n-1]).  Rows of F are read in chunks of kStage
-// rows into the shared staging buffer (any block's rows); then every vector
-// advances with no cluster barrier: a group of g lanes per vector forms the
-// dot product and its leader divides by L[t][t].
+// L[t][0..t] and L^T[t][t..n-1]).  Rows of F are staged kStage at a time
+// (any block's rows, loads batched across the rows) with no cluster
+// barrier.  Per chunk, a group of g lanes per vector first forms the kStage
+// dot products with the entries already solved (independent sums, one pass
+// over them), then resolves the chunk's triangle serially in registers:
+// the serial chain per row is at most kStage - 1 terms long.
 constexpr int kStage = 8;
 static_assert(2 * kCholK <= kStage, "the Cholesky panels share the staging buffer");
 template <bool SM, bool UPPER, typename T>
@@ -381,31 +427,67 @@ __device__ void local_solve(const DenseArgs<T>& A, T* F, T* Z, int c_lo, int c_h
   const int grp = threadIdx.x / g, gl = threadIdx.x % g;
   const int ngrp = blockDim.x / g;
   const int vmax = ((nvec + ngrp - 1) / ngrp) * ngrp;
+  __shared__ T rdiag[kStage];
   for (int k0 = 0; k0 < n; k0 += kStage) {
     const int rows = min(kStage, n - k0);
     const int c0 = UPPER ? n - k0 - rows : k0;     // first row of the chunk
-    for (int e = threadIdx.x; e < rows * n; e += blockDim.x) {
-      const int t = c0 + e / n, q = e % n;
-      if (UPPER ? q >= t : q <= t) stage[e] = rd<SM>(any<SM>(A, F, t, n) + q);
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+      T x[kStage];
+#pragma unroll
+      for (int u = 0; u < kStage; ++u) {
+        const int t = c0 + u;
+        x[u] = (u < rows && (UPPER ? q >= t : q <= t)) ? rd<SM>(any<SM>(A, F, t, n) + q) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < kStage; ++u)
+        if (u < rows) {
+          stage[(size_t)u * n + q] = x[u];
+          if (q == c0 + u) rdiag[u] = T(1) / x[u];   // reciprocal pivots, off the chain
+        }
     }
     __syncthreads();
-    for (int step = 0; step < rows; ++step) {
-      const int t = UPPER ? c0 + rows - 1 - step : c0 + step;
-      const T* lt = stage + (size_t)(t - c0) * n;
-      for (int v = grp; v < vmax; v += ngrp) {
-        const bool act = v < nvec;
-        T* z = act ? own<SM>(A, Z, b + (v0 + v) * NB, n) : nullptr;
-        T acc = 0;
-        if (act) {
-          if (UPPER)
-            for (int q = t + 1 + gl; q < n; q += g) acc += lt[q] * z[q];
-          else
-            for (int q = gl; q < t; q += g) acc += lt[q] * z[q];
+    const int qa = UPPER ? c0 + rows : 0, qb = UPPER ? n : c0;   // entries already solved
+    for (int v = grp; v < vmax; v += ngrp) {
+      const bool act = v < nvec;
+      T* z = act ? own<SM>(A, Z, b + (v0 + v) * NB, n) : nullptr;
+      T part[kStage];
+#pragma unroll
+      for (int u = 0; u < kStage; ++u) part[u] = T(0);
+      if (act)
+        for (int q = qa + gl; q < qb; q += g) {
+          const T zq = z[q];
+#pragma unroll
+          for (int u = 0; u < kStage; ++u) part[u] += stage[(size_t)u * n + q] * zq;
         }
-        for (int o = g / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, g);
-        if (act && gl == 0) z[t] = (z[t] - acc) / lt[t];
-        __syncwarp();
+#pragma unroll
+      for (int u = 0; u < kStage; ++u)
+        for (int o = g / 2; o > 0; o >>= 1) part[u] += __shfl_xor_sync(0xffffffffu, part[u], o, g);
+      if (act) {                                  // the chunk's triangle, every lane alike
+        T zc[kStage];
+#pragma unroll
+        for (int u = 0; u < kStage; ++u) zc[u] = u < rows ? z[c0 + u] : T(0);
+#pragma unroll
+        for (int s = 0; s < kStage; ++s) {
+          const int u = UPPER ? kStage - 1 - s : s;
+          if (u < rows) {
+            T acc = part[u];
+            if (UPPER) {
+#pragma unroll
+              for (int w = u + 1; w < kStage; ++w)
+                if (w < rows) acc += stage[(size_t)u * n + c0 + w] * zc[w];
+            } else {
+#pragma unroll
+              for (int w = 0; w < u; ++w) acc += stage[(size_t)u * n + c0 + w] * zc[w];
+            }
+            zc[u] = (zc[u] - acc) * rdiag[u];
+          }
+        }
+        if (gl == 0)
+#pragma unroll
+          for (int u = 0; u < kStage; ++u)
+            if (u < rows) z[c0 + u] = zc[u];
       }
+      __syncwarp();
     }
     __syncthreads();
   }
@@ -429,10 +511,10 @@ __device__ void form_C(const DenseArgs<T>& A, T* sv) {
   __syncthreads();
   local_solve<SM, false>(A, A.LM, A.S2, 0, n, stage);   // S2 rows: columns of X
   csync();
-  for (int i = b; i < n; i += NB) {                 // X rows into S1
-    T* x = own<SM>(A, A.S1, i, n);
-    for (int j = threadIdx.x; j < n; j += blockDim.x) x[j] = rd<SM>(any<SM>(A, A.S2, j, n) + i);
-  }
+  batched_copy<T>(                                  // X rows into S1
+      ((n - b + NB - 1) / NB) * n,
+      [&](int e) { return rd<SM>(any<SM>(A, A.S2, e - (e / n) * n, n) + b + (e / n) * NB); },
+      [&](int e, T v) { own<SM>(A, A.S1, b + (e / n) * NB, n)[e - (e / n) * n] = v; });
   __syncthreads();
   local_solve<SM, false>(A, A.LN, A.S1, 0, n, stage);   // S1 rows: rows of C
   csync();  // every block done reading S2 before it becomes W
@@ -600,15 +682,14 @@ template <> struct GkRange<float> { static constexpr float big = 0x1p+48f, small
 template <typename T>
 __device__ int gk_count(const T* d, const T* e, int n, T x, T pivmin) {
   if constexpr (sizeof(T) == 4) {
-    // FP32: the LDL^T ratios q_k = -x - off(k)^2 / q_{k-1} (the FP32
-    // division is cheap)
+    // FP32: the LDL^T ratios q_k = -x - off(k)^2 / q_{k-1}
     int cnt = 0;
     T q = -x;
     if (fabs(q) < pivmin) q = -pivmin;
     cnt += q < T(0);
     for (int k = 1; k < 2 * n; ++k) {
       T o = gk_off(d, e, k);
-      q = -x - o * o / q;
+      q = -x - __fdividef(o * o, q);   // fast division: a 2-ulp error is a tiny perturbation of off(k)^2
       if (fabs(q) < pivmin) q = -pivmin;
       cnt += q < T(0);
     }
@@ -761,8 +842,13 @@ __device__ void bidiag_triplets(const DenseArgs<T>& A, T* sv) {
     int a1 = a0 + 1;
     while (a1 < r && __ldcg(A.sig + a1) - __ldcg(A.sig + a1 - 1) <= ortol) ++a1;
     if (c++ % GW != gw) continue;
+    // the factors and the iterate of the serial solves in shared memory (the
+    // block's rows of S2, free in this phase) when they fit, else in the
+    // global scratch; the converged iterate is kept in the global scratch for
+    // the later members of the cluster
+    const bool wsm = SM && (w + 1) * 6 * m <= A.RP * n;
     for (int a = a0; a < a1; ++a) {
-      T* base = A.z + (size_t)a * 6 * m;
+      T* base = wsm ? A.S2 + (size_t)w * 6 * m : A.z + (size_t)a * 6 * m;
       T *dd = base, *du = base + m, *du2 = base + 2 * m, *dl = base + 3 * m, *pv = base + 4 * m;
       T* zv = base + 5 * m;
       if (lane == 0) gk_factor(d, e, m, __ldcg(A.sig + a), pert, dd, du, du2, dl, pv);
@@ -793,6 +879,8 @@ __device__ void bidiag_triplets(const DenseArgs<T>& A, T* sv) {
         for (int k = lane; k < m; k += 32) zv[k] *= inv;
         __syncwarp();
       }
+      if (wsm && a + 1 < a1)
+        for (int k = lane; k < m; k += 32) A.z[(size_t)a * 6 * m + 5 * m + k] = zv[k];
       T nv = 0;                                   // right vector: even positions
       for (int i = lane; i < n; i += 32) nv += zv[2 * i] * zv[2 * i];
       nv = warp_sum(nv);
@@ -802,34 +890,52 @@ __device__ void bidiag_triplets(const DenseArgs<T>& A, T* sv) {
     }
   }
   csync();
+  constexpr int kReg = 8;                         // vector / reflector entries per lane
   for (int a = gw; a < r; a += GW) {              // v~ = P_B v_D, last reflector first
     T* y = A.vb + (size_t)a * n;
-    constexpr int kReg = 8;                       // reflector entries held per lane
-    for (int k = n - 2; k >= 0; --k) {
-      const T tau = taup[k];
-      if (tau == T(0)) continue;
-      const T* p = any<SM>(A, A.S3, k, n);
-      T pr[kReg];
-      T s = 0;
+    if (n <= 32 * kReg) {
+      // y and the reflectors in registers at the absolute positions
+      // lane + 32 q; reflector k - 1 is fetched while reflector k is applied
+      T yr[kReg], pr[kReg], nx[kReg];
+      auto fetch = [&](int k, T (&dst)[kReg]) {
+        const T* p = any<SM>(A, A.S3, k, n);
 #pragma unroll
-      for (int q = 0; q < kReg; ++q) {            // loads issued together
-        const int j = k + 1 + lane + 32 * q;
-        pr[q] = j < n ? rd<SM>(p + j) : T(0);
+        for (int q = 0; q < kReg; ++q) {
+          const int j = lane + 32 * q;
+          dst[q] = (j > k && j < n) ? rd<SM>(p + j) : T(0);
+        }
+      };
+#pragma unroll
+      for (int q = 0; q < kReg; ++q) yr[q] = lane + 32 * q < n ? y[lane + 32 * q] : T(0);
+      if (n >= 2) fetch(n - 2, pr);
+      for (int k = n - 2; k >= 0; --k) {
+        if (k > 0) fetch(k - 1, nx);
+        const T tau = taup[k];
+        if (tau != T(0)) {
+          T s = 0;
+#pragma unroll
+          for (int q = 0; q < kReg; ++q) s += pr[q] * yr[q];
+          s = warp_sum(s) * tau;
+#pragma unroll
+          for (int q = 0; q < kReg; ++q) yr[q] -= s * pr[q];
+        }
+#pragma unroll
+        for (int q = 0; q < kReg; ++q) pr[q] = nx[q];
       }
 #pragma unroll
-      for (int q = 0; q < kReg; ++q) {
-        const int j = k + 1 + lane + 32 * q;
-        if (j < n) s += pr[q] * y[j];
+      for (int q = 0; q < kReg; ++q)
+        if (lane + 32 * q < n) y[lane + 32 * q] = yr[q];
+    } else {
+      for (int k = n - 2; k >= 0; --k) {
+        const T tau = taup[k];
+        if (tau == T(0)) continue;
+        const T* p = any<SM>(A, A.S3, k, n);
+        T s = 0;
+        for (int j = k + 1 + lane; j < n; j += 32) s += rd<SM>(p + j) * y[j];
+        s = warp_sum(s) * tau;
+        for (int j = k + 1 + lane; j < n; j += 32) y[j] -= s * rd<SM>(p + j);
+        __syncwarp();
       }
-      for (int j = k + 1 + lane + 32 * kReg; j < n; j += 32) s += rd<SM>(p + j) * y[j];
-      s = warp_sum(s) * tau;
-#pragma unroll
-      for (int q = 0; q < kReg; ++q) {
-        const int j = k + 1 + lane + 32 * q;
-        if (j < n) y[j] -= s * pr[q];
-      }
-      for (int j = k + 1 + lane + 32 * kReg; j < n; j += 32) y[j] -= s * rd<SM>(p + j);
-      __syncwarp();
     }
   }
   csync();
@@ -995,7 +1101,8 @@ __device__ void triplets_local(const DenseArgs<T>& A, T* sv, T* red) {
     } else {
       const T s = part_sum<SM>(A, c - r);
       const T sc = s > T(0) ? T(1) / sqrt(s) : T(0);
-      for (int i = threadIdx.x; i < n; i += blockDim.x) z[i] = rd<SM>(any<SM>(A, A.R, i, r2) + c) * sc;
+      batched_copy<T>(
+          n, [&](int i) { return rd<SM>(any<SM>(A, A.R, i, r2) + c); }, [&](int i, T v) { z[i] = v * sc; });
     }
   }
   __syncthreads();

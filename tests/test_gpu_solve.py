@@ -125,6 +125,23 @@ def test_vcycle_matches_oracle(api, prec):
     assert np.abs(z - zo).max() <= tol * np.abs(zo).max()
 
 
+@pytest.mark.parametrize("nu", [(0, 2), (2, 1), (1, 4)])
+def test_vcycle_sweep_counts_match_oracle(api, nu):
+    """The coarse levels run as one cluster kernel: zero pre-sweeps and odd
+    and even sweep counts (the result lands in either work vector) agree
+    with the oracle V-cycle, here from the finest level down (all levels
+    small) and below a larger finest level."""
+    for side, levels in ((40, 3), (96, 4)):
+        ch = cg.tandem(side)
+        kw = dict(r=8, max_levels=levels, coarse_min=1, seed=3, nu_pre=nu[0], nu_post=nu[1])
+        h = gpu_setup(api, ch, precision="fp64", **kw)
+        H = oracle_setup(ch, **kw)
+        b = H.levels[0].B @ rng_vec(ch.n, 7)
+        z = h.vcycle(torch.from_numpy(b).cuda()).cpu().numpy()
+        zo = So.vcycle(H, b)
+        assert np.abs(z - zo).max() <= 1e-7 * np.abs(zo).max(), (side, nu)
+
+
 def rng_vec(n, seed):
     from oracle import rng
     return rng.uniform_pm1(seed, 0, n)
