@@ -1051,10 +1051,10 @@ __device__ void triplets_rows(const DenseArgs<T>& A, T* sv, T* red) {
   csync();
 }
 
-// The same triplets with the 2r back substitutions as local solves: vector
-// c (c < r: v~_c, else u~_(c-r)) is the own row c of S2 of block c mod NB,
-// solved with no cluster barrier (L_N^T for v, L_M^T for u); the owner of v_a
-// also takes its sign and publishes it for the owner of u_a.
+// The same triplets with the 2r back substitutions as local solves, with no
+// cluster barrier: the v~_a on the first half of the blocks (L_N^T), the u~_a
+// on the second half (L_M^T); the owner of v_a also takes its sign and
+// publishes it for the owner of u_a.
 template <bool SM, typename T>
 __device__ void triplets_local(const DenseArgs<T>& A, T* sv, T* red) {
   const int n = A.n, r = A.r, r2 = 2 * r, NB = nblocks<SM>(A), b = blockIdx.x;
@@ -1092,33 +1092,44 @@ __device__ void triplets_local(const DenseArgs<T>& A, T* sv, T* red) {
     if (threadIdx.x == 0) part[n + r2 + 1] = s;
   }
   csync();
-  // own vectors into the rows of S2: v~_a from vb, u~_a gathered from the
-  // rows of R and normalised
-  for (int c = b; c < r2; c += NB) {
-    T* z = own<SM>(A, A.S2, c, n);
-    if (c < r) {
-      for (int i = threadIdx.x; i < n; i += blockDim.x) z[i] = __ldcg(A.vb + (size_t)c * n + i);
+  // v~_a on the first half of the blocks, u~_a on the second, vpb per block:
+  // vector a of kind f (0: v, 1: u) is the own row b + slot NB of S2 of block
+  // b = f half + a / vpb (slot = a mod vpb), so each block solves with one
+  // factor only and both kinds advance together
+  const int half = NB / 2, vpb = (r + half - 1) / half;
+  const int f = b < half ? 0 : 1, a_lo = (b - f * half) * vpb;
+  const int nv = b < 2 * half ? max(0, min(vpb, r - a_lo)) : 0;
+  for (int v = 0; v < nv; ++v) {
+    const int a = a_lo + v;
+    T* z = own<SM>(A, A.S2, b + v * NB, n);
+    if (f == 0) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) z[i] = __ldcg(A.vb + (size_t)a * n + i);
     } else {
-      const T s = part_sum<SM>(A, c - r);
+      const T s = part_sum<SM>(A, a);
       const T sc = s > T(0) ? T(1) / sqrt(s) : T(0);
       batched_copy<T>(
-          n, [&](int i) { return rd<SM>(any<SM>(A, A.R, i, r2) + c); }, [&](int i, T v) { z[i] = v * sc; });
+          n, [&](int i) { return rd<SM>(any<SM>(A, A.R, i, r2) + r + a); }, [&](int i, T x) { z[i] = x * sc; });
     }
   }
   __syncthreads();
   T* stage = SM ? A.pub : sv + 3 * n;
-  local_solve<SM, true>(A, A.LN, A.S2, 0, r, stage);
-  local_solve<SM, true>(A, A.LM, A.S2, r, r2, stage);
+  if (nv > 0) {
+    if (f == 0)
+      local_solve<SM, true>(A, A.LN, A.S2, b, b + nv * NB, stage);
+    else
+      local_solve<SM, true>(A, A.LM, A.S2, b, b + nv * NB, stage);
+  }
   // signs of the own v_a (largest |v_i| positive, lowest index on ties) and
   // ||v_0||^2, published in the partial slots n + 2a and n + 2r
   __shared__ int redi[kWarps];
-  for (int c = b; c < r; c += NB) {
-    const T* z = own<SM>(A, A.S2, c, n);
+  for (int v = 0; v < (f == 0 ? nv : 0); ++v) {
+    const int a = a_lo + v;
+    const T* z = own<SM>(A, A.S2, b + v * NB, n);
     T best = T(-1);
     int bi = n;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const T v = fabs(z[i]);
-      if (v > best) { best = v; bi = i; }
+      const T x = fabs(z[i]);
+      if (x > best) { best = x; bi = i; }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -1132,10 +1143,10 @@ __device__ void triplets_local(const DenseArgs<T>& A, T* sv, T* red) {
     if (threadIdx.x == 0) {
       for (int k = 1; k < kWarps; ++k)
         if (red[k] > best || (red[k] == best && redi[k] < bi)) { best = red[k]; bi = redi[k]; }
-      part[n + 2 * c] = (bi < n && z[bi] < T(0)) ? T(-1) : T(1);
+      part[n + 2 * a] = (bi < n && z[bi] < T(0)) ? T(-1) : T(1);
     }
     __syncthreads();
-    if (c == 0) {
+    if (a == 0) {
       T s0 = 0;
       for (int i = threadIdx.x; i < n; i += blockDim.x) s0 += z[i] * z[i];
       s0 = block_sum(s0, red);
@@ -1145,11 +1156,11 @@ __device__ void triplets_local(const DenseArgs<T>& A, T* sv, T* red) {
   csync();
   const T uconst = T(1) / sqrt(part_sum<SM>(A, n + r2 + 1));   // 1 / sqrt(1^T M 1)
   const bool null0 = __ldcg(A.sig) <= null_tol;
-  for (int c = b; c < r2; c += NB) {
-    const T* z = own<SM>(A, A.S2, c, n);
-    const int a = c < r ? c : c - r;
-    const T sg = rd<SM>(part_r<SM>(A, a % NB) + n + 2 * a);
-    if (c < r) {
+  for (int v = 0; v < nv; ++v) {
+    const int a = a_lo + v;
+    const T* z = own<SM>(A, A.S2, b + v * NB, n);
+    const T sg = rd<SM>(part_r<SM>(A, a / vpb) + n + 2 * a);   // from the owner of v_a
+    if (f == 0) {
       for (int i = threadIdx.x; i < n; i += blockDim.x) A.V[(size_t)i * r + a] = double(sg * z[i]);
       if (a == 0) {
         const T s0 = part[n + r2];
@@ -1169,8 +1180,10 @@ __device__ void triplets_local(const DenseArgs<T>& A, T* sv, T* red) {
 
 template <bool SM, typename T>
 __device__ void triplets(const DenseArgs<T>& A, T* sv, T* red) {
-  const int NB = nblocks<SM>(A);
-  const bool fits = SM ? (2 * A.r + NB - 1) / NB <= A.RP : 2 * A.r <= A.n;
+  const int NB = nblocks<SM>(A), half = NB / 2;
+  // the vpb vectors of a block are its own rows b + v NB of S2
+  const int vpb = half > 0 ? (A.r + half - 1) / half : A.n + 1;
+  const bool fits = half > 0 && (SM ? vpb <= A.RP : NB - 1 + (vpb - 1) * NB < A.n);
   if (fits)
     triplets_local<SM>(A, sv, red);
   else
