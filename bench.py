@@ -53,6 +53,11 @@ FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (4 partitions x 32)
 COARSEST_TRAFFIC = {"source": "paper_1402_4005_gb300/csrc/dense.cu",
                     "sha256": "c513d57d5035aa0b3c4b577d0ebae91759354a7674874ffbf5327476d9b1fe36",
                     "bytes": 1692672 + 1280}
+# the same for one relax_block_kernel<float,16> launch on the 2048 x 2048
+# tandem queue (ncu reports MB to two decimals)
+SPARSE_TRAFFIC = {"source": "paper_1402_4005_gb300/csrc/blockops.cu",
+                  "sha256": "e59e63a6c6ba37b715b3c4b55aecf05cb43d8f0e71343e78d8ee326804b05701",
+                  "bytes": 436_170_000 + 239_260_000, "side": 2048}
 
 
 def env_int(name, default):
@@ -341,7 +346,8 @@ def roofline_sparse(api, torch, stream, side=2048, ld=16):
     return {"bound": "hbm", "kernel": "relax_block_kernel<float,16> (finest level, r=16)",
             "workload": f"tandem queue {side}x{side} (n={n}, nnz(B)={nnz})",
             "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-            "traffic": None, "peak_source": src, "launch_us": round(ms * 1e3, 2), "alg_bytes": alg}
+            "traffic": captured_traffic(SPARSE_TRAFFIC) if side == SPARSE_TRAFFIC["side"] else None,
+            "peak_source": src, "launch_us": round(ms * 1e3, 2), "alg_bytes": alg}
 
 
 # ---------------------------------------------------------------- learned (config 5)
