@@ -12,6 +12,7 @@ Streams used here (counter = stream * 2^32 + i):
   V test vector k  -> stream 2k
   U test vector k  -> stream 2k + 1
   MIS priorities on level l -> stream 4096 + l
+  colouring priorities on level l -> stream 6144 + l
 """
 import numpy as np
 

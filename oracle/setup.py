@@ -53,6 +53,7 @@ class Params:
     seed: int = 1
     restriction: str = "ls"           # or "average" (Section 5 comparison)
     cycles: int = 1                   # bootstrap setup cycles (2 = BAMG^2)
+    smoother: str = "jacobi"          # V-cycle smoother: "jacobi", "mcgs" or "gs" (natural order)
 
 
 @dataclass
@@ -72,6 +73,8 @@ class Level:
     Q: sp.csr_matrix | None = None
     s: np.ndarray | None = None
     t: np.ndarray | None = None
+    colour: np.ndarray | None = None   # multicolour Gauss-Seidel: colours and row order
+    order: np.ndarray | None = None
 
 
 @dataclass
@@ -216,4 +219,19 @@ def bamg_setup(A: sp.csr_matrix, p: Params, grid=None, U0=None, V0=None) -> Hier
         sig, U, V = bamg_mle(H, 0, U, V, sig)
     H.sigma, H.U, H.V = sig, U, V
     H.x0 = initial_x(sig, V)
+    prepare_smoother(H)
     return H
+
+
+def prepare_smoother(H: Hierarchy) -> None:
+    """Row orders of the Gauss-Seidel V-cycle smoother on every non-coarsest
+    level: the greedy colouring of the level's symmetrised graph (priorities
+    SplitMix64 stream 6144 + l), rows by colour then index; or the natural
+    order."""
+    p = H.params
+    for l, lev in enumerate(H.levels[:-1]):
+        if p.smoother == "mcgs":
+            lev.colour = smoothing.level_colouring(lev.B, lev.Bt, p.seed, l)
+            lev.order = smoothing.multicolour_order(lev.colour)
+        elif p.smoother == "gs":
+            lev.order = np.arange(lev.n)

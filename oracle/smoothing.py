@@ -7,11 +7,15 @@ splitting F = D / omega, and that is the reading used here.
 
 Gauss-Seidel is one of the admissible splittings listed in Section 3.  It is
 given here in the natural (lexicographic) order of the paper and in a
-multicolour order; Jacobi is order-independent, so its multicolour schedule
-is the plain sweep.
+multicolour order (rows of one colour share no edge of the symmetrised graph
+of B, so they can be updated together); Jacobi is order-independent, so its
+multicolour schedule is the plain sweep.  The V-cycle takes either smoother
+(Params.smoother); the setup relaxations stay weighted Jacobi.
 """
 import numpy as np
 import scipy.sparse as sp
+
+from . import rng
 
 
 def jacobi(B: sp.csr_matrix, d: np.ndarray, X: np.ndarray, rhs=None,
@@ -23,19 +27,18 @@ def jacobi(B: sp.csr_matrix, d: np.ndarray, X: np.ndarray, rhs=None,
     return X + omega * R / d[:, None]
 
 
-def gauss_seidel(B: sp.csr_matrix, x: np.ndarray, b: np.ndarray, order) -> np.ndarray:
-    """One forward Gauss-Seidel sweep visiting the rows in ``order``."""
+def gauss_seidel(B: sp.csr_matrix, x: np.ndarray, b: np.ndarray, order, d=None) -> np.ndarray:
+    """One forward Gauss-Seidel sweep visiting the rows in ``order``:
+    x_i <- x_i + (b_i - sum_j b_ij x_j) / d_i with the current x, which is
+    (b_i - sum_{j != i} b_ij x_j) / b_ii for the default d_i = b_ii."""
     x = x.copy()
+    if d is None:
+        d = B.diagonal()
     for i in order:
         s = b[i]
-        dii = 0.0
         for p in range(B.indptr[i], B.indptr[i + 1]):
-            j = B.indices[p]
-            if j == i:
-                dii = B.data[p]
-            else:
-                s -= B.data[p] * x[j]
-        x[i] = s / dii
+            s -= B.data[p] * x[B.indices[p]]
+        x[i] = x[i] + s / d[i]
     return x
 
 
@@ -59,3 +62,16 @@ def greedy_colouring(B: sp.csr_matrix, Bt: sp.csr_matrix, key: np.ndarray) -> np
 def multicolour_order(colour: np.ndarray) -> np.ndarray:
     """Rows grouped by colour, ascending index inside each colour."""
     return np.lexsort((np.arange(colour.shape[0]), colour))
+
+
+COLOUR_STREAM = 6144
+
+
+def colouring_priorities(n: int, seed: int, level: int) -> np.ndarray:
+    return rng.draw(seed, COLOUR_STREAM + level, n)
+
+
+def level_colouring(B: sp.csr_matrix, Bt: sp.csr_matrix, seed: int, level: int) -> np.ndarray:
+    """Greedy colouring of the symmetrised graph of level ``level`` with the
+    SplitMix64 priorities of that level."""
+    return greedy_colouring(B, Bt, colouring_priorities(B.shape[0], seed, level))

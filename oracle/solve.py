@@ -19,6 +19,7 @@ from __future__ import annotations
 import numpy as np
 import scipy.sparse as sp
 
+from . import smoothing
 from .setup import Hierarchy
 
 
@@ -29,12 +30,22 @@ def vcycle(H: Hierarchy, b: np.ndarray, l: int = 0) -> np.ndarray:
         return H.Bpinv @ b
     z = np.zeros_like(b)
     for _ in range(p.nu_pre):
-        z = z + p.omega * (b - lev.B @ z) / lev.d
+        z = smooth(H, lev, z, b)
     res = b - lev.B @ z
     z = z + lev.P @ vcycle(H, lev.Q @ res, l + 1)
     for _ in range(p.nu_post):
-        z = z + p.omega * (b - lev.B @ z) / lev.d
+        z = smooth(H, lev, z, b)
     return z
+
+
+def smooth(H: Hierarchy, lev, z: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """One sweep of the V-cycle smoother (Section 3): weighted Jacobi, or
+    Gauss-Seidel (unweighted) in the level's row order with the Jacobi
+    divisor d (b_ii where b_ii > 0)."""
+    p = H.params
+    if p.smoother == "jacobi":
+        return z + p.omega * (b - lev.B @ z) / lev.d
+    return smoothing.gauss_seidel(lev.B, z, b, lev.order, lev.d)
 
 
 def rel_res_1(B, x):

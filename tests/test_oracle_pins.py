@@ -123,6 +123,59 @@ def test_multicolour_jacobi_equals_natural_and_gs_orders_converge():
         assert np.linalg.norm(B @ z) < 0.6 * np.linalg.norm(B @ zp)
 
 
+def test_colouring_is_the_greedy_definition():
+    """Every vertex takes the smallest colour absent from its neighbours of
+    higher priority (SplitMix64 key descending, ties by index), and no edge
+    of the symmetrised graph joins two vertices of one colour."""
+    for ch in (cg.delaunay_walk(300, seed=5), cg.tandem(11)):
+        B = operators.build_B(ch.csr())
+        Bt = operators.transpose(B)
+        key = smoothing.colouring_priorities(ch.n, 7, 2)
+        col = smoothing.level_colouring(B, Bt, 7, 2)
+        Bs = (abs(B) + abs(Bt)).tocsr()
+        for v in range(ch.n):
+            nb = [int(j) for j in Bs.indices[Bs.indptr[v]:Bs.indptr[v + 1]] if j != v]
+            higher = [j for j in nb if key[j] > key[v] or (key[j] == key[v] and j < v)]
+            free = sorted(set(range(len(higher) + 1)) - {int(col[j]) for j in higher})
+            assert col[v] == free[0]
+            assert all(col[j] != col[v] for j in nb)
+
+
+def _vcycle_factor(H, iters=16):
+    """Asymptotic factor of x <- x + C(-Bx) from 1 + 0.5u (geometric mean of
+    the residual 1-norm ratios over the second half)."""
+    B = H.levels[0].B
+    x = 1 + 0.5 * rng.uniform_pm1(9, 8193, H.levels[0].n)
+    rs = []
+    for _ in range(iters):
+        r = -(B @ x)
+        rs.append(np.abs(r).sum())
+        x = x + So.vcycle(H, r)
+    q = [rs[k + 1] / rs[k] for k in range(iters // 2, iters - 1)]
+    return float(np.exp(np.mean(np.log(q))))
+
+
+def test_gauss_seidel_multicolour_order_keeps_the_convergence_factor():
+    """Gauss-Seidel V-cycles in the paper's natural order and in the
+    multicolour order: on the uniform walk the two factors agree closely; on
+    the tandem queue (a directed flow) the natural order runs against the
+    flow and is much slower, the multicolour order still converges."""
+    ch = cg.uniform2d(24)
+    f = {}
+    for sm in ("gs", "mcgs"):
+        H = S.bamg_setup(ch.csr(), S.Params(r=8, max_levels=3, coarse_min=1, seed=2, smoother=sm),
+                         grid=(ch.nx, ch.ny))
+        f[sm] = _vcycle_factor(H)
+    assert f["gs"] < 0.3 and f["mcgs"] < 0.3
+    assert abs(f["gs"] - f["mcgs"]) <= 0.1 * f["gs"], f
+    ch = cg.tandem(24)
+    H = S.bamg_setup(ch.csr(), S.Params(r=8, max_levels=3, coarse_min=1, seed=2, smoother="mcgs"),
+                     grid=(24, 24))
+    assert _vcycle_factor(H) < 0.7
+    xo, its, _ = So.bamg_solve(H, tol=1e-10, restart=20)
+    assert So.rel_res_1(H.levels[0].B, xo) <= 1e-10
+
+
 # --------------------------------------------------------------- coarsening
 def test_geometric_split_and_sets_brute_force():
     nx, ny = 7, 6
