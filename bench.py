@@ -9,6 +9,8 @@ mixed-precision path (FP32 V-cycle and setup relaxation inside FP64 GMRES);
 the plain FP64 GPU path is timed beside it on the same chain.
 
 Beside the headline line the same JSON object reports, on the same GPU:
+  mcgs_smoother     the same step with multicolour Gauss-Seidel as the
+                    V-cycle smoother instead of weighted Jacobi
   roofline          the dominant kernel of a step (coarsest-level solver),
                     timed live with CUDA events
   roofline_sparse   the finest-level block relaxation on a 2048 x 2048
@@ -51,13 +53,13 @@ FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (4 partitions x 32)
 # workload from an ncu capture, valid only while the kernel's source file is
 # byte-identical to the one captured (else the roofline reports null)
 COARSEST_TRAFFIC = {"source": "paper_1402_4005_gb300/csrc/dense.cu",
-                    "sha256": "c513d57d5035aa0b3c4b577d0ebae91759354a7674874ffbf5327476d9b1fe36",
-                    "bytes": 1692672 + 1280}
+                    "sha256": "7a303679a004cf5f97f794f4e7196d0602a73bf5c61f156c5e0e3fa5756ae1a1",
+                    "bytes": 1741568 + 0}
 # the same for one relax_block_kernel<float,16> launch on the 2048 x 2048
 # tandem queue (ncu reports MB to two decimals)
 SPARSE_TRAFFIC = {"source": "paper_1402_4005_gb300/csrc/blockops.cu",
-                  "sha256": "e59e63a6c6ba37b715b3c4b55aecf05cb43d8f0e71343e78d8ee326804b05701",
-                  "bytes": 436_170_000 + 239_260_000, "side": 2048}
+                  "sha256": "e4ddb26dd524f4c4e237597f9bc1e406775e40abf13a66ebd9de981b5d2752dd",
+                  "bytes": 436_170_000 + 239_300_000, "side": 2048}
 
 
 def env_int(name, default):
@@ -162,17 +164,17 @@ def gpu_arm(args, rank: int, world: int):
     rp, ci, va = chain_tensors(torch, ch)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def one_step(prec):
-        p = api.bamg_params_default(precision=prec, **KW)
+    def one_step(prec, **extra):
+        p = api.bamg_params_default(precision=prec, **KW, **extra)
         h = api.bamg_setup(rp, ci, va, ch.n, p, nx=SIDE, ny=SIDE, stream=stream)
         x, info = api.bamg_solve(h, restart=20, tol=1e-10, stream=stream)
         return h, x, info
 
-    def timed(prec, steps, warmup):
+    def timed(prec, steps, warmup, **extra):
         times, infos = [], []
         with torch.cuda.stream(stream):
             for _ in range(warmup):
-                h, x, info = one_step(prec)
+                h, x, info = one_step(prec, **extra)
                 h.destroy()
             torch.cuda.synchronize()
             if world > 1:
@@ -181,7 +183,7 @@ def gpu_arm(args, rank: int, world: int):
             for _ in range(steps):
                 flush.fill_(1.0)                     # evict the 129 MB L2 between steps
                 torch.cuda.synchronize()
-                ms, (h, x, info) = event_ms(torch, stream, lambda: one_step(prec))
+                ms, (h, x, info) = event_ms(torch, stream, lambda: one_step(prec, **extra))
                 times.append(ms)
                 infos.append(info)
                 last = (h, x)
@@ -192,6 +194,18 @@ def gpu_arm(args, rank: int, world: int):
     with ClockSampler(dev) as clk:
         t_mix, i_mix, (h_mix, x_mix), launches = timed("mixed", args.steps, args.warmup)
     t_64, i_64, (h_64, x_64), _ = timed("fp64", max(3, args.steps // 2), 3)
+    # the Gauss-Seidel splitting of Section 3 in multicolour order as the
+    # V-cycle smoother (same hierarchy construction)
+    try:
+        t_gs, i_gs, (h_gs, x_gs), _ = timed("mixed", 3, 3, smoother="mcgs")
+        gs = {"ms_per_step": round(statistics.mean(t_gs), 3),
+              "setup_ms": round(statistics.mean(i["setup_ms"] for i in i_gs), 3),
+              "solve_ms": round(statistics.mean(i["solve_ms"] for i in i_gs), 3),
+              "iterations": i_gs[-1]["iterations"], "rel_res_1": i_gs[-1]["rel_res_1"],
+              "err_l1_vs_jacobi": None}
+        h_gs.destroy()
+    except Exception as exc:          # a variant failure must not lose the headline
+        gs, x_gs = {"error": f"{type(exc).__name__}: {exc}"[:300]}, None
 
     ms = statistics.mean(t_mix)
     if world > 1:
@@ -199,6 +213,8 @@ def gpu_arm(args, rank: int, world: int):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
     err_vs_fp64 = float((x_mix - x_64).abs().sum().item())
+    if x_gs is not None:
+        gs["err_l1_vs_jacobi"] = float((x_gs - x_mix).abs().sum().item())
 
     # end to end through host buffers (pinned), copies inside the timed region
     hrp = torch.from_numpy(ch.row_ptr).pin_memory().numpy()
@@ -217,7 +233,7 @@ def gpu_arm(args, rank: int, world: int):
         "ms": ms, "t_mix": t_mix, "i_mix": i_mix, "t_64": t_64, "i_64": i_64, "launches": launches,
         "clocks": clk.summary(), "err_vs_fp64": err_vs_fp64, "e2e_ms": statistics.mean(e2e),
         "h2d": hrp.nbytes + hci.nbytes + hva.nbytes, "d2h": xh.nbytes,
-        "roofline": roofline_coarsest(api, torch, stream, h_mix),
+        "roofline": roofline_coarsest(api, torch, stream, h_mix), "mcgs": gs,
     }
     h_mix.destroy()
     h_64.destroy()
@@ -609,6 +625,7 @@ def main():
                        "solve_ms": round(statistics.mean(i["solve_ms"] for i in r["i_64"]), 3),
                        "iterations": r["i_64"][-1]["iterations"]},
         "op_cplx": r["i_mix"][-1]["op_cplx"], "grid_cplx": r["i_mix"][-1]["grid_cplx"],
+        "mcgs_smoother": r["mcgs"],
         "e2e": {"value": round(r["e2e_ms"], 3), "unit": "ms", "h2d_bytes_per_step": r["h2d"],
                 "d2h_bytes_per_step": r["d2h"]},
         "gpu_launches": r["launches"],

@@ -54,6 +54,7 @@ enum { BAMG_COARSEN_GEOMETRIC = 0, BAMG_COARSEN_MIS = 1 };
 enum { BAMG_PREC_FP64 = 0, BAMG_PREC_MIXED = 1 };
 enum { BAMG_RESTRICT_LS = 0, BAMG_RESTRICT_AVERAGE = 1 };
 enum { BAMG_INTERP_LS = 0, BAMG_INTERP_MLP = 1 };
+enum { BAMG_SMOOTH_JACOBI = 0, BAMG_SMOOTH_MCGS = 1 };
 
 /* CSR of the column-stochastic A (row i = probabilities of entering state i).
  * row_ptr[n+1], col_idx[nnz] (ascending within each row, 0 <= col < n),
@@ -101,6 +102,14 @@ typedef struct {
                         Section 7): each later cycle rebuilds the hierarchy from
                         the previous cycle's finest triplets; must be 1 with
                         network fits                                          */
+  int smoother;      /* V-cycle smoother: BAMG_SMOOTH_JACOBI (weighted Jacobi,
+                        Section 7) or BAMG_SMOOTH_MCGS (Gauss-Seidel, one of
+                        the splittings of Section 3, in multicolour order: the
+                        greedy colouring of the symmetrised graph of each
+                        level's B, SplitMix64 priorities, stream 6144 + level;
+                        x_i += (b_i - (Bx)_i) / d_i, unweighted, d the Jacobi
+                        divisor).  The setup relaxations stay weighted Jacobi.
+                        Not available for batches.                            */
 } bamg_params;
 
 typedef struct {
@@ -262,6 +271,10 @@ typedef struct {
   const double* s;                  /* sqrt LS weights of V (r)                */
   const double* t;                  /* sqrt LS weights of U (r, t[0] = 0)      */
   int jacobi_l1_rows;               /* rows with b_ii <= 0 (l1 Jacobi divisor)  */
+  const int32_t* colour;            /* multicolour smoother: colour of each row
+                                       (NULL unless smoother = MCGS, and on the
+                                       coarsest level)                         */
+  int ncolours;
 } bamg_level_view;
 
 int bamg_num_levels(const bamg_hierarchy* h);

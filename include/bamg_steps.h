@@ -119,6 +119,34 @@ bamg_status bamg_step_coarsen_mis(int n, const int32_t* B_rp, const int32_t* B_c
                                   uint64_t seed, int level, int8_t* cf, int32_t* cmap,
                                   int* nc_host, void* stream);
 
+/* Greedy colouring of the symmetrised graph of B (Section 3: Gauss-Seidel is
+ * an admissible splitting; rows of one colour are updated together): the
+ * vertices in decreasing SplitMix64 priority (seed, stream 6144 + level,
+ * ties by lower index), each taking the smallest colour absent from its
+ * neighbours taken before it; computed in parallel rounds with the same
+ * result bit for bit.  B and B^T as CSR (device, int32); colour[n] (device,
+ * caller-owned) receives colours 0 .. *ncolours_host - 1.  Synchronises the
+ * stream. */
+bamg_status bamg_step_colour(int n, const int32_t* B_rp, const int32_t* B_ci, const int32_t* Bt_rp,
+                             const int32_t* Bt_ci, uint64_t seed, int level, int32_t* colour, int* ncolours_host,
+                             void* stream);
+
+/* Rows grouped by colour, ascending inside a colour: rows[n] (device) and
+ * colour_rp_host[ncolours + 1] (host) with the rows of colour c at
+ * rows[colour_rp_host[c] .. colour_rp_host[c + 1]).  Synchronises the
+ * stream. */
+bamg_status bamg_step_colour_rows(int n, const int32_t* colour, int ncolours, int32_t* colour_rp_host,
+                                  int32_t* rows, void* stream);
+
+/* One forward multicolour Gauss-Seidel sweep in place on x[n] (device):
+ * colour by colour, x_i <- x_i + (b_i - (B x)_i) * dinv_i over the rows of
+ * the colour (unweighted; dinv = 1 / Jacobi divisor).  val, dinv, b, x are
+ * double (prec = 0) or float (prec = 1); colour_rp_host and rows as from
+ * bamg_step_colour_rows.  Stream-ordered. */
+bamg_status bamg_step_mcgs_sweep(int prec, int n, const int32_t* rp, const int32_t* ci, const void* val,
+                                 const void* dinv, int ncolours, const int32_t* colour_rp_host, const int32_t* rows,
+                                 const void* b, void* x, void* stream);
+
 /* Interpolation sets on a graph: per fine point, coarse neighbours ranked by
  * strength |b_ij| + |b_ji| (descending, ties by index), at most c_max, topped
  * up to c_min from distance two by the largest strength product.  Output J

@@ -35,7 +35,7 @@ class Params(C.Structure):
                 ("nu_pre", i32), ("nu_post", i32), ("c_min", i32), ("c_max", i32),
                 ("omega", f64), ("coarsening", i32), ("precision", i32), ("restriction", i32),
                 ("seed", u64), ("stochastic_tol", f64), ("max_coarse_dense", i32),
-                ("interp", i32), ("mlp_params", vp), ("setup_cycles", i32)]
+                ("interp", i32), ("mlp_params", vp), ("setup_cycles", i32), ("smoother", i32)]
 
 
 class SolveParams(C.Structure):
@@ -58,7 +58,7 @@ class CsrView(C.Structure):
 class LevelView(C.Structure):
     _fields_ = [("n", i32), ("B", CsrView), ("M", CsrView), ("N", CsrView), ("P", CsrView),
                 ("Qt", CsrView), ("Q", CsrView), ("cf", vp), ("cmap", vp), ("s", vp), ("t", vp),
-                ("jacobi_l1_rows", i32)]
+                ("jacobi_l1_rows", i32), ("colour", vp), ("ncolours", i32)]
 
 
 # name -> (restype, argtypes)
@@ -105,6 +105,9 @@ SIGNATURES = {
     "bamg_step_coarsen_geometric": (i32, [i32, i32, vp, vp, vp, vp, ip, vp]),
     "bamg_step_coarsen_mis": (i32, [i32, vp, vp, vp, vp, u64, i32, vp, vp, ip, vp]),
     "bamg_step_graph_sets": (i32, [i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, vp, vp, vp]),
+    "bamg_step_colour": (i32, [i32, vp, vp, vp, vp, u64, i32, vp, ip, vp]),
+    "bamg_step_colour_rows": (i32, [i32, vp, i32, vp, vp, vp]),
+    "bamg_step_mcgs_sweep": (i32, [i32, i32, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp]),
     "bamg_step_ls_fit": (i32, [i32, i32, i32, i32, vp, vp, vp, vp, i32, vp, ip, vp]),
     "bamg_step_spgemm_symbolic": (i32, [i32, vp, vp, vp, vp, vp, i64p, vp]),
     "bamg_step_spgemm_numeric": (i32, [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),

@@ -43,7 +43,8 @@ def bamg_params_default(**overrides) -> _lib.Params:
     names = {"coarsening": {"geometric": 0, "mis": 1},
              "precision": {"fp64": 0, "mixed": 1},
              "restriction": {"ls": 0, "average": 1},
-             "interp": {"ls": 0, "mlp": 1}}
+             "interp": {"ls": 0, "mlp": 1},
+             "smoother": {"jacobi": 0, "mcgs": 1}}
     for k, v in overrides.items():
         if k in names and isinstance(v, str):
             v = names[k][v]
@@ -108,6 +109,9 @@ class Hierarchy:
         if v.cf:
             out["cf"] = _copy_dev(v.cf, v.n, torch.int8)
             out["cmap"] = _copy_dev(v.cmap, v.n, torch.int32)
+        if v.colour:
+            out["colour"] = _copy_dev(v.colour, v.n, torch.int32)
+            out["ncolours"] = v.ncolours
         return out
 
     def triplets(self, r: int) -> dict:
@@ -394,6 +398,37 @@ def bamg_step_coarsen_mis(B_rp, B_ci, Bt_rp, Bt_ci, seed: int, level: int, strea
     check(lib().bamg_step_coarsen_mis(n, _p(B_rp), _p(B_ci), _p(Bt_rp), _p(Bt_ci), seed, level, _p(cf), _p(cmap),
                                       C.byref(nc), _stream(stream)), "coarsen_mis")
     return cf, cmap, nc.value
+
+
+def bamg_step_colour(B_rp, B_ci, Bt_rp, Bt_ci, seed: int, level: int, stream=None):
+    """(colour[n] int32 device tensor, number of colours) of the symmetrised graph."""
+    n = B_rp.shape[0] - 1
+    colour = torch.empty(n, dtype=torch.int32, device="cuda")
+    nc = C.c_int()
+    check(lib().bamg_step_colour(n, _p(B_rp), _p(B_ci), _p(Bt_rp), _p(Bt_ci), seed, level, _p(colour), C.byref(nc),
+                                 _stream(stream)), "colour")
+    return colour, nc.value
+
+
+def bamg_step_colour_rows(colour, ncolours: int, stream=None):
+    """(colour offsets as a host numpy int32 array of ncolours + 1, rows tensor)."""
+    import numpy as np
+    n = colour.shape[0]
+    crp = np.zeros(ncolours + 1, dtype=np.int32)
+    rows = torch.empty(n, dtype=torch.int32, device="cuda")
+    check(lib().bamg_step_colour_rows(n, _p(colour), ncolours, crp.ctypes.data, _p(rows), _stream(stream)),
+          "colour_rows")
+    return crp, rows
+
+
+def bamg_step_mcgs_sweep(rp, ci, val, dinv, crp, rows, b, x, stream=None):
+    """One multicolour Gauss-Seidel sweep on x in place (float32 or float64)."""
+    import numpy as np
+    prec = 1 if x.dtype == torch.float32 else 0
+    crp = np.ascontiguousarray(crp, dtype=np.int32)
+    check(lib().bamg_step_mcgs_sweep(prec, x.shape[0], _p(rp), _p(ci), _p(val), _p(dinv), crp.shape[0] - 1,
+                                     crp.ctypes.data, _p(rows), _p(b), _p(x), _stream(stream)), "mcgs_sweep")
+    return x
 
 
 def bamg_step_graph_sets(B_rp, B_ci, B_val, Bt_rp, Bt_ci, Bt_val, cf, c_min: int, c_max: int, stream=None):

@@ -96,6 +96,7 @@ static bamg_status check_params(const bamg_csr* A, const bamg_params* p) {
   BAMG_CHECK_ARG(p->interp == BAMG_INTERP_LS || p->interp == BAMG_INTERP_MLP);
   BAMG_CHECK_ARG(p->setup_cycles >= 1 && p->setup_cycles <= 8);
   BAMG_CHECK_ARG(p->interp == BAMG_INTERP_LS || p->setup_cycles == 1);
+  BAMG_CHECK_ARG(p->smoother == BAMG_SMOOTH_JACOBI || p->smoother == BAMG_SMOOTH_MCGS);
   if (p->interp == BAMG_INTERP_MLP) {
     BAMG_CHECK_ARG(p->mlp_params != nullptr);
     if (p->coarsening != BAMG_COARSEN_GEOMETRIC) {
@@ -281,6 +282,8 @@ bamg_status bamg_level(const bamg_hierarchy* h, int l, bamg_level_view* out) {
   out->s = L.s.as<double>();
   out->t = L.t.as<double>();
   out->jacobi_l1_rows = L.nsafe;
+  out->colour = L.ncol > 0 ? L.colour.as<int32_t>() : nullptr;
+  out->ncolours = L.ncol;
   return BAMG_OK;
 }
 
@@ -409,6 +412,35 @@ bamg_status bamg_step_coarsen_mis(int n, const int32_t* B_rp, const int32_t* B_c
                                   int* nc_host, void* stream) {
   BAMG_CHECK_ARG(n >= 1 && B_rp && B_ci && Bt_rp && Bt_ci && cf && cmap && level >= 0);
   return coarsen_mis(n, B_rp, B_ci, Bt_rp, Bt_ci, seed, level, cf, cmap, nc_host, S(stream));
+}
+
+bamg_status bamg_step_colour(int n, const int32_t* B_rp, const int32_t* B_ci, const int32_t* Bt_rp,
+                             const int32_t* Bt_ci, uint64_t seed, int level, int32_t* colour, int* ncolours_host,
+                             void* stream) {
+  BAMG_CHECK_ARG(n >= 1 && B_rp && B_ci && Bt_rp && Bt_ci && colour && ncolours_host && level >= 0);
+  return colour_graph(n, B_rp, B_ci, Bt_rp, Bt_ci, seed, level, colour, ncolours_host, S(stream));
+}
+
+bamg_status bamg_step_colour_rows(int n, const int32_t* colour, int ncolours, int32_t* colour_rp_host,
+                                  int32_t* rows, void* stream) {
+  BAMG_CHECK_ARG(n >= 1 && colour && ncolours >= 1 && colour_rp_host && rows);
+  bamg_status st = colour_rows(n, colour, ncolours, colour_rp_host, rows, S(stream));
+  if (st == BAMG_OK && cudaStreamSynchronize(S(stream)) != cudaSuccess) return BAMG_ERR_CUDA;
+  return st;
+}
+
+bamg_status bamg_step_mcgs_sweep(int prec, int n, const int32_t* rp, const int32_t* ci, const void* val,
+                                 const void* dinv, int ncolours, const int32_t* colour_rp_host, const int32_t* rows,
+                                 const void* b, void* x, void* stream) {
+  BAMG_CHECK_ARG(n >= 1 && rp && ci && val && dinv && ncolours >= 1 && colour_rp_host && rows && b && x);
+  BAMG_CHECK_ARG(colour_rp_host[0] == 0 && colour_rp_host[ncolours] == n && (prec == 0 || prec == 1));
+  for (int c = 0; c < ncolours; ++c) BAMG_CHECK_ARG(colour_rp_host[c + 1] >= colour_rp_host[c]);
+  const int G = 4;
+  if (prec == 1)
+    return mcgs_sweep<float>(G, ncolours, colour_rp_host, rows, rp, ci, (const float*)val, (const float*)dinv,
+                             (const float*)b, (float*)x, S(stream));
+  return mcgs_sweep<double>(G, ncolours, colour_rp_host, rows, rp, ci, (const double*)val, (const double*)dinv,
+                            (const double*)b, (double*)x, S(stream));
 }
 
 bamg_status bamg_step_graph_sets(int n, const int32_t* B_rp, const int32_t* B_ci, const double* B_val,

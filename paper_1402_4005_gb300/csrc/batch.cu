@@ -671,6 +671,10 @@ extern "C" bamg_status bamg_setup_batched(const bamg_csr* As, int nchains, const
                                           void* stream, bamg_batch** out) {
   BAMG_CHECK_ARG(As && p && out && nchains >= 1);
   *out = nullptr;
+  if (p->smoother != BAMG_SMOOTH_JACOBI) {
+    set_error("batches take the weighted Jacobi smoother only");
+    return BAMG_ERR_UNSUPPORTED;
+  }
   bamg_batch* bt = new (std::nothrow) bamg_batch();
   if (!bt) return BAMG_ERR_OOM;
   bt->p = *p;

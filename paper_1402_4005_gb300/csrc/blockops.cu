@@ -17,16 +17,18 @@ struct Blk {
   static_assert(LD % VW == 0 && LPR >= 1 && LPR <= 32, "bad block width");
 };
 
-// Layout of the row kernels (relaxation, block SpMM): rows of 64 bytes or
-// more are split into NV = 2 interleaved 16-byte vectors per lane (lane q of
-// the row group holds vectors q and q + LPR), so a row group has half the
-// lanes, a warp twice the rows, and each gather instruction of the group
-// covers contiguous 32-byte sectors.
-template <typename T, int LD>
+// Layout of the row kernels (relaxation, block SpMM): on large levels
+// (W = 2) rows of 64 bytes or more are split into NV = 2 interleaved 16-byte
+// vectors per lane (lane q of the row group holds vectors q and q + LPR), so
+// a row group has half the lanes, a warp twice the rows, and each gather
+// instruction of the group covers contiguous 32-byte sectors; small levels
+// (W = 1) keep one vector per lane and twice the warps.
+constexpr int kRowPairMin = 1 << 17;               // rows from which W = 2
+template <typename T, int LD, int W = 2>
 struct RowBlk {
   static constexpr int VW = Vec16<T>::W;
   static constexpr int NVR = LD / VW;              // 16-byte vectors per row
-  static constexpr int NV = NVR >= 4 ? 2 : 1;      // vectors per lane
+  static constexpr int NV = (NVR >= 4 && W == 2) ? 2 : 1;   // vectors per lane
   static constexpr int LPR = NVR / NV;             // lanes per row
   static constexpr int RPW = 32 / LPR;             // rows per warp
   static_assert(LD % VW == 0 && LPR >= 1 && LPR <= 32, "bad block width");
@@ -36,11 +38,11 @@ struct RowBlk {
 // acc = (A X)_row for the lane's NV vectors; the nonzeros are taken four at
 // a time (indices and values first, then the row gathers) so that more loads
 // are in flight per row group.
-template <typename T, int LD>
+template <typename T, int LD, int W>
 __device__ inline void row_times_block(int i, int q, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                        const T* __restrict__ va, const T* __restrict__ X,
-                                       T (&acc)[RowBlk<T, LD>::NV][RowBlk<T, LD>::VW]) {
-  using C = RowBlk<T, LD>;
+                                       T (&acc)[RowBlk<T, LD, W>::NV][RowBlk<T, LD, W>::VW]) {
+  using C = RowBlk<T, LD, W>;
 #pragma unroll
   for (int v = 0; v < C::NV; ++v)
 #pragma unroll
@@ -84,9 +86,9 @@ __device__ inline void row_times_block(int i, int q, const int32_t* __restrict__
 // weighted Jacobi, Section 3).  keep0: column 0 copied unchanged.  Two
 // independent jobs (the V and U relaxations) share one launch: blockIdx.y
 // selects the job.
-template <typename T, int LD>
+template <typename T, int LD, int W>
 __global__ void __launch_bounds__(256, 6) relax_block_kernel(RelaxJob<T> j0, RelaxJob<T> j1) {
-  using C = RowBlk<T, LD>;
+  using C = RowBlk<T, LD, W>;
   const RelaxJob<T>& a = blockIdx.y ? j1 : j0;
   int lane = threadIdx.x & 31;
   int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -94,7 +96,7 @@ __global__ void __launch_bounds__(256, 6) relax_block_kernel(RelaxJob<T> j0, Rel
   int q = lane % C::LPR;
   if (i >= a.n) return;
   T acc[C::NV][C::VW];
-  row_times_block<T, LD>(i, q, a.rp, a.ci, a.va, a.X, acc);
+  row_times_block<T, LD, W>(i, q, a.rp, a.ci, a.va, a.X, acc);
   const T di = __ldg(a.dinv + i);
 #pragma unroll
   for (int v = 0; v < C::NV; ++v) {
@@ -120,9 +122,9 @@ __global__ void __launch_bounds__(256, 6) relax_block_kernel(RelaxJob<T> j0, Rel
 
 // Y = A X  (rows x LD) for a CSR A; up to three independent products per
 // launch (blockIdx.y selects one).
-template <typename T, int LD>
+template <typename T, int LD, int W>
 __global__ void __launch_bounds__(256, 6) spmm_block_kernel(SpmmJob<T> j0, SpmmJob<T> j1, SpmmJob<T> j2) {
-  using C = RowBlk<T, LD>;
+  using C = RowBlk<T, LD, W>;
   const SpmmJob<T>& a = blockIdx.y == 0 ? j0 : (blockIdx.y == 1 ? j1 : j2);
   int lane = threadIdx.x & 31;
   int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -130,7 +132,7 @@ __global__ void __launch_bounds__(256, 6) spmm_block_kernel(SpmmJob<T> j0, SpmmJ
   int q = lane % C::LPR;
   if (i >= a.rows) return;
   T acc[C::NV][C::VW];
-  row_times_block<T, LD>(i, q, a.rp, a.ci, a.va, a.X, acc);
+  row_times_block<T, LD, W>(i, q, a.rp, a.ci, a.va, a.X, acc);
 #pragma unroll
   for (int v = 0; v < C::NV; ++v) vstore(a.Y + (size_t)i * LD + C::col(q, v), acc[v]);
 }
@@ -361,21 +363,31 @@ __global__ void diag_inv_kernel(int n, const int32_t* __restrict__ rp, const int
 }
 
 // =================================================================== host
+template <typename T, int LD, int W>
+static bamg_status relax_lw(int n, const RelaxJob<T>& j0, const RelaxJob<T>* j1, cudaStream_t s) {
+  using C = RowBlk<T, LD, W>;
+  unsigned blocks = cdiv(n, 8 * C::RPW);
+  return launch(relax_block_kernel<T, LD, W>, dim3(blocks, j1 ? 2 : 1), dim3(256), 0, s, j0, j1 ? *j1 : j0);
+}
+
 template <typename T, int LD>
 static bamg_status relax_ld(const RelaxJob<T>& j0, const RelaxJob<T>* j1, cudaStream_t s) {
-  using C = RowBlk<T, LD>;
   const int n = j1 && j1->n > j0.n ? j1->n : j0.n;
-  unsigned blocks = cdiv(n, 8 * C::RPW);
-  return launch(relax_block_kernel<T, LD>, dim3(blocks, j1 ? 2 : 1), dim3(256), 0, s, j0, j1 ? *j1 : j0);
+  return n >= kRowPairMin ? relax_lw<T, LD, 2>(n, j0, j1, s) : relax_lw<T, LD, 1>(n, j0, j1, s);
+}
+
+template <typename T, int LD, int W>
+static bamg_status spmm_lw(int rows, const SpmmJob<T>* jobs, int k, cudaStream_t s) {
+  using C = RowBlk<T, LD, W>;
+  return launch(spmm_block_kernel<T, LD, W>, dim3(cdiv(rows, 8 * C::RPW), k), dim3(256), 0, s, jobs[0],
+                jobs[k > 1 ? 1 : 0], jobs[k > 2 ? 2 : 0]);
 }
 
 template <typename T, int LD>
 static bamg_status spmm_ld(const SpmmJob<T>* jobs, int k, cudaStream_t s) {
-  using C = RowBlk<T, LD>;
   int rows = 0;
   for (int q = 0; q < k; ++q) rows = jobs[q].rows > rows ? jobs[q].rows : rows;
-  return launch(spmm_block_kernel<T, LD>, dim3(cdiv(rows, 8 * C::RPW), k), dim3(256), 0, s, jobs[0],
-                jobs[k > 1 ? 1 : 0], jobs[k > 2 ? 2 : 0]);
+  return rows >= kRowPairMin ? spmm_lw<T, LD, 2>(rows, jobs, k, s) : spmm_lw<T, LD, 1>(rows, jobs, k, s);
 }
 
 #define BAMG_LD_DISPATCH(ld, CALL)                 \

@@ -41,6 +41,11 @@ struct Level {
   DevMem s, t;            // sqrt LS weights (double[ld])
   // V-cycle vectors in the V-cycle precision
   DevMem vb, vz, vt, vr;
+  // multicolour Gauss-Seidel smoother: colours, rows by colour, and the
+  // colour offsets (host copy, ncol + 1 entries)
+  DevMem colour, crows;
+  std::vector<int32_t> crp;
+  int ncol = 0;
 };
 
 }  // namespace bamg

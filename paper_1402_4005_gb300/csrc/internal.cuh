@@ -90,6 +90,16 @@ bamg_status csr_vec(int mode, int n, int G, const int32_t* rp, const int32_t* ci
                     T omega, const T* x, const T* b, T* y, cudaStream_t s);
 template <typename T>
 bamg_status dense_gemv(int n, const T* A, const T* x, T* y, cudaStream_t s);
+
+// smooth.cu: multicolour Gauss-Seidel (greedy colouring of the symmetrised
+// graph of B in SplitMix64 priority order, rows by colour, sweeps)
+bamg_status colour_graph(int n, const int32_t* brp, const int32_t* bci, const int32_t* trp, const int32_t* tci,
+                         uint64_t seed, int level, int32_t* colour, int* ncolours, cudaStream_t s);
+bamg_status colour_rows(int n, const int32_t* colour, int ncolours, int32_t* colour_rp_host, int32_t* rows,
+                        cudaStream_t s);
+template <typename T>
+bamg_status mcgs_sweep(int G, int ncolours, const int32_t* crp, const int32_t* rows, const int32_t* rp,
+                       const int32_t* ci, const T* va, const T* dinv, const T* b, T* x, cudaStream_t s);
 template <typename S, typename D>
 bamg_status convert(size_t n, const S* a, D* b, cudaStream_t s);
 template <typename T>

@@ -178,23 +178,38 @@ struct BackTile {
   __nv_bfloat16 d3[16 * kO], d2[16 * kH], d1[16 * kH];
 };
 
-// Forward + backward on rows [0, M): accumulates d(loss)/d(params) into G
-// (FP32, global) and the loss sum into loss[0].  loss = sum mask (y - t)^2 / count.
+// Sum over the lanes of one bias column: the two row halves in the lane,
+// then the eight row groups g (lanes differing in bits 2-4), fixed order.
+__device__ inline float bias_col_sum(float lo, float hi) {
+  float v = lo + hi;
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 8);
+  v += __shfl_xor_sync(0xffffffffu, v, 16);
+  return v;
+}
+
+// Forward + backward on rows [0, M): writes this block's d(loss)/d(params)
+// to part[blockIdx.x] (FP32, parameter layout) and adds the loss sum to
+// loss[0].  loss = sum mask (y - t)^2 / count.  Each warp accumulates its
+// tiles into its own shared copy without atomics and the block sums the
+// copies in warp order, so the gradient does not depend on scheduling.
 __global__ void __launch_bounds__(kMlpThreads) mlp_grad_kernel(int M, float inv_count, const float* __restrict__ P,
                                                                const __nv_bfloat16* __restrict__ X,
                                                                const float* __restrict__ Tg,
                                                                const float* __restrict__ mask,
-                                                               float* __restrict__ G, float* __restrict__ loss) {
+                                                               float* __restrict__ part, float* __restrict__ loss) {
   extern __shared__ unsigned char dyn[];
   MlpSmem& S = *reinterpret_cast<MlpSmem*>(dyn);
-  GradSmem& D = *reinterpret_cast<GradSmem*>(dyn + sizeof(MlpSmem));
-  WarpTile* tiles = reinterpret_cast<WarpTile*>(dyn + sizeof(MlpSmem) + sizeof(GradSmem));
-  BackTile* btiles = reinterpret_cast<BackTile*>(dyn + sizeof(MlpSmem) + sizeof(GradSmem) + kMlpWarps * sizeof(WarpTile));
+  GradSmem* Dall = reinterpret_cast<GradSmem*>(dyn + sizeof(MlpSmem));
+  WarpTile* tiles = reinterpret_cast<WarpTile*>(dyn + sizeof(MlpSmem) + kMlpWarps * sizeof(GradSmem));
+  BackTile* btiles =
+      reinterpret_cast<BackTile*>(dyn + sizeof(MlpSmem) + kMlpWarps * sizeof(GradSmem) + kMlpWarps * sizeof(WarpTile));
   load_weights(S, P);
-  for (int i = threadIdx.x; i < (int)(sizeof(GradSmem) / sizeof(float)); i += blockDim.x)
-    reinterpret_cast<float*>(&D)[i] = 0.f;
+  for (int i = threadIdx.x; i < (int)(kMlpWarps * sizeof(GradSmem) / sizeof(float)); i += blockDim.x)
+    reinterpret_cast<float*>(Dall)[i] = 0.f;
   __syncthreads();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  GradSmem& D = Dall[w];
   WarpTile& T = tiles[w];
   BackTile& Bk = btiles[w];
   float lsum = 0.f;
@@ -205,22 +220,32 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_grad_kernel(int M, float inv_
     float y[2][4];
     forward_tile(S, T, y);
     // dL/dy = 2 mask (y - t) / count
+    {
+      float dv[2][4];
 #pragma unroll
-    for (int nt = 0; nt < 2; ++nt)
+      for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        int r = g + (q >> 1) * 8, col = nt * 8 + 2 * t + (q & 1);
-        int row = row0 + r;
-        float d = 0.f;
-        if (row < M) {
-          float m = mask[(size_t)row * kO + col];
-          float e = y[nt][q] - Tg[(size_t)row * kO + col];
-          lsum += m * e * e;
-          d = 2.f * m * e * inv_count;
+        for (int q = 0; q < 4; ++q) {
+          int r = g + (q >> 1) * 8, col = nt * 8 + 2 * t + (q & 1);
+          int row = row0 + r;
+          float d = 0.f;
+          if (row < M) {
+            float m = mask[(size_t)row * kO + col];
+            float e = y[nt][q] - Tg[(size_t)row * kO + col];
+            lsum += m * e * e;
+            d = 2.f * m * e * inv_count;
+          }
+          Bk.d3[r * kO + col] = __float2bfloat16(d);
+          dv[nt][q] = d;
         }
-        Bk.d3[r * kO + col] = __float2bfloat16(d);
-        atomicAdd(&D.b3[col], d);
-      }
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float v = bias_col_sum(dv[nt][h], dv[nt][2 + h]);
+          if (g == 0) D.b3[nt * 8 + 2 * t + h] += v;
+        }
+    }
     __syncwarp();
     // dW3 (16 x 64) += d3^T h2
     {
@@ -233,7 +258,7 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_grad_kernel(int M, float inv_
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           int i = g + (q >> 1) * 8, n = nt * 8 + 2 * t + (q & 1);
-          atomicAdd(&D.w3[i * kH + n], c[nt][q]);
+          D.w3[i * kH + n] += c[nt][q];
         }
     }
     // d2 = (d3 W3) * relu'(h2)
@@ -243,14 +268,21 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_grad_kernel(int M, float inv_
       warp_gemm<16, 8>(c, [&](int i, int k) { return Bk.d3[i * kO + k]; },
                        [&](int k, int n) { return S.w3[k * kH + n]; });
 #pragma unroll
-      for (int nt = 0; nt < 8; ++nt)
+      for (int nt = 0; nt < 8; ++nt) {
+        float vv[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           int r = g + (q >> 1) * 8, col = nt * 8 + 2 * t + (q & 1);
           float v = __bfloat162float(T.h2[r * kH + col]) > 0.f ? c[nt][q] : 0.f;
           Bk.d2[r * kH + col] = __float2bfloat16(v);
-          atomicAdd(&D.b2[col], v);
+          vv[q] = v;
         }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float v = bias_col_sum(vv[h], vv[2 + h]);
+          if (g == 0) D.b2[nt * 8 + 2 * t + h] += v;
+        }
+      }
     }
     __syncwarp();
     // dW2 (64 x 64) += d2^T h1, four row tiles
@@ -265,7 +297,7 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_grad_kernel(int M, float inv_
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           int i = mt * 16 + g + (q >> 1) * 8, n = nt * 8 + 2 * t + (q & 1);
-          atomicAdd(&D.w2[i * kH + n], c[nt][q]);
+          D.w2[i * kH + n] += c[nt][q];
         }
     }
     // d1 = (d2 W2) * relu'(h1)
@@ -275,14 +307,21 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_grad_kernel(int M, float inv_
       warp_gemm<kH, 8>(c, [&](int i, int k) { return Bk.d2[i * kH + k]; },
                        [&](int k, int n) { return S.w2[k * kH + n]; });
 #pragma unroll
-      for (int nt = 0; nt < 8; ++nt)
+      for (int nt = 0; nt < 8; ++nt) {
+        float vv[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           int r = g + (q >> 1) * 8, col = nt * 8 + 2 * t + (q & 1);
           float v = __bfloat162float(T.h1[r * kH + col]) > 0.f ? c[nt][q] : 0.f;
           Bk.d1[r * kH + col] = __float2bfloat16(v);
-          atomicAdd(&D.b1[col], v);
+          vv[q] = v;
         }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float v = bias_col_sum(vv[h], vv[2 + h]);
+          if (g == 0) D.b1[nt * 8 + 2 * t + h] += v;
+        }
+      }
     }
     __syncwarp();
     // dW1 (64 x 64) += d1^T x
@@ -297,19 +336,46 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_grad_kernel(int M, float inv_
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           int i = mt * 16 + g + (q >> 1) * 8, n = nt * 8 + 2 * t + (q & 1);
-          atomicAdd(&D.w1[i * kF + n], c[nt][q]);
+          D.w1[i * kF + n] += c[nt][q];
         }
     }
     __syncwarp();
   }
   lsum = warp_sum(lsum);
-  if (lane == 0) atomicAdd(loss, lsum * inv_count);
+  if (lane == 0) atomicAdd(loss, lsum * inv_count);   // reported only
   __syncthreads();
-  for (int i = threadIdx.x; i < kH * kF; i += blockDim.x) atomicAdd(&G[kW1 + i], D.w1[i]);
-  for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) atomicAdd(&G[kW2 + i], D.w2[i]);
-  for (int i = threadIdx.x; i < kO * kH; i += blockDim.x) atomicAdd(&G[kW3 + i], D.w3[i]);
-  for (int i = threadIdx.x; i < kH; i += blockDim.x) { atomicAdd(&G[kB1 + i], D.b1[i]); atomicAdd(&G[kB2 + i], D.b2[i]); }
-  for (int i = threadIdx.x; i < kO; i += blockDim.x) atomicAdd(&G[kB3 + i], D.b3[i]);
+  float* out = part + (size_t)blockIdx.x * kNParam;
+  auto wsum = [&](const float* (&src)[kMlpWarps], int i) {
+    float v = 0.f;
+#pragma unroll
+    for (int k = 0; k < kMlpWarps; ++k) v += src[k][i];
+    return v;
+  };
+  const float* s1[kMlpWarps];
+  const float* s2[kMlpWarps];
+  const float* s3[kMlpWarps];
+  const float* c1[kMlpWarps];
+  const float* c2[kMlpWarps];
+  const float* c3[kMlpWarps];
+#pragma unroll
+  for (int k = 0; k < kMlpWarps; ++k) {
+    s1[k] = Dall[k].w1; s2[k] = Dall[k].w2; s3[k] = Dall[k].w3;
+    c1[k] = Dall[k].b1; c2[k] = Dall[k].b2; c3[k] = Dall[k].b3;
+  }
+  for (int i = threadIdx.x; i < kH * kF; i += blockDim.x) out[kW1 + i] = wsum(s1, i);
+  for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) out[kW2 + i] = wsum(s2, i);
+  for (int i = threadIdx.x; i < kO * kH; i += blockDim.x) out[kW3 + i] = wsum(s3, i);
+  for (int i = threadIdx.x; i < kH; i += blockDim.x) { out[kB1 + i] = wsum(c1, i); out[kB2 + i] = wsum(c2, i); }
+  for (int i = threadIdx.x; i < kO; i += blockDim.x) out[kB3 + i] = wsum(c3, i);
+}
+
+// G[i] += sum over the blocks of part[b][i], blocks in order.
+__global__ void grad_reduce_kernel(int nb, const float* __restrict__ part, float* __restrict__ G) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kNParam) return;
+  float v = 0.f;
+  for (int b = 0; b < nb; ++b) v += part[(size_t)b * kNParam + i];
+  G[i] += v;
 }
 
 __global__ void adam_kernel(int np, float* __restrict__ P, float* __restrict__ m, float* __restrict__ v,
@@ -450,7 +516,7 @@ static size_t fwd_smem() { return sizeof(MlpSmem) + kMlpWarps * sizeof(WarpTile)
 
 static std::atomic<uint64_t> g_fwd_attr{0}, g_grad_attr{0};
 static size_t grad_smem() {
-  return sizeof(MlpSmem) + sizeof(GradSmem) + kMlpWarps * (sizeof(WarpTile) + sizeof(BackTile));
+  return sizeof(MlpSmem) + kMlpWarps * (sizeof(GradSmem) + sizeof(WarpTile) + sizeof(BackTile));
 }
 
 bamg_status mlp_forward(int M, const float* P, const void* X, float* Y, cudaStream_t s) {
@@ -472,10 +538,14 @@ bamg_status mlp_grad(int M, float inv_count, const float* P, const void* X, cons
   int max_dyn = 0;
   BAMG_TRY(allow_max_smem((const void*)mlp_grad_kernel, g_grad_attr, &max_dyn));
   int tiles = (M + 15) / 16;
-  int grid = (int)cdiv(tiles, kMlpWarps * 4);   // each warp takes a few tiles: fewer global gradient adds
-  if (grid > 2 * num_sms()) grid = 2 * num_sms();
-  return launch(mlp_grad_kernel, dim3(grid), dim3(kMlpThreads), sm, s, M, inv_count, P,
-                (const __nv_bfloat16*)X, T, mask, G, loss);
+  int grid = (int)cdiv(tiles, kMlpWarps * 4);   // each warp takes a few tiles: fewer partial gradients
+  if (grid > num_sms()) grid = num_sms();
+  DevMem part;
+  BAMG_TRY(part.alloc(sizeof(float) * (size_t)grid * kNParam, s));
+  BAMG_TRY(launch(mlp_grad_kernel, dim3(grid), dim3(kMlpThreads), sm, s, M, inv_count, P,
+                  (const __nv_bfloat16*)X, T, mask, part.as<float>(), loss));
+  return launch(grad_reduce_kernel, dim3(cdiv(kNParam, 256)), dim3(256), 0, s, grid, (const float*)part.as<float>(),
+                G);
 }
 
 // Features of the fine points of a geometric level, in ascending fine index.

@@ -47,6 +47,23 @@ static bamg_status vcycle_level(bamg_hierarchy* h, int l, cudaStream_t s) {
   const T* bv = L.B.vals<T>();
   T* cur = z;
   T* alt = L.vt.as<T>();
+  if (p.smoother == BAMG_SMOOTH_MCGS) {
+    // multicolour Gauss-Seidel, in place (Section 3 splitting)
+    auto sweep = [&](T* x) {
+      return mcgs_sweep<T>(L.vec_g, L.ncol, L.crp.data(), L.crows.as<int32_t>(), L.B.r(), L.B.c(), bv, dv, b, x, s);
+    };
+    BAMG_CUDA(cudaMemsetAsync(z, 0, sizeof(T) * L.n, s));
+    for (int it = 0; it < p.nu_pre; ++it) BAMG_TRY(sweep(z));
+    BAMG_TRY(csr_vec<T>(VEC_RESID, L.n, L.vec_g, L.B.r(), L.B.c(), bv, dv, om, z, b, L.vr.as<T>(), s));
+    Level& C = h->lv[l + 1];
+    BAMG_TRY(csr_vec<T>(VEC_SPMV, L.nc, lanes_for(L.Q), L.Q.r(), L.Q.c(), L.Q.vals<T>(), dv, om, L.vr.as<T>(),
+                        nullptr, C.vb.as<T>(), s));
+    BAMG_TRY(vcycle_level<T>(h, l + 1, s));
+    BAMG_TRY(csr_vec<T>(VEC_SPMV_ADD, L.n, lanes_for(L.P), L.P.r(), L.P.c(), L.P.vals<T>(), dv, om,
+                        C.vz.as<T>(), nullptr, z, s));
+    for (int it = 0; it < p.nu_post; ++it) BAMG_TRY(sweep(z));
+    return BAMG_OK;
+  }
   if (p.nu_pre == 0) {
     BAMG_CUDA(cudaMemsetAsync(cur, 0, sizeof(T) * L.n, s));
   } else {
@@ -108,6 +125,16 @@ bamg_status vcycle_prepare(bamg_hierarchy* h, cudaStream_t s) {
   }
   BAMG_TRY(h->io_in.alloc(sizeof(double) * h->lv[0].n, s));
   BAMG_TRY(h->io_out.alloc(sizeof(double) * h->lv[0].n, s));
+  if (h->p.smoother == BAMG_SMOOTH_MCGS)
+    for (size_t l = 0; l + 1 < h->lv.size(); ++l) {     // colourings of the smoothed levels
+      Level& L = h->lv[l];
+      BAMG_TRY(L.colour.alloc(sizeof(int32_t) * L.n, s));
+      BAMG_TRY(L.crows.alloc(sizeof(int32_t) * L.n, s));
+      BAMG_TRY(colour_graph(L.n, L.B.r(), L.B.c(), L.Bt.r(), L.Bt.c(), h->p.seed, (int)l, L.colour.as<int32_t>(),
+                            &L.ncol, s));
+      L.crp.assign(L.ncol + 1, 0);
+      BAMG_TRY(colour_rows(L.n, L.colour.as<int32_t>(), L.ncol, L.crp.data(), L.crows.as<int32_t>(), s));
+    }
   BAMG_CUDA(cudaStreamSynchronize(s));
   if (!h->cap_stream) BAMG_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   uint64_t before = t_launches;

@@ -131,6 +131,24 @@ def test_adam_step_and_training(api):
     assert losses[-1] < 0.5 * losses[0]
 
 
+def test_gradient_and_training_are_deterministic(api):
+    """No atomics decide the order of any gradient sum: repeated gradients
+    and repeated training runs agree bit for bit (many blocks, ragged tail)."""
+    m = 16 * 700 + 5
+    X, T, mask = rand_rows(m, 4)
+    Xt, Tt, Mt = torch.from_numpy(X), torch.from_numpy(T), torch.from_numpy(mask)
+    params = api.bamg_mlp_init(seed=21)
+    g1 = api.bamg_mlp_grad(params, Xt, Tt, Mt)[1]
+    g2 = api.bamg_mlp_grad(params, Xt, Tt, Mt)[1]
+    assert torch.equal(g1, g2)
+    runs = []
+    for _ in range(2):
+        p = api.bamg_mlp_init(seed=22)
+        api.bamg_mlp_train(p, Xt, Tt, Mt, epochs=3, batch=4096, lr=2e-3)
+        runs.append(p)
+    assert torch.equal(runs[0], runs[1])
+
+
 def _dataset(api, chains):
     Xs, Ts, Ms = [], [], []
     for ch in chains:
