@@ -126,6 +126,10 @@ typedef struct {
   double setup_ms, solve_ms;
   double op_cplx, grid_cplx; /* eq. operator_complexity_def; sum n_l / n      */
   double min_x;      /* smallest entry of the normalised x                     */
+  int fallback_iterations; /* mixed precision only: iterations with FP32
+                        V-cycles before the solve stalled and continued with
+                        FP64 V-cycles from the current x (0 = no fallback;
+                        the hierarchy then stays FP64)                        */
 } bamg_solve_info;
 
 typedef struct bamg_hierarchy bamg_hierarchy;
@@ -149,7 +153,11 @@ bamg_status bamg_vcycle(bamg_hierarchy* h, const double* r_dev, double* z_dev,
 /* Solves B x = 0 by V-cycle-preconditioned flexible GMRES on the residual
  * equation started from the setup's x^(0) (Section 6).  x_dev: device array
  * of n doubles receiving x > 0 with ||x||_1 = 1.  info may be NULL.
- * Returns BAMG_ERR_NOT_CONVERGED (x still written) when max_iter is hit. */
+ * In mixed precision, a solve that hits max_iter (or breaks down) with FP32
+ * V-cycles switches the hierarchy to FP64 V-cycles (coarsest pseudo-inverse
+ * recomputed in FP64) and continues from its current x with a fresh max_iter
+ * (info->fallback_iterations > 0).  Returns BAMG_ERR_NOT_CONVERGED (x still
+ * written) when max_iter is hit in FP64. */
 bamg_status bamg_solve(bamg_hierarchy* h, double* x_dev, const bamg_solve_params* sp,
                        bamg_solve_info* info, void* stream);
 

@@ -45,7 +45,7 @@ class SolveParams(C.Structure):
 class SolveInfo(C.Structure):
     _fields_ = [("iterations", i32), ("iters_to_1e7", i32), ("levels", i32),
                 ("rel_res_1", f64), ("setup_ms", f64), ("solve_ms", f64),
-                ("op_cplx", f64), ("grid_cplx", f64), ("min_x", f64)]
+                ("op_cplx", f64), ("grid_cplx", f64), ("min_x", f64), ("fallback_iterations", i32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -210,6 +210,24 @@ bamg_status bamg_solve(bamg_hierarchy* h, double* x_dev, const bamg_solve_params
   bamg_solve_info tmp;
   std::memset(&tmp, 0, sizeof(tmp));
   bamg_status st = fgmres(h, x_dev, sp, &tmp, S(stream));
+  if ((st == BAMG_ERR_NOT_CONVERGED || st == BAMG_ERR_BREAKDOWN) && h->mixed) {
+    // the FP32 V-cycle stalled: continue from the current x with FP64 V-cycles
+    const int mixed_its = tmp.iterations;
+    bamg_status pr = promote_fp64(h, S(stream));
+    if (pr == BAMG_OK)
+      pr = cudaMemcpyAsync(h->x0.p, x_dev, sizeof(double) * h->lv[0].n, cudaMemcpyDeviceToDevice, S(stream)) ==
+                   cudaSuccess
+               ? BAMG_OK
+               : BAMG_ERR_CUDA;
+    if (pr != BAMG_OK) {
+      st = pr;
+    } else {
+      st = fgmres(h, x_dev, sp, &tmp, S(stream));
+      tmp.iterations += mixed_its;
+      tmp.fallback_iterations = mixed_its;
+      if (tmp.iters_to_1e7 >= 0) tmp.iters_to_1e7 += mixed_its;
+    }
+  }
   cudaStreamSynchronize(S(stream));
   tmp.solve_ms = now_ms() - t0;
   tmp.setup_ms = h->setup_ms;

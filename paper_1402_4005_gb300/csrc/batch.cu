@@ -653,6 +653,7 @@ static bamg_status batched_fgmres(bamg_batch* bt, double* x, const bamg_solve_pa
       inf.grid_cplx = hc->grid_cplx;
       inf.setup_ms = bt->setup_ms;
       inf.min_x = 0.0;
+      inf.fallback_iterations = 0;
     }
   }
   if (!ok) {
@@ -748,6 +749,11 @@ extern "C" bamg_status bamg_solve_batched(bamg_batch* bt, double* x_dev, const b
   const int n0 = bt->lv[0].n;
   DevMem xb;
   BAMG_TRY(xb.alloc(sizeof(double) * n0, s));
+  std::vector<bamg_solve_info> local;
+  if (!infos) {
+    local.assign(bt->nch, bamg_solve_info{});
+    infos = local.data();
+  }
   bamg_status r = batched_fgmres(bt, xb.as<double>(), sp, infos, s);
   for (int pos = 0; pos < bt->nch; ++pos) {
     int c = bt->order[pos];
@@ -755,6 +761,27 @@ extern "C" bamg_status bamg_solve_batched(bamg_batch* bt, double* x_dev, const b
                               sizeof(double) * (bt->in_off[c + 1] - bt->in_off[c]), cudaMemcpyDeviceToDevice, s));
   }
   BAMG_CUDA(cudaStreamSynchronize(s));
+  if ((r == BAMG_ERR_NOT_CONVERGED || r == BAMG_ERR_BREAKDOWN) && bt->mixed) {
+    // chains whose FP32 V-cycle stalled continue alone, from their current
+    // x, with FP64 V-cycles (the batch's own V-cycle stays FP32)
+    r = BAMG_OK;
+    for (int c = 0; c < bt->nch; ++c) {
+      if (infos[c].rel_res_1 <= sp->tol) continue;
+      bamg_hierarchy* hc = bt->h[c];
+      double* xc = x_dev + bt->in_off[c];
+      BAMG_TRY(promote_fp64(hc, s));
+      BAMG_CUDA(cudaMemcpyAsync(hc->x0.p, xc, sizeof(double) * hc->lv[0].n, cudaMemcpyDeviceToDevice, s));
+      bamg_solve_info ic{};
+      bamg_status rc = fgmres(hc, xc, sp, &ic, s);
+      const int mixed_its = infos[c].iterations;
+      infos[c].iterations = mixed_its + ic.iterations;
+      infos[c].fallback_iterations = mixed_its;
+      infos[c].rel_res_1 = ic.rel_res_1;
+      infos[c].min_x = ic.min_x;
+      if (rc != BAMG_OK) r = rc;
+    }
+    BAMG_CUDA(cudaStreamSynchronize(s));
+  }
   double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (infos)
     for (int c = 0; c < bt->nch; ++c) infos[c].solve_ms = ms;

@@ -81,6 +81,7 @@ namespace bamg {
 template <typename T> bamg_status vcycle_body(bamg_hierarchy* h, cudaStream_t s);
 bamg_status vcycle_prepare(bamg_hierarchy* h, cudaStream_t s);
 bamg_status vcycle_run(bamg_hierarchy* h, cudaStream_t s);
+bamg_status promote_fp64(bamg_hierarchy* h, cudaStream_t s);
 bamg_status fgmres(bamg_hierarchy* h, double* x, const bamg_solve_params* sp, bamg_solve_info* info,
                    cudaStream_t s);
 bamg_status setup_finest(bamg_hierarchy* h, const bamg_csr* A, cudaStream_t s);

@@ -154,6 +154,43 @@ bamg_status vcycle_prepare(bamg_hierarchy* h, cudaStream_t s) {
   return BAMG_OK;
 }
 
+// Switches a mixed-precision hierarchy to FP64 V-cycles: the coarsest
+// pseudo-inverse recomputed in FP64 (one triplet, discarded), the V-cycle
+// vectors reallocated in FP64, the V-cycle and Arnoldi graphs captured again.
+bamg_status promote_fp64(bamg_hierarchy* h, cudaStream_t s) {
+  if (!h->mixed) return BAMG_OK;
+  Level& LL = h->lv.back();
+  const int nL = LL.n;
+  const size_t nn = (size_t)nL * nL;
+  DevMem Bd, Md, Nd, sg, Ud, Vd;
+  BAMG_TRY(Bd.alloc(sizeof(double) * nn, s));
+  BAMG_TRY(Md.alloc(sizeof(double) * nn, s));
+  BAMG_TRY(Nd.alloc(sizeof(double) * nn, s));
+  BAMG_TRY(sg.alloc(sizeof(double), s));
+  BAMG_TRY(Ud.alloc(sizeof(double) * nL, s));
+  BAMG_TRY(Vd.alloc(sizeof(double) * nL, s));
+  BAMG_TRY(csr_to_dense(nL, LL.B.r(), LL.B.c(), LL.B.v(), Bd.as<double>(), s));
+  if (LL.M.empty()) {
+    std::vector<double> I(nn, 0.0);
+    for (int i = 0; i < nL; ++i) I[(size_t)i * nL + i] = 1.0;
+    BAMG_CUDA(cudaMemcpyAsync(Md.p, I.data(), sizeof(double) * nn, cudaMemcpyHostToDevice, s));
+    BAMG_CUDA(cudaMemcpyAsync(Nd.p, I.data(), sizeof(double) * nn, cudaMemcpyHostToDevice, s));
+    BAMG_CUDA(cudaStreamSynchronize(s));
+  } else {
+    BAMG_TRY(csr_to_dense(nL, LL.M.r(), LL.M.c(), LL.M.v(), Md.as<double>(), s));
+    BAMG_TRY(csr_to_dense(nL, LL.N.r(), LL.N.c(), LL.N.v(), Nd.as<double>(), s));
+  }
+  BAMG_TRY(coarsest_solve(0, nL, 1, Bd.as<double>(), Md.as<double>(), Nd.as<double>(), sg.as<double>(),
+                          Ud.as<double>(), Vd.as<double>(), h->Bpinv.as<double>(), s));
+  h->mixed = 0;
+  gmres_release(h);
+  if (h->vexec) cudaGraphExecDestroy(h->vexec);
+  if (h->vgraph) cudaGraphDestroy(h->vgraph);
+  h->vexec = nullptr;
+  h->vgraph = nullptr;
+  return vcycle_prepare(h, s);
+}
+
 bamg_status vcycle_run(bamg_hierarchy* h, cudaStream_t s) {
   BAMG_CUDA(cudaGraphLaunch(h->vexec, s));
   g_launches.fetch_add(h->vgraph_kernels);

@@ -82,3 +82,48 @@ def test_mis_batch_of_mixed_chains(api):
         cf = closed_form(ch)
         if cf is not None:
             assert np.abs(xk - cf).sum() <= 1e-8, k
+
+
+# A 242 x 242 weighted lattice whose MIS hierarchy (l1-divisor rows on three
+# coarse levels) stalls with FP32 V-cycles while FP64 V-cycles converge.
+STALL_KW = dict(r=16, coarse_min=150, coarsening="mis", c_min=1, c_max=3, nu_pre=5, nu_post=5, seed=3)
+
+
+def stall_chain():
+    return cg.lattice2d(242, seed=373709097)
+
+
+def test_mixed_solve_falls_back_to_fp64(api):
+    """Solved to 1e-12: this slowly mixing lattice needs a residual below
+    1e-10 for x within 1e-8 of its closed form."""
+    ch = stall_chain()
+    xs = closed_form(ch)
+    p = api.bamg_params_default(precision="mixed", **STALL_KW)
+    h = api.bamg_setup(torch.from_numpy(ch.row_ptr).cuda(), torch.from_numpy(ch.col).cuda(),
+                       torch.from_numpy(ch.val).cuda(), ch.n, p)
+    x, info = api.bamg_solve(h, restart=30, tol=1e-12, max_iter=150)
+    assert info["fallback_iterations"] == 150
+    assert info["iterations"] > 150 and info["rel_res_1"] <= 1e-12
+    assert np.abs(x.cpu().numpy() - xs).sum() <= 1e-8
+    # a hierarchy whose FP32 V-cycle converges takes no fallback
+    ch2 = cg.lattice2d(48, seed=9)
+    h2 = api.bamg_setup(torch.from_numpy(ch2.row_ptr).cuda(), torch.from_numpy(ch2.col).cuda(),
+                        torch.from_numpy(ch2.val).cuda(), ch2.n, p)
+    _, info2 = api.bamg_solve(h2, restart=30, tol=1e-10)
+    assert info2["fallback_iterations"] == 0
+
+
+def test_batch_falls_back_per_chain(api):
+    chains = [cg.delaunay_walk(3000, seed=8), stall_chain(), cg.tandem(40)]
+    p = api.bamg_params_default(precision="mixed", **STALL_KW)
+    b = api.bamg_setup_batched([spec(c) for c in chains], p, host_threads=3)
+    x, infos = api.bamg_solve_batched(b, restart=30, tol=1e-12, max_iter=150)
+    off = np.concatenate([[0], np.cumsum([c.n for c in chains])])
+    assert infos[1]["fallback_iterations"] == 150
+    assert infos[0]["fallback_iterations"] == 0 and infos[2]["fallback_iterations"] == 0
+    x = x.cpu().numpy()
+    for k, ch in enumerate(chains):
+        assert infos[k]["rel_res_1"] <= 1e-12
+        xs = closed_form(ch)
+        if xs is not None:
+            assert np.abs(x[off[k]:off[k + 1]] - xs).sum() <= 1e-8, k
