@@ -18,6 +18,8 @@ Beside the headline line the same JSON object reports, on the same GPU:
   learned           network fits vs LS fits on the 2048 x 2048 tandem queue
   batched           256 seeded chains of 1k-65k states, batched vs a loop
   delaunay          random walk on the Delaunay graph of 2^20 points (MIS)
+  birthdeath        the paper's birth-death table: BAMG, BAMG^2 and
+                    GMRES(50) without preconditioning, n = 2^k + 1
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                   [--sections all|none|learned,batched,...] [--no-cpu-baseline]
@@ -47,7 +49,7 @@ WORKLOAD = {"workload": "tandem queue 256x256 (65,536 states, nnz(B)=261,121), r
             "setup_relaxations": 5}
 SIDE = 256
 KW = dict(r=16, max_levels=5, coarse_min=1, seed=2)
-SECTIONS = ("learned", "batched", "delaunay", "sparse")
+SECTIONS = ("learned", "batched", "delaunay", "sparse", "birthdeath")
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (4 partitions x 32)
 # DRAM bytes (read + write) of one coarsest_kernel<float> launch of this
 # workload from an ncu capture, valid only while the kernel's source file is
@@ -243,7 +245,7 @@ def gpu_arm(args, rank: int, world: int):
 def run_sections(args, api, torch, stream, out):
     for name, fn in (("sparse", lambda *a: roofline_sparse(*a, side=args.sparse_side)),
                      ("learned", learned_section), ("batched", batched_section),
-                     ("delaunay", delaunay_section)):
+                     ("delaunay", delaunay_section), ("birthdeath", birthdeath_section)):
         if name in args.sections:
             try:
                 out[name] = fn(api, torch, stream)
@@ -437,6 +439,46 @@ def learned_section(api, torch, stream, eval_side=2048):
     for name in xs:
         res[name]["err_l1_vs_ls_tuned"] = float((xs[name] - ref).abs().sum().item())
     return res
+
+
+# ---------------------------------------------------------------- birth-death (Table birthdeath)
+def birthdeath_section(api, torch, stream, sizes=(1025, 2049, 4097, 8193, 16385)):
+    """The paper's birth-death table: n = 2^k + 1, mu = 0.96, geometric
+    coarsening while n > 29, c = 2, r = 8, 3+3 Jacobi; one and two bootstrap
+    cycles against GMRES(50) without preconditioning (at most 1000
+    iterations).  Iterations to the paper's ||Bx||_2/||x||_2 <= 1e-7 (2-norm
+    estimate) and to ||Bx||_1/||x||_1 <= 1e-10, FP64."""
+    import chaingen as cg
+    out = {"paper_context": {"gmres50": ">1000", "bamg": [3, 3, 3, 4, 4, 4, 5], "bamg2": [1, 1, 1, 1, 1, 2, 2],
+                             "sizes": [1025, 2049, 4097, 8193, 16385, 32769, 65537],
+                             "note": "the paper counts iterations to 1e-7 in its own norm"}}
+    for n in sizes:
+        ch = cg.birth_death(n)
+        rp, ci, va = chain_tensors(torch, ch)
+        row = {}
+        with torch.cuda.stream(stream):
+            for name, kw in (("bamg", {}), ("bamg2", {"setup_cycles": 2})):
+                p = api.bamg_params_default(r=8, coarse_min=29, seed=2, **kw)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                h = api.bamg_setup(rp, ci, va, ch.n, p, nx=n, ny=1, stream=stream)
+                x, info = api.bamg_solve(h, restart=20, tol=1e-10, stream=stream, allow_not_converged=True)
+                torch.cuda.synchronize()
+                row[name] = {"ms": round((time.perf_counter() - t0) * 1e3, 2), "iters_to_1e7": info["iters_to_1e7"],
+                             "iterations": info["iterations"], "levels": info["levels"],
+                             "rel_res_1": info["rel_res_1"], "converged": info["rel_res_1"] <= 1e-10}
+                if name == "bamg":
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    _, pinfo = api.bamg_solve(h, restart=50, tol=1e-7, max_iter=1000, plain=True, stream=stream,
+                                              allow_not_converged=True)
+                    torch.cuda.synchronize()
+                    row["gmres50"] = {"ms": round((time.perf_counter() - t0) * 1e3, 2),
+                                      "iterations": pinfo["iterations"], "rel_res_1": pinfo["rel_res_1"],
+                                      "converged_1e7": pinfo["rel_res_1"] <= 1e-7}
+                h.destroy()
+        out[str(n)] = row
+    return out
 
 
 # ---------------------------------------------------------------- batched (config 4)
@@ -633,7 +675,7 @@ def main():
         "cpu_baseline": cpu,
         "clocks": r["clocks"],
     }
-    for k in ("sparse", "learned", "batched", "delaunay"):
+    for k in ("sparse", "learned", "batched", "delaunay", "birthdeath"):
         if k in r:
             line["roofline_sparse" if k == "sparse" else k] = r[k]
     print(json.dumps(line))

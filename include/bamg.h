@@ -116,6 +116,9 @@ typedef struct {
   int restart;       /* GMRES restart length m (>= 1)                          */
   int max_iter;      /* total iteration limit                                  */
   double tol;        /* stop when ||B x||_1 / ||x||_1 <= tol                   */
+  int plain;         /* 1: GMRES(restart) without the V-cycle (the identity as
+                        preconditioner), started from the uniform vector: the
+                        unpreconditioned comparator of Section 7; 0: BAMG      */
 } bamg_solve_params;
 
 typedef struct {

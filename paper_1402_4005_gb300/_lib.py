@@ -39,7 +39,7 @@ class Params(C.Structure):
 
 
 class SolveParams(C.Structure):
-    _fields_ = [("restart", i32), ("max_iter", i32), ("tol", f64)]
+    _fields_ = [("restart", i32), ("max_iter", i32), ("tol", f64), ("plain", i32)]
 
 
 class SolveInfo(C.Structure):

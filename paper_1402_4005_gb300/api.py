@@ -203,10 +203,11 @@ def bamg_vcycle(h: Hierarchy, r: torch.Tensor, z: torch.Tensor | None = None, st
 
 
 def bamg_solve(h: Hierarchy, x: torch.Tensor | None = None, restart: int = 20, max_iter: int = 500,
-               tol: float = 1e-10, stream=None, allow_not_converged: bool = False):
-    """Returns (x, info dict); x > 0 with unit 1-norm."""
+               tol: float = 1e-10, stream=None, allow_not_converged: bool = False, plain: bool = False):
+    """Returns (x, info dict); x > 0 with unit 1-norm.  plain: GMRES(restart)
+    without the V-cycle from the uniform vector (the paper's comparator)."""
     x = torch.empty(h.n, dtype=torch.float64, device="cuda") if x is None else x
-    sp = bamg_solve_params_default(restart=restart, max_iter=max_iter, tol=tol)
+    sp = bamg_solve_params_default(restart=restart, max_iter=max_iter, tol=tol, plain=int(plain))
     info = _lib.SolveInfo()
     allow = (0, 5) if allow_not_converged else (0,)
     check(lib().bamg_solve(C.c_void_p(h.handle), _p(x), C.byref(sp), C.byref(info), _stream(stream)),

@@ -54,6 +54,7 @@ bamg_status bamg_solve_params_default(bamg_solve_params* p) {
   p->restart = 20;
   p->max_iter = 500;
   p->tol = 1e-10;
+  p->plain = 0;
   return BAMG_OK;
 }
 
@@ -210,7 +211,7 @@ bamg_status bamg_solve(bamg_hierarchy* h, double* x_dev, const bamg_solve_params
   bamg_solve_info tmp;
   std::memset(&tmp, 0, sizeof(tmp));
   bamg_status st = fgmres(h, x_dev, sp, &tmp, S(stream));
-  if ((st == BAMG_ERR_NOT_CONVERGED || st == BAMG_ERR_BREAKDOWN) && h->mixed) {
+  if ((st == BAMG_ERR_NOT_CONVERGED || st == BAMG_ERR_BREAKDOWN) && h->mixed && !sp->plain) {
     // the FP32 V-cycle stalled: continue from the current x with FP64 V-cycles
     const int mixed_its = tmp.iterations;
     bamg_status pr = promote_fp64(h, S(stream));

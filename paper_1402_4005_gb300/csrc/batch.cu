@@ -744,6 +744,10 @@ extern "C" bamg_status bamg_solve_batched(bamg_batch* bt, double* x_dev, const b
                                           bamg_solve_info* infos, void* stream) {
   BAMG_CHECK_ARG(bt && x_dev && sp);
   BAMG_CHECK_ARG(sp->restart >= 1 && sp->restart <= 64 && sp->max_iter >= 1 && sp->tol > 0.0);
+  if (sp->plain) {
+    set_error("batches are solved with the V-cycle only (plain = 0)");
+    return BAMG_ERR_UNSUPPORTED;
+  }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   auto t0 = std::chrono::steady_clock::now();
   const int n0 = bt->lv[0].n;

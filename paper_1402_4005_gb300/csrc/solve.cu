@@ -93,6 +93,11 @@ __global__ void copy_d_kernel(size_t n, const double* __restrict__ a, double* __
   if (t < n) b[t] = a[t];
 }
 
+__global__ void fill_kernel(size_t n, double v, double* __restrict__ b) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) b[t] = v;
+}
+
 template <typename T>
 bamg_status vcycle_body(bamg_hierarchy* h, cudaStream_t s) {
   Level& L0 = h->lv[0];
@@ -413,6 +418,7 @@ static bamg_status true_residual(bamg_hierarchy* h, Gm& G, const double* x, doub
 // hierarchy's private stream, which outlives them.
 struct GmresState {
   int m = 0;
+  int plain = 0;             // 1: the identity instead of the V-cycle
   Gm G;
   DevMem dj;                 // step index j of the current restart cycle
   double* st_host = nullptr; // pinned: {|g_{j+1}|, ||w||} of the last step
@@ -443,7 +449,11 @@ static bamg_status arnoldi_body(bamg_hierarchy* h, GmresState& S, cudaStream_t s
   const int* dj = S.dj.as<int>();
   double* V = G.V.as<double>();
   BAMG_TRY(launch(column_io_kernel, dim3(gv), dim3(256), 0, s, n, dj, 1, V, h->io_in.as<double>()));
-  BAMG_TRY(h->mixed ? vcycle_body<float>(h, s) : vcycle_body<double>(h, s));
+  if (S.plain)
+    BAMG_TRY(launch(copy_d_kernel, dim3(gv), dim3(256), 0, s, (size_t)n, (const double*)h->io_in.as<double>(),
+                    h->io_out.as<double>()));
+  else
+    BAMG_TRY(h->mixed ? vcycle_body<float>(h, s) : vcycle_body<double>(h, s));
   BAMG_TRY(launch(column_io_kernel, dim3(gv), dim3(256), 0, s, n, dj, 0, G.Z.as<double>(), h->io_out.as<double>()));
   BAMG_TRY(csr_vec<double>(VEC_SPMV, n, L.vec_g, L.B.r(), L.B.c(), L.B.v(), L.dinv.as<double>(), 1.0,
                            (const double*)h->io_out.as<double>(), nullptr, G.w.as<double>(), s));
@@ -467,13 +477,14 @@ static bamg_status arnoldi_body(bamg_hierarchy* h, GmresState& S, cudaStream_t s
   return BAMG_OK;
 }
 
-static bamg_status gmres_prepare(bamg_hierarchy* h, int m) {
-  if (h->gm && h->gm->m == m) return BAMG_OK;
+static bamg_status gmres_prepare(bamg_hierarchy* h, int m, int plain) {
+  if (h->gm && h->gm->m == m && h->gm->plain == plain) return BAMG_OK;
   gmres_release(h);
   cudaStream_t cs = h->cap_stream;
   GmresState* S = new (std::nothrow) GmresState();
   if (!S) return BAMG_ERR_OOM;
   h->gm = S;
+  S->plain = plain;
   const int n = h->lv[0].n;
   Gm& G = S->G;
   S->m = m;
@@ -521,10 +532,13 @@ bamg_status fgmres(bamg_hierarchy* h, double* x, const bamg_solve_params* sp, ba
                    cudaStream_t s) {
   Level& L = h->lv[0];
   const int n = L.n, m = sp->restart;
-  BAMG_TRY(gmres_prepare(h, m));
+  BAMG_TRY(gmres_prepare(h, m, sp->plain ? 1 : 0));
   GmresState& S = *h->gm;
   Gm& G = S.G;
-  BAMG_CUDA(cudaMemcpyAsync(x, h->x0.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  if (sp->plain)        // unpreconditioned comparator: from the uniform vector
+    BAMG_TRY(launch(fill_kernel, dim3(cdiv(n, 256)), dim3(256), 0, s, (size_t)n, 1.0 / n, x));
+  else
+    BAMG_CUDA(cudaMemcpyAsync(x, h->x0.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
 
   double rel = 0.0, xn1 = 1.0;
   BAMG_TRY(true_residual(h, G, x, &rel, &xn1, s));

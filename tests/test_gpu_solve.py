@@ -235,3 +235,57 @@ def test_deep_tandem_hierarchy_uses_l1_divisor_rows(api):
         # accuracy of the whole vector (||x||_1 = 1)
         assert np.abs(np.minimum(xs[prec], 0.0)).sum() <= 1e-8
     assert np.abs(xs["mixed"] - xs["fp64"]).sum() <= 1e-8
+
+
+def birth_death_closed_form(ch):
+    up, dn = ch.meta["p_up"], ch.meta["p_dn"]
+    xs = np.ones(ch.n)
+    for k in range(ch.n - 1):
+        xs[k + 1] = xs[k] * up[k] / dn[k + 1]
+    return xs / xs.sum()
+
+
+@pytest.mark.parametrize("cycles", [1, 2])
+def test_birth_death_chain_and_unpreconditioned_comparator(api, cycles):
+    """Table birthdeath setting: n = 2^k + 1, mu = 0.96, geometric coarsening
+    (every other state) while n > 29, two interpolation points, r = 8, 3+3
+    Jacobi.  x against the detailed-balance closed form (entries from
+    O(mu^n) to O(1)), iteration counts against the oracle's (FP64: within
+    two for one cycle, at most twice for two); GMRES(50) without
+    preconditioning is still far from the tolerance after 300 iterations."""
+    for n in (1025, 4097):
+        ch = cg.birth_death(n)
+        kw = dict(r=8, coarse_min=29, seed=2)
+        h = gpu_setup(api, ch, setup_cycles=cycles, **kw)
+        x, info = api.bamg_solve(h, restart=20, tol=1e-12)
+        x = x.cpu().numpy()
+        xs = birth_death_closed_form(ch)
+        H = S.bamg_setup(ch.csr(), S.Params(cycles=cycles, **kw), grid=(n, 1))
+        _, its, _ = So.bamg_solve(H, tol=1e-12, restart=20)
+        assert info["rel_res_1"] <= 1e-12, info
+        if cycles == 1:
+            assert abs(info["iterations"] - its) <= 2, (info, its)
+        else:
+            # the second cycle starts from triplets whose entries span
+            # O(mu^n)..O(1): rounding differences move its count more
+            assert info["iterations"] <= 2 * its, (info, its)
+        assert np.abs(x - xs).sum() <= 1e-8
+        assert np.abs(np.minimum(x, 0.0)).sum() <= 1e-8     # entries down to O(mu^n): R-24
+        if cycles == 1:
+            _, pinfo = api.bamg_solve(h, restart=50, tol=1e-7, max_iter=300, plain=True,
+                                      allow_not_converged=True)
+            assert pinfo["iterations"] == 300 and pinfo["rel_res_1"] > 1e-7, pinfo
+
+
+def test_unpreconditioned_gmres_reaches_the_closed_form(api):
+    """The comparator itself is a correct GMRES: on a small weighted lattice
+    it converges to the closed form from the uniform vector."""
+    ch = cg.lattice2d(12, seed=5)
+    h = gpu_setup(api, ch, r=8, max_levels=2, coarse_min=1, seed=1)
+    x, info = api.bamg_solve(h, restart=50, tol=1e-10, max_iter=2000, plain=True)
+    xs = ch.meta["wdeg"] / ch.meta["wdeg"].sum()
+    assert info["rel_res_1"] <= 1e-10
+    assert np.abs(x.cpu().numpy() - xs).sum() <= 1e-8
+    # and the same hierarchy still solves with the V-cycle afterwards
+    x2, info2 = api.bamg_solve(h, restart=20, tol=1e-10)
+    assert info2["iterations"] < info["iterations"]
