@@ -210,20 +210,26 @@ constexpr int kRedBlocks = 256;
 // same graph serves every step.  Partial sums use the fixed row stride m+1.
 
 // part[b * (m+1) + k] = block b's share of V_k . w for k <= j
-__global__ void multidot_kernel(int n, int m, const int* __restrict__ dj, const double* __restrict__ V,
-                                size_t ldv, const double* __restrict__ w, double* __restrict__ part) {
-  const int k = blockIdx.y;
-  if (k > dj[0]) return;
-  const double* v = V + (size_t)k * ldv;
-  double s = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) s += v[i] * w[i];
-  s = warp_sum(s);
-  __shared__ double sh[8];
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+// part[b * (m+1) + k] = the block's share of V_k . w for k <= j: every block
+// takes all j + 1 columns over its rows (one wave of blocks, w read once
+// per column from L2), warp sums kept per warp and added in warp order.
+constexpr int kMultidotMax = 65;   // m + 1 <= 65 (restart <= 64)
+__global__ void __launch_bounds__(256) multidot_kernel(int n, int m, const int* __restrict__ dj,
+                                                       const double* __restrict__ V, size_t ldv,
+                                                       const double* __restrict__ w, double* __restrict__ part) {
+  __shared__ double sh[8][kMultidotMax];
+  const int K = dj[0] + 1, lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  for (int k = 0; k < K; ++k) {
+    const double* v = V + (size_t)k * ldv;
+    double s = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) s += v[i] * w[i];
+    s = warp_sum(s);
+    if (lane == 0) sh[wp][k] = s;
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
     double t = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q][k];
     part[(size_t)blockIdx.x * (m + 1) + k] = t;
   }
 }
@@ -459,7 +465,7 @@ static bamg_status arnoldi_body(bamg_hierarchy* h, GmresState& S, cudaStream_t s
                            (const double*)h->io_out.as<double>(), nullptr, G.w.as<double>(), s));
   for (int pass = 0; pass < 2; ++pass) {       // classical Gram-Schmidt, twice
     double* hc = pass ? G.h2.as<double>() : G.h1.as<double>();
-    BAMG_TRY(launch(multidot_kernel, dim3(nb, m + 1), dim3(256), 0, s, n, m, dj, (const double*)V, (size_t)n,
+    BAMG_TRY(launch(multidot_kernel, dim3(nb), dim3(256), 0, s, n, m, dj, (const double*)V, (size_t)n,
                     (const double*)G.w.as<double>(), G.part.as<double>()));
     BAMG_TRY(launch(multidot_reduce_kernel, dim3(m + 1), dim3(256), 0, s, nb, m, dj,
                     (const double*)G.part.as<double>(), hc));
