@@ -126,7 +126,9 @@ bamg_status bamg_step_coarsen_mis(int n, const int32_t* B_rp, const int32_t* B_c
  * neighbours taken before it; computed in parallel rounds with the same
  * result bit for bit.  B and B^T as CSR (device, int32); colour[n] (device,
  * caller-owned) receives colours 0 .. *ncolours_host - 1.  Synchronises the
- * stream. */
+ * stream.  BAMG_ERR_NUMERIC if the rounds do not finish within n + 1 (not
+ * reachable on valid input: each round colours at least the highest-priority
+ * uncoloured vertex). */
 bamg_status bamg_step_colour(int n, const int32_t* B_rp, const int32_t* B_ci, const int32_t* Bt_rp,
                              const int32_t* Bt_ci, uint64_t seed, int level, int32_t* colour, int* ncolours_host,
                              void* stream);
@@ -142,7 +144,9 @@ bamg_status bamg_step_colour_rows(int n, const int32_t* colour, int ncolours, in
  * colour by colour, x_i <- x_i + (b_i - (B x)_i) * dinv_i over the rows of
  * the colour (unweighted; dinv = 1 / Jacobi divisor).  val, dinv, b, x are
  * double (prec = 0) or float (prec = 1); colour_rp_host and rows as from
- * bamg_step_colour_rows.  Stream-ordered. */
+ * bamg_step_colour_rows (BAMG_ERR_ARG unless colour_rp_host runs from 0 to n
+ * without decreasing).  Stream-ordered; x is updated in place, so rows of one
+ * colour must not be coupled by B (true for the colouring above). */
 bamg_status bamg_step_mcgs_sweep(int prec, int n, const int32_t* rp, const int32_t* ci, const void* val,
                                  const void* dinv, int ncolours, const int32_t* colour_rp_host, const int32_t* rows,
                                  const void* b, void* x, void* stream);
