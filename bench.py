@@ -131,6 +131,18 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def max_over_ranks(torch, value: float, world: int) -> float:
+    """The slowest rank's value (every rank gets it); NCCL tensors live on
+    the GPU, gloo ones on the host."""
+    if world <= 1:
+        return value
+    dist = torch.distributed
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def event_ms(torch, stream, fn, reps=1):
     """Mean CUDA-event time of fn() on `stream` over reps calls (ms)."""
     e0 = torch.cuda.Event(enable_timing=True)
@@ -209,11 +221,7 @@ def gpu_arm(args, rank: int, world: int):
     except Exception as exc:          # a variant failure must not lose the headline
         gs, x_gs = {"error": f"{type(exc).__name__}: {exc}"[:300]}, None
 
-    ms = statistics.mean(t_mix)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(torch, statistics.mean(t_mix), world)
     err_vs_fp64 = float((x_mix - x_64).abs().sum().item())
     if x_gs is not None:
         gs["err_l1_vs_jacobi"] = float((x_gs - x_mix).abs().sum().item())
