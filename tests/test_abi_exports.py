@@ -39,3 +39,22 @@ def test_status_strings_without_gpu():
     assert L.bamg_params_default(ctypes.byref(p)) == 0
     assert (p.r, p.nu_pre, p.nu_post, round(p.omega, 12)) == (8, 3, 3, 0.7)
     assert L.bamg_setup(None, None, None, None) == 1      # BAMG_ERR_ARG, no device touched
+
+
+def test_parameter_structs_match_the_header():
+    """bamg_params_default zeroes the whole C struct before setting the
+    defaults: bytes past the binding's struct must stay untouched (the two
+    layouts agree), and the defaults of the later fields are as declared."""
+    from paper_1402_4005_gb300 import _lib
+    L = _lib.lib()
+    size = ctypes.sizeof(_lib.Params)
+    buf = (ctypes.c_ubyte * (size + 64))(*([0xAB] * (size + 64)))
+    assert L.bamg_params_default(ctypes.cast(buf, ctypes.POINTER(_lib.Params))) == 0
+    assert all(b == 0xAB for b in buf[size:]), "bamg_params is larger in the header than in the binding"
+    p = _lib.Params.from_buffer(buf)
+    assert (p.setup_cycles, p.interp, p.smoother, p.max_coarse_dense) == (1, 0, 0, 1024)
+    assert p.mlp_params is None
+    sp = _lib.SolveParams()
+    sp.plain = 7
+    assert L.bamg_solve_params_default(ctypes.byref(sp)) == 0
+    assert (sp.restart, sp.max_iter, sp.tol, sp.plain) == (20, 500, 1e-10, 0)
