@@ -1,11 +1,13 @@
 // Solve phase (Section 6): V-cycle preconditioner and flexible GMRES.
 //
 // V-cycle (Section 3, eq. error_propagator_twogrid): from z = 0, nu_pre
-// weighted-Jacobi sweeps, residual, r_c = Q r, recursion (B_L^+ r_L on the
-// coarsest level), z += P e_c, nu_post sweeps.  It runs in the hierarchy's
-// V-cycle precision (FP64, or FP32 in mixed mode) and is captured once into a
-// CUDA graph that reads a fixed FP64 input buffer and writes a fixed FP64
-// output buffer.
+// weighted-Jacobi sweeps (or multicolour Gauss-Seidel sweeps), residual,
+// r_c = Q r, recursion (B_L^+ r_L on the coarsest level), z += P e_c,
+// nu_post sweeps.  It runs in the hierarchy's V-cycle precision (FP64, or
+// FP32 in mixed mode) and is captured once into a CUDA graph that reads a
+// fixed FP64 input buffer and writes a fixed FP64 output buffer.  A mixed
+// hierarchy can be switched to FP64 V-cycles (promote_fp64) when its solve
+// stalls.
 //
 // GMRES on the residual equation B e = -B x^(0) (eq. residual), written as
 // B x = 0 from x^(0).  The V-cycle is applied on the right (flexible GMRES,
@@ -13,7 +15,9 @@
 // classical Gram-Schmidt with one re-orthogonalisation, Givens rotations and
 // the small triangular solve run on the device in FP64.  The stopping rule
 // is the true ||B x||_1 / ||x||_1, evaluated whenever the 2-norm estimate
-// allows it to hold.
+// allows it to hold.  With the identity in place of the V-cycle and the
+// uniform start vector the same code is the unpreconditioned GMRES(m) the
+// paper compares against (Section 7).
 #include <chrono>
 #include <cmath>
 #include <new>
