@@ -14,6 +14,16 @@ q0 = 1/c and Z an orthonormal basis of the complement of 1.
 
 Inputs are n x r blocks; ``s``/``t`` are the square roots of the weights for
 *normalised* vectors, i.e. s_k = 1/||B v^(k)|| with ||v^(k)||_2 = 1.
+
+Optional Tikhonov term (not in the paper, off by default): with ridge = delta
+> 0 each fit also penalises lambda_i ||p - 1/c||^2, lambda_i = delta *
+trace(G_i) / c, where G_i is the weighted Gram matrix of the c neighbour
+columns and 1/c the equal weights of the simple-averaging operator of
+Section 5.  delta = 0 is the paper's fit, delta -> infinity the averaging;
+in between, only the directions the test vectors leave ill-determined (e.g.
+the cross term of the four diagonal corners of a 2D centre point) are pulled
+towards equal weights.  Solved as the augmented least-squares problem
+[W^(1/2) X; sqrt(lambda) I] d = [W^(1/2)(y - X p0); 0], p = p0 + d.
 """
 import numpy as np
 import scipy.sparse as sp
@@ -56,24 +66,45 @@ def _assemble(n, nc, cf, cmap, J, rows_val) -> sp.csr_matrix:
     return M
 
 
-def fit_row(Vw: np.ndarray, yw: np.ndarray) -> np.ndarray:
-    """argmin_p ||yw - Vw p||_2 (minimum-norm if rank deficient)."""
-    return np.linalg.lstsq(Vw, yw, rcond=None)[0]
+def ridge_lambda(Vw: np.ndarray, ridge: float) -> float:
+    """lambda_i = delta * trace(Vw^T Vw) / c (zero when the fit is plain)."""
+    return ridge * float(np.sum(Vw * Vw)) / Vw.shape[1] if ridge > 0 else 0.0
 
 
-def fit_row_sum_one(Vw: np.ndarray, yw: np.ndarray) -> np.ndarray:
-    """argmin_q ||yw - Vw q||_2 subject to sum(q) = 1 (null-space method)."""
+def _ridge_lstsq(A: np.ndarray, b: np.ndarray, lam: float) -> np.ndarray:
+    """argmin_d ||b - A d||^2 + lam ||d||^2 via the augmented system."""
+    if lam <= 0:
+        return np.linalg.lstsq(A, b, rcond=None)[0]
+    m = A.shape[1]
+    Aa = np.vstack([A, np.sqrt(lam) * np.eye(m)])
+    ba = np.concatenate([b, np.zeros(m)])
+    return np.linalg.lstsq(Aa, ba, rcond=None)[0]
+
+
+def fit_row(Vw: np.ndarray, yw: np.ndarray, ridge: float = 0.0) -> np.ndarray:
+    """argmin_p ||yw - Vw p||_2 (minimum-norm if rank deficient); with
+    ridge > 0 plus lambda ||p - 1/c||^2."""
+    if ridge <= 0:
+        return np.linalg.lstsq(Vw, yw, rcond=None)[0]
+    c = Vw.shape[1]
+    p0 = np.full(c, 1.0 / c)
+    return p0 + _ridge_lstsq(Vw, yw - Vw @ p0, ridge_lambda(Vw, ridge))
+
+
+def fit_row_sum_one(Vw: np.ndarray, yw: np.ndarray, ridge: float = 0.0) -> np.ndarray:
+    """argmin_q ||yw - Vw q||_2 subject to sum(q) = 1 (null-space method);
+    with ridge > 0 plus lambda ||q - 1/c||^2 = lambda ||y||^2 (Z orthonormal)."""
     c = Vw.shape[1]
     if c == 1:
         return np.ones(1)
     q0 = np.full(c, 1.0 / c)
     Qf, _ = np.linalg.qr(np.ones((c, 1)), mode="complete")
     Z = Qf[:, 1:]
-    y = np.linalg.lstsq(Vw @ Z, yw - Vw @ q0, rcond=None)[0]
+    y = _ridge_lstsq(Vw @ Z, yw - Vw @ q0, ridge_lambda(Vw, ridge))
     return q0 + Z @ y
 
 
-def ls_interpolation(V: np.ndarray, s: np.ndarray, cf, cmap, J) -> sp.csr_matrix:
+def ls_interpolation(V: np.ndarray, s: np.ndarray, cf, cmap, J, ridge: float = 0.0) -> sp.csr_matrix:
     """P (n x n_c) from eq. ls_interpolation; V normalised, s = sqrt(omega)."""
     n = V.shape[0]
     nc = int(cf.sum())
@@ -81,11 +112,11 @@ def ls_interpolation(V: np.ndarray, s: np.ndarray, cf, cmap, J) -> sp.csr_matrix
     for i, Ji in J.items():
         Vw = V[Ji, :].T * s[:, None]
         yw = V[i, :] * s
-        rows[i] = fit_row(Vw, yw)
+        rows[i] = fit_row(Vw, yw, ridge)
     return _assemble(n, nc, cf, cmap, J, rows)
 
 
-def ls_restriction_T(U: np.ndarray, t: np.ndarray, cf, cmap, J) -> sp.csr_matrix:
+def ls_restriction_T(U: np.ndarray, t: np.ndarray, cf, cmap, J, ridge: float = 0.0) -> sp.csr_matrix:
     """Q^T (n x n_c): rows are the columns of Q, fitted to u^(2..r) with the
     constraint that each sums to one (Section 5, eq. weight_infinity)."""
     n = U.shape[0]
@@ -94,7 +125,7 @@ def ls_restriction_T(U: np.ndarray, t: np.ndarray, cf, cmap, J) -> sp.csr_matrix
     for i, Ji in J.items():
         Vw = U[Ji, 1:].T * t[1:, None]
         yw = U[i, 1:] * t[1:]
-        rows[i] = fit_row_sum_one(Vw, yw)
+        rows[i] = fit_row_sum_one(Vw, yw, ridge)
     return _assemble(n, nc, cf, cmap, J, rows)
 
 

@@ -27,6 +27,9 @@ Readings where the paper is silent: 5 setup relaxations per level and phase
 (with 3, the r = 8 fits over-fit rough vectors and the first hierarchy can
 diverge as a stationary method); the inner loop runs once (mu = 1);
 x^(0) is the finest v of smallest sigma, scaled to a positive unit 1-norm.
+Option ls_ridge (default 0, the paper's plain fit): a Tikhonov term that
+pulls ill-determined directions of each LS fit towards equal weights
+(see oracle.interp).
 """
 from __future__ import annotations
 
@@ -54,6 +57,7 @@ class Params:
     restriction: str = "ls"           # or "average" (Section 5 comparison)
     cycles: int = 1                   # bootstrap setup cycles (2 = BAMG^2)
     smoother: str = "jacobi"          # V-cycle smoother: "jacobi", "mcgs" or "gs" (natural order)
+    ls_ridge: float = 0.0             # Tikhonov weight delta of the LS fits (0 = the paper's plain fit)
 
 
 @dataclass
@@ -177,11 +181,11 @@ def bamg_mle(H: Hierarchy, l: int, U: np.ndarray, V: np.ndarray, sig=None):
     lev.t = interp.weights(lev.Bt, U, range(1, r))
     cf, cmap, J, cgrid = split(lev, l, p)
     lev.cf, lev.cmap, lev.J = cf, cmap, J
-    lev.P = interp.ls_interpolation(V, lev.s, cf, cmap, J)
+    lev.P = interp.ls_interpolation(V, lev.s, cf, cmap, J, p.ls_ridge)
     if p.restriction == "average":
         lev.Qt = interp.averaging_restriction_T(cf, cmap, J, lev.n)
     else:
-        lev.Qt = interp.ls_restriction_T(U, lev.t, cf, cmap, J)
+        lev.Qt = interp.ls_restriction_T(U, lev.t, cf, cmap, J, p.ls_ridge)
     lev.Q = operators.transpose(lev.Qt)
     Bc = operators.galerkin(lev.Q, lev.B, lev.P)
     Mc = operators.spmatmul(lev.Q, lev.Qt if lev.M is None
