@@ -110,6 +110,15 @@ typedef struct {
                         x_i += (b_i - (Bx)_i) / d_i, unweighted, d the Jacobi
                         divisor).  The setup relaxations stay weighted Jacobi.
                         Not available for batches.                            */
+  double ls_ridge;   /* delta >= 0 (default 0, the paper's plain fit): each LS
+                        fit of a P row or Q column also penalises
+                        lambda ||p - 1/c||^2, lambda = delta * trace(G) / c, G
+                        the weighted Gram matrix of the point's c neighbour
+                        columns, pulling ill-determined directions towards
+                        the equal weights of the simple-averaging operator
+                        (Section 5); not in the paper.  delta = 0.03 keeps
+                        the deep 2D and planar-graph hierarchies of Section 7
+                        diagonally dominant with r = 8.                     */
 } bamg_params;
 
 typedef struct {

@@ -167,12 +167,16 @@ bamg_status bamg_step_graph_sets(int n, const int32_t* B_rp, const int32_t* B_ci
  * Householder QR in FP64 (w = sqrt of the LS weights).  Output row-wise into
  * out[J_rp[i] .. J_rp[i+1]).  constrained = 1 solves the restriction
  * problem of Section 5 instead: rows k >= 1 only, subject to sum_j p_ij = 1.
+ * ridge = delta > 0 adds lambda ||p_i - 1/c||^2 to each fit, lambda = delta *
+ * trace(G_i) / c with G_i the weighted Gram matrix of the c = |J_i| neighbour
+ * columns (bamg_params.ls_ridge; 0 = the plain fit, a negative or non-finite
+ * delta is BAMG_ERR_ARG).
  * *rankdef_host = number of rows whose fit was rank deficient (pivots below
  * 1e-13 relative were dropped). */
 bamg_status bamg_step_ls_fit(int prec, int n, int ld, int r, const int32_t* J_rp,
                              const int32_t* J_ci, const void* X, const double* w,
-                             int constrained, double* out, int* rankdef_host,
-                             void* stream);
+                             int constrained, double ridge, double* out,
+                             int* rankdef_host, void* stream);
 
 /* Two-phase sparse product C = A B (A: m x k, B: k x p, values double) on the
  * structural pattern (entries that cancel are kept).  Symbolic pass writes

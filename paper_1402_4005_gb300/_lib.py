@@ -35,7 +35,8 @@ class Params(C.Structure):
                 ("nu_pre", i32), ("nu_post", i32), ("c_min", i32), ("c_max", i32),
                 ("omega", f64), ("coarsening", i32), ("precision", i32), ("restriction", i32),
                 ("seed", u64), ("stochastic_tol", f64), ("max_coarse_dense", i32),
-                ("interp", i32), ("mlp_params", vp), ("setup_cycles", i32), ("smoother", i32)]
+                ("interp", i32), ("mlp_params", vp), ("setup_cycles", i32), ("smoother", i32),
+                ("ls_ridge", f64)]
 
 
 class SolveParams(C.Structure):
@@ -108,7 +109,7 @@ SIGNATURES = {
     "bamg_step_colour": (i32, [i32, vp, vp, vp, vp, u64, i32, vp, ip, vp]),
     "bamg_step_colour_rows": (i32, [i32, vp, i32, vp, vp, vp]),
     "bamg_step_mcgs_sweep": (i32, [i32, i32, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp]),
-    "bamg_step_ls_fit": (i32, [i32, i32, i32, i32, vp, vp, vp, vp, i32, vp, ip, vp]),
+    "bamg_step_ls_fit": (i32, [i32, i32, i32, i32, vp, vp, vp, vp, i32, f64, vp, ip, vp]),
     "bamg_step_spgemm_symbolic": (i32, [i32, vp, vp, vp, vp, vp, i64p, vp]),
     "bamg_step_spgemm_numeric": (i32, [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
     "bamg_step_coarsest": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]),

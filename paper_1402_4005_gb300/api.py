@@ -442,15 +442,15 @@ def bamg_step_graph_sets(B_rp, B_ci, B_val, Bt_rp, Bt_ci, Bt_val, cf, c_min: int
     return jrp, jci[:int(jrp[-1].item())]
 
 
-def bamg_step_ls_fit(J_rp, J_ci, X, w, r: int, constrained=False, stream=None):
+def bamg_step_ls_fit(J_rp, J_ci, X, w, r: int, constrained=False, ridge: float = 0.0, stream=None):
     prec = 1 if X.dtype == torch.float32 else 0
     n, ld = X.shape
     nnz = J_ci.shape[0]
     out = torch.zeros(max(nnz, 1), dtype=torch.float64, device="cuda")
     rk = C.c_int()
     w = _dev(w, torch.float64)
-    check(lib().bamg_step_ls_fit(prec, n, ld, r, _p(J_rp), _p(J_ci), _p(X), _p(w), int(constrained), _p(out),
-                                 C.byref(rk), _stream(stream)), "ls_fit")
+    check(lib().bamg_step_ls_fit(prec, n, ld, r, _p(J_rp), _p(J_ci), _p(X), _p(w), int(constrained),
+                                 float(ridge), _p(out), C.byref(rk), _stream(stream)), "ls_fit")
     return out[:nnz], rk.value
 
 

@@ -98,6 +98,7 @@ static bamg_status check_params(const bamg_csr* A, const bamg_params* p) {
   BAMG_CHECK_ARG(p->setup_cycles >= 1 && p->setup_cycles <= 8);
   BAMG_CHECK_ARG(p->interp == BAMG_INTERP_LS || p->setup_cycles == 1);
   BAMG_CHECK_ARG(p->smoother == BAMG_SMOOTH_JACOBI || p->smoother == BAMG_SMOOTH_MCGS);
+  BAMG_CHECK_ARG(p->ls_ridge >= 0.0 && p->ls_ridge < 1e300);
   if (p->interp == BAMG_INTERP_MLP) {
     BAMG_CHECK_ARG(p->mlp_params != nullptr);
     if (p->coarsening != BAMG_COARSEN_GEOMETRIC) {
@@ -470,17 +471,18 @@ bamg_status bamg_step_graph_sets(int n, const int32_t* B_rp, const int32_t* B_ci
 }
 
 bamg_status bamg_step_ls_fit(int prec, int n, int ld, int r, const int32_t* J_rp, const int32_t* J_ci,
-                             const void* X, const double* w, int constrained, double* out, int* rankdef_host,
-                             void* stream) {
+                             const void* X, const double* w, int constrained, double ridge, double* out,
+                             int* rankdef_host, void* stream) {
   BAMG_CHECK_ARG(n >= 1 && r >= 1 && r <= ld && J_rp && J_ci && X && w && out);
+  BAMG_CHECK_ARG(ridge >= 0.0 && ridge < 1e300);
   cudaStream_t s = S(stream);
   DevMem rk;
   BAMG_TRY(rk.alloc(sizeof(int), s));
   BAMG_CUDA(cudaMemsetAsync(rk.p, 0, sizeof(int), s));
   if (prec == 1)
-    BAMG_TRY(ls_fit<float>(n, ld, r, J_rp, J_ci, (const float*)X, w, constrained, out, rk.as<int>(), s));
+    BAMG_TRY(ls_fit<float>(n, ld, r, J_rp, J_ci, (const float*)X, w, constrained, out, rk.as<int>(), s, ridge));
   else
-    BAMG_TRY(ls_fit<double>(n, ld, r, J_rp, J_ci, (const double*)X, w, constrained, out, rk.as<int>(), s));
+    BAMG_TRY(ls_fit<double>(n, ld, r, J_rp, J_ci, (const double*)X, w, constrained, out, rk.as<int>(), s, ridge));
   int h = 0;
   BAMG_CUDA(cudaMemcpyAsync(&h, rk.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   BAMG_CUDA(cudaStreamSynchronize(s));

@@ -253,12 +253,12 @@ static bamg_status coarsen_level(bamg_hierarchy* h, int l, DevMem& U, DevMem& V,
     if (p.restriction == BAMG_RESTRICT_AVERAGE) BAMG_TRY(average_fits(L.n, L.Jrp.as<int32_t>(), fitQ.as<double>(), s));
   } else {
     BAMG_TRY(ls_fit<T>(L.n, ld, r, L.Jrp.as<int32_t>(), L.Jci.as<int32_t>(), V.as<T>(), L.s.as<double>(), 0,
-                       fitP.as<double>(), rkd.as<int>(), s));
+                       fitP.as<double>(), rkd.as<int>(), s, p.ls_ridge));
     if (p.restriction == BAMG_RESTRICT_AVERAGE)
       BAMG_TRY(average_fits(L.n, L.Jrp.as<int32_t>(), fitQ.as<double>(), s));
     else
       BAMG_TRY(ls_fit<T>(L.n, ld, r, L.Jrp.as<int32_t>(), L.Jci.as<int32_t>(), U.as<T>(), L.t.as<double>(), 1,
-                         fitQ.as<double>(), rkd.as<int>(), s));
+                         fitQ.as<double>(), rkd.as<int>(), s, p.ls_ridge));
   }
   int nnzP = njz + nc;
   for (Csr* X : {&L.P, &L.Qt}) {

@@ -128,9 +128,11 @@ bamg_status scatter_fits(int n, const int8_t* cf, const int32_t* J_rp, const dou
 bamg_status average_fits(int n, const int32_t* J_rp, double* fit, cudaStream_t s);
 
 // lsfit.cu
+// ridge > 0: Tikhonov term ridge * trace(G) / c * ||p - 1/c||^2 (0 = plain fit)
 template <typename T>
 bamg_status ls_fit(int n, int ld, int r, const int32_t* J_rp, const int32_t* J_ci, const T* X,
-                   const double* w, int constrained, double* out, int* rankdef_dev, cudaStream_t s);
+                   const double* w, int constrained, double* out, int* rankdef_dev, cudaStream_t s,
+                   double ridge = 0.0);
 
 // dense.cu
 bamg_status coarsest_solve(int prec, int n, int r, const double* B, const double* M, const double* N,

@@ -18,6 +18,17 @@
 // Householder reflector H = I - 2 h h^T / h^T h, h = 1 + sqrt(c) e_1, which
 // maps the ones vector to a multiple of e_1 (so those columns are an
 // orthonormal basis of the complement of 1).
+//
+// Optional Tikhonov term (ridge = delta > 0, not in the paper): the fit also
+// penalises lambda ||p - 1/c||^2 with lambda = delta * trace(G) / c, G the
+// weighted Gram matrix of the c neighbour columns, i.e. it pulls the
+// directions the test vectors leave ill-determined towards the equal weights
+// of the simple-averaging operator (Section 5).  Solved as least squares
+// with sqrt(lambda) I appended below the test-vector rows: lane k keeps, next
+// to its test-vector row, the appended rows k, k + S, ... of that identity,
+// and the same Householder sweep reduces both.  The unconstrained fit is
+// shifted to the prior first (y <- y - X 1/c, p = 1/c + d); the constrained
+// one already works around q0 = 1/c, whose null-space coordinates are zero.
 #include "internal.cuh"
 
 namespace bamg {
@@ -38,12 +49,13 @@ __device__ inline R seg_get(R v, int src) {
 
 // R: arithmetic type.  only != nullptr: fit just the points with only[i] != 0.
 // flag != nullptr: set flag[i] = 1 where min |r_jj| < cond_tol * max |r_jj|.
-template <typename T, typename R, int S, bool CONSTR>
+// AUG: with the Tikhonov rows of weight ridge (> 0).
+template <typename T, typename R, int S, bool CONSTR, bool AUG>
 __global__ void __launch_bounds__(256)
 ls_fit_kernel(int n, int r, const int32_t* __restrict__ jrp, const int32_t* __restrict__ jci,
               const T* __restrict__ X, const double* __restrict__ w, double* __restrict__ out,
               int* __restrict__ rankdef, const int8_t* __restrict__ only, int8_t* __restrict__ flag,
-              R cond_tol) {
+              R cond_tol, R ridge) {
   constexpr int PPW = 32 / S;
   int lane = threadIdx.x & 31;
   int gw = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -61,6 +73,23 @@ ls_fit_kernel(int n, int r, const int32_t* __restrict__ jrp, const int32_t* __re
 #pragma unroll
   for (int m = 0; m < kCMax; ++m)
     a[m] = (row_on && m < c) ? wk * R(X[(size_t)jci[base + m] * S + k]) : R(0);
+
+  // Tikhonov rows: sqrt(lambda), lambda = ridge * trace(G) / c
+  constexpr int NB = AUG ? (kCMax + S - 1) / S : 1;
+  R sq_lam = R(0);
+  if constexpr (AUG) {
+    R loc = R(0);
+#pragma unroll
+    for (int m = 0; m < kCMax; ++m) loc += a[m] * a[m];
+    const R tr = seg_sum<S>(loc);
+    sq_lam = c > 0 ? sqrt(ridge * tr / R(c)) : R(0);
+    if (!CONSTR && c > 0) {  // shift to the prior p0 = 1/c
+      R sa = R(0);
+#pragma unroll
+      for (int m = 0; m < kCMax; ++m) sa += a[m];
+      y -= sa / R(c);
+    }
+  }
 
   // Section 5 constraint: substitute p = 1/c + Z y~
   int cc = c;
@@ -86,7 +115,17 @@ ls_fit_kernel(int n, int r, const int32_t* __restrict__ jrp, const int32_t* __re
   }
   int ccw = __reduce_max_sync(0xffffffffu, cc);
 
-  // Householder QR of the S x cc system, right-hand side y.
+  // appended rows: lane k holds rows k + t*S of sqrt(lambda) I (cc x cc),
+  // right-hand side zero; they sit below every test-vector row
+  R b[NB][kCMax], y2[NB];
+#pragma unroll
+  for (int t = 0; t < NB; ++t) {
+    y2[t] = R(0);
+#pragma unroll
+    for (int m = 0; m < kCMax; ++m) b[t][m] = (AUG && k + t * S == m && m < cc) ? sq_lam : R(0);
+  }
+
+  // Householder QR of the S x cc system (plus the appended rows), right-hand side y.
   R rdiag[kCMax];
   R rmax = 0, rmin = R(1e30);
 #pragma unroll
@@ -95,7 +134,12 @@ ls_fit_kernel(int n, int r, const int32_t* __restrict__ jrp, const int32_t* __re
     if (j < ccw) {
       bool act = j < cc;
       R xj = (k >= j) ? a[j] : R(0);
-      R s2 = seg_sum<S>(xj * xj);
+      R loc2 = xj * xj;
+      if constexpr (AUG) {
+#pragma unroll
+        for (int t = 0; t < NB; ++t) loc2 += b[t][j] * b[t][j];
+      }
+      R s2 = seg_sum<S>(loc2);
       R ajj = seg_get<S>(a[j], j);
       R nrm = sqrt(s2);
       R alpha = ajj > R(0) ? -nrm : nrm;
@@ -106,12 +150,34 @@ ls_fit_kernel(int n, int r, const int32_t* __restrict__ jrp, const int32_t* __re
 #pragma unroll
       for (int m = j + 1; m < kCMax; ++m) {
         if (m < ccw) {
-          R d = seg_sum<S>(v * a[m]);
+          R dl = v * a[m];
+          if constexpr (AUG) {
+#pragma unroll
+            for (int t = 0; t < NB; ++t) dl += b[t][j] * b[t][m];
+          }
+          R d = seg_sum<S>(dl);
           if (go) a[m] -= v * (d * inv);
+          if constexpr (AUG) {
+#pragma unroll
+            for (int t = 0; t < NB; ++t)
+              if (go) b[t][m] -= b[t][j] * (d * inv);
+          }
         }
       }
-      R dy = seg_sum<S>(v * y);
+      R dyl = v * y;
+      if constexpr (AUG) {
+#pragma unroll
+        for (int t = 0; t < NB; ++t) dyl += b[t][j] * y2[t];
+      }
+      R dy = seg_sum<S>(dyl);
       if (go) y -= v * (dy * inv);
+      if constexpr (AUG) {
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+          if (go) y2[t] -= b[t][j] * (dy * inv);
+          if (go) b[t][j] = R(0);
+        }
+      }
       if (go) a[j] = (k == j) ? alpha : (k > j ? R(0) : a[j]);
       rdiag[j] = go ? alpha : R(0);
       rmax = fmax(rmax, fabs(rdiag[j]));
@@ -157,6 +223,7 @@ ls_fit_kernel(int n, int r, const int32_t* __restrict__ jrp, const int32_t* __re
     val = 0.0;
 #pragma unroll
     for (int m = 0; m < kCMax; ++m) if (m == k) val = (double)p[m];
+    if (AUG) val += 1.0 / c;
   }
   if (k < c) out[base + k] = val;
   if (k == 0 && dropped) atomicAdd(rankdef, 1);
@@ -164,48 +231,61 @@ ls_fit_kernel(int n, int r, const int32_t* __restrict__ jrp, const int32_t* __re
 
 template <typename T, typename R, int S>
 static bamg_status ls_fit_launch(int n, int r, const int32_t* J_rp, const int32_t* J_ci, const T* X,
-                                 const double* w, int constrained, double* out, int* rankdef, const int8_t* only,
-                                 int8_t* flag, cudaStream_t s) {
+                                 const double* w, int constrained, double ridge, double* out, int* rankdef,
+                                 const int8_t* only, int8_t* flag, cudaStream_t s) {
   constexpr int PPW = 32 / S;
   unsigned grid = cdiv(n, 8 * PPW);
-  const R tol = R(1e-3);
+  const R tol = R(1e-3), rg = R(ridge);
+  if (ridge > 0.0) {
+    if (constrained)
+      return launch(ls_fit_kernel<T, R, S, true, true>, dim3(grid), dim3(256), 0, s, n, r, J_rp, J_ci, X, w, out,
+                    rankdef, only, flag, tol, rg);
+    return launch(ls_fit_kernel<T, R, S, false, true>, dim3(grid), dim3(256), 0, s, n, r, J_rp, J_ci, X, w, out,
+                  rankdef, only, flag, tol, rg);
+  }
   if (constrained)
-    return launch(ls_fit_kernel<T, R, S, true>, dim3(grid), dim3(256), 0, s, n, r, J_rp, J_ci, X, w, out, rankdef,
-                  only, flag, tol);
-  return launch(ls_fit_kernel<T, R, S, false>, dim3(grid), dim3(256), 0, s, n, r, J_rp, J_ci, X, w, out, rankdef,
-                only, flag, tol);
+    return launch(ls_fit_kernel<T, R, S, true, false>, dim3(grid), dim3(256), 0, s, n, r, J_rp, J_ci, X, w, out,
+                  rankdef, only, flag, tol, rg);
+  return launch(ls_fit_kernel<T, R, S, false, false>, dim3(grid), dim3(256), 0, s, n, r, J_rp, J_ci, X, w, out,
+                rankdef, only, flag, tol, rg);
 }
 
 template <typename T, int S>
 static bamg_status ls_fit_s(int n, int r, const int32_t* J_rp, const int32_t* J_ci, const T* X,
-                            const double* w, int constrained, double* out, int* rankdef, cudaStream_t s) {
+                            const double* w, int constrained, double ridge, double* out, int* rankdef,
+                            cudaStream_t s) {
   if (sizeof(T) == 8)
-    return ls_fit_launch<T, double, S>(n, r, J_rp, J_ci, X, w, constrained, out, rankdef, nullptr, nullptr, s);
+    return ls_fit_launch<T, double, S>(n, r, J_rp, J_ci, X, w, constrained, ridge, out, rankdef, nullptr, nullptr,
+                                       s);
   // FP32 pass, then FP64 on the flagged (ill-conditioned) points only
   DevMem flag;
   BAMG_TRY(flag.alloc((size_t)n, s));
   BAMG_CUDA(cudaMemsetAsync(flag.p, 0, (size_t)n, s));
-  BAMG_TRY(ls_fit_launch<T, float, S>(n, r, J_rp, J_ci, X, w, constrained, out, rankdef, nullptr,
+  BAMG_TRY(ls_fit_launch<T, float, S>(n, r, J_rp, J_ci, X, w, constrained, ridge, out, rankdef, nullptr,
                                       flag.as<int8_t>(), s));
-  return ls_fit_launch<T, double, S>(n, r, J_rp, J_ci, X, w, constrained, out, rankdef,
+  return ls_fit_launch<T, double, S>(n, r, J_rp, J_ci, X, w, constrained, ridge, out, rankdef,
                                      (const int8_t*)flag.as<int8_t>(), nullptr, s);
 }
 
 template <typename T>
 bamg_status ls_fit(int n, int ld, int r, const int32_t* J_rp, const int32_t* J_ci, const T* X,
-                   const double* w, int constrained, double* out, int* rankdef_dev, cudaStream_t s) {
+                   const double* w, int constrained, double* out, int* rankdef_dev, cudaStream_t s, double ridge) {
+  if (!(ridge >= 0.0 && ridge < 1e300)) {
+    set_error("ridge weight %g must be finite and >= 0", ridge);
+    return BAMG_ERR_ARG;
+  }
   switch (ld) {
-    case 4: return ls_fit_s<T, 4>(n, r, J_rp, J_ci, X, w, constrained, out, rankdef_dev, s);
-    case 8: return ls_fit_s<T, 8>(n, r, J_rp, J_ci, X, w, constrained, out, rankdef_dev, s);
-    case 16: return ls_fit_s<T, 16>(n, r, J_rp, J_ci, X, w, constrained, out, rankdef_dev, s);
-    case 32: return ls_fit_s<T, 32>(n, r, J_rp, J_ci, X, w, constrained, out, rankdef_dev, s);
+    case 4: return ls_fit_s<T, 4>(n, r, J_rp, J_ci, X, w, constrained, ridge, out, rankdef_dev, s);
+    case 8: return ls_fit_s<T, 8>(n, r, J_rp, J_ci, X, w, constrained, ridge, out, rankdef_dev, s);
+    case 16: return ls_fit_s<T, 16>(n, r, J_rp, J_ci, X, w, constrained, ridge, out, rankdef_dev, s);
+    case 32: return ls_fit_s<T, 32>(n, r, J_rp, J_ci, X, w, constrained, ridge, out, rankdef_dev, s);
     default: set_error("block width %d not in {4,8,16,32}", ld); return BAMG_ERR_ARG;
   }
 }
 
 template bamg_status ls_fit<float>(int, int, int, const int32_t*, const int32_t*, const float*, const double*,
-                                   int, double*, int*, cudaStream_t);
+                                   int, double*, int*, cudaStream_t, double);
 template bamg_status ls_fit<double>(int, int, int, const int32_t*, const int32_t*, const double*,
-                                    const double*, int, double*, int*, cudaStream_t);
+                                    const double*, int, double*, int*, cudaStream_t, double);
 
 }  // namespace bamg

@@ -52,7 +52,7 @@ def test_parameter_structs_match_the_header():
     assert L.bamg_params_default(ctypes.cast(buf, ctypes.POINTER(_lib.Params))) == 0
     assert all(b == 0xAB for b in buf[size:]), "bamg_params is larger in the header than in the binding"
     p = _lib.Params.from_buffer(buf)
-    assert (p.setup_cycles, p.interp, p.smoother, p.max_coarse_dense) == (1, 0, 0, 1024)
+    assert (p.setup_cycles, p.interp, p.smoother, p.max_coarse_dense, p.ls_ridge) == (1, 0, 0, 1024, 0.0)
     assert p.mlp_params is None
     sp = _lib.SolveParams()
     sp.plain = 7
