@@ -171,3 +171,24 @@ def test_delaunay_three_to_eight_points_with_penalty(api):
     xs = ch.meta["deg"] / ch.meta["deg"].sum()
     assert info["rel_res_1"] <= 1e-11
     assert np.abs(x.cpu().numpy() - xs).sum() <= 1e-8
+
+
+def test_second_cycle_with_penalty_on_paper_tandem(api):
+    """BAMG^2 with the penalised fits on the tandem queue with the paper's
+    rates (Table tandem setting, 129^2 states): hierarchy of the second cycle
+    against the oracle, solve within 1e-8 of the oracle's stationary vector,
+    and fewer iterations than one cycle needs."""
+    ch = cg.tandem(129, lam=11 / 31, mu1=10 / 31, mu2=10 / 31)
+    kw = dict(r=8, coarse_min=17 * 17, c_max=4, seed=2)
+    its = []
+    for cycles in (1, 2):
+        p = api.bamg_params_default(ls_ridge=0.03, setup_cycles=cycles, **kw)
+        h = api.bamg_setup(dev(ch.row_ptr), dev(ch.col), dev(ch.val), ch.n, p, nx=129, ny=129)
+        H = S.bamg_setup(ch.csr(), S.Params(ls_ridge=0.03, cycles=cycles, **kw), grid=(129, 129))
+        compare_hierarchies(h, H, 1e-8)
+        x, info = api.bamg_solve(h, restart=20, tol=1e-10)
+        xo, _, _ = So.bamg_solve(H, tol=1e-12, restart=20)
+        assert info["rel_res_1"] <= 1e-10
+        assert np.abs(x.cpu().numpy() - xo).sum() <= 1e-8
+        its.append(info["iterations"])
+    assert its[1] < its[0], its
