@@ -171,6 +171,9 @@ bamg_status bamg_step_graph_sets(int n, const int32_t* B_rp, const int32_t* B_ci
  * trace(G_i) / c with G_i the weighted Gram matrix of the c = |J_i| neighbour
  * columns (bamg_params.ls_ridge; 0 = the plain fit, a negative or non-finite
  * delta is BAMG_ERR_ARG).
+ * Sets must satisfy |J_i| <= min(ld, 8) (bamg_setup guarantees it through
+ * c_max <= 8 and c_max <= block width); larger sets are not detected and
+ * give unspecified weights.
  * *rankdef_host = number of rows whose fit was rank deficient (pivots below
  * 1e-13 relative were dropped). */
 bamg_status bamg_step_ls_fit(int prec, int n, int ld, int r, const int32_t* J_rp,
