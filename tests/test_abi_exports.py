@@ -58,3 +58,23 @@ def test_parameter_structs_match_the_header():
     sp.plain = 7
     assert L.bamg_solve_params_default(ctypes.byref(sp)) == 0
     assert (sp.restart, sp.max_iter, sp.tol, sp.plain) == (20, 500, 1e-10, 0)
+
+
+def test_penalty_weight_is_validated_before_any_device_call():
+    """bamg_params.ls_ridge must be finite and >= 0; the check runs before
+    the library touches a device, so it needs no GPU."""
+    import numpy as np
+    from paper_1402_4005_gb300 import _lib
+    L = _lib.lib()
+    rp = np.array([0, 1, 2], np.int32)
+    ci = np.array([1, 0], np.int32)
+    va = np.array([1.0, 1.0])
+    A = _lib.Csr(n=2, nnz=2, row_ptr=rp.ctypes.data, col_idx=ci.ctypes.data, val=va.ctypes.data,
+                 on_device=0, nx=2, ny=1)
+    for bad in (-0.5, float("nan"), float("inf")):
+        p = _lib.Params()
+        assert L.bamg_params_default(ctypes.byref(p)) == 0
+        p.ls_ridge = bad
+        out = ctypes.c_void_p()
+        assert L.bamg_setup(ctypes.byref(A), ctypes.byref(p), None, ctypes.byref(out)) == 1, bad
+        assert not out.value
