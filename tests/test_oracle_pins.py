@@ -587,8 +587,9 @@ def test_ridge_fit_keeps_a_deep_2d_hierarchy_convergent():
         H = S.bamg_setup(ch.csr(), S.Params(r=8, coarse_min=17 * 17, c_max=4, seed=2, ls_ridge=0.03, cycles=cyc),
                          grid=(129, 129))
         assert min(float(l.B.diagonal().min()) for l in H.levels) > 0
-        _, its, hist = So.bamg_solve(H, tol=1e-10, restart=20, max_iter=40)
+        x, its, hist = So.bamg_solve(H, tol=1e-10, restart=20, max_iter=40)
         assert its < 40
+        assert np.abs(x - ch.meta["wdeg"] / ch.meta["wdeg"].sum()).sum() <= 1e-8     # x proportional to degree
         i7.append(next(i for i, h in enumerate(hist) if h <= 1e-7))
     assert i7[0] <= 2 * tab["uniform2d"]["bamg"][3], i7
     assert i7[1] < i7[0], i7
