@@ -333,6 +333,21 @@ def test_ridge_constrained_fit_matches_kkt_and_keeps_sum_one():
         assert abs(q.sum() - 1.0) <= 8 * np.finfo(float).eps
 
 
+
+def test_ridge_limit_is_the_simple_averaging_operator():
+    """delta -> infinity: the penalised restriction becomes the simple
+    averaging of Section 5 (every entry of a column 1/c), on real sets and
+    test vectors of a tandem queue."""
+    ch = cg.tandem(15)
+    B = operators.build_B(ch.csr())
+    cf, cmap, _ = coarsening.geometric(15, 15)
+    J = coarsening.geometric_sets(15, 15, cf)
+    U = np.stack([np.ones(ch.n)] + [rng.uniform_pm1(3, k, ch.n) for k in range(1, 6)], axis=1)
+    t = np.concatenate([[0.0], np.full(5, 0.7)])
+    Qt = interp.ls_restriction_T(U, t, cf, cmap, J, ridge=1e14).toarray()
+    Qa = interp.averaging_restriction_T(cf, cmap, J, ch.n).toarray()
+    assert np.abs(Qt - Qa).max() <= 1e-10
+
 def test_ridge_keeps_exactly_reproduced_bilinear_weights():
     """When the test vectors are reproduced exactly by the equal weights
     (bilinear 1, x, y, xy on the 2D grid), the penalty does not move them."""
