@@ -15,10 +15,11 @@ Modules
   coarsening  geometric and greedy-MIS C/F splitting, interpolation sets J_i
   smoothing   weighted Jacobi, lexicographic and multicolour Gauss-Seidel
   interp      least-squares interpolation P and constrained restriction Q
-              (eq. ls_interpolation, eq. ls_weights, Section 5)
+              (eq. ls_interpolation, eq. ls_weights, Section 5), with an
+              optional Tikhonov term towards equal weights (not in the paper)
   coarsest    generalized singular triplets and pseudo-inverse on the
               coarsest level (eq. generalized_eigenvalue)
-  setup       Algorithm 1 (bamg_mle), the first bootstrap cycle
+  setup       Algorithm 1 (bamg_mle), the first and later bootstrap cycles
   solve       V-cycle (eq. error_propagator_twogrid), right FGMRES, the
               paper's left-preconditioned GMRES (eq. prec_residual),
               unpreconditioned GMRES(m), reference stationary vectors
