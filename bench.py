@@ -17,7 +17,8 @@ Beside the headline line the same JSON object reports, on the same GPU:
                     tandem queue (4.2M states, inputs far above L2) vs HBM
   learned           network fits vs LS fits on the 2048 x 2048 tandem queue
   batched           256 seeded chains of 1k-65k states, batched vs a loop
-  delaunay          random walk on the Delaunay graph of 2^20 points (MIS)
+  delaunay          random walk on the Delaunay graph of 2^20 points (MIS),
+                    plus sets of 3-8 points with the penalised LS fit
   birthdeath        the paper's birth-death table: BAMG, BAMG^2 and
                     GMRES(50) without preconditioning, n = 2^k + 1
 
