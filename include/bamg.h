@@ -117,8 +117,9 @@ typedef struct {
                         columns, pulling ill-determined directions towards
                         the equal weights of the simple-averaging operator
                         (Section 5); not in the paper.  delta = 0.03 keeps
-                        the deep 2D and planar-graph hierarchies of Section 7
-                        diagonally dominant with r = 8.                     */
+                        the coarse diagonals of the deep 2D and planar-graph
+                        hierarchies of Section 7 positive with r = 8; a
+                        negative or non-finite delta is BAMG_ERR_ARG.       */
 } bamg_params;
 
 typedef struct {
