@@ -608,3 +608,109 @@ def test_ridge_fit_keeps_a_deep_2d_hierarchy_convergent():
         i7.append(next(i for i, h in enumerate(hist) if h <= 1e-7))
     assert i7[0] <= 2 * tab["uniform2d"]["bamg"][3], i7
     assert i7[1] < i7[0], i7
+
+
+# --------------------------------------------------------------- weights, Rayleigh quotient, x^(0)
+def _path3_B():
+    """B = I - A of the walk on the path 0 - 1 - 2 (A column stochastic:
+    0 -> 1 and 2 -> 1 with probability 1, 1 -> 0 and 1 -> 2 with 1/2)."""
+    A = np.array([[0.0, 0.5, 0.0], [1.0, 0.0, 1.0], [0.0, 0.5, 0.0]])
+    return sp.csr_matrix(np.eye(3) - A)
+
+
+def test_ls_weights_by_hand_and_their_effect_on_P():
+    """eq. ls_weights: omega_k = 1/||B v^(k)||_2^2 of the unit test vector.
+    Worked by hand on the 3-state path with v1 = (2, 1, 0), v2 = (1, 1, 1):
+    ||B v1||^2 = 3.5 and ||v1||^2 = 5, so omega_1 = 10/7; ||B v2||^2 = 1.5 and
+    ||v2||^2 = 3, so omega_2 = 2.  The fit of fine point 0 from coarse point 1
+    is then p = sum_k omega_k v0 v1 / sum_k omega_k v1^2 = (26/21)/(20/21) =
+    1.3 (and 0.7 for point 2), whereas equal weights give 11/8 and
+    omega = 1/||Bv|| (a dropped square) gives 1.33646..."""
+    B = _path3_B()
+    V = np.array([[2.0, 1.0], [1.0, 1.0], [0.0, 1.0]])
+    Vn = interp.normalise(V)
+    assert np.allclose(np.linalg.norm(Vn, axis=0), 1.0, rtol=0, atol=1e-15)
+    s = interp.weights(B, Vn)
+    assert np.allclose(s ** 2, [10.0 / 7.0, 2.0], rtol=1e-14, atol=0)
+    # only the chosen columns get a weight (u^(1) = 1 takes none, Section 5)
+    s1 = interp.weights(B, Vn, range(1, 2))
+    assert s1[0] == 0.0 and abs(s1[1] ** 2 - 2.0) <= 1e-14
+    cf = np.array([False, True, False])
+    cmap = np.array([-1, 0, -1])
+    J = {0: np.array([1]), 2: np.array([1])}
+    P = interp.ls_interpolation(Vn, s, cf, cmap, J).toarray()
+    assert abs(P[0, 0] - 1.3) <= 1e-14
+    assert abs(P[2, 0] - 0.7) <= 1e-14      # (omega_2 / 3) / (20/21): v1 is zero at point 2
+    assert P[1, 0] == 1.0                                        # eq. Pstructure
+    # the same fit with the weights a plausible misreading would give
+    P_eq = interp.ls_interpolation(Vn, np.ones(2), cf, cmap, J).toarray()
+    P_sq = interp.ls_interpolation(Vn, np.sqrt(s), cf, cmap, J).toarray()
+    assert abs(P_eq[0, 0] - 11.0 / 8.0) <= 1e-14
+    assert abs(P_sq[0, 0] - 1.3) > 0.03
+
+
+def _exact_triplets(n=12, seed=7):
+    """A level with a random column-stochastic B = I - A and distinct SPD
+    M, N, and its exact generalized singular triplets B v = s M u,
+    B^T u = s N v from the SVD of L_M^{-1} B L_N^{-T} (eq. generalized_eigenvalue)."""
+    g = np.random.default_rng(seed)
+    A = g.uniform(0.0, 1.0, (n, n)) * (g.uniform(size=(n, n)) < 0.5)
+    A += np.eye(n, k=1) + np.eye(n, k=-1)
+    A /= A.sum(axis=0, keepdims=True)
+    Bd = np.eye(n) - A
+    G1 = g.standard_normal((n, n)); Md = G1 @ G1.T / n + np.eye(n)
+    G2 = g.standard_normal((n, n)); Nd = G2 @ G2.T / n + 0.5 * np.eye(n)
+    LM = np.linalg.cholesky(Md)
+    LN = np.linalg.cholesky(Nd)
+    C = np.linalg.solve(LM, np.linalg.solve(LN, Bd.T).T)
+    Ut, sv, Vth = np.linalg.svd(C)
+    U = np.linalg.solve(LM.T, Ut)
+    V = np.linalg.solve(LN.T, Vth.T)
+    lev = S.make_level(sp.csr_matrix(Bd), sp.csr_matrix(Md), sp.csr_matrix(Nd))
+    return lev, Bd, Md, Nd, sv, U, V
+
+
+def test_rayleigh_quotient_reproduces_exact_singular_values():
+    """eq. singular_value at exact generalized triplets returns sigma, for
+    any positive scaling of u and v (the denominator is the product of the
+    M- and N-norms), and for M = N = I the ordinary singular values."""
+    lev, Bd, Md, Nd, sv, U, V = _exact_triplets()
+    assert np.allclose(Bd @ V, Md @ U * sv, atol=1e-12)          # the construction
+    assert np.allclose(Bd.T @ U, Nd @ V * sv, atol=1e-12)
+    got = S.rayleigh(lev, 3.0 * U, 0.25 * V)
+    assert np.abs(got - sv).max() <= 1e-13 * sv.max()
+    # swapping the roles of M and N changes the quotient
+    swapped = S.make_level(lev.B, lev.N, lev.M)
+    assert np.abs(S.rayleigh(swapped, U, V) - sv).max() > 1e-3
+    # the finest level carries M = N = I: plain singular triplets of B
+    Ub, sb, Vbh = np.linalg.svd(Bd)
+    lev0 = S.make_level(sp.csr_matrix(Bd))
+    assert np.abs(S.rayleigh(lev0, 2.0 * Ub, Vbh.T) - sb).max() <= 1e-13 * sb.max()
+
+
+def test_inhomogeneous_relaxation_fixes_exact_triplets():
+    """Algorithm 1, last smoothing loop: an exact triplet solves both
+    systems B v = sigma M u and B^T u = sigma N v, so the weighted Jacobi
+    sweeps and the sigma update leave it unchanged; a perturbed one moves."""
+    lev, Bd, Md, Nd, sv, U, V = _exact_triplets()
+    k = np.array([0, 3, 7, 11])
+    p = S.Params(nu_setup=4)
+    sig, Un, Vn = S.relax_inhomogeneous(lev, sv[k].copy(), U[:, k].copy(), V[:, k].copy(), p)
+    assert np.abs(sig - sv[k]).max() <= 1e-12 * sv.max()
+    assert np.abs(Un - U[:, k]).max() <= 1e-12 * np.abs(U).max()
+    assert np.abs(Vn - V[:, k]).max() <= 1e-12 * np.abs(V).max()
+    # a wrong singular value is not a fixed point of the inhomogeneous sweeps
+    _, _, Vw = S.relax_inhomogeneous(lev, 1.5 * sv[k], U[:, k].copy(), V[:, k].copy(), p)
+    assert np.abs(Vw - V[:, k]).max() > 1e-3 * np.abs(V).max()
+
+
+def test_initial_x_takes_smallest_abs_sigma_positive_sum_unit_l1():
+    """x^(0): the v of the smallest |sigma| (here column 2, not the most
+    negative sigma of column 1), oriented to a positive sum and scaled to
+    unit 1-norm: (-3, 1, -2) becomes (1/2, -1/6, 1/3)."""
+    sig = np.array([0.5, -0.3, 0.01])
+    V = np.array([[1.0, 4.0, -3.0], [2.0, 5.0, 1.0], [3.0, 6.0, -2.0]])
+    x = S.initial_x(sig, V)
+    assert np.allclose(x, [0.5, -1.0 / 6.0, 1.0 / 3.0], rtol=0, atol=1e-15)
+    x2 = S.initial_x(np.array([0.2, -1e-3]), np.array([[1.0, 2.0], [1.0, 2.0]]))
+    assert np.allclose(x2, [0.5, 0.5], rtol=0, atol=1e-15)
