@@ -93,7 +93,8 @@ bamg_status bamg_step_norms_weights(int prec, int n, int ld, int r, const int32_
  * bamg_step_norms_weights; scratch lives in a fixed ~0.8 MB device array
  * that each GPU loading the library keeps until the process exits.  The
  * first call on a device looks up that array's address (make it before any
- * stream capture).  ld must be 4, 8, 16 or 32 and r <= ld, else
+ * stream capture); after a cudaDeviceReset the next call looks it up again
+ * in the new context.  ld must be 4, 8, 16 or 32 and r <= ld, else
  * BAMG_ERR_ARG.  All calls share the array: calls that overlap on the GPU
  * race and must be serialised by the caller. */
 bamg_status bamg_step_norms_weights_noalloc(int prec, int n, int ld, int r, const int32_t* rp,
@@ -172,10 +173,11 @@ bamg_status bamg_step_graph_sets(int n, const int32_t* B_rp, const int32_t* B_ci
  * columns (bamg_params.ls_ridge; 0 = the plain fit, a negative or non-finite
  * delta is BAMG_ERR_ARG).
  * Sets must satisfy |J_i| <= min(ld, 8) (bamg_setup guarantees it through
- * c_max <= 8 and c_max <= block width); larger sets are not detected and
- * give unspecified weights.
+ * c_max <= 8 and c_max <= block width); rows with larger sets are left
+ * unwritten and the call returns BAMG_ERR_ARG (the other rows are fitted).
  * *rankdef_host = number of rows whose fit was rank deficient (pivots below
- * 1e-13 relative were dropped). */
+ * 1e-13 relative were dropped); in FP32 (prec = 1) a row that is refitted in
+ * FP64 is counted by the FP64 fit only. */
 bamg_status bamg_step_ls_fit(int prec, int n, int ld, int r, const int32_t* J_rp,
                              const int32_t* J_ci, const void* X, const double* w,
                              int constrained, double ridge, double* out,

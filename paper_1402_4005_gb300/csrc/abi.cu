@@ -477,16 +477,20 @@ bamg_status bamg_step_ls_fit(int prec, int n, int ld, int r, const int32_t* J_rp
   BAMG_CHECK_ARG(ridge >= 0.0 && ridge < 1e300);
   cudaStream_t s = S(stream);
   DevMem rk;
-  BAMG_TRY(rk.alloc(sizeof(int), s));
-  BAMG_CUDA(cudaMemsetAsync(rk.p, 0, sizeof(int), s));
+  BAMG_TRY(rk.alloc(2 * sizeof(int), s));
+  BAMG_CUDA(cudaMemsetAsync(rk.p, 0, 2 * sizeof(int), s));
   if (prec == 1)
     BAMG_TRY(ls_fit<float>(n, ld, r, J_rp, J_ci, (const float*)X, w, constrained, out, rk.as<int>(), s, ridge));
   else
     BAMG_TRY(ls_fit<double>(n, ld, r, J_rp, J_ci, (const double*)X, w, constrained, out, rk.as<int>(), s, ridge));
-  int h = 0;
-  BAMG_CUDA(cudaMemcpyAsync(&h, rk.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  int h[2] = {0, 0};
+  BAMG_CUDA(cudaMemcpyAsync(h, rk.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   BAMG_CUDA(cudaStreamSynchronize(s));
-  if (rankdef_host) *rankdef_host = h;
+  if (rankdef_host) *rankdef_host = h[0];
+  if (h[1] > 0) {
+    set_error("%d interpolation sets exceed min(ld, 8) = %d entries", h[1], ld < 8 ? ld : 8);
+    return BAMG_ERR_ARG;
+  }
   return BAMG_OK;
 }
 

@@ -446,10 +446,10 @@ static bamg_status run_setup(bamg_hierarchy* h, cudaStream_t s) {
   DevMem scale, norms, rkd, sig, sig64;
   BAMG_TRY(scale.alloc(sizeof(T) * ld, s));
   BAMG_TRY(norms.alloc(sizeof(double) * ld, s));
-  BAMG_TRY(rkd.alloc(sizeof(int), s));
+  BAMG_TRY(rkd.alloc(2 * sizeof(int), s));
   BAMG_TRY(sig.alloc(sizeof(T) * ld, s));
   BAMG_TRY(sig64.alloc(sizeof(double) * ld, s));
-  BAMG_CUDA(cudaMemsetAsync(rkd.p, 0, sizeof(int), s));
+  BAMG_CUDA(cudaMemsetAsync(rkd.p, 0, 2 * sizeof(int), s));
   // bootstrap cycles: each later cycle rebuilds the hierarchy below the
   // finest level from the previous cycle's finest triplets (Section 4)
   const int cycles = learned ? 1 : p.setup_cycles;

@@ -128,7 +128,9 @@ bamg_status scatter_fits(int n, const int8_t* cf, const int32_t* J_rp, const dou
 bamg_status average_fits(int n, const int32_t* J_rp, double* fit, cudaStream_t s);
 
 // lsfit.cu
-// ridge > 0: Tikhonov term ridge * trace(G) / c * ||p - 1/c||^2 (0 = plain fit)
+// ridge > 0: Tikhonov term ridge * trace(G) / c * ||p - 1/c||^2 (0 = plain fit).
+// rankdef_dev points to two counters: rank-deficient rows, and rows whose set
+// exceeds min(ld, 8) (skipped, nothing written).
 template <typename T>
 bamg_status ls_fit(int n, int ld, int r, const int32_t* J_rp, const int32_t* J_ci, const T* X,
                    const double* w, int constrained, double* out, int* rankdef_dev, cudaStream_t s,

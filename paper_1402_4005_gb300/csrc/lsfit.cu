@@ -50,12 +50,14 @@ __device__ inline R seg_get(R v, int src) {
 // R: arithmetic type.  only != nullptr: fit just the points with only[i] != 0.
 // flag != nullptr: set flag[i] = 1 where min |r_jj| < cond_tol * max |r_jj|.
 // AUG: with the Tikhonov rows of weight ridge (> 0).
+// A set larger than min(S, 8) cannot be held by the segment: the row is
+// skipped (nothing written) and counted in *oversize.
 template <typename T, typename R, int S, bool CONSTR, bool AUG>
 __global__ void __launch_bounds__(256)
 ls_fit_kernel(int n, int r, const int32_t* __restrict__ jrp, const int32_t* __restrict__ jci,
               const T* __restrict__ X, const double* __restrict__ w, double* __restrict__ out,
               int* __restrict__ rankdef, const int8_t* __restrict__ only, int8_t* __restrict__ flag,
-              R cond_tol, R ridge) {
+              R cond_tol, R ridge, int* __restrict__ oversize) {
   constexpr int PPW = 32 / S;
   int lane = threadIdx.x & 31;
   int gw = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -64,6 +66,10 @@ ls_fit_kernel(int n, int r, const int32_t* __restrict__ jrp, const int32_t* __re
   bool valid = i < n && (only == nullptr || only[i] != 0);
   int c = valid ? jrp[i + 1] - jrp[i] : 0;
   int base = valid ? jrp[i] : 0;
+  if (c > (S < kCMax ? S : kCMax)) {
+    if (k == 0) atomicAdd(oversize, 1);
+    c = 0;
+  }
   if (__reduce_max_sync(0xffffffffu, c) == 0) return;  // warp-uniform exit
 
   bool row_on = valid && c > 0 && k < r && !(CONSTR && k == 0);
@@ -201,7 +207,9 @@ ls_fit_kernel(int n, int r, const int32_t* __restrict__ jrp, const int32_t* __re
     }
   }
   if (!valid || c == 0) return;
-  if (flag != nullptr && k == 0 && cc > 0 && rmin < cond_tol * rmax) flag[i] = 1;
+  // a row flagged for the FP64 refit is counted by that refit alone
+  const bool refit = flag != nullptr && cc > 0 && rmin < cond_tol * rmax;
+  if (refit && k == 0) flag[i] = 1;
   // the constrained weights are assembled in FP64 from the null-space
   // coordinates, so they sum to one to FP64 rounding in either precision
   double val;
@@ -226,59 +234,60 @@ ls_fit_kernel(int n, int r, const int32_t* __restrict__ jrp, const int32_t* __re
     if (AUG) val += 1.0 / c;
   }
   if (k < c) out[base + k] = val;
-  if (k == 0 && dropped) atomicAdd(rankdef, 1);
+  if (k == 0 && dropped && !refit) atomicAdd(rankdef, 1);
 }
 
 template <typename T, typename R, int S>
 static bamg_status ls_fit_launch(int n, int r, const int32_t* J_rp, const int32_t* J_ci, const T* X,
                                  const double* w, int constrained, double ridge, double* out, int* rankdef,
-                                 const int8_t* only, int8_t* flag, cudaStream_t s) {
+                                 const int8_t* only, int8_t* flag, int* oversize, cudaStream_t s) {
   constexpr int PPW = 32 / S;
   unsigned grid = cdiv(n, 8 * PPW);
   const R tol = R(1e-3), rg = R(ridge);
   if (ridge > 0.0) {
     if (constrained)
       return launch(ls_fit_kernel<T, R, S, true, true>, dim3(grid), dim3(256), 0, s, n, r, J_rp, J_ci, X, w, out,
-                    rankdef, only, flag, tol, rg);
+                    rankdef, only, flag, tol, rg, oversize);
     return launch(ls_fit_kernel<T, R, S, false, true>, dim3(grid), dim3(256), 0, s, n, r, J_rp, J_ci, X, w, out,
-                  rankdef, only, flag, tol, rg);
+                  rankdef, only, flag, tol, rg, oversize);
   }
   if (constrained)
     return launch(ls_fit_kernel<T, R, S, true, false>, dim3(grid), dim3(256), 0, s, n, r, J_rp, J_ci, X, w, out,
-                  rankdef, only, flag, tol, rg);
+                  rankdef, only, flag, tol, rg, oversize);
   return launch(ls_fit_kernel<T, R, S, false, false>, dim3(grid), dim3(256), 0, s, n, r, J_rp, J_ci, X, w, out,
-                rankdef, only, flag, tol, rg);
+                rankdef, only, flag, tol, rg, oversize);
 }
 
 template <typename T, int S>
 static bamg_status ls_fit_s(int n, int r, const int32_t* J_rp, const int32_t* J_ci, const T* X,
                             const double* w, int constrained, double ridge, double* out, int* rankdef,
-                            cudaStream_t s) {
+                            int* oversize, cudaStream_t s) {
   if (sizeof(T) == 8)
     return ls_fit_launch<T, double, S>(n, r, J_rp, J_ci, X, w, constrained, ridge, out, rankdef, nullptr, nullptr,
-                                       s);
+                                       oversize, s);
   // FP32 pass, then FP64 on the flagged (ill-conditioned) points only
   DevMem flag;
   BAMG_TRY(flag.alloc((size_t)n, s));
   BAMG_CUDA(cudaMemsetAsync(flag.p, 0, (size_t)n, s));
   BAMG_TRY(ls_fit_launch<T, float, S>(n, r, J_rp, J_ci, X, w, constrained, ridge, out, rankdef, nullptr,
-                                      flag.as<int8_t>(), s));
+                                      flag.as<int8_t>(), oversize, s));
   return ls_fit_launch<T, double, S>(n, r, J_rp, J_ci, X, w, constrained, ridge, out, rankdef,
-                                     (const int8_t*)flag.as<int8_t>(), nullptr, s);
+                                     (const int8_t*)flag.as<int8_t>(), nullptr, oversize, s);
 }
 
 template <typename T>
 bamg_status ls_fit(int n, int ld, int r, const int32_t* J_rp, const int32_t* J_ci, const T* X,
                    const double* w, int constrained, double* out, int* rankdef_dev, cudaStream_t s, double ridge) {
+  // rankdef_dev[0]: rank-deficient rows; rankdef_dev[1]: rows whose set exceeds min(ld, 8)
   if (!(ridge >= 0.0 && ridge < 1e300)) {
     set_error("ridge weight %g must be finite and >= 0", ridge);
     return BAMG_ERR_ARG;
   }
   switch (ld) {
-    case 4: return ls_fit_s<T, 4>(n, r, J_rp, J_ci, X, w, constrained, ridge, out, rankdef_dev, s);
-    case 8: return ls_fit_s<T, 8>(n, r, J_rp, J_ci, X, w, constrained, ridge, out, rankdef_dev, s);
-    case 16: return ls_fit_s<T, 16>(n, r, J_rp, J_ci, X, w, constrained, ridge, out, rankdef_dev, s);
-    case 32: return ls_fit_s<T, 32>(n, r, J_rp, J_ci, X, w, constrained, ridge, out, rankdef_dev, s);
+    case 4: return ls_fit_s<T, 4>(n, r, J_rp, J_ci, X, w, constrained, ridge, out, rankdef_dev, rankdef_dev + 1, s);
+    case 8: return ls_fit_s<T, 8>(n, r, J_rp, J_ci, X, w, constrained, ridge, out, rankdef_dev, rankdef_dev + 1, s);
+    case 16: return ls_fit_s<T, 16>(n, r, J_rp, J_ci, X, w, constrained, ridge, out, rankdef_dev, rankdef_dev + 1, s);
+    case 32: return ls_fit_s<T, 32>(n, r, J_rp, J_ci, X, w, constrained, ridge, out, rankdef_dev, rankdef_dev + 1, s);
     default: set_error("block width %d not in {4,8,16,32}", ld); return BAMG_ERR_ARG;
   }
 }

@@ -15,6 +15,14 @@
 // on that device; make that first call before any stream capture.  All calls
 // share the array: calls that overlap on the GPU (other streams, other host
 // threads) race on it and must be serialised by the caller.
+//
+// cudaDeviceReset loads the module into a new context, where the array may
+// sit at another address: the cached address is kept with the identifier of
+// the context it was looked up in (cuCtxGetId, reached through the runtime's
+// driver entry points, so the library does not link the driver library), and
+// a call from a different context looks the address up again.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "internal.cuh"
@@ -30,8 +38,38 @@ static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
 static std::mutex g_noalloc_mu;
 static double* g_noalloc_addr[256] = {nullptr};
+static unsigned long long g_noalloc_ctx[256] = {0};
 
-// Device address of the scratch array on the current device.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Identifier of the calling thread's current context, 0 if none or if the
+// driver does not provide it.
+static unsigned long long current_ctx_id() {
+  static CtxGetCurrentFn get_cur = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    looked = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_cur = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+  }
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (!get_cur || !get_id || get_cur(&c) != CUDA_SUCCESS || c == nullptr || get_id(c, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+// Device address of the scratch array on the current device (looked up once
+// per device and context).
 static bamg_status noalloc_scratch(double** out) {
   int dev = 0;
   BAMG_CUDA(cudaGetDevice(&dev));
@@ -40,6 +78,10 @@ static bamg_status noalloc_scratch(double** out) {
     return BAMG_ERR_UNSUPPORTED;
   }
   std::lock_guard<std::mutex> g(g_noalloc_mu);
+  if (g_noalloc_addr[dev]) {
+    const unsigned long long id = current_ctx_id();
+    if (id == 0 || id != g_noalloc_ctx[dev]) g_noalloc_addr[dev] = nullptr;
+  }
   if (!g_noalloc_addr[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -48,6 +90,7 @@ static bamg_status noalloc_scratch(double** out) {
       return BAMG_ERR_CUDA;
     }
     g_noalloc_addr[dev] = static_cast<double*>(p);
+    g_noalloc_ctx[dev] = current_ctx_id();
   }
   *out = g_noalloc_addr[dev];
   return BAMG_OK;
