@@ -192,20 +192,29 @@ def delaunay_walk(n: int, seed: int = 3, cache_dir: str | None = None) -> Chain:
 
 
 def chain_mix(count: int, seed: int = 4, side_lo: int = 32, side_hi: int = 256,
-              del_lo: int = 1024, del_hi: int = 65536) -> list:
-    """Seeded mix of weighted lattices, tandem queues and Delaunay walks."""
+              del_lo: int = 1024, del_hi: int = 65536, log_sizes: bool = False) -> list:
+    """Seeded mix of weighted lattices, tandem queues and Delaunay walks.
+    Sizes are uniform in the side (lattices, queues) and in the point count
+    (Delaunay walks), or with log_sizes uniform in their logarithms (about
+    4.3M states for 256 chains instead of 7.4M)."""
     rng = np.random.default_rng(seed)
+
+    def draw(lo, hi):
+        if log_sizes:
+            return int(round(float(np.exp(rng.uniform(np.log(lo), np.log(hi))))))
+        return int(rng.integers(lo, hi + 1))
+
     out = []
     for c in range(count):
         kind = int(rng.integers(0, 3))
         if kind == 0:
-            side = int(rng.integers(side_lo, side_hi + 1))
+            side = draw(side_lo, side_hi)
             out.append(lattice2d(side, side, seed=int(rng.integers(1 << 30))))
         elif kind == 1:
-            side = int(rng.integers(side_lo, side_hi + 1))
+            side = draw(side_lo, side_hi)
             out.append(tandem(side))
         else:
-            npts = int(rng.integers(del_lo, del_hi + 1))
+            npts = draw(del_lo, del_hi)
             out.append(delaunay_walk(npts, seed=int(rng.integers(1 << 30))))
     return out
 

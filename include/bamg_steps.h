@@ -74,6 +74,21 @@ bamg_status bamg_step_spmm_block(int prec, int rows, int ld, const int32_t* rp,
                                  const int32_t* ci, const void* val, const void* X,
                                  void* Y, void* stream);
 
+/* The vector kernel of the V-cycle (Section 3, eq. error_propagator_twogrid)
+ * and of GMRES (Section 6): one group of lanes per row of the n x n CSR
+ * matrix B with nnz entries (the group width follows nnz / n, as in the
+ * solver).  mode 0: y = x + omega dinv .* (b - B x), a weighted Jacobi sweep;
+ * mode 1: y = omega dinv .* b, the first sweep from zero; mode 2:
+ * y = b - B x, the residual; mode 3: y = B x; mode 4: y += B x.  x, b, y,
+ * dinv: device vectors of n values in the precision prec (0 = double,
+ * 1 = float); b is not read in modes 3 and 4, x not in mode 1, dinv only in
+ * modes 0 and 1 (NULL allowed otherwise).  y may not alias x or b.
+ * BAMG_ERR_ARG for a missing argument or an unknown mode. */
+bamg_status bamg_step_csr_vec(int prec, int mode, int n, int64_t nnz, const int32_t* rp,
+                              const int32_t* ci, const void* val, const void* dinv,
+                              double omega, const void* x, const void* b, void* y,
+                              void* stream);
+
 /* eq. ls_weights with unit test vectors: for each column k < r,
  * norm_host[k] = ||x_k||_2 and w_host[k] = ||x_k||_2 / ||B x_k||_2 (the
  * square root of omega_k after normalising x_k).  When normalise = 1 the

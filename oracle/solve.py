@@ -159,6 +159,28 @@ def dense_nullvector(A_dense: np.ndarray) -> np.ndarray:
     return normalise_x(Vt[-1])
 
 
+def direct_nullvector(A: sp.csr_matrix) -> np.ndarray:
+    """Stationary vector from its definition (Section 2: B x = 0, x > 0,
+    sum 1) by one sparse LU solve: for an irreducible chain B = I - A has
+    rank n - 1 and 1^T B = 0, so the last equation is implied by the others;
+    replacing it by x_{n-1} = 1 (nonzero, since x > 0) gives a nonsingular
+    system.  One step of iterative refinement, then the 1-norm scaling."""
+    import scipy.sparse.linalg as spl
+    A = sp.csr_matrix(A)
+    n = A.shape[0]
+    C = (sp.identity(n, format="csr") - A).tocoo()
+    keep = C.row != n - 1
+    K = sp.csc_matrix((np.concatenate([C.data[keep], [1.0]]),
+                       (np.concatenate([C.row[keep], [n - 1]]), np.concatenate([C.col[keep], [n - 1]]))),
+                      shape=(n, n))
+    b = np.zeros(n)
+    b[n - 1] = 1.0
+    lu = spl.splu(K, permc_spec="MMD_AT_PLUS_A")
+    x = lu.solve(b)
+    x += lu.solve(b - K @ x)
+    return normalise_x(x)
+
+
 def power_iteration(A: sp.csr_matrix, tol: float = 1e-13, max_iter: int = 10 ** 6):
     """x <- (I + A) x / 2 (lazy chain, aperiodic), 1-norm normalised."""
     n = A.shape[0]

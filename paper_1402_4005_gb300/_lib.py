@@ -101,6 +101,7 @@ SIGNATURES = {
     "bamg_step_relax_block": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, f64, i32, vp]),
     "bamg_step_spmm_block": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp]),
     "bamg_step_jacobi_divisor": (i32, [i32, vp, vp, vp, vp, vp, vp, ip, vp]),
+    "bamg_step_csr_vec": (i32, [i32, i32, i32, C.c_int64, vp, vp, vp, vp, f64, vp, vp, vp, vp]),
     "bamg_step_norms_weights": (i32, [i32, i32, i32, i32, vp, vp, vp, vp, i32, i32, dp, dp, vp]),
     "bamg_step_norms_weights_noalloc": (i32, [i32, i32, i32, i32, vp, vp, vp, vp, i32, i32, dp, dp, vp]),
     "bamg_step_coarsen_geometric": (i32, [i32, i32, vp, vp, vp, vp, ip, vp]),

@@ -357,6 +357,21 @@ def bamg_step_spmm_block(rp, ci, val, X, rows: int, stream=None):
     return Y
 
 
+VEC_MODES = {"jacobi": 0, "jacobi_zero": 1, "resid": 2, "spmv": 3, "spmv_add": 4}
+
+
+def bamg_step_csr_vec(mode: str, rp, ci, val, x=None, b=None, dinv=None, omega=0.7, y=None, stream=None):
+    """One launch of the V-cycle / GMRES vector kernel (see bamg_steps.h)."""
+    ref = x if x is not None else b
+    prec = 1 if ref.dtype == torch.float32 else 0
+    n = rp.shape[0] - 1
+    if y is None:
+        y = torch.zeros(n, dtype=ref.dtype, device="cuda")
+    check(lib().bamg_step_csr_vec(prec, VEC_MODES[mode], n, int(ci.shape[0]), _p(rp), _p(ci), _p(val), _p(dinv),
+                                  float(omega), _p(x), _p(b), _p(y), _stream(stream)), "csr_vec")
+    return y
+
+
 def bamg_step_norms_weights(rp, ci, val, X, r: int, normalise=True, skip_col0=False, stream=None):
     prec = 1 if X.dtype == torch.float32 else 0
     n, ld = X.shape

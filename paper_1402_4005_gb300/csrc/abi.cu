@@ -400,6 +400,22 @@ bamg_status bamg_step_spmm_block(int prec, int rows, int ld, const int32_t* rp, 
   return spmm_block<double>(rows, ld, rp, ci, (const double*)val, (const double*)X, (double*)Y, S(stream));
 }
 
+bamg_status bamg_step_csr_vec(int prec, int mode, int n, int64_t nnz, const int32_t* rp, const int32_t* ci,
+                              const void* val, const void* dinv, double omega, const void* x, const void* b,
+                              void* y, void* stream) {
+  BAMG_CHECK_ARG(n >= 1 && nnz >= 0 && rp && ci && val && y && (prec == 0 || prec == 1));
+  BAMG_CHECK_ARG(mode >= VEC_JACOBI && mode <= VEC_SPMV_ADD);
+  BAMG_CHECK_ARG(mode == VEC_SPMV || mode == VEC_SPMV_ADD || b);
+  BAMG_CHECK_ARG(mode == VEC_JACOBI_ZERO || x);
+  BAMG_CHECK_ARG((mode != VEC_JACOBI && mode != VEC_JACOBI_ZERO) || dinv);
+  const int G = vec_lanes((double)nnz / n);
+  if (prec == 1)
+    return csr_vec<float>(mode, n, G, rp, ci, (const float*)val, (const float*)dinv, (float)omega,
+                          (const float*)x, (const float*)b, (float*)y, S(stream));
+  return csr_vec<double>(mode, n, G, rp, ci, (const double*)val, (const double*)dinv, omega, (const double*)x,
+                         (const double*)b, (double*)y, S(stream));
+}
+
 bamg_status bamg_step_norms_weights(int prec, int n, int ld, int r, const int32_t* rp, const int32_t* ci,
                                     const void* val, void* X, int normalise, int skip_col0, double* norm_host,
                                     double* w_host, void* stream) {

@@ -141,7 +141,7 @@ static bamg_status finish_level(bamg_hierarchy* h, Level& L, int l, cudaStream_t
                             L.dflags.as<int>(), L.dflags.as<int>() + 1, s));
   (void)l;
   double avg = L.n ? (double)L.B.nnz / L.n : 1.0;
-  L.vec_g = avg <= 3 ? 2 : avg <= 6 ? 4 : avg <= 12 ? 8 : avg <= 24 ? 16 : 32;
+  L.vec_g = vec_lanes(avg);
   if (h->mixed) {
     BAMG_TRY(L.B.make32(s));
     BAMG_TRY(L.Bt.make32(s));

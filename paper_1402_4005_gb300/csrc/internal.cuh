@@ -7,6 +7,9 @@ namespace bamg {
 
 enum VecModeHost { VEC_JACOBI = 0, VEC_JACOBI_ZERO = 1, VEC_RESID = 2, VEC_SPMV = 3, VEC_SPMV_ADD = 4 };
 
+// Lanes per row of the vector kernels for a matrix with `avg` entries per row.
+inline int vec_lanes(double avg) { return avg <= 3 ? 2 : avg <= 6 ? 4 : avg <= 12 ? 8 : avg <= 24 ? 16 : 32; }
+
 // sparse.cu
 bamg_status check_rowptr(int n, const int32_t* rp, int64_t nnz, cudaStream_t s);
 bamg_status transpose_csr(int rows, int cols, int nnz, const int32_t* rp, const int32_t* ci,

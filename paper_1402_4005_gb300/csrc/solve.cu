@@ -28,8 +28,7 @@
 namespace bamg {
 
 static int lanes_for(const Csr& A) {
-  double avg = A.rows ? (double)A.nnz / A.rows : 1.0;
-  return avg <= 3 ? 2 : avg <= 6 ? 4 : avg <= 12 ? 8 : avg <= 24 ? 16 : 32;
+  return vec_lanes(A.rows ? (double)A.nnz / A.rows : 1.0);
 }
 
 template <typename T> static const T* dinv_t(const Level& L);

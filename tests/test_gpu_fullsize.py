@@ -138,3 +138,34 @@ def test_ls_fit_counts_rank_deficient_rows_once(api, prec):
         ref = np.linalg.lstsq(A, X[i, :r], rcond=None)[0]
         tol = 1e-12 if prec == "fp64" else 1e-5
         assert np.abs(fit[a:b] - ref).max() <= tol * np.linalg.cond(A) * 10 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("name", ["small", "delaunay", "tandem"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_csr_vec_modes_against_oracle(api, name, prec):
+    """The V-cycle / GMRES vector kernel in all five modes against the
+    oracle's Jacobi sweep and sparse products (1e-12 / 1e-5 scaled)."""
+    if name == "small":
+        ch = cg.delaunay_walk(2999, seed=12)
+        B = operators.build_B(ch.csr()); B.sort_indices()
+        d = operators.diag(B)
+    else:
+        ch, B, d = chain(name)
+    n = ch.n
+    x = rng.uniform_pm1(31, 0, n)
+    b = rng.uniform_pm1(31, 1, n)
+    y0 = rng.uniform_pm1(31, 2, n)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    rp, ci = dev(B.indptr.astype(np.int32)), dev(B.indices.astype(np.int32))
+    va = dev(B.data).to(dt)
+    xd, bd, dinv = dev(x).to(dt), dev(b).to(dt), dev(1.0 / d).to(dt)
+    got = lambda mode, **k: api.bamg_step_csr_vec(mode, rp, ci, va, **k).double().cpu().numpy()
+    ref = smoothing.jacobi(B, d, x[:, None], b[:, None], 0.7)[:, 0]
+    assert scaled_err(got("jacobi", x=xd, b=bd, dinv=dinv), ref, B, x, b) <= tol
+    assert np.abs(got("jacobi_zero", b=bd, dinv=dinv) - 0.7 * b / d).max() <= tol * np.abs(b / d).max()
+    assert scaled_err(got("resid", x=xd, b=bd), b - B @ x, B, x, b) <= tol
+    assert scaled_err(got("spmv", x=xd), B @ x, B, x) <= tol
+    y = dev(y0).to(dt)
+    api.bamg_step_csr_vec("spmv_add", rp, ci, va, x=xd, y=y)
+    assert scaled_err(y.double().cpu().numpy(), y0 + B @ x, B, x, y0) <= tol

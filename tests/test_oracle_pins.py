@@ -714,3 +714,26 @@ def test_initial_x_takes_smallest_abs_sigma_positive_sum_unit_l1():
     assert np.allclose(x, [0.5, -1.0 / 6.0, 1.0 / 3.0], rtol=0, atol=1e-15)
     x2 = S.initial_x(np.array([0.2, -1e-3]), np.array([[1.0, 2.0], [1.0, 2.0]]))
     assert np.allclose(x2, [0.5, 0.5], rtol=0, atol=1e-15)
+
+
+def test_direct_nullvector_against_closed_forms_and_dense():
+    """The sparse direct stationary solve (the definition B x = 0, sum 1)
+    against detailed balance (weighted lattice, Delaunay walk, birth-death)
+    and the dense null space of a tandem queue."""
+    ch = cg.lattice2d(23, 17, seed=9)
+    x = So.direct_nullvector(ch.csr())
+    assert np.abs(x - ch.meta["wdeg"] / ch.meta["wdeg"].sum()).sum() <= 1e-13
+    ch = cg.delaunay_walk(3000, seed=4)
+    x = So.direct_nullvector(ch.csr())
+    assert np.abs(x - ch.meta["deg"] / ch.meta["deg"].sum()).sum() <= 1e-13
+    n = 301
+    ch = cg.birth_death(n, 0.96)
+    x = So.direct_nullvector(ch.csr())
+    A = ch.csr().toarray()
+    xb = np.ones(n)
+    for k in range(n - 1):                 # x_{k+1} = x_k p(k -> k+1) / p(k+1 -> k)
+        xb[k + 1] = xb[k] * A[k + 1, k] / A[k, k + 1]
+    xb /= xb.sum()
+    assert np.abs(x - xb).sum() <= 1e-12
+    ch = cg.tandem(8)
+    assert np.abs(So.direct_nullvector(ch.csr()) - So.dense_nullvector(ch.csr().toarray())).sum() <= 1e-13
