@@ -41,6 +41,11 @@ class Chain:
     meta: dict = field(default_factory=dict)
 
     @property
+    def kind(self) -> str:
+        """Generator family: lattice, uniform, tandem, birthdeath, delaunay."""
+        return self.name.rstrip("0123456789x")
+
+    @property
     def nnz(self) -> int:
         return int(self.row_ptr[-1])
 
