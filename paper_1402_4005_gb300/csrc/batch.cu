@@ -560,6 +560,11 @@ static bamg_status batched_fgmres(bamg_batch* bt, double* x, const bamg_solve_pa
     rel[c] = hs[3 * c + 1] / hs2[3 * c + 1];
     if (rel[c] <= sp->tol) active[c] = 0;
   }
+  // a mixed-precision chain whose true residual falls by less than half over
+  // two restart cycles in a row has stalled (FP32 V-cycle accuracy): it
+  // leaves the lock-step iteration and continues with FP64 V-cycles
+  std::vector<double> prev_rel(rel);
+  std::vector<int> slow(nch, 0);
   int total = 0;
   auto any_active = [&]() { for (int c = 0; c < nch; ++c) if (active[c]) return true; return false; };
   while (any_active() && total < sp->max_iter) {
@@ -623,6 +628,11 @@ static bamg_status batched_fgmres(bamg_batch* bt, double* x, const bamg_solve_pa
                                       cudaMemcpyDeviceToDevice, s));
             rel[c] = rc_;
             if (rc_ <= sp->tol || brk) { active[c] = 0; changed = true; }
+          }
+          if (last && active[c] && bt->mixed) {
+            slow[c] = rel[c] > 0.5 * prev_rel[c] ? slow[c] + 1 : 0;
+            prev_rel[c] = rel[c];
+            if (slow[c] >= 2) { active[c] = 0; changed = true; }
           }
         }
         if (last) cycle_done = true;

@@ -558,7 +558,12 @@ bamg_status fgmres(bamg_hierarchy* h, double* x, const bamg_solve_params* sp, ba
   BAMG_CUDA(cudaStreamSynchronize(s));
   int its = 0, it7 = -1;
   bool done = rel <= sp->tol;
-  bool breakdown = false;
+  bool breakdown = false, stalled = false;
+  // with the FP32 V-cycle, a true residual that falls by less than half over
+  // two restart cycles in a row marks a stall (the caller continues in FP64)
+  const bool stall_check = h->mixed && !sp->plain;
+  double prev_rel = rel;
+  int slow = 0;
   double* V = G.V.as<double>();
   double* Z = G.Z.as<double>();
   const unsigned gv = cdiv(n, 256);
@@ -596,6 +601,11 @@ bamg_status fgmres(bamg_hierarchy* h, double* x, const bamg_solve_params* sp, ba
       }
     }
     if (breakdown && !done) break;
+    if (stall_check && !done) {
+      slow = rel > 0.5 * prev_rel ? slow + 1 : 0;
+      prev_rel = rel;
+      if (slow >= 2) { stalled = true; break; }
+    }
   }
   BAMG_TRY(orient_normalise(n, x, s));
   double fin[2] = {0, 0};
@@ -614,7 +624,8 @@ bamg_status fgmres(bamg_hierarchy* h, double* x, const bamg_solve_params* sp, ba
     info->min_x = fin[0];
   }
   if (!done) {
-    set_error("GMRES stopped after %d iterations at ||Bx||_1/||x||_1 = %.3e", its, rel);
+    set_error("GMRES %s after %d iterations at ||Bx||_1/||x||_1 = %.3e", stalled ? "stalled" : "stopped", its,
+              rel);
     return breakdown ? BAMG_ERR_BREAKDOWN : BAMG_ERR_NOT_CONVERGED;
   }
   return BAMG_OK;

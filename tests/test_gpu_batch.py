@@ -29,6 +29,16 @@ def closed_form(ch):
     return None
 
 
+def reference(ch):
+    """Closed form where detailed balance gives one, else the oracle's
+    direct solve of B x = 0, sum(x) = 1."""
+    cf = closed_form(ch)
+    if cf is not None:
+        return cf
+    from oracle import solve as So
+    return So.direct_nullvector(ch.csr())
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_geometric_batch_matches_single_chain_solves(api, prec):
     chains = [cg.lattice2d(24, seed=3), cg.tandem(20), cg.lattice2d(32, seed=7), cg.tandem(33),
@@ -41,12 +51,7 @@ def test_geometric_batch_matches_single_chain_solves(api, prec):
         xk = x[b.offsets[k]:b.offsets[k + 1]]
         assert infos[k]["rel_res_1"] <= 1e-10, (k, infos[k])
         assert xk.min() > 0 and abs(xk.sum() - 1) < 1e-12
-        h = api.bamg_setup(ch.row_ptr, ch.col, ch.val, ch.n, p, nx=ch.nx, ny=ch.ny)
-        xs, _ = api.bamg_solve(h, restart=20, tol=1e-10)
-        assert np.abs(xk - xs.cpu().numpy()).sum() <= 1e-8, k
-        cf = closed_form(ch)
-        if cf is not None:
-            assert np.abs(xk - cf).sum() <= 1e-8, k
+        assert np.abs(xk - reference(ch)).sum() <= 1e-8, k
 
 
 def test_batched_vcycle_equals_per_chain_vcycles(api):
@@ -102,8 +107,11 @@ def test_mixed_solve_falls_back_to_fp64(api):
     h = api.bamg_setup(torch.from_numpy(ch.row_ptr).cuda(), torch.from_numpy(ch.col).cuda(),
                        torch.from_numpy(ch.val).cuda(), ch.n, p)
     x, info = api.bamg_solve(h, restart=30, tol=1e-12, max_iter=150)
-    assert info["fallback_iterations"] == 150
-    assert info["iterations"] > 150 and info["rel_res_1"] <= 1e-12
+    # the stall is detected at the end of a restart cycle (residual falling by
+    # less than half over two cycles), at the latest when max_iter is reached
+    fb = info["fallback_iterations"]
+    assert 0 < fb <= 150 and (fb % 30 == 0 or fb == 150), fb
+    assert info["iterations"] > fb and info["rel_res_1"] <= 1e-12
     assert np.abs(x.cpu().numpy() - xs).sum() <= 1e-8
     # a hierarchy whose FP32 V-cycle converges takes no fallback
     ch2 = cg.lattice2d(48, seed=9)
@@ -119,11 +127,9 @@ def test_batch_falls_back_per_chain(api):
     b = api.bamg_setup_batched([spec(c) for c in chains], p, host_threads=3)
     x, infos = api.bamg_solve_batched(b, restart=30, tol=1e-12, max_iter=150)
     off = np.concatenate([[0], np.cumsum([c.n for c in chains])])
-    assert infos[1]["fallback_iterations"] == 150
+    assert 0 < infos[1]["fallback_iterations"] <= 150
     assert infos[0]["fallback_iterations"] == 0 and infos[2]["fallback_iterations"] == 0
     x = x.cpu().numpy()
     for k, ch in enumerate(chains):
         assert infos[k]["rel_res_1"] <= 1e-12
-        xs = closed_form(ch)
-        if xs is not None:
-            assert np.abs(x[off[k]:off[k + 1]] - xs).sum() <= 1e-8, k
+        assert np.abs(x[off[k]:off[k + 1]] - reference(ch)).sum() <= 1e-8, k
