@@ -139,6 +139,9 @@ bamg_status ls_fit(int n, int ld, int r, const int32_t* J_rp, const int32_t* J_c
                    const double* w, int constrained, double* out, int* rankdef_dev, cudaStream_t s,
                    double ridge = 0.0);
 
+// mlp_tc.cu: network inference on the tensor cores (err_dev: timeout flag)
+bamg_status mlp_forward_tc(int M, const float* P, const void* X, float* Y, int* err_dev, cudaStream_t s);
+
 // dense.cu
 bamg_status coarsest_solve(int prec, int n, int r, const double* B, const double* M, const double* N,
                            double* sigma, double* U, double* V, double* Bpinv, cudaStream_t s);

@@ -13,9 +13,10 @@
 // order of J_i.  Q weights are shifted to sum to one (Section 5 constraint).
 //
 // Network 64 -> 64 -> 64 -> 16, ReLU, weights and activations BF16,
-// products accumulated in FP32 with mma.sync m16n8k16 tensor-core
-// instructions.  One warp handles 16 points; layer outputs are handed to
-// the next layer through shared memory.  Training: mean squared error on
+// products accumulated in FP32.  Inference runs on the tcgen05 tensor cores
+// with TMEM accumulators (mlp_tc.cu).  The training kernel here uses
+// mma.sync m16n8k16 tiles: one warp handles 16 points, layer outputs are
+// handed to the next layer through shared memory.  Training: mean squared error on
 // the used slots, gradients of all layers by the same warp tiles (block-local
 // FP32 accumulation, one global add per block), Adam on FP32 master weights.
 #include <cuda_bf16.h>
@@ -26,12 +27,10 @@
 #include <vector>
 
 #include "hierarchy.cuh"
+#include "mlp_layout.cuh"
 
 namespace bamg {
 
-constexpr int kF = 64, kH = 64, kO = 16;
-constexpr int kW1 = 0, kB1 = kW1 + kH * kF, kW2 = kB1 + kH, kB2 = kW2 + kH * kH, kW3 = kB2 + kH,
-              kB3 = kW3 + kO * kH, kNParam = kB3 + kO;   // 9360 parameters
 constexpr int kMlpWarps = 4;
 constexpr int kMlpThreads = kMlpWarps * 32;
 
@@ -141,33 +140,6 @@ __device__ inline void load_tile_x(WarpTile& T, const __nv_bfloat16* __restrict_
     T.x[e] = row0 + r < M ? X[(size_t)(row0 + r) * kF + k] : __float2bfloat16(0.f);
   }
   __syncwarp();
-}
-
-// Inference: Y[M x 16] (FP32).
-__global__ void __launch_bounds__(kMlpThreads) mlp_forward_kernel(int M, const float* __restrict__ P,
-                                                                  const __nv_bfloat16* __restrict__ X,
-                                                                  float* __restrict__ Y) {
-  extern __shared__ unsigned char dyn[];
-  MlpSmem& S = *reinterpret_cast<MlpSmem*>(dyn);
-  WarpTile* tiles = reinterpret_cast<WarpTile*>(dyn + sizeof(MlpSmem));
-  load_weights(S, P);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  WarpTile& T = tiles[w];
-  const int ntiles = (M + 15) / 16;
-  for (int tile = blockIdx.x * kMlpWarps + w; tile < ntiles; tile += gridDim.x * kMlpWarps) {
-    const int row0 = tile * 16;
-    load_tile_x(T, X, row0, M);
-    float y[2][4];
-    forward_tile(S, T, y);
-#pragma unroll
-    for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        int row = row0 + g + (q >> 1) * 8, col = nt * 8 + 2 * t + (q & 1);
-        if (row < M) Y[(size_t)row * kO + col] = y[nt][q];
-      }
-    __syncwarp();
-  }
 }
 
 struct GradSmem {
@@ -512,23 +484,27 @@ __global__ void cf_count_kernel(int n, const int8_t* __restrict__ cf, int32_t* _
 }
 
 // ============================================================ host side
-static size_t fwd_smem() { return sizeof(MlpSmem) + kMlpWarps * sizeof(WarpTile); }
-
-static std::atomic<uint64_t> g_fwd_attr{0}, g_grad_attr{0};
+static std::atomic<uint64_t> g_grad_attr{0};
 static size_t grad_smem() {
   return sizeof(MlpSmem) + kMlpWarps * (sizeof(GradSmem) + sizeof(WarpTile) + sizeof(BackTile));
 }
 
+// Inference on the tcgen05 tensor cores (mlp_tc.cu); synchronises the
+// stream to read the kernel's timeout flag.
 bamg_status mlp_forward(int M, const float* P, const void* X, float* Y, cudaStream_t s) {
   if (M <= 0) return BAMG_OK;
-  size_t sm = fwd_smem();
-  int max_dyn = 0;
-  BAMG_TRY(allow_max_smem((const void*)mlp_forward_kernel, g_fwd_attr, &max_dyn));
-  int tiles = (M + 15) / 16;
-  int grid = (int)cdiv(tiles, kMlpWarps);
-  if (grid > 8 * num_sms()) grid = 8 * num_sms();
-  return launch(mlp_forward_kernel, dim3(grid), dim3(kMlpThreads), sm, s, M, P,
-                (const __nv_bfloat16*)X, Y);
+  DevMem err;
+  BAMG_TRY(err.alloc(sizeof(int), s));
+  BAMG_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+  BAMG_TRY(mlp_forward_tc(M, P, X, Y, err.as<int>(), s));
+  int h = 0;
+  BAMG_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BAMG_CUDA(cudaStreamSynchronize(s));
+  if (h) {
+    set_error("network inference kernel gave up waiting for its copies or tensor-core operations");
+    return BAMG_ERR_TIMEOUT;
+  }
+  return BAMG_OK;
 }
 
 bamg_status mlp_grad(int M, float inv_count, const float* P, const void* X, const float* T, const float* mask,

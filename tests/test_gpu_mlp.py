@@ -98,6 +98,24 @@ def test_forward_matches_oracle(api):
     assert Y0.shape == (0, 16)
 
 
+def test_forward_many_tiles_per_block_matches_oracle(api):
+    """The tensor-core inference kernel is persistent over 128-row tiles with
+    double-buffered feature loads: enough rows that every block takes
+    several tiles (both buffers, several barrier phases), a ragged last
+    tile, and an input that starts at a 16-byte offset into its storage."""
+    params = api.bamg_mlp_init(seed=14)
+    m = 128 * 2 * torch.cuda.get_device_properties(0).multi_processor_count * 3 + 77
+    X, _, _ = rand_rows(m + 1, 5)
+    Xt = torch.from_numpy(X).to(torch.bfloat16).cuda()
+    Xv = Xt.view(-1)[64:].view(m, 64)               # rows 1..m of the same storage
+    Y = api.bamg_mlp_forward(params, Xv).cpu().numpy().astype(np.float64)
+    p = params.cpu().numpy().astype(np.float64)
+    Ye = OM.forward(p, X[1:], emulate=True)
+    assert np.linalg.norm(Y - Ye) <= 2e-3 * np.linalg.norm(Ye)
+    rows = np.linalg.norm(Y - Ye, axis=1) / np.maximum(np.linalg.norm(Ye, axis=1), 1e-30)
+    assert np.quantile(rows, 0.999) <= 2e-2
+
+
 def test_gradient_matches_oracle(api):
     params = api.bamg_mlp_init(seed=12)
     m = 16 * 29 + 9
