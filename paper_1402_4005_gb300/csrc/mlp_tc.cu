@@ -4,22 +4,24 @@
 // The network proposes the P-row and Q-column weights of a fine point in
 // place of the least-squares fit of eq. ls_interpolation (not in the paper).
 //
-// Mapping (one CTA of 4 warps, persistent over 128-row tiles, two CTAs per SM):
+// Mapping (one CTA of 8 warps, persistent over 128-row tiles, four CTAs per
+// SM):
 //  * the three weight matrices are converted to BF16 once per CTA and kept
 //    in shared memory in the 128-byte-swizzled K-major layout of the MMA
 //    operands (a row of 64 BF16 = 128 bytes, 8-row groups 1024 bytes apart,
 //    the 16-byte chunk c of row r stored at chunk c ^ (r mod 8));
 //  * the feature tile [128 x 64] is brought in by TMA (cp.async.bulk.tensor,
 //    same swizzle, rows past M zero-filled), double buffered so the next
-//    tile loads while the current one is computed;
+//    tile loads while the current one is computed; once the first layer has
+//    consumed it, the same buffer holds the hidden activations of the tile;
 //  * one thread issues the MMAs (M = 128, K = 16 per instruction, four per
 //    layer) with the accumulators in tensor memory: layer 1 in columns
-//    0-63, layer 2 in 64-127, layer 3 (N = 16) in 128-143;
-//  * after each MMA group completes (tcgen05.commit on an mbarrier), every
-//    thread reads its row of the accumulator (tcgen05.ld, warp w owns TMEM
-//    lanes 32w..32w+31), adds the bias, applies ReLU and writes the BF16 row
-//    into the swizzled A-operand tile of the next layer; the last layer's row
-//    goes straight to global memory (64 contiguous bytes per thread).
+//    0-63, layer 2 in 64-127, layer 3 (N = 16) again in 0-15;
+//  * after each MMA group completes (tcgen05.commit on an mbarrier), the
+//    threads read the accumulator (tcgen05.ld; warps w and w + 4 share the
+//    TMEM lanes 32(w mod 4).., one half of the columns each), add the bias,
+//    apply ReLU and write BF16 rows into the swizzled A-operand tile of the
+//    next layer; the last layer's row goes straight to global memory.
 // Every wait is bounded (2 s of globaltimer); a CTA that gives up sets
 // *err, waits (bounded) for its copies and MMAs in flight, frees its tensor
 // memory and returns.
@@ -37,22 +39,20 @@ namespace bamg {
 namespace {
 
 constexpr int kTileM = 128;
-constexpr int kTcThreads = 128;
-constexpr uint32_t kTmemCols = 256;
+constexpr int kTcThreads = 256;
+constexpr uint32_t kTmemCols = 128;
 constexpr uint32_t kTileBytes = kTileM * 128;            // 128 rows of 64 BF16
 // shared memory map (byte offsets from a 1024-byte aligned base)
 constexpr uint32_t kOffW1 = 0;                           // 64 rows
 constexpr uint32_t kOffW2 = kOffW1 + 64 * 128;           // 64 rows
 constexpr uint32_t kOffW3 = kOffW2 + 64 * 128;           // 16 rows
-constexpr uint32_t kOffX0 = kOffW3 + 16 * 128;           // feature tile, buffer 0
-constexpr uint32_t kOffX1 = kOffX0 + kTileBytes;         // feature tile, buffer 1
-constexpr uint32_t kOffH1 = kOffX1 + kTileBytes;         // layer-1 activations
-constexpr uint32_t kOffH2 = kOffH1 + kTileBytes;         // layer-2 activations
-constexpr uint32_t kOffBias = kOffH2 + kTileBytes;       // b1, b2, b3 (FP32)
-constexpr uint32_t kOffBar = kOffBias + 1024;            // mbarriers, TMEM address, flags
+constexpr uint32_t kOffX0 = kOffW3 + 16 * 128;           // feature / activation tile, buffer 0
+constexpr uint32_t kOffX1 = kOffX0 + kTileBytes;         // buffer 1
+constexpr uint32_t kOffBias = kOffX1 + kTileBytes;       // b1, b2, b3 (FP32)
+constexpr uint32_t kOffBar = kOffBias + 1024;            // mbarriers, TMEM address
 constexpr uint32_t kSmemUsed = kOffBar + 64;
 constexpr uint32_t kSmemAlloc = kSmemUsed + 1024;        // slack for the 1024-byte alignment
-static_assert(kOffX0 % 1024 == 0 && kOffH1 % 1024 == 0 && kOffH2 % 1024 == 0, "operand tiles 1024-aligned");
+static_assert(kOffX0 % 1024 == 0 && kOffX1 % 1024 == 0, "operand tiles 1024-aligned");
 
 constexpr unsigned long long kWaitNs = 2000000000ull;    // bound of every wait
 
@@ -157,21 +157,20 @@ __device__ inline void stage_weights(uint8_t* base, uint32_t off, const float* _
   }
 }
 
-// accumulator columns [col, col + 64) of this thread's row, + bias, ReLU,
+// accumulator columns [32 h, 32 h + 32) of this thread's row, + bias, ReLU,
 // BF16 into row `row` of the swizzled tile at `off`
-__device__ inline void hidden_epilogue(uint8_t* base, uint32_t off, uint32_t tacc, const float* bias, int row) {
-  uint32_t r[64];
-  tmem_ld16(tacc + 0, *reinterpret_cast<uint32_t(*)[16]>(r + 0));
-  tmem_ld16(tacc + 16, *reinterpret_cast<uint32_t(*)[16]>(r + 16));
-  tmem_ld16(tacc + 32, *reinterpret_cast<uint32_t(*)[16]>(r + 32));
-  tmem_ld16(tacc + 48, *reinterpret_cast<uint32_t(*)[16]>(r + 48));
+__device__ inline void hidden_epilogue(uint8_t* base, uint32_t off, uint32_t tacc, const float* bias, int row,
+                                       int h) {
+  uint32_t r[32];
+  tmem_ld16(tacc + 32 * h, *reinterpret_cast<uint32_t(*)[16]>(r + 0));
+  tmem_ld16(tacc + 32 * h + 16, *reinterpret_cast<uint32_t(*)[16]>(r + 16));
   tmem_wait_ld();
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
+  for (int c = 0; c < 4; ++c) {
     float v[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = fmaxf(__uint_as_float(r[8 * c + q]) + bias[8 * c + q], 0.f);
-    *reinterpret_cast<uint4*>(base + off + sw128(row, c)) =
+    for (int q = 0; q < 8; ++q) v[q] = fmaxf(__uint_as_float(r[8 * c + q]) + bias[32 * h + 8 * c + q], 0.f);
+    *reinterpret_cast<uint4*>(base + off + sw128(row, 4 * h + c)) =
         make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
   }
 }
@@ -185,7 +184,7 @@ __device__ inline void issue_layer(uint32_t sbase, uint32_t a_off, uint32_t b_of
 
 }  // namespace
 
-__global__ void __launch_bounds__(kTcThreads, 2)
+__global__ void __launch_bounds__(kTcThreads, 4)
 mlp_forward_tc_kernel(const __grid_constant__ CUtensorMap xmap, int M, const float* __restrict__ P,
                       float* __restrict__ Y, int* __restrict__ err) {
   extern __shared__ uint8_t dyn_smem[];
@@ -221,7 +220,8 @@ mlp_forward_tc_kernel(const __grid_constant__ CUtensorMap xmap, int M, const flo
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;   // this warp's TMEM lanes
+  const int row = tid & (kTileM - 1), half = tid >> 7;
+  const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;   // this warp's TMEM lanes
   const uint32_t id64 = idesc_bf16(kTileM, 64), id16 = idesc_bf16(kTileM, 16);
 
   const int ntiles = (M + kTileM - 1) / kTileM;
@@ -266,13 +266,13 @@ mlp_forward_tc_kernel(const __grid_constant__ CUtensorMap xmap, int M, const flo
     par_m ^= 1u;
     mma_pending = false;
     fence_after_sync();
-    hidden_epilogue(base, kOffH1, tmem + lane_off + 0, bias, tid);
+    hidden_epilogue(base, offx, tmem + lane_off + 0, bias, row, half);
     fence_async_smem();
     fence_before_sync();
     __syncthreads();
     if (tid == 0) {
       fence_after_sync();
-      issue_layer(sbase, kOffH1, kOffW2, tmem + 64, id64);
+      issue_layer(sbase, offx, kOffW2, tmem + 64, id64);
       mma_commit(bar_mma);
       mma_pending = true;
     }
@@ -282,13 +282,13 @@ mlp_forward_tc_kernel(const __grid_constant__ CUtensorMap xmap, int M, const flo
     par_m ^= 1u;
     mma_pending = false;
     fence_after_sync();
-    hidden_epilogue(base, kOffH2, tmem + lane_off + 64, bias + 64, tid);
+    hidden_epilogue(base, offx, tmem + lane_off + 64, bias + 64, row, half);
     fence_async_smem();
     fence_before_sync();
     __syncthreads();
     if (tid == 0) {
       fence_after_sync();
-      issue_layer(sbase, kOffH2, kOffW3, tmem + 128, id16);
+      issue_layer(sbase, offx, kOffW3, tmem + 0, id16);
       mma_commit(bar_mma);
       mma_pending = true;
     }
@@ -298,13 +298,13 @@ mlp_forward_tc_kernel(const __grid_constant__ CUtensorMap xmap, int M, const flo
     par_m ^= 1u;
     mma_pending = false;
     fence_after_sync();
-    {
+    if (half == 0) {
       uint32_t r[16];
-      tmem_ld16(tmem + lane_off + 128, r);
+      tmem_ld16(tmem + lane_off + 0, r);
       tmem_wait_ld();
-      const int row = t * kTileM + tid;
-      if (row < M) {
-        float4* y = reinterpret_cast<float4*>(Y + (size_t)row * kO);
+      const int grow = t * kTileM + row;
+      if (grow < M) {
+        float4* y = reinterpret_cast<float4*>(Y + (size_t)grow * kO);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
           y[q] = make_float4(__uint_as_float(r[4 * q + 0]) + bias[128 + 4 * q + 0],
@@ -389,7 +389,7 @@ bamg_status mlp_forward_tc(int M, const float* P, const void* X, float* Y, int* 
     return BAMG_ERR_UNSUPPORTED;
   }
   const int ntiles = (M + kTileM - 1) / kTileM;
-  int grid = 2 * num_sms();
+  int grid = 4 * num_sms();
   if (grid > ntiles) grid = ntiles;
   return launch(mlp_forward_tc_kernel, dim3(grid), dim3(kTcThreads), (size_t)kSmemAlloc, s, map, M, P, Y, err_dev);
 }
