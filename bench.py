@@ -84,7 +84,7 @@ def load_peaks():
 
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 50 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -99,7 +99,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "50"],
+                 "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -207,6 +207,9 @@ def gpu_arm(args, rank: int, world: int):
         return times, infos, last, launches
 
     with ClockSampler(dev) as clk:
+        # nvidia-smi's start-up (driver initialisation) stalls CUDA calls of
+        # this process for a moment: let it pass before the warm-up steps
+        time.sleep(1.0)
         t_mix, i_mix, (h_mix, x_mix), launches = timed("mixed", args.steps, args.warmup)
     t_64, i_64, (h_64, x_64), _ = timed("fp64", max(3, args.steps // 2), 3)
     # the Gauss-Seidel splitting of Section 3 in multicolour order as the

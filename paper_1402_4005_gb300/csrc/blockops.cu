@@ -283,32 +283,67 @@ __global__ void inject_kernel(int nc, const int32_t* __restrict__ cpt, const T* 
 }
 
 // ------------------------------------------------------- vector kernels
-// One group of G lanes per row; modes of the V-cycle and GMRES.
+// One group of G lanes per row, RU consecutive rows per group; modes of the
+// V-cycle and GMRES.  The loads of the RU rows are issued together (column
+// indices and values, then the gathers of x) so that RU times more memory
+// requests are in flight per lane than with one row per group; each row
+// still sums its products lane by lane in the order p0 + g, p0 + g + G, ...
+// and then across the group, so the result does not depend on RU.
 enum VecMode { kJacobi = 0, kJacobiZero = 1, kResid = 2, kSpmv = 3, kSpmvAdd = 4 };
 
-template <typename T, int G, int MODE>
+template <typename T, int G, int MODE, int RU>
 __global__ void __launch_bounds__(256)
 csr_vec_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                const T* __restrict__ va, const T* __restrict__ dinv, T omega, const T* __restrict__ x,
                const T* __restrict__ b, T* __restrict__ y) {
-  int lane = threadIdx.x & 31;
-  int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) / G);
-  int g = lane % G;
-  bool valid = i < n;  // every lane joins the shuffles below
-  T acc = T(0);
+  const int lane = threadIdx.x & 31;
+  const size_t grp = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int g = lane % G;
+  const long long i0 = (long long)grp * RU;   // every lane joins the shuffles below
+  T acc[RU];
+#pragma unroll
+  for (int u = 0; u < RU; ++u) acc[u] = T(0);
   if (MODE != kJacobiZero) {
-    if (valid) {
-      int p1 = __ldg(rp + i + 1);
-      for (int p = __ldg(rp + i) + g; p < p1; p += G) acc = fma(__ldg(va + p), __ldg(x + __ldg(ci + p)), acc);
+    int p0[RU], p1[RU];
+    int len = 0;
+#pragma unroll
+    for (int u = 0; u < RU; ++u) {
+      const bool v = i0 + u < n;
+      p0[u] = v ? __ldg(rp + i0 + u) : 0;
+      p1[u] = v ? __ldg(rp + i0 + u + 1) : 0;
+      len = max(len, p1[u] - p0[u]);
     }
-    acc = group_sum<G>(acc);
+    for (int off = g; off < len; off += G) {
+      int c[RU];
+      T a[RU];
+#pragma unroll
+      for (int u = 0; u < RU; ++u) {
+        const int p = p0[u] + off;
+        const bool in = p < p1[u];
+        c[u] = in ? __ldg(ci + p) : -1;
+        a[u] = in ? __ldg(va + p) : T(0);
+      }
+      T xv[RU];
+#pragma unroll
+      for (int u = 0; u < RU; ++u) xv[u] = c[u] >= 0 ? __ldg(x + c[u]) : T(0);
+#pragma unroll
+      for (int u = 0; u < RU; ++u)
+        if (c[u] >= 0) acc[u] = fma(a[u], xv[u], acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < RU; ++u) acc[u] = group_sum<G>(acc[u]);
   }
-  if (!valid || g != 0) return;
-  if (MODE == kJacobi) y[i] = x[i] + (omega * (b[i] - acc)) * dinv[i];
-  else if (MODE == kJacobiZero) y[i] = (omega * b[i]) * dinv[i];
-  else if (MODE == kResid) y[i] = b[i] - acc;
-  else if (MODE == kSpmv) y[i] = acc;
-  else y[i] = y[i] + acc;
+  if (g != 0) return;
+#pragma unroll
+  for (int u = 0; u < RU; ++u) {
+    const long long i = i0 + u;
+    if (i >= n) break;
+    if (MODE == kJacobi) y[i] = x[i] + (omega * (b[i] - acc[u])) * dinv[i];
+    else if (MODE == kJacobiZero) y[i] = (omega * b[i]) * dinv[i];
+    else if (MODE == kResid) y[i] = b[i] - acc[u];
+    else if (MODE == kSpmv) y[i] = acc[u];
+    else y[i] = y[i] + acc[u];
+  }
 }
 
 template <typename T>
@@ -530,16 +565,26 @@ bamg_status inject(int nc, int ld, const int32_t* cpt, const T* X, T* Xc, cudaSt
   BAMG_LD_DISPATCH(ld, return launch(inject_kernel<T, LDC>, dim3(g), dim3(256), 0, s, nc, cpt, X, Xc));
 }
 
+// rows per lane group: short rows take several per group
+template <int G> constexpr int vec_rows() { return G <= 4 ? 4 : G == 8 ? 2 : 1; }
+
+template <typename T, int G, int MODE>
+static bamg_status vec_launch(int n, const int32_t* rp, const int32_t* ci, const T* va, const T* dinv, T omega,
+                              const T* x, const T* b, T* y, cudaStream_t s) {
+  constexpr int RU = vec_rows<G>();
+  const unsigned g = cdiv((long long)cdiv(n, RU) * G, 256);
+  return launch(csr_vec_kernel<T, G, MODE, RU>, dim3(g), dim3(256), 0, s, n, rp, ci, va, dinv, omega, x, b, y);
+}
+
 template <typename T, int MODE>
 static bamg_status vec_g(int n, int G, const int32_t* rp, const int32_t* ci, const T* va, const T* dinv,
                          T omega, const T* x, const T* b, T* y, cudaStream_t s) {
-  unsigned g = cdiv((long long)n * G, 256);
   switch (G) {
-    case 2: return launch(csr_vec_kernel<T, 2, MODE>, dim3(g), dim3(256), 0, s, n, rp, ci, va, dinv, omega, x, b, y);
-    case 4: return launch(csr_vec_kernel<T, 4, MODE>, dim3(g), dim3(256), 0, s, n, rp, ci, va, dinv, omega, x, b, y);
-    case 8: return launch(csr_vec_kernel<T, 8, MODE>, dim3(g), dim3(256), 0, s, n, rp, ci, va, dinv, omega, x, b, y);
-    case 16: return launch(csr_vec_kernel<T, 16, MODE>, dim3(g), dim3(256), 0, s, n, rp, ci, va, dinv, omega, x, b, y);
-    default: return launch(csr_vec_kernel<T, 32, MODE>, dim3(g), dim3(256), 0, s, n, rp, ci, va, dinv, omega, x, b, y);
+    case 2: return vec_launch<T, 2, MODE>(n, rp, ci, va, dinv, omega, x, b, y, s);
+    case 4: return vec_launch<T, 4, MODE>(n, rp, ci, va, dinv, omega, x, b, y, s);
+    case 8: return vec_launch<T, 8, MODE>(n, rp, ci, va, dinv, omega, x, b, y, s);
+    case 16: return vec_launch<T, 16, MODE>(n, rp, ci, va, dinv, omega, x, b, y, s);
+    default: return vec_launch<T, 32, MODE>(n, rp, ci, va, dinv, omega, x, b, y, s);
   }
 }
 
