@@ -50,7 +50,7 @@ WORKLOAD = {"workload": "tandem queue 256x256 (65,536 states, nnz(B)=261,121), r
             "setup_relaxations": 5}
 SIDE = 256
 KW = dict(r=16, max_levels=5, coarse_min=1, seed=2)
-SECTIONS = ("learned", "batched", "delaunay", "sparse", "birthdeath", "kernels")
+SECTIONS = ("learned", "batched", "delaunay", "sparse", "birthdeath", "kernels", "mlpfwd")
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (4 partitions x 32)
 # DRAM bytes (read + write) of one coarsest_kernel<float> launch of this
 # workload from an ncu capture, valid only while the kernel's source file is
@@ -258,6 +258,8 @@ def gpu_arm(args, rank: int, world: int):
 def run_sections(args, api, torch, stream, out):
     for name, fn in (("sparse", lambda *a: roofline_sparse(*a, side=args.sparse_side)),
                      ("kernels", kernel_rooflines),
+                     ("mlpfwd", lambda a, t, st: mlp_forward_roofline(a, t, st) if "kernels" not in args.sections
+                      else {"in": "roofline_kernels"}),
                      ("learned", learned_section), ("batched", batched_section),
                      ("delaunay", delaunay_section), ("birthdeath", birthdeath_section)):
         if name in args.sections:
@@ -479,16 +481,30 @@ def kernel_rooflines(api, torch, stream):
                     note="step call: two launches (FP32 pass, FP64 refit of flagged rows) and a host read")
             X = V = None
             torch.cuda.empty_cache()
-        # network inference on the fine points of config 5 (3/4 of 2048^2)
+    out.update(mlp_forward_roofline(api, torch, stream, flush))
+    return out
+
+
+def mlp_forward_roofline(api, torch, stream, flush=None):
+    """Network inference (tcgen05) on the 3,145,728 fine points of the
+    2048 x 2048 tandem queue (random BF16 features), against HBM."""
+    hbm, src, _ = load_peaks()
+    if flush is None:
+        flush = (torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda"),
+                 torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda"))
+    with torch.cuda.stream(stream):
         params = api.bamg_mlp_init(seed=5, stream=stream)
         npts = 3 * 2048 * 2048 // 4
         Xf = (torch.rand((npts, 64), device="cuda") * 2 - 1).to(torch.bfloat16)
         ms = per_launch_ms(torch, stream, lambda: api.bamg_mlp_forward(params, Xf, stream=stream), 8, flush)
-        alg = npts * (64 * 2 + 16 * 4)
-        rec("mlp_forward_config5", alg, ms, kernel="mlp_forward_kernel", workload=f"{npts} fine points",
-            flops=npts * 2 * (64 * 64 * 2 + 64 * 16))
-        out["mlp_forward_config5"]["tflops"] = round(npts * 2 * (64 * 64 * 2 + 64 * 16) / (ms * 1e-3) / 1e12, 2)
-    return out
+    alg = npts * (64 * 2 + 16 * 4)
+    flops = npts * 2 * (64 * 64 * 2 + 64 * 16)
+    gbs = alg / (ms * 1e-3) / 1e9
+    return {"mlp_forward_config5": {
+        "bound": "hbm", "achieved": round(gbs, 1), "frac": round(gbs / hbm, 4), "unit": "GB/s",
+        "launch_us": round(ms * 1e3, 2), "alg_bytes": int(alg), "kernel": "mlp_forward_tc_kernel (tcgen05)",
+        "workload": f"{npts} fine points", "flops": flops, "tflops": round(flops / (ms * 1e-3) / 1e12, 2),
+        "note": "CUDA events around the step call: the kernel plus its host part (flag set/read, tensor map)"}}
 
 
 # ---------------------------------------------------------------- learned (config 5)
@@ -982,7 +998,7 @@ def main():
         **acc,
         "clocks": r["clocks"],
     }
-    for k in ("sparse", "kernels", "learned", "batched", "delaunay", "birthdeath"):
+    for k in ("sparse", "kernels", "learned", "batched", "delaunay", "birthdeath"):   # mlpfwd: profiling runs only
         if k in r:
             line["roofline_sparse" if k == "sparse" else "roofline_kernels" if k == "kernels" else k] = r[k]
     print(json.dumps(line))
