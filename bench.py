@@ -508,19 +508,6 @@ def mlp_forward_roofline(api, torch, stream, flush=None):
 
 
 # ---------------------------------------------------------------- learned (config 5)
-def training_chains(count=512, seed=6, lo=64, hi=512):
-    """The seeded training set of the network: half tandem queues, half
-    weighted lattices, sides uniform in [lo, hi]."""
-    import numpy as np
-    import chaingen as cg
-    g = np.random.default_rng(seed)
-    out = []
-    for k in range(count):
-        side = int(g.integers(lo, hi + 1))
-        out.append(cg.tandem(side) if k % 2 == 0 else cg.lattice2d(side, seed=int(g.integers(1 << 30))))
-    return out
-
-
 def learned_section(api, torch, stream, eval_side=2048, train_count=512, rows_per_level=2048):
     """Network fits against LS fits on a 2048 x 2048 tandem queue.  The
     network is trained first, on the LS weights of bootstrap setups of 512
@@ -531,7 +518,8 @@ def learned_section(api, torch, stream, eval_side=2048, train_count=512, rows_pe
     1-norm error to 1e-8."""
     import numpy as np
     t0 = time.perf_counter()
-    train = training_chains(train_count)
+    import chaingen as cg
+    train = cg.training_mix(train_count, seed=6)
     t_gen = time.perf_counter() - t0
     Xs, Ts, Ms = [], [], []
     dropped = 0

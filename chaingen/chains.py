@@ -226,3 +226,15 @@ def chain_mix(count: int, seed: int = 4, side_lo: int = 32, side_hi: int = 256,
 
 def to_dense(ch: Chain) -> np.ndarray:
     return ch.csr().toarray()
+
+
+def training_mix(count: int = 512, seed: int = 6, lo: int = 64, hi: int = 512) -> list:
+    """Seeded training chains of the interpolation network: tandem queues and
+    weighted lattices alternating, sides uniform in [lo, hi]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        side = int(rng.integers(lo, hi + 1))
+        out.append(tandem(side) if k % 2 == 0 else lattice2d(side, side, seed=int(rng.integers(1 << 30))))
+    return out
+
