@@ -363,6 +363,14 @@ __global__ void convert_kernel(size_t n, const S* __restrict__ a, D* __restrict_
   if (t < n) b[t] = D(a[t]);
 }
 
+// up to kConvMany double arrays to float in one launch (blockIdx.y = array)
+__global__ void convert_many_kernel(ConvMany job) {
+  const int q = blockIdx.y;
+  const size_t n = job.n[q];
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    job.dst[q][t] = float(job.src[q][t]);
+}
+
 // Jacobi divisor of row i (Section 3: x <- x + omega D^{-1} (b - B x)).
 // d_i = b_ii when b_ii > 0.  A coarse Petrov-Galerkin operator Q B P may have
 // b_ii <= 0, where that step is undefined; there d_i is the larger of the l1
@@ -608,6 +616,15 @@ bamg_status dense_gemv(int n, const T* A, const T* x, T* y, cudaStream_t s) {
 template <typename S, typename D>
 bamg_status convert(size_t n, const S* a, D* b, cudaStream_t s) {
   return launch(convert_kernel<S, D>, dim3(cdiv((long long)n, 256)), dim3(256), 0, s, n, a, b);
+}
+
+bamg_status convert_many(const ConvMany& job, cudaStream_t s) {
+  if (job.k <= 0) return BAMG_OK;
+  size_t mx = 0;
+  for (int q = 0; q < job.k; ++q) mx = job.n[q] > mx ? job.n[q] : mx;
+  unsigned g = cdiv((long long)(mx > 0 ? mx : 1), 256);
+  if (g > 4096u) g = 4096u;
+  return launch(convert_many_kernel, dim3(g, job.k), dim3(256), 0, s, job);
 }
 
 template <typename T>

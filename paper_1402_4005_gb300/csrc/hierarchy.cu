@@ -143,12 +143,16 @@ static bamg_status finish_level(bamg_hierarchy* h, Level& L, int l, cudaStream_t
   double avg = L.n ? (double)L.B.nnz / L.n : 1.0;
   L.vec_g = vec_lanes(avg);
   if (h->mixed) {
-    BAMG_TRY(L.B.make32(s));
-    BAMG_TRY(L.Bt.make32(s));
+    ConvMany job;
+    BAMG_TRY(L.B.add32(job, s));
+    BAMG_TRY(L.Bt.add32(job, s));
     BAMG_TRY(L.dinv32.alloc(sizeof(float) * L.n, s));
-    BAMG_TRY(convert<double, float>((size_t)L.n, L.dinv.as<double>(), L.dinv32.as<float>(), s));
-    if (!L.M.empty()) BAMG_TRY(L.M.make32(s));
-    if (!L.N.empty()) BAMG_TRY(L.N.make32(s));
+    job.src[job.k] = L.dinv.as<double>();
+    job.dst[job.k] = L.dinv32.as<float>();
+    job.n[job.k++] = (size_t)L.n;
+    if (!L.M.empty()) BAMG_TRY(L.M.add32(job, s));
+    if (!L.N.empty()) BAMG_TRY(L.N.add32(job, s));
+    BAMG_TRY(convert_many(job, s));
   }
   return BAMG_OK;
 }
@@ -304,9 +308,11 @@ static bamg_status coarsen_level(bamg_hierarchy* h, int l, DevMem& U, DevMem& V,
   BAMG_TRY(finish_level(h, Lc, l + 1, s));
   tr.mark(s, "finish coarse", l);
   if (h->mixed) {
-    BAMG_TRY(Lf.P.make32(s));
-    BAMG_TRY(Lf.Qt.make32(s));
-    BAMG_TRY(Lf.Q.make32(s));
+    ConvMany job;
+    BAMG_TRY(Lf.P.add32(job, s));
+    BAMG_TRY(Lf.Qt.add32(job, s));
+    BAMG_TRY(Lf.Q.add32(job, s));
+    BAMG_TRY(convert_many(job, s));
   }
   if (learned) return BAMG_OK;
   // injection of the test vectors

@@ -24,6 +24,16 @@ struct Csr {
     BAMG_TRY(va32.alloc(sizeof(float) * (nnz > 0 ? nnz : 1), s));
     return convert<double, float>((size_t)nnz, v(), va32.as<float>(), s);
   }
+  // allocate the float copy and queue its conversion in `job` (one launch
+  // for several matrices)
+  bamg_status add32(ConvMany& job, cudaStream_t s) {
+    BAMG_TRY(va32.alloc(sizeof(float) * (nnz > 0 ? nnz : 1), s));
+    job.src[job.k] = v();
+    job.dst[job.k] = va32.as<float>();
+    job.n[job.k] = (size_t)nnz;
+    ++job.k;
+    return BAMG_OK;
+  }
   bool empty() const { return rows == 0; }
 };
 template <> inline const double* Csr::vals<double>() const { return va.as<double>(); }

@@ -7,6 +7,27 @@ namespace bamg {
 
 enum VecModeHost { VEC_JACOBI = 0, VEC_JACOBI_ZERO = 1, VEC_RESID = 2, VEC_SPMV = 3, VEC_SPMV_ADD = 4 };
 
+// Several double -> float conversions in one launch.
+constexpr int kConvMany = 8;
+struct ConvMany {
+  int k = 0;
+  const double* src[kConvMany];
+  float* dst[kConvMany];
+  size_t n[kConvMany];
+};
+bamg_status convert_many(const ConvMany& job, cudaStream_t s);
+
+// Several exclusive scans (out[q][0..n[q]], out[q][n[q]] = total), one
+// launch when every array is short enough for one block.
+constexpr int kScanMany = 4;
+struct ScanMany {
+  int k = 0;
+  const int32_t* in[kScanMany];
+  int32_t* out[kScanMany];
+  int n[kScanMany];
+};
+bamg_status scan_many(const ScanMany& job, cudaStream_t s);
+
 // Lanes per row of the vector kernels for a matrix with `avg` entries per row.
 inline int vec_lanes(double avg) { return avg <= 3 ? 2 : avg <= 6 ? 4 : avg <= 12 ? 8 : avg <= 24 ? 16 : 32; }
 

@@ -122,14 +122,15 @@ __global__ void scan_apply(const int32_t* __restrict__ in, int n, const long lon
 }
 
 // Arrays up to kScanOneBlock entries: one block of 1024 threads, each
-// scanning a contiguous chunk of at most 8 (chunk sums, a block scan of
+// scanning a contiguous chunk of at most 64 (chunk sums, a block scan of
 // them, then the chunk prefixes), so the scan is a single launch.  Larger
 // arrays take the three-launch tiled scan, which spreads over the SMs.
 constexpr int kScanOneThreads = 1024;
-constexpr int kScanOneBlock = 8 * kScanOneThreads;
+constexpr int kScanOneBlock = 64 * kScanOneThreads;
 
-__global__ void __launch_bounds__(kScanOneThreads) scan_one_block(const int32_t* __restrict__ in, int n,
-                                                                   int32_t* __restrict__ out) {
+// Exclusive scan of in[0..n) into out[0..n] by the calling block (1024
+// threads, n <= kScanOneBlock).
+__device__ void scan_block_body(const int32_t* __restrict__ in, int n, int32_t* __restrict__ out) {
   __shared__ long long sh[kScanOneThreads / 32];
   const int chunk = (n + kScanOneThreads - 1) / kScanOneThreads;
   const int b = threadIdx.x * chunk, e = min(n, b + chunk);
@@ -160,6 +161,25 @@ __global__ void __launch_bounds__(kScanOneThreads) scan_one_block(const int32_t*
     run += in[i];
   }
   if (threadIdx.x == kScanOneThreads - 1) out[n] = (int32_t)sh[kScanOneThreads / 32 - 1];
+}
+
+__global__ void __launch_bounds__(kScanOneThreads) scan_one_block(const int32_t* __restrict__ in, int n,
+                                                                   int32_t* __restrict__ out) {
+  scan_block_body(in, n, out);
+}
+
+// several independent scans, one block each (blockIdx.x = array)
+__global__ void __launch_bounds__(kScanOneThreads) scan_many_kernel(ScanMany job) {
+  const int q = blockIdx.x;
+  scan_block_body(job.in[q], job.n[q], job.out[q]);
+}
+
+bamg_status scan_many(const ScanMany& job, cudaStream_t s) {
+  bool one = true;
+  for (int q = 0; q < job.k; ++q) one = one && job.n[q] <= kScanOneBlock;
+  if (one) return job.k > 0 ? launch(scan_many_kernel, dim3(job.k), dim3(kScanOneThreads), 0, s, job) : BAMG_OK;
+  for (int q = 0; q < job.k; ++q) BAMG_TRY(scan_counts(job.in[q], job.out[q], job.n[q], s, nullptr));
+  return BAMG_OK;
 }
 
 bamg_status scan_counts(const int32_t* counts, int32_t* out, int n, cudaStream_t s,

@@ -294,6 +294,62 @@ __global__ void compact_rows_kernel(int m, const int32_t* __restrict__ src_rp, c
   }
 }
 
+// ------------------------------------------------- several products at once
+// Up to kMaxJobs independent products share each launch (blockIdx.y = job).
+constexpr int kMaxJobs = 4;
+struct SpJobs {
+  int k = 0;
+  int m[kMaxJobs];
+  const int32_t *arp[kMaxJobs], *aci[kMaxJobs], *brp[kMaxJobs], *bci[kMaxJobs];
+  const double *ava[kMaxJobs], *bva[kMaxJobs];
+  int32_t *prod[kMaxJobs], *offs[kMaxJobs], *cnts[kMaxJobs];
+  int* stats[kMaxJobs];
+  int32_t* scol[kMaxJobs];
+  double* sval[kMaxJobs];
+  const int32_t* crp[kMaxJobs];
+  int32_t* cci[kMaxJobs];
+  double* cva[kMaxJobs];
+};
+
+__global__ void count_products_multi(SpJobs J) {
+  const int q = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= J.m[q]) return;
+  long long c = 0;
+  for (int p = J.arp[q][i]; p < J.arp[q][i + 1]; ++p) {
+    const int k = J.aci[q][p];
+    c += J.brp[q][k + 1] - J.brp[q][k];
+  }
+  const int ci = c > INT32_MAX ? INT32_MAX : (int)c;
+  J.prod[q][i] = ci;
+  atomicMax(J.stats[q], ci);
+  atomicAdd(reinterpret_cast<unsigned long long*>(J.stats[q] + 2), (unsigned long long)c);
+}
+
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) spgemm_warp_multi(SpJobs J) {
+  __shared__ unsigned long long skey[kWarpsPerBlock][kWarpCap];
+  __shared__ double sval[kWarpsPerBlock][kWarpCap];
+  __shared__ int sflag[kWarpsPerBlock][kWarpCap];
+  const int q = blockIdx.y;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kWarpsPerBlock + w;
+  if (i >= J.m[q]) return;
+  row_product<32, true>(i, -1, kWarpCap, J.prod[q], J.arp[q], J.aci[q], J.ava[q], J.brp[q], J.bci[q], J.bva[q],
+                        J.cnts[q], J.offs[q], J.scol[q], J.sval[q], skey[w], sval[w], sflag[w], lane);
+}
+
+__global__ void compact_rows_multi(SpJobs J) {
+  const int q = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (i >= J.m[q]) return;
+  const int a = J.offs[q][i], b = J.crp[q][i], c = J.cnts[q][i];
+  for (int t = lane; t < c; t += 32) {
+    J.cci[q][b + t] = J.scol[q][a + t];
+    J.cva[q][b + t] = J.sval[q][a + t];
+  }
+}
+
 // One expansion pass: each row's sorted, summed entries go to a scratch
 // slot of its product count, then the rows are packed into C.  Two host
 // reads: the product statistics (buffer sizes) and nnz(C).
@@ -326,6 +382,11 @@ bamg_status spgemm(int m, const int32_t* arp, const int32_t* aci, const double* 
 // then the nnz of every result), so k products cost two host reads.
 bamg_status spgemm_multi(SpgemmJob* jobs, int k, cudaStream_t s) {
   if (k <= 0) return BAMG_OK;
+  if (k > kMaxJobs) {
+    for (int q0 = 0; q0 < k; q0 += kMaxJobs)
+      BAMG_TRY(spgemm_multi(jobs + q0, k - q0 < kMaxJobs ? k - q0 : kMaxJobs, s));
+    return BAMG_OK;
+  }
   // one int32 buffer for the statistics and the per-row arrays of all jobs
   // (product counts, their offsets, entry counts), one pair for the scratch
   std::vector<size_t> ro(k + 1, 0);
@@ -335,14 +396,21 @@ bamg_status spgemm_multi(SpgemmJob* jobs, int k, cudaStream_t s) {
   int* stats = ints.as<int>();
   int32_t* rows = ints.as<int32_t>() + 4 * k;
   BAMG_CUDA(cudaMemsetAsync(ints.p, 0, sizeof(int32_t) * (4 * (size_t)k + ro[k]), s));
-  auto prod = [&](int q) { return rows + ro[q]; };
-  auto offs = [&](int q) { return rows + ro[q] + (jobs[q].m + 1); };
-  auto cnts = [&](int q) { return rows + ro[q] + 2 * (size_t)(jobs[q].m + 1); };
+  SpJobs J;
+  J.k = k;
+  int maxm = 0;
   for (int q = 0; q < k; ++q) {
-    SpgemmJob& J = jobs[q];
-    BAMG_TRY(launch(count_products_kernel, dim3(cdiv(J.m, 256)), dim3(256), 0, s, J.m, J.arp, J.aci, J.brp,
-                    prod(q), stats + 4 * q));
+    const SpgemmJob& S = jobs[q];
+    J.m[q] = S.m;
+    J.arp[q] = S.arp; J.aci[q] = S.aci; J.ava[q] = S.ava;
+    J.brp[q] = S.brp; J.bci[q] = S.bci; J.bva[q] = S.bva;
+    J.prod[q] = rows + ro[q];
+    J.offs[q] = rows + ro[q] + (S.m + 1);
+    J.cnts[q] = rows + ro[q] + 2 * (size_t)(S.m + 1);
+    J.stats[q] = stats + 4 * q;
+    maxm = S.m > maxm ? S.m : maxm;
   }
+  BAMG_TRY(launch(count_products_multi, dim3(cdiv(maxm, 256), k), dim3(256), 0, s, J));
   std::vector<int> h(4 * k);
   BAMG_CUDA(cudaMemcpyAsync(h.data(), stats, sizeof(int) * 4 * k, cudaMemcpyDeviceToHost, s));
   BAMG_CUDA(cudaStreamSynchronize(s));
@@ -366,30 +434,51 @@ bamg_status spgemm_multi(SpgemmJob* jobs, int k, cudaStream_t s) {
   DevMem scol, sval;
   BAMG_TRY(scol.alloc(sizeof(int32_t) * (so[k] > 0 ? so[k] : 1), s));
   BAMG_TRY(sval.alloc(sizeof(double) * (so[k] > 0 ? so[k] : 1), s));
+  ScanMany sc;
   for (int q = 0; q < k; ++q) {
-    SpgemmJob& J = jobs[q];
-    BAMG_TRY(scan_counts(prod(q), offs(q), J.m, s, nullptr));
-    BAMG_TRY(run_rows<true>(J.m, prod(q), pl[q].maxprod, J.arp, J.aci, J.ava, J.brp, J.bci, J.bva, cnts(q),
-                            offs(q), scol.as<int32_t>() + so[q], sval.as<double>() + so[q], s));
-    BAMG_TRY(J.crp->alloc(sizeof(int32_t) * (J.m + 1), s));
-    BAMG_TRY(scan_counts(cnts(q), J.crp->as<int32_t>(), J.m, s, nullptr));
+    J.scol[q] = scol.as<int32_t>() + so[q];
+    J.sval[q] = sval.as<double>() + so[q];
+    sc.in[sc.k] = J.prod[q];
+    sc.out[sc.k] = J.offs[q];
+    sc.n[sc.k++] = jobs[q].m;
   }
+  BAMG_TRY(scan_many(sc, s));
+  // rows of up to kWarpCap products: one warp each, all products in one
+  // launch; longer rows: a block each, per product
+  BAMG_TRY(launch(spgemm_warp_multi, dim3(cdiv(maxm, kWarpsPerBlock), k), dim3(kWarpsPerBlock * 32), 0, s, J));
+  for (int q = 0; q < k; ++q)
+    if (pl[q].maxprod > kWarpCap) {
+      size_t sm = big_smem(true);
+      static std::atomic<uint64_t> attr_done{0};
+      int max_dyn = 0;
+      BAMG_TRY(allow_max_smem((const void*)spgemm_block_kernel<true>, attr_done, &max_dyn));
+      BAMG_TRY(launch(spgemm_block_kernel<true>, dim3(J.m[q]), dim3(kBigThreads), sm, s, J.m[q], J.prod[q],
+                      J.arp[q], J.aci[q], J.ava[q], J.brp[q], J.bci[q], J.bva[q], J.cnts[q], J.offs[q], J.scol[q],
+                      J.sval[q]));
+    }
+  ScanMany sc2;
+  for (int q = 0; q < k; ++q) {
+    BAMG_TRY(jobs[q].crp->alloc(sizeof(int32_t) * (jobs[q].m + 1), s));
+    J.crp[q] = jobs[q].crp->as<int32_t>();
+    sc2.in[sc2.k] = J.cnts[q];
+    sc2.out[sc2.k] = jobs[q].crp->as<int32_t>();
+    sc2.n[sc2.k++] = jobs[q].m;
+  }
+  BAMG_TRY(scan_many(sc2, s));
   std::vector<int32_t> nz(k);
   for (int q = 0; q < k; ++q)
     BAMG_CUDA(cudaMemcpyAsync(&nz[q], jobs[q].crp->as<int32_t>() + jobs[q].m, sizeof(int32_t),
                               cudaMemcpyDeviceToHost, s));
   BAMG_CUDA(cudaStreamSynchronize(s));
   for (int q = 0; q < k; ++q) {
-    SpgemmJob& J = jobs[q];
-    J.nnz = nz[q];
-    BAMG_TRY(J.cci->alloc(sizeof(int32_t) * (J.nnz > 0 ? J.nnz : 1), s));
-    BAMG_TRY(J.cva->alloc(sizeof(double) * (J.nnz > 0 ? J.nnz : 1), s));
-    BAMG_TRY(launch(compact_rows_kernel, dim3(cdiv((long long)J.m * 32, 256)), dim3(256), 0, s, J.m,
-                    (const int32_t*)offs(q), (const int32_t*)cnts(q),
-                    (const int32_t*)scol.as<int32_t>() + so[q], (const double*)sval.as<double>() + so[q],
-                    (const int32_t*)J.crp->as<int32_t>(), J.cci->as<int32_t>(), J.cva->as<double>()));
+    SpgemmJob& S = jobs[q];
+    S.nnz = nz[q];
+    BAMG_TRY(S.cci->alloc(sizeof(int32_t) * (S.nnz > 0 ? S.nnz : 1), s));
+    BAMG_TRY(S.cva->alloc(sizeof(double) * (S.nnz > 0 ? S.nnz : 1), s));
+    J.cci[q] = S.cci->as<int32_t>();
+    J.cva[q] = S.cva->as<double>();
   }
-  return BAMG_OK;
+  return launch(compact_rows_multi, dim3(cdiv((long long)maxm * 32, 256), k), dim3(256), 0, s, J);
 }
 
 bamg_status spgemm_numeric(int m, const int32_t* arp, const int32_t* aci, const double* ava,
