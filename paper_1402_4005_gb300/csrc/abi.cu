@@ -109,7 +109,13 @@ static bamg_status check_params(const bamg_csr* A, const bamg_params* p) {
   return BAMG_OK;
 }
 
-bamg_status bamg_setup(const bamg_csr* A, const bamg_params* p, void* stream, bamg_hierarchy** out) {
+}  // extern "C"
+
+namespace bamg {
+// prepare = false leaves the V-cycle's vectors and graph to the first
+// V-cycle, FGMRES or factor call (batched setups, whose chains are solved
+// through the batch's own V-cycle)
+bamg_status setup_impl(const bamg_csr* A, const bamg_params* p, void* stream, bamg_hierarchy** out, bool prepare) {
   if (!out) return BAMG_ERR_ARG;
   *out = nullptr;
   BAMG_TRY(check_params(A, p));
@@ -145,8 +151,10 @@ bamg_status bamg_setup(const bamg_csr* A, const bamg_params* p, void* stream, ba
       st = BAMG_ERR_UNSUPPORTED;
       break;
     }
-    st = vcycle_prepare(h, s);
-    if (st != BAMG_OK) break;
+    if (prepare) {
+      st = vcycle_prepare(h, s);
+      if (st != BAMG_OK) break;
+    }
     if (cudaStreamSynchronize(s) != cudaSuccess) { st = BAMG_ERR_CUDA; break; }
   } while (false);
   if (st != BAMG_OK) {
@@ -158,10 +166,18 @@ bamg_status bamg_setup(const bamg_csr* A, const bamg_params* p, void* stream, ba
   *out = h;
   return BAMG_OK;
 }
+}  // namespace bamg
+
+extern "C" {
+
+bamg_status bamg_setup(const bamg_csr* A, const bamg_params* p, void* stream, bamg_hierarchy** out) {
+  return setup_impl(A, p, stream, out, true);
+}
 
 bamg_status bamg_vcycle(bamg_hierarchy* h, const double* r_dev, double* z_dev, void* stream) {
   BAMG_CHECK_ARG(h && r_dev && z_dev && r_dev != z_dev);
   cudaStream_t s = S(stream);
+  BAMG_TRY(vcycle_prepare(h, s));
   size_t n = h->lv[0].n;
   BAMG_CUDA(cudaMemcpyAsync(h->io_in.p, r_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   BAMG_TRY(vcycle_run(h, s));

@@ -713,7 +713,7 @@ extern "C" bamg_status bamg_setup_batched(const bamg_csr* As, int nchains, const
       cudaSetDevice(bt->device);
       cudaStream_t ts = bt->wstreams[t];
       for (int c = t; c < nchains; c += T) {
-        st[c] = bamg_setup(&As[c], p, ts, &bt->h[c]);
+        st[c] = setup_impl(&As[c], p, ts, &bt->h[c], false);
         if (st[c] != BAMG_OK) err[c] = bamg_last_error();
       }
       cudaStreamSynchronize(ts);

@@ -95,6 +95,8 @@ bamg_status promote_fp64(bamg_hierarchy* h, cudaStream_t s);
 bamg_status fgmres(bamg_hierarchy* h, double* x, const bamg_solve_params* sp, bamg_solve_info* info,
                    cudaStream_t s);
 bamg_status setup_finest(bamg_hierarchy* h, const bamg_csr* A, cudaStream_t s);
+// abi.cu: bamg_setup, optionally without preparing the V-cycle (done lazily)
+bamg_status setup_impl(const bamg_csr* A, const bamg_params* p, void* stream, bamg_hierarchy** out, bool prepare);
 template <typename T> bamg_status run_setup(bamg_hierarchy* h, cudaStream_t s);
 void gmres_release(bamg_hierarchy* h);
 // mlp.cu: P rows and Q columns of a geometric level from the network

@@ -541,6 +541,7 @@ bamg_status fgmres(bamg_hierarchy* h, double* x, const bamg_solve_params* sp, ba
                    cudaStream_t s) {
   Level& L = h->lv[0];
   const int n = L.n, m = sp->restart;
+  BAMG_TRY(vcycle_prepare(h, s));
   BAMG_TRY(gmres_prepare(h, m, sp->plain ? 1 : 0));
   GmresState& S = *h->gm;
   Gm& G = S.G;
@@ -648,6 +649,7 @@ __global__ void add_kernel(int n, const double* __restrict__ z, double* __restri
 // side), so the ratio of its 1-norms over the second half of the run
 // estimates the asymptotic convergence factor on the range of B.
 bamg_status vcycle_factor(bamg_hierarchy* h, int iters, uint64_t seed, double* factor, cudaStream_t s) {
+  BAMG_TRY(vcycle_prepare(h, s));
   Level& L = h->lv[0];
   const int n = L.n;
   DevMem x, r, zero, sums;
