@@ -737,3 +737,21 @@ def test_direct_nullvector_against_closed_forms_and_dense():
     assert np.abs(x - xb).sum() <= 1e-12
     ch = cg.tandem(8)
     assert np.abs(So.direct_nullvector(ch.csr()) - So.dense_nullvector(ch.csr().toarray())).sum() <= 1e-13
+
+
+def test_chain_mixes_are_seeded_and_sized():
+    """The batch and training mixes the bench uses: deterministic in their
+    seed, the log-uniform batch about 4.3M states, kinds as generated."""
+    a = cg.chain_mix(12, seed=4, log_sizes=True)
+    b = cg.chain_mix(12, seed=4, log_sizes=True)
+    assert [c.name for c in a] == [c.name for c in b]
+    assert all(np.array_equal(x.val, y.val) for x, y in zip(a, b))
+    assert {c.kind for c in a} <= {"lattice", "tandem", "delaunay"}
+    for c in a:
+        if c.kind != "delaunay":
+            assert 32 <= c.nx <= 256 and c.nx == c.ny
+        else:
+            assert 1024 <= c.n <= 65536
+    t = cg.training_mix(6, seed=6)
+    assert [c.kind for c in t] == ["tandem", "lattice"] * 3
+    assert all(64 <= c.nx <= 512 for c in t)
