@@ -139,16 +139,21 @@ bamg_status coarsen_mis(int n, const int32_t* brp, const int32_t* bci, const int
   BAMG_TRY(cnt.alloc(sizeof(int32_t) * (n + 1), s));
   BAMG_TRY(pre.alloc(sizeof(int32_t) * (n + 1), s));
   BAMG_CUDA(cudaMemsetAsync(state.p, 0, n, s));
-  for (int round = 0;; ++round) {
+  // rounds are queued four at a time before the host reads the count of
+  // undecided vertices (a round over a fully decided state changes nothing)
+  constexpr int kRoundsPerCheck = 4;
+  for (int round = 0;; round += kRoundsPerCheck) {
     if (round > n + 1) {
       set_error("independent-set rounds did not terminate");
       return BAMG_ERR_NUMERIC;
     }
-    BAMG_CUDA(cudaMemsetAsync(und.p, 0, sizeof(int), s));
-    BAMG_TRY(launch(mis_select_kernel, dim3(cdiv(n, 256)), dim3(256), 0, s, n, brp, bci, trp, tci, seed,
-                    level, state.as<int8_t>()));
-    BAMG_TRY(launch(mis_finalize_kernel, dim3(cdiv(n, 256)), dim3(256), 0, s, n, brp, bci, trp, tci,
-                    state.as<int8_t>(), und.as<int>()));
+    for (int q = 0; q < kRoundsPerCheck; ++q) {
+      BAMG_CUDA(cudaMemsetAsync(und.p, 0, sizeof(int), s));
+      BAMG_TRY(launch(mis_select_kernel, dim3(cdiv(n, 256)), dim3(256), 0, s, n, brp, bci, trp, tci, seed,
+                      level, state.as<int8_t>()));
+      BAMG_TRY(launch(mis_finalize_kernel, dim3(cdiv(n, 256)), dim3(256), 0, s, n, brp, bci, trp, tci,
+                      state.as<int8_t>(), und.as<int>()));
+    }
     int h = 0;
     BAMG_CUDA(cudaMemcpyAsync(&h, und.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     BAMG_CUDA(cudaStreamSynchronize(s));
