@@ -167,6 +167,49 @@ __device__ inline T group_sum(T v) {
   return v;
 }
 
+// Bitonic sort of 32 E keys held in registers by one warp, element
+// lane * E + e in key[e] (ascending; keys are distinct).  Partners closer
+// than E elements are in the same lane; farther ones are exchanged with
+// shuffles.  Values travel with their keys.
+template <int E, bool VALS>
+__device__ inline void warp_sort_regs(unsigned long long (&key)[E], double (&val)[E], int lane) {
+  constexpr int N = 32 * E;
+#pragma unroll
+  for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= E) {
+        const int lm = j / E;
+        const bool lower = (lane & lm) == 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const unsigned long long pk = __shfl_xor_sync(0xffffffffu, key[e], lm);
+          double pv = 0.0;
+          if (VALS) pv = __shfl_xor_sync(0xffffffffu, val[e], lm);
+          const bool up = ((lane * E + e) & k) == 0;
+          const bool take = (lower == up) ? (pk < key[e]) : (pk > key[e]);
+          if (take) {
+            key[e] = pk;
+            if (VALS) val[e] = pv;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          if ((e & j) == 0) {
+            const int f = e | j;
+            const bool up = ((lane * E + e) & k) == 0;
+            if ((key[e] > key[f]) == up) {
+              const unsigned long long t = key[e]; key[e] = key[f]; key[f] = t;
+              if (VALS) { const double tv = val[e]; val[e] = val[f]; val[f] = tv; }
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
 // ----------------------------------------------------- small internal APIs
 // Exclusive scan of n int32 counts into out[0..n] (out[n] = total), int64
 // total returned through total_host when non-null (synchronises the stream).

@@ -344,23 +344,38 @@ __global__ void transpose_scatter_kernel(int rows, const int32_t* __restrict__ r
 }
 
 // Sort each output row by column (the source row), making the result
-// independent of the scatter order.
-__global__ void sort_rows_kernel(int rows, const int32_t* __restrict__ rp, int32_t* __restrict__ ci,
-                                 double* __restrict__ va) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+// independent of the scatter order: one warp per row, rows of up to 32
+// entries sorted in registers (the columns of a transposed row are
+// distinct), longer rows by insertion on lane 0.
+__global__ void sort_rows_warp_kernel(int rows, const int32_t* __restrict__ rp, int32_t* __restrict__ ci,
+                                      double* __restrict__ va) {
+  const int lane = threadIdx.x & 31;
+  const int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (i >= rows) return;
-  int b = rp[i], e = rp[i + 1];
-  for (int p = b + 1; p < e; ++p) {
-    int k = ci[p];
-    double v = va ? va[p] : 0.0;
-    int q = p - 1;
-    while (q >= b && ci[q] > k) {
-      ci[q + 1] = ci[q];
-      if (va) va[q + 1] = va[q];
-      --q;
+  const int b = rp[i], e = rp[i + 1], len = e - b;
+  if (len <= 1) return;
+  if (len > 32) {
+    if (lane != 0) return;
+    for (int p = b + 1; p < e; ++p) {
+      int k = ci[p];
+      double v = va ? va[p] : 0.0;
+      int q = p - 1;
+      while (q >= b && ci[q] > k) {
+        ci[q + 1] = ci[q];
+        if (va) va[q + 1] = va[q];
+        --q;
+      }
+      ci[q + 1] = k;
+      if (va) va[q + 1] = v;
     }
-    ci[q + 1] = k;
-    if (va) va[q + 1] = v;
+    return;
+  }
+  unsigned long long key[1] = {lane < len ? (unsigned long long)(unsigned)ci[b + lane] : ~0ull};
+  double v[1] = {(va && lane < len) ? va[b + lane] : 0.0};
+  warp_sort_regs<1, true>(key, v, lane);
+  if (lane < len) {
+    ci[b + lane] = (int32_t)key[0];
+    if (va) va[b + lane] = v[0];
   }
 }
 
@@ -375,8 +390,8 @@ bamg_status transpose_csr(int rows, int cols, int nnz, const int32_t* rp, const 
   BAMG_CUDA(cudaMemcpyAsync(fill.p, trp, sizeof(int32_t) * cols, cudaMemcpyDeviceToDevice, s));
   BAMG_TRY(launch(transpose_scatter_kernel, dim3(cdiv(rows, 256)), dim3(256), 0, s, rows, rp, ci, va,
                   fill.as<int32_t>(), tci, tva));
-  BAMG_TRY(launch(sort_rows_kernel, dim3(cdiv(cols, 128)), dim3(128), 0, s, cols, (const int32_t*)trp,
-                  tci, tva));
+  BAMG_TRY(launch(sort_rows_warp_kernel, dim3(cdiv((long long)cols * 32, 256)), dim3(256), 0, s, cols,
+                  (const int32_t*)trp, tci, tva));
   return BAMG_OK;
 }
 

@@ -21,21 +21,31 @@ constexpr int kBlockCap = 8192;    // products per row handled by one block
 constexpr int kWarpsPerBlock = 4;
 constexpr int kBigThreads = 256;
 
-// stats[0] = largest row product count, stats[1..2] = 64-bit total
+// stats[0] = largest row product count, stats[1..2] = 64-bit total (one
+// atomic pair per warp)
 __global__ void count_products_kernel(int m, const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
                                       const int32_t* __restrict__ brp, int32_t* __restrict__ prod,
                                       int* __restrict__ stats) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m) return;
   long long c = 0;
-  for (int p = arp[i]; p < arp[i + 1]; ++p) {
-    int k = aci[p];
-    c += brp[k + 1] - brp[k];
+  if (i < m) {
+    for (int p = arp[i]; p < arp[i + 1]; ++p) {
+      int k = aci[p];
+      c += brp[k + 1] - brp[k];
+    }
+    prod[i] = c > INT32_MAX ? INT32_MAX : (int)c;
   }
-  int ci = c > INT32_MAX ? INT32_MAX : (int)c;
-  prod[i] = ci;
-  atomicMax(stats, ci);
-  atomicAdd(reinterpret_cast<unsigned long long*>(stats + 2), (unsigned long long)c);
+  int mx = c > INT32_MAX ? INT32_MAX : (int)c;
+  unsigned long long sum = (unsigned long long)c;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  }
+  if ((threadIdx.x & 31) == 0 && sum > 0) {
+    atomicMax(stats, mx);
+    atomicAdd(reinterpret_cast<unsigned long long*>(stats + 2), sum);
+  }
 }
 
 template <int G>
@@ -62,6 +72,26 @@ __device__ void group_sort(unsigned long long* key, double* val, int m, int lane
       gsync<G>();
     }
   }
+}
+
+// The smem rows key/val of mp (a power of two, 32 E) entries sorted through
+// registers by one warp.
+template <int E, bool VALS>
+__device__ inline void warp_sort_smem(unsigned long long* key, double* val, int lane) {
+  unsigned long long k[E];
+  double v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    k[e] = key[lane * E + e];
+    v[e] = VALS ? val[lane * E + e] : 0.0;
+  }
+  warp_sort_regs<E, VALS>(k, v, lane);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    key[lane * E + e] = k[e];
+    if (VALS) val[lane * E + e] = v[e];
+  }
+  __syncwarp();
 }
 
 // Expand the products of row i into key/val (count entries), pad to pow2.
@@ -108,7 +138,23 @@ __device__ void row_product(int i, int lo, int hi, const int32_t* __restrict__ p
   int count = prod[i];
   if (count <= lo || count > hi) return;
   int mp = expand_row<G, NUMERIC>(i, arp, aci, ava, brp, bci, bva, count, key, val, lane);
-  group_sort<G, NUMERIC>(key, val, mp, lane);
+  if constexpr (G == 32) {
+    // rows of up to 256 products: the sort in registers (padding keys ~0
+    // fill the row to 32 E entries)
+    if (mp <= 256) {
+      const int E = mp <= 32 ? 1 : mp <= 64 ? 2 : mp <= 128 ? 4 : 8;
+      for (int t = mp + lane; t < 32 * E; t += 32) key[t] = ~0ull;
+      __syncwarp();
+      if (E == 1) warp_sort_smem<1, NUMERIC>(key, val, lane);
+      else if (E == 2) warp_sort_smem<2, NUMERIC>(key, val, lane);
+      else if (E == 4) warp_sort_smem<4, NUMERIC>(key, val, lane);
+      else warp_sort_smem<8, NUMERIC>(key, val, lane);
+    } else {
+      group_sort<G, NUMERIC>(key, val, mp, lane);
+    }
+  } else {
+    group_sort<G, NUMERIC>(key, val, mp, lane);
+  }
   // segment starts
   for (int t = lane; t < count; t += G) {
     unsigned c = (unsigned)(key[t] >> 32);
@@ -311,19 +357,30 @@ struct SpJobs {
   double* cva[kMaxJobs];
 };
 
+// products per row, and per job their maximum and total (one atomic pair
+// per warp: a million rows updating two counters one by one serialise)
 __global__ void count_products_multi(SpJobs J) {
   const int q = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= J.m[q]) return;
   long long c = 0;
-  for (int p = J.arp[q][i]; p < J.arp[q][i + 1]; ++p) {
-    const int k = J.aci[q][p];
-    c += J.brp[q][k + 1] - J.brp[q][k];
+  if (i < J.m[q]) {
+    for (int p = J.arp[q][i]; p < J.arp[q][i + 1]; ++p) {
+      const int k = J.aci[q][p];
+      c += J.brp[q][k + 1] - J.brp[q][k];
+    }
+    J.prod[q][i] = c > INT32_MAX ? INT32_MAX : (int)c;
   }
-  const int ci = c > INT32_MAX ? INT32_MAX : (int)c;
-  J.prod[q][i] = ci;
-  atomicMax(J.stats[q], ci);
-  atomicAdd(reinterpret_cast<unsigned long long*>(J.stats[q] + 2), (unsigned long long)c);
+  int mx = c > INT32_MAX ? INT32_MAX : (int)c;
+  unsigned long long sum = (unsigned long long)c;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  }
+  if ((threadIdx.x & 31) == 0 && sum > 0) {
+    atomicMax(J.stats[q], mx);
+    atomicAdd(reinterpret_cast<unsigned long long*>(J.stats[q] + 2), sum);
+  }
 }
 
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) spgemm_warp_multi(SpJobs J) {
