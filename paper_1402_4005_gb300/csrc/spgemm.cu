@@ -16,7 +16,7 @@
 
 namespace bamg {
 
-constexpr int kWarpCap = 512;      // products per row handled by one warp
+constexpr int kWarpCap = 256;      // products per row handled by one warp (20 KB of shared memory per block of 4)
 constexpr int kBlockCap = 8192;    // products per row handled by one block
 constexpr int kWarpsPerBlock = 4;
 constexpr int kBigThreads = 256;
