@@ -206,15 +206,31 @@ ls_fit_kernel(int n, int r, const int32_t* __restrict__ jrp, const int32_t* __re
       p[j] = seg_get<S>(pj, j);
     }
   }
-  if (!valid || c == 0) return;
-  // a row flagged for the FP64 refit is counted by that refit alone
-  const bool refit = flag != nullptr && cc > 0 && rmin < cond_tol * rmax;
-  if (refit && k == 0) flag[i] = 1;
-  // the constrained weights are assembled in FP64 from the null-space
-  // coordinates, so they sum to one to FP64 rounding in either precision
-  double val;
+  // the constrained weights from the null-space coordinates: in FP64 for an
+  // FP64 fit; in FP32 for an FP32 fit (FP64 division and square root are
+  // costly on this part), after which the entry of the last lane is moved
+  // by 1 - (the FP64 sum of the segment's weights), so that the weights
+  // still sum to one to FP64 rounding
+  double val = 0.0;
   if (CONSTR) {
-    if (c == 1) {
+    if constexpr (sizeof(R) == 4) {
+      float vf = 1.0f;
+      if (c > 1) {
+        const float sq = sqrtf((float)c), h2 = 2.0f * c + 2.0f * sq;
+        float sy = 0.0f;
+#pragma unroll
+        for (int m = 0; m < kCMax - 1; ++m) sy += (m < c - 1) ? (float)p[m] : 0.0f;
+        const float g = 2.0f * sy / h2;
+        float ym = 0.0f;
+#pragma unroll
+        for (int m = 1; m < kCMax; ++m) if (m == k) ym = (float)p[m - 1];
+        vf = 1.0f / (float)c + (k == 0 ? -(1.0f + sq) * g : ym - g);
+      }
+      const double tot = seg_sum<S>((valid && k < c) ? (double)vf : 0.0);   // every lane shuffles
+      val = (double)vf;
+      if (c > 1 && k == c - 1) val += 1.0 - tot;
+      if (c == 1) val = 1.0;
+    } else if (c == 1) {
       val = 1.0;
     } else {
       const double sq = sqrt((double)c), h2 = 2.0 * c + 2.0 * sq;
@@ -228,11 +244,14 @@ ls_fit_kernel(int n, int r, const int32_t* __restrict__ jrp, const int32_t* __re
       val = 1.0 / c + (k == 0 ? -(1.0 + sq) * g : ym - g);
     }
   } else {
-    val = 0.0;
 #pragma unroll
     for (int m = 0; m < kCMax; ++m) if (m == k) val = (double)p[m];
     if (AUG) val += 1.0 / c;
   }
+  if (!valid || c == 0) return;
+  // a row flagged for the FP64 refit is counted by that refit alone
+  const bool refit = flag != nullptr && cc > 0 && rmin < cond_tol * rmax;
+  if (refit && k == 0) flag[i] = 1;
   if (k < c) out[base + k] = val;
   if (k == 0 && dropped && !refit) atomicAdd(rankdef, 1);
 }
