@@ -188,9 +188,14 @@ def gpu_arm(args, rank: int, world: int):
     def timed(prec, steps, warmup, **extra):
         times, infos = [], []
         with torch.cuda.stream(stream):
-            for _ in range(warmup):
+            # at least `warmup` steps and at least a second of them: a GPU
+            # that sat idle (e.g. during the build) needs that long to reach
+            # its clocks
+            t_w, k = time.perf_counter(), 0
+            while k < warmup or time.perf_counter() - t_w < 1.0:
                 h, x, info = one_step(prec, **extra)
                 h.destroy()
+                k += 1
             torch.cuda.synchronize()
             if world > 1:
                 torch.distributed.barrier()
