@@ -79,10 +79,12 @@ bamg_status bamg_step_spmm_block(int prec, int rows, int ld, const int32_t* rp,
  * matrix B with nnz entries (the group width follows nnz / n, as in the
  * solver).  mode 0: y = x + omega dinv .* (b - B x), a weighted Jacobi sweep;
  * mode 1: y = omega dinv .* b, the first sweep from zero; mode 2:
- * y = b - B x, the residual; mode 3: y = B x; mode 4: y += B x.  x, b, y,
- * dinv: device vectors of n values in the precision prec (0 = double,
- * 1 = float); b is not read in modes 3 and 4, x not in mode 1, dinv only in
- * modes 0 and 1 (NULL allowed otherwise).  y may not alias x or b.
+ * y = b - B x, the residual; mode 3: y = B x; mode 4: y += B x; mode 5:
+ * the first two sweeps from zero in one pass, bit for bit mode 1 followed by
+ * mode 0.  x, b, y, dinv: device vectors of n values in the precision prec
+ * (0 = double, 1 = float); b is not read in modes 3 and 4, x not in modes 1
+ * and 5, dinv only in modes 0, 1 and 5 (NULL allowed otherwise).  y may not
+ * alias x or b.
  * BAMG_ERR_ARG for a missing argument or an unknown mode. */
 bamg_status bamg_step_csr_vec(int prec, int mode, int n, int64_t nnz, const int32_t* rp,
                               const int32_t* ci, const void* val, const void* dinv,

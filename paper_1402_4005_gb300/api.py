@@ -357,7 +357,7 @@ def bamg_step_spmm_block(rp, ci, val, X, rows: int, stream=None):
     return Y
 
 
-VEC_MODES = {"jacobi": 0, "jacobi_zero": 1, "resid": 2, "spmv": 3, "spmv_add": 4}
+VEC_MODES = {"jacobi": 0, "jacobi_zero": 1, "resid": 2, "spmv": 3, "spmv_add": 4, "jacobi_zero2": 5}
 
 
 def bamg_step_csr_vec(mode: str, rp, ci, val, x=None, b=None, dinv=None, omega=0.7, y=None, stream=None):

@@ -420,10 +420,10 @@ bamg_status bamg_step_csr_vec(int prec, int mode, int n, int64_t nnz, const int3
                               const void* val, const void* dinv, double omega, const void* x, const void* b,
                               void* y, void* stream) {
   BAMG_CHECK_ARG(n >= 1 && nnz >= 0 && rp && ci && val && y && (prec == 0 || prec == 1));
-  BAMG_CHECK_ARG(mode >= VEC_JACOBI && mode <= VEC_SPMV_ADD);
+  BAMG_CHECK_ARG(mode >= VEC_JACOBI && mode <= VEC_JACOBI_ZERO2);
   BAMG_CHECK_ARG(mode == VEC_SPMV || mode == VEC_SPMV_ADD || b);
-  BAMG_CHECK_ARG(mode == VEC_JACOBI_ZERO || x);
-  BAMG_CHECK_ARG((mode != VEC_JACOBI && mode != VEC_JACOBI_ZERO) || dinv);
+  BAMG_CHECK_ARG(mode == VEC_JACOBI_ZERO || mode == VEC_JACOBI_ZERO2 || x);
+  BAMG_CHECK_ARG((mode != VEC_JACOBI && mode != VEC_JACOBI_ZERO && mode != VEC_JACOBI_ZERO2) || dinv);
   const int G = vec_lanes((double)nnz / n);
   if (prec == 1)
     return csr_vec<float>(mode, n, G, rp, ci, (const float*)val, (const float*)dinv, (float)omega,

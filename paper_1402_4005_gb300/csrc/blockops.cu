@@ -289,13 +289,22 @@ __global__ void inject_kernel(int nc, const int32_t* __restrict__ cpt, const T* 
 // requests are in flight per lane than with one row per group; each row
 // still sums its products lane by lane in the order p0 + g, p0 + g + G, ...
 // and then across the group, so the result does not depend on RU.
-enum VecMode { kJacobi = 0, kJacobiZero = 1, kResid = 2, kSpmv = 3, kSpmvAdd = 4 };
+// kJacobiZero2: the first two sweeps from zero in one pass.  The first
+// sweep's value at a neighbour, (omega b_j) dinv_j, is recomputed from b and
+// dinv with the same two rounded products, so the result is bit for bit that
+// of kJacobiZero followed by kJacobi.
+enum VecMode { kJacobi = 0, kJacobiZero = 1, kResid = 2, kSpmv = 3, kSpmvAdd = 4, kJacobiZero2 = 5 };
+
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
 template <typename T, int G, int MODE, int RU>
 __global__ void __launch_bounds__(256)
 csr_vec_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                const T* __restrict__ va, const T* __restrict__ dinv, T omega, const T* __restrict__ x,
                const T* __restrict__ b, T* __restrict__ y) {
+  pdl_wait();
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const size_t grp = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int g = lane % G;
@@ -324,8 +333,14 @@ csr_vec_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict_
         a[u] = in ? __ldg(va + p) : T(0);
       }
       T xv[RU];
+      if (MODE == kJacobiZero2) {
 #pragma unroll
-      for (int u = 0; u < RU; ++u) xv[u] = c[u] >= 0 ? __ldg(x + c[u]) : T(0);
+        for (int u = 0; u < RU; ++u)
+          xv[u] = c[u] >= 0 ? mul_rn(mul_rn(omega, __ldg(b + c[u])), __ldg(dinv + c[u])) : T(0);
+      } else {
+#pragma unroll
+        for (int u = 0; u < RU; ++u) xv[u] = c[u] >= 0 ? __ldg(x + c[u]) : T(0);
+      }
 #pragma unroll
       for (int u = 0; u < RU; ++u)
         if (c[u] >= 0) acc[u] = fma(a[u], xv[u], acc[u]);
@@ -339,6 +354,7 @@ csr_vec_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict_
     const long long i = i0 + u;
     if (i >= n) break;
     if (MODE == kJacobi) y[i] = x[i] + (omega * (b[i] - acc[u])) * dinv[i];
+    else if (MODE == kJacobiZero2) y[i] = mul_rn(mul_rn(omega, b[i]), dinv[i]) + (omega * (b[i] - acc[u])) * dinv[i];
     else if (MODE == kJacobiZero) y[i] = (omega * b[i]) * dinv[i];
     else if (MODE == kResid) y[i] = b[i] - acc[u];
     else if (MODE == kSpmv) y[i] = acc[u];
@@ -348,6 +364,8 @@ csr_vec_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict_
 
 template <typename T>
 __global__ void dense_gemv_kernel(int n, const T* __restrict__ A, const T* __restrict__ x, T* __restrict__ y) {
+  pdl_wait();
+  pdl_trigger();
   int lane = threadIdx.x & 31;
   int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (i >= n) return;
@@ -604,6 +622,7 @@ bamg_status csr_vec(int mode, int n, int G, const int32_t* rp, const int32_t* ci
     case kJacobiZero: return vec_g<T, kJacobiZero>(n, G, rp, ci, va, dinv, omega, x, b, y, s);
     case kResid: return vec_g<T, kResid>(n, G, rp, ci, va, dinv, omega, x, b, y, s);
     case kSpmv: return vec_g<T, kSpmv>(n, G, rp, ci, va, dinv, omega, x, b, y, s);
+    case kJacobiZero2: return vec_g<T, kJacobiZero2>(n, G, rp, ci, va, dinv, omega, x, b, y, s);
     default: return vec_g<T, kSpmvAdd>(n, G, rp, ci, va, dinv, omega, x, b, y, s);
   }
 }

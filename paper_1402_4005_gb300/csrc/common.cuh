@@ -43,15 +43,50 @@ extern thread_local uint64_t t_launches;
     }                                                                \
   } while (0)
 
+// Programmatic dependent launch (sm_90 and later).  While t_pdl is set (the
+// captures of the V-cycle and Arnoldi graphs, which hold kernel nodes only),
+// launch() gives each kernel the programmatic-serialisation attribute: the
+// kernel may start while its predecessor on the stream is still running, so
+// its launch latency overlaps the predecessor's work.  Every kernel launched
+// that way calls pdl_wait() before its first global memory access; it
+// returns once the predecessor grid has completed and its writes are
+// visible (at once for a kernel launched normally).  pdl_trigger() then lets
+// the successor begin launching; it only schedules, it orders nothing.
+extern thread_local bool t_pdl;
+struct PdlScope {
+  bool prev;
+  PdlScope() : prev(t_pdl) { t_pdl = true; }
+  ~PdlScope() { t_pdl = prev; }
+  PdlScope(const PdlScope&) = delete;
+  PdlScope& operator=(const PdlScope&) = delete;
+};
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Launch a kernel, count it and check the launch.
 template <typename... KArgs, typename... Args>
 inline bamg_status launch(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem,
                           cudaStream_t s, Args&&... args) {
   if (grid.x == 0 || grid.y == 0 || grid.z == 0) return BAMG_OK;
-  k<<<grid, block, smem, s>>>(std::forward<Args>(args)...);
+  cudaError_t e;
+  if (t_pdl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+  } else {
+    k<<<grid, block, smem, s>>>(std::forward<Args>(args)...);
+    e = cudaGetLastError();
+  }
   g_launches.fetch_add(1, std::memory_order_relaxed);
   ++t_launches;
-  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error("kernel launch failed: %s", cudaGetErrorString(e));
     return BAMG_ERR_CUDA;

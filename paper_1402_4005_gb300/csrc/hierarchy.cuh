@@ -88,7 +88,11 @@ struct bamg_hierarchy {
 };
 
 namespace bamg {
-template <typename T> bamg_status vcycle_body(bamg_hierarchy* h, cudaStream_t s);
+// z = C in (in: n doubles, or the column col[0] of an n-row array when col is
+// given); z is written to out and, with out_col, to the column col[0] of out_col.
+template <typename T>
+bamg_status vcycle_body(bamg_hierarchy* h, cudaStream_t s, const double* in, const int* col, double* out,
+                        double* out_col);
 bamg_status vcycle_prepare(bamg_hierarchy* h, cudaStream_t s);
 bamg_status vcycle_run(bamg_hierarchy* h, cudaStream_t s);
 bamg_status promote_fp64(bamg_hierarchy* h, cudaStream_t s);

@@ -5,7 +5,8 @@
 
 namespace bamg {
 
-enum VecModeHost { VEC_JACOBI = 0, VEC_JACOBI_ZERO = 1, VEC_RESID = 2, VEC_SPMV = 3, VEC_SPMV_ADD = 4 };
+enum VecModeHost { VEC_JACOBI = 0, VEC_JACOBI_ZERO = 1, VEC_RESID = 2, VEC_SPMV = 3, VEC_SPMV_ADD = 4,
+                   VEC_JACOBI_ZERO2 = 5 };
 
 // Several double -> float conversions in one launch.
 constexpr int kConvMany = 8;

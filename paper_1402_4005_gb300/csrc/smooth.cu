@@ -146,6 +146,8 @@ __global__ void __launch_bounds__(256)
 mcgs_kernel(int cnt, const int32_t* __restrict__ rows, const int32_t* __restrict__ rp,
             const int32_t* __restrict__ ci, const T* __restrict__ va, const T* __restrict__ dinv,
             const T* __restrict__ b, T* x) {
+  pdl_wait();
+  pdl_trigger();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int k = t / G, g = threadIdx.x % G;
   const bool valid = k < cnt;      // every lane joins the shuffles below

@@ -39,6 +39,14 @@ template <> const double* pinv_t<double>(const bamg_hierarchy* h) { return h->Bp
 template <> const float* pinv_t<float>(const bamg_hierarchy* h) { return h->Bpinv32.as<float>(); }
 
 template <typename T>
+__global__ void zero_kernel(size_t n, T* __restrict__ y) {
+  pdl_wait();
+  pdl_trigger();
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) y[t] = T(0);
+}
+
+template <typename T>
 static bamg_status vcycle_level(bamg_hierarchy* h, int l, cudaStream_t s) {
   Level& L = h->lv[l];
   T* b = L.vb.as<T>();
@@ -48,14 +56,13 @@ static bamg_status vcycle_level(bamg_hierarchy* h, int l, cudaStream_t s) {
   const T om = T(p.omega);
   const T* dv = dinv_t<T>(L);
   const T* bv = L.B.vals<T>();
-  T* cur = z;
-  T* alt = L.vt.as<T>();
+  const unsigned gn = cdiv(L.n, 256);
   if (p.smoother == BAMG_SMOOTH_MCGS) {
     // multicolour Gauss-Seidel, in place (Section 3 splitting)
     auto sweep = [&](T* x) {
       return mcgs_sweep<T>(L.vec_g, L.ncol, L.crp.data(), L.crows.as<int32_t>(), L.B.r(), L.B.c(), bv, dv, b, x, s);
     };
-    BAMG_CUDA(cudaMemsetAsync(z, 0, sizeof(T) * L.n, s));
+    BAMG_TRY(launch(zero_kernel<T>, dim3(gn), dim3(256), 0, s, (size_t)L.n, z));
     for (int it = 0; it < p.nu_pre; ++it) BAMG_TRY(sweep(z));
     BAMG_TRY(csr_vec<T>(VEC_RESID, L.n, L.vec_g, L.B.r(), L.B.c(), bv, dv, om, z, b, L.vr.as<T>(), s));
     Level& C = h->lv[l + 1];
@@ -67,11 +74,19 @@ static bamg_status vcycle_level(bamg_hierarchy* h, int l, cudaStream_t s) {
     for (int it = 0; it < p.nu_post; ++it) BAMG_TRY(sweep(z));
     return BAMG_OK;
   }
+  // Jacobi sweeps alternate between z and the scratch vt; the first two
+  // pre-sweeps from zero take one pass.  The start buffer is chosen so that
+  // the last sweep writes z.
+  const int swaps = (p.nu_pre >= 2 ? p.nu_pre - 2 : 0) + p.nu_post;
+  T* cur = swaps % 2 == 0 ? z : L.vt.as<T>();
+  T* alt = cur == z ? L.vt.as<T>() : z;
   if (p.nu_pre == 0) {
-    BAMG_CUDA(cudaMemsetAsync(cur, 0, sizeof(T) * L.n, s));
-  } else {
+    BAMG_TRY(launch(zero_kernel<T>, dim3(gn), dim3(256), 0, s, (size_t)L.n, cur));
+  } else if (p.nu_pre == 1) {
     BAMG_TRY(csr_vec<T>(VEC_JACOBI_ZERO, L.n, L.vec_g, L.B.r(), L.B.c(), bv, dv, om, nullptr, b, cur, s));
-    for (int it = 1; it < p.nu_pre; ++it) {
+  } else {
+    BAMG_TRY(csr_vec<T>(VEC_JACOBI_ZERO2, L.n, L.vec_g, L.B.r(), L.B.c(), bv, dv, om, nullptr, b, cur, s));
+    for (int it = 2; it < p.nu_pre; ++it) {
       BAMG_TRY(csr_vec<T>(VEC_JACOBI, L.n, L.vec_g, L.B.r(), L.B.c(), bv, dv, om, cur, b, alt, s));
       std::swap(cur, alt);
     }
@@ -87,7 +102,10 @@ static bamg_status vcycle_level(bamg_hierarchy* h, int l, cudaStream_t s) {
     BAMG_TRY(csr_vec<T>(VEC_JACOBI, L.n, L.vec_g, L.B.r(), L.B.c(), bv, dv, om, cur, b, alt, s));
     std::swap(cur, alt);
   }
-  if (cur != z) BAMG_CUDA(cudaMemcpyAsync(z, cur, sizeof(T) * L.n, cudaMemcpyDeviceToDevice, s));
+  if (cur != z) {
+    set_error("V-cycle level %d: the last sweep did not write z", l);
+    return BAMG_ERR_CUDA;
+  }
   return BAMG_OK;
 }
 
@@ -101,24 +119,43 @@ __global__ void fill_kernel(size_t n, double v, double* __restrict__ b) {
   if (t < n) b[t] = v;
 }
 
+// V-cycle input: b = in, or the column col[0] of the n-row array in,
+// converted to the V-cycle precision.
 template <typename T>
-bamg_status vcycle_body(bamg_hierarchy* h, cudaStream_t s) {
+__global__ void vc_in_kernel(int n, const double* __restrict__ in, const int* __restrict__ col, T* __restrict__ b) {
+  pdl_wait();
+  pdl_trigger();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double* src = col ? in + (size_t)col[0] * n : in;
+  b[i] = T(src[i]);
+}
+
+// V-cycle output: out = z in FP64, and the same values into the column
+// col[0] of out_col when out_col is given.
+template <typename T>
+__global__ void vc_out_kernel(int n, const T* __restrict__ z, double* __restrict__ out, const int* __restrict__ col,
+                              double* __restrict__ out_col) {
+  pdl_wait();
+  pdl_trigger();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = double(z[i]);
+  out[i] = v;
+  if (out_col) out_col[(size_t)col[0] * n + i] = v;
+}
+
+// z = C in (in: n doubles, or the column col[0] of an n-row array); z goes
+// to out and, with out_col, also to the column col[0] of out_col.
+template <typename T>
+bamg_status vcycle_body(bamg_hierarchy* h, cudaStream_t s, const double* in, const int* col, double* out,
+                        double* out_col) {
   Level& L0 = h->lv[0];
-  size_t n = L0.n;
-  if (sizeof(T) == 4) {
-    BAMG_TRY(convert<double, float>(n, h->io_in.as<double>(), (float*)L0.vb.p, s));
-  } else {
-    BAMG_TRY(launch(copy_d_kernel, dim3(cdiv((long long)n, 256)), dim3(256), 0, s, n,
-                    (const double*)h->io_in.as<double>(), (double*)L0.vb.p));
-  }
+  const int n = L0.n;
+  BAMG_TRY(launch(vc_in_kernel<T>, dim3(cdiv(n, 256)), dim3(256), 0, s, n, in, col, L0.vb.as<T>()));
   BAMG_TRY(vcycle_level<T>(h, 0, s));
-  if (sizeof(T) == 4) {
-    BAMG_TRY(convert<float, double>(n, (const float*)L0.vz.p, h->io_out.as<double>(), s));
-  } else {
-    BAMG_TRY(launch(copy_d_kernel, dim3(cdiv((long long)n, 256)), dim3(256), 0, s, n,
-                    (const double*)L0.vz.p, h->io_out.as<double>()));
-  }
-  return BAMG_OK;
+  return launch(vc_out_kernel<T>, dim3(cdiv(n, 256)), dim3(256), 0, s, n, (const T*)L0.vz.as<T>(), out, col,
+                out_col);
 }
 
 // Allocates the V-cycle vectors and captures the V-cycle into a graph.
@@ -147,7 +184,14 @@ bamg_status vcycle_prepare(bamg_hierarchy* h, cudaStream_t s) {
   if (!h->cap_stream) BAMG_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   uint64_t before = t_launches;
   BAMG_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-  bamg_status st = h->mixed ? vcycle_body<float>(h, h->cap_stream) : vcycle_body<double>(h, h->cap_stream);
+  bamg_status st;
+  {
+    PdlScope pdl;
+    double* in = h->io_in.as<double>();
+    double* out = h->io_out.as<double>();
+    st = h->mixed ? vcycle_body<float>(h, h->cap_stream, in, nullptr, out, nullptr)
+                  : vcycle_body<double>(h, h->cap_stream, in, nullptr, out, nullptr);
+  }
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
   if (st != BAMG_OK) {
@@ -206,85 +250,164 @@ bamg_status vcycle_run(bamg_hierarchy* h, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------- FGMRES kernels
-constexpr int kRedBlocks = 256;
 
 // The Arnoldi step of FGMRES runs as one captured graph; its kernels read
 // the step index j (basis vectors 0..j in use) from device memory, so the
 // same graph serves every step.  Partial sums use the fixed row stride m+1.
 
-// part[b * (m+1) + k] = block b's share of V_k . w for k <= j
-// part[b * (m+1) + k] = the block's share of V_k . w for k <= j: every block
-// takes all j + 1 columns over its rows (one wave of blocks, w read once
-// per column from L2), warp sums kept per warp and added in warp order.
+// Classical Gram-Schmidt against the basis V_0 .. V_j (K = j + 1 columns of
+// n rows, stride ldv), three fused forms:
+//   kGsDots:   out[k] = V_k . w;
+//   kGsUpDots: w -= sum_k hin[k] V_k, then out[k] = V_k . w (the first pass's
+//              update and the second pass's products: V read once for both);
+//   kGsUpNorm: w -= sum_k hin[k] V_k, then out[0] = ||w||_2.
+// One wave of at most kRedBlocks blocks; each thread takes the rows
+// tid, tid + stride, ...; loads of eight columns are issued together.  A
+// block adds its warp sums in warp order into part (row stride m + 1); the
+// last block to finish adds the blocks' shares (thread t takes block t,
+// then warp sums in warp order) and resets the arrival counter.  The order
+// is fixed, so every run gives the same result.
 constexpr int kMultidotMax = 65;   // m + 1 <= 65 (restart <= 64)
-__global__ void __launch_bounds__(256) multidot_kernel(int n, int m, const int* __restrict__ dj,
-                                                       const double* __restrict__ V, size_t ldv,
-                                                       const double* __restrict__ w, double* __restrict__ part) {
+constexpr int kRedBlocks = 256;
+enum { kGsDots = 0, kGsUpDots = 1, kGsUpNorm = 2 };
+
+template <int MODE>
+__global__ void __launch_bounds__(256) gs_kernel(int n, int m, const int* __restrict__ dj,
+                                                 const double* __restrict__ V, size_t ldv,
+                                                 const double* __restrict__ hin, double* __restrict__ w,
+                                                 double* __restrict__ part, unsigned* __restrict__ arrived,
+                                                 double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sh[8][kMultidotMax];
+  __shared__ double hs[kMultidotMax];
+  __shared__ bool last;
   const int K = dj[0] + 1, lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  for (int k = 0; k < K; ++k) {
-    const double* v = V + (size_t)k * ldv;
-    double s = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) s += v[i] * w[i];
-    s = warp_sum(s);
-    if (lane == 0) sh[wp][k] = s;
+  const int stride = gridDim.x * blockDim.x, i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  double ss = 0.0;
+  if (MODE != kGsDots) {
+    for (int k = threadIdx.x; k < K; k += blockDim.x) hs[k] = hin[k];
+    __syncthreads();
+    for (int i = i0; i < n; i += stride) {
+      double acc = w[i];
+      for (int kc = 0; kc < K; kc += 8) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = kc + u < K ? V[(size_t)(kc + u) * ldv + i] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (kc + u < K) acc -= hs[kc + u] * v[u];
+      }
+      w[i] = acc;
+      if (MODE == kGsUpNorm) ss += acc * acc;
+    }
+  }
+  if (MODE == kGsUpNorm) {
+    ss = warp_sum(ss);
+    if (lane == 0) sh[wp][0] = ss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int q = 0; q < 8; ++q) t += sh[q][0];
+      part[blockIdx.x] = t;
+    }
+  } else {
+    for (int kc = 0; kc < K; kc += 8) {
+      double sd[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) sd[u] = 0.0;
+      for (int i = i0; i < n; i += stride) {
+        const double wi = w[i];
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = kc + u < K ? V[(size_t)(kc + u) * ldv + i] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) sd[u] += v[u] * wi;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const double r = warp_sum(sd[u]);
+        if (lane == 0 && kc + u < K) sh[wp][kc + u] = r;
+      }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+      double t = 0.0;
+      for (int q = 0; q < 8; ++q) t += sh[q][k];
+      part[(size_t)blockIdx.x * (m + 1) + k] = t;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(arrived, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int t = threadIdx.x, nb = gridDim.x;
+  if (MODE == kGsUpNorm) {
+    double r = t < nb ? __ldcg(part + t) : 0.0;
+    r = warp_sum(r);
+    if (lane == 0) sh[wp][0] = r;
+    __syncthreads();
+    if (t == 0) {
+      double a = 0.0;
+      for (int q = 0; q < 8; ++q) a += sh[q][0];
+      out[0] = sqrt(a);
+      *arrived = 0u;
+    }
+    return;
+  }
+  for (int kc = 0; kc < K; kc += 8) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = (kc + u < K && t < nb) ? __ldcg(part + (size_t)t * (m + 1) + kc + u) : 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const double r = warp_sum(v[u]);
+      if (lane == 0 && kc + u < K) sh[wp][kc + u] = r;
+    }
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    double t = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q][k];
-    part[(size_t)blockIdx.x * (m + 1) + k] = t;
+  for (int k = t; k < K; k += blockDim.x) {
+    double a = 0.0;
+    for (int q = 0; q < 8; ++q) a += sh[q][k];
+    out[k] = a;
   }
+  if (t == 0) *arrived = 0u;
 }
 
-// out[k] = sum over the nb blocks of part[b * (m+1) + k], k <= j (fixed order)
-__global__ void multidot_reduce_kernel(int nb, int m, const int* __restrict__ dj, const double* __restrict__ part,
-                                       double* __restrict__ out) {
-  __shared__ double sh[8];
-  const int k = blockIdx.x;
-  if (k > dj[0]) return;
-  double s = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[(size_t)b * (m + 1) + k];
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+// Unpreconditioned step: out = V_j and Z_j = V_j.
+__global__ void plain_io_kernel(int n, const int* __restrict__ dj, const double* __restrict__ V,
+                                double* __restrict__ out, double* __restrict__ Z) {
+  pdl_wait();
+  pdl_trigger();
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const size_t o = (size_t)dj[0] * n + i;
+  const double v = V[o];
+  out[i] = v;
+  Z[o] = v;
+}
+
+// V_{j+1} = w / ||w||, then j <- j + 1: the last block to finish (every
+// block has read j by then) increments j and resets the arrival counter.
+__global__ void next_basis_kernel(int n, int* __restrict__ dj, const double* __restrict__ w,
+                                  const double* __restrict__ nrm, double* __restrict__ V,
+                                  unsigned* __restrict__ arrived) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ bool last;
+  const int j = dj[0];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) V[(size_t)(j + 1) * n + i] = w[i] / nrm[0];
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
-    out[k] = t;
+  if (threadIdx.x == 0) last = atomicAdd(arrived, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    dj[0] = j + 1;
+    *arrived = 0u;
   }
 }
-
-// w -= sum_{k <= j} h[k] V_k
-__global__ void orth_update_kernel(int n, const int* __restrict__ dj, const double* __restrict__ V, size_t ldv,
-                                   const double* __restrict__ h, double* __restrict__ w) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int K = dj[0] + 1;
-  double acc = w[i];
-  for (int k = 0; k < K; ++k) acc -= h[k] * V[(size_t)k * ldv + i];
-  w[i] = acc;
-}
-
-// out = V_j (get = 1) or V_j = in (get = 0)
-__global__ void column_io_kernel(int n, const int* __restrict__ dj, int get, double* __restrict__ V,
-                                 double* __restrict__ io) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double* v = V + (size_t)dj[0] * n;
-  if (get) io[i] = v[i];
-  else v[i] = io[i];
-}
-
-// V_{j+1} = w / ||w||
-__global__ void next_basis_kernel(int n, const int* __restrict__ dj, const double* __restrict__ w,
-                                  const double* __restrict__ nrm, double* __restrict__ V) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  V[(size_t)(dj[0] + 1) * n + i] = w[i] / nrm[0];
-}
-
-__global__ void step_kernel(int* dj) { dj[0] += 1; }
 
 // y = x + sum_k c[k] Z_k
 __global__ void combine_kernel(int n, int K, const double* __restrict__ Z, size_t ldz,
@@ -304,35 +427,57 @@ __global__ void scale_by_kernel(int n, const double* __restrict__ a, const doubl
   b[i] = a[i] * s;
 }
 
-__global__ void sumsq_kernel(int n, const double* __restrict__ x, double* __restrict__ part) {
+// out[0] = ||x||_2: per-block sums of squares (warp sums added in warp
+// order), then the last block to finish adds the nb block sums in a fixed
+// order (thread t takes blocks t, t + 256, ..., then warp sums in warp
+// order), takes the square root and resets the arrival counter.
+__global__ void __launch_bounds__(256) norm2_kernel(int n, const double* __restrict__ x, double* __restrict__ part,
+                                                   unsigned* __restrict__ arrived, double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ double sh[8];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   double s = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) s += x[i] * x[i];
   s = warp_sum(s);
-  __shared__ double sh[8];
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  if (lane == 0) sh[wp] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
+    for (int q = 0; q < 8; ++q) t += sh[q];
     part[blockIdx.x] = t;
+    __threadfence();
+    last = atomicAdd(arrived, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double r = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += 256) r += __ldcg(part + b);
+  r = warp_sum(r);
+  if (lane == 0) sh[wp] = r;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += sh[q];
+    out[0] = sqrt(t);
+    *arrived = 0u;
   }
 }
 
-__global__ void sqrt_kernel(double* v) { v[0] = sqrt(v[0]); }
-
-// Arnoldi column j: H(:, j) = h1 + h2 (two CGS passes), H(j+1, j) = ||w||.
-// Applies the previous Givens rotations, forms the new one, updates g, and
-// solves R y = g(0..j).  st[0] = |g(j+1)| (residual 2-norm estimate),
-// st[1] = H(j+1, j) before rotation.
 // Column j of the Hessenberg matrix (h1 + h2 from the two Gram-Schmidt
 // passes, then ||w||) through the previous rotations into R, a new rotation,
-// the rotated right-hand side g; st = {|g_{j+1}|, ||w||}.  One thread; the
+// the rotated right-hand side g; st[2 (j mod 2) + {0, 1}] = {|g_{j+1}|, ||w||}
+// (two slots, so that step j + 1 may run while the host reads step j).  One thread; the
 // column is streamed (each rotation only needs the entry carried from the
 // previous one).
 __global__ void givens_kernel(const int* __restrict__ dj, int m, const double* __restrict__ h1,
                               const double* __restrict__ h2, const double* __restrict__ wnorm,
                               double* __restrict__ R, double* __restrict__ cs, double* __restrict__ sn,
                               double* __restrict__ g, double* __restrict__ st) {
+  pdl_wait();
+  pdl_trigger();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int j = dj[0];
   const double hn = wnorm[0];
@@ -350,8 +495,8 @@ __global__ void givens_kernel(const int* __restrict__ dj, int m, const double* _
   R[(size_t)j * m + j] = d;
   g[j + 1] = -sk * g[j];
   g[j] = c * g[j];
-  st[0] = fabs(g[j + 1]);
-  st[1] = hn;
+  st[2 * (j & 1)] = fabs(g[j + 1]);
+  st[2 * (j & 1) + 1] = hn;
 }
 
 // y = R^{-1} g for the leading (j+1) x (j+1) block (back substitution).
@@ -389,7 +534,8 @@ bamg_status orient_normalise(int n, double* x, cudaStream_t s);
 
 struct Gm {
   int n, m;
-  DevMem V, Z, w, w2, xj, zeros, h1, h2, part, R, cs, sn, g, y, st, scal, sums;
+  DevMem V, Z, w, w2, xj, zeros, h1, h2, part, R, cs, sn, g, y, scal, sums;
+  DevMem arrived;   // arrival counters of the last-block reductions
 };
 
 static int red_blocks(int n) {
@@ -397,11 +543,11 @@ static int red_blocks(int n) {
   return nb < kRedBlocks ? (nb > 0 ? nb : 1) : kRedBlocks;
 }
 
+enum { kArrMultidot = 0, kArrNorm = 1, kArrBasis = 2, kArrCount = 3 };
+
 static bamg_status norm2_dev(Gm& G, const double* x, double* out, cudaStream_t s) {
-  int nb = red_blocks(G.n);
-  BAMG_TRY(launch(sumsq_kernel, dim3(nb), dim3(256), 0, s, G.n, x, G.part.as<double>()));
-  BAMG_TRY(reduce_partials(G.part.as<double>(), nb, 1, out, s));
-  return launch(sqrt_kernel, dim3(1), dim3(1), 0, s, out);
+  return launch(norm2_kernel, dim3(red_blocks(G.n)), dim3(256), 0, s, G.n, x, G.part.as<double>(),
+                G.arrived.as<unsigned>() + kArrNorm, out);
 }
 
 
@@ -430,13 +576,17 @@ struct GmresState {
   int plain = 0;             // 1: the identity instead of the V-cycle
   Gm G;
   DevMem dj;                 // step index j of the current restart cycle
-  double* st_host = nullptr; // pinned: {|g_{j+1}|, ||w||} of the last step
+  double* st_host = nullptr; // pinned, mapped: {|g_{j+1}|, ||w||} of steps j even / odd
+  double* st_dev = nullptr;  // the same memory as the device sees it
+  cudaEvent_t done[2] = {nullptr, nullptr};   // recorded after steps j even / odd
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   uint64_t kernels = 0;
   ~GmresState() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
+    for (cudaEvent_t e : done)
+      if (e) cudaEventDestroy(e);
     if (st_host) cudaFreeHost(st_host);
   }
 };
@@ -446,44 +596,44 @@ void gmres_release(bamg_hierarchy* h) {
   h->gm = nullptr;
 }
 
-// One Arnoldi step j (read from the device): z_j = C v_j (V-cycle), w = B z_j,
-// two classical Gram-Schmidt passes, ||w||, the Givens update of column j,
-// v_{j+1} = w / ||w||, j <- j + 1, and {|g_{j+1}|, ||w||} to pinned memory.
+// One Arnoldi step j (read from the device): z_j = C v_j (V-cycle, into Z_j
+// and io_out), w = B z_j, two classical Gram-Schmidt passes, ||w||, the
+// Givens update of column j with {|g_{j+1}|, ||w||} to pinned memory,
+// v_{j+1} = w / ||w||, j <- j + 1.  Kernel nodes only (programmatic
+// dependent launches).
 static bamg_status arnoldi_body(bamg_hierarchy* h, GmresState& S, cudaStream_t s) {
   Level& L = h->lv[0];
   Gm& G = S.G;
   const int n = G.n, m = G.m;
   const unsigned gv = cdiv(n, 256);
   const int nb = red_blocks(n);
-  const int* dj = S.dj.as<int>();
+  int* dj = S.dj.as<int>();
   double* V = G.V.as<double>();
-  BAMG_TRY(launch(column_io_kernel, dim3(gv), dim3(256), 0, s, n, dj, 1, V, h->io_in.as<double>()));
+  double* Z = G.Z.as<double>();
+  double* zo = h->io_out.as<double>();
+  unsigned* arr = G.arrived.as<unsigned>();
   if (S.plain)
-    BAMG_TRY(launch(copy_d_kernel, dim3(gv), dim3(256), 0, s, (size_t)n, (const double*)h->io_in.as<double>(),
-                    h->io_out.as<double>()));
+    BAMG_TRY(launch(plain_io_kernel, dim3(gv), dim3(256), 0, s, n, (const int*)dj, (const double*)V, zo, Z));
   else
-    BAMG_TRY(h->mixed ? vcycle_body<float>(h, s) : vcycle_body<double>(h, s));
-  BAMG_TRY(launch(column_io_kernel, dim3(gv), dim3(256), 0, s, n, dj, 0, G.Z.as<double>(), h->io_out.as<double>()));
+    BAMG_TRY(h->mixed ? vcycle_body<float>(h, s, V, dj, zo, Z) : vcycle_body<double>(h, s, V, dj, zo, Z));
   BAMG_TRY(csr_vec<double>(VEC_SPMV, n, L.vec_g, L.B.r(), L.B.c(), L.B.v(), L.dinv.as<double>(), 1.0,
-                           (const double*)h->io_out.as<double>(), nullptr, G.w.as<double>(), s));
-  for (int pass = 0; pass < 2; ++pass) {       // classical Gram-Schmidt, twice
-    double* hc = pass ? G.h2.as<double>() : G.h1.as<double>();
-    BAMG_TRY(launch(multidot_kernel, dim3(nb), dim3(256), 0, s, n, m, dj, (const double*)V, (size_t)n,
-                    (const double*)G.w.as<double>(), G.part.as<double>()));
-    BAMG_TRY(launch(multidot_reduce_kernel, dim3(m + 1), dim3(256), 0, s, nb, m, dj,
-                    (const double*)G.part.as<double>(), hc));
-    BAMG_TRY(launch(orth_update_kernel, dim3(gv), dim3(256), 0, s, n, dj, (const double*)V, (size_t)n,
-                    (const double*)hc, G.w.as<double>()));
-  }
-  BAMG_TRY(norm2_dev(G, G.w.as<double>(), G.scal.as<double>(), s));
-  BAMG_TRY(launch(givens_kernel, dim3(1), dim3(32), 0, s, dj, m, (const double*)G.h1.as<double>(),
-                  (const double*)G.h2.as<double>(), (const double*)G.scal.as<double>(), G.R.as<double>(),
-                  G.cs.as<double>(), G.sn.as<double>(), G.g.as<double>(), G.st.as<double>()));
-  BAMG_TRY(launch(next_basis_kernel, dim3(gv), dim3(256), 0, s, n, dj, (const double*)G.w.as<double>(),
-                  (const double*)G.scal.as<double>(), V));
-  BAMG_TRY(launch(step_kernel, dim3(1), dim3(1), 0, s, S.dj.as<int>()));
-  BAMG_CUDA(cudaMemcpyAsync(S.st_host, G.st.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  return BAMG_OK;
+                           (const double*)zo, nullptr, G.w.as<double>(), s));
+  // classical Gram-Schmidt, twice: h1 = V^T w; w -= V h1, h2 = V^T w;
+  // w -= V h2, ||w||
+  double* h1 = G.h1.as<double>();
+  double* h2 = G.h2.as<double>();
+  const double* Vc = V;
+  BAMG_TRY(launch(gs_kernel<kGsDots>, dim3(nb), dim3(256), 0, s, n, m, (const int*)dj, Vc, (size_t)n,
+                  (const double*)nullptr, G.w.as<double>(), G.part.as<double>(), arr + kArrMultidot, h1));
+  BAMG_TRY(launch(gs_kernel<kGsUpDots>, dim3(nb), dim3(256), 0, s, n, m, (const int*)dj, Vc, (size_t)n,
+                  (const double*)h1, G.w.as<double>(), G.part.as<double>(), arr + kArrMultidot, h2));
+  BAMG_TRY(launch(gs_kernel<kGsUpNorm>, dim3(nb), dim3(256), 0, s, n, m, (const int*)dj, Vc, (size_t)n,
+                  (const double*)h2, G.w.as<double>(), G.part.as<double>(), arr + kArrNorm, G.scal.as<double>()));
+  BAMG_TRY(launch(givens_kernel, dim3(1), dim3(32), 0, s, (const int*)dj, m, (const double*)h1, (const double*)h2,
+                  (const double*)G.scal.as<double>(), G.R.as<double>(), G.cs.as<double>(), G.sn.as<double>(),
+                  G.g.as<double>(), S.st_dev));
+  return launch(next_basis_kernel, dim3(gv), dim3(256), 0, s, n, dj, (const double*)G.w.as<double>(),
+                (const double*)G.scal.as<double>(), V, arr + kArrBasis);
 }
 
 static bamg_status gmres_prepare(bamg_hierarchy* h, int m, int plain) {
@@ -513,16 +663,23 @@ static bamg_status gmres_prepare(bamg_hierarchy* h, int m, int plain) {
   BAMG_TRY(G.sn.alloc(sizeof(double) * m, cs));
   BAMG_TRY(G.g.alloc(sizeof(double) * (m + 1), cs));
   BAMG_TRY(G.y.alloc(sizeof(double) * m, cs));
-  BAMG_TRY(G.st.alloc(sizeof(double) * 2, cs));
   BAMG_TRY(G.scal.alloc(sizeof(double) * 2, cs));
   BAMG_TRY(G.sums.alloc(sizeof(double) * 4, cs));
+  BAMG_TRY(G.arrived.alloc(sizeof(unsigned) * kArrCount, cs));
   BAMG_TRY(S->dj.alloc(sizeof(int), cs));
   BAMG_CUDA(cudaMemsetAsync(G.zeros.p, 0, sizeof(double) * n, cs));
-  BAMG_CUDA(cudaHostAlloc(&S->st_host, 2 * sizeof(double), cudaHostAllocDefault));
+  BAMG_CUDA(cudaMemsetAsync(G.arrived.p, 0, sizeof(unsigned) * kArrCount, cs));
+  BAMG_CUDA(cudaHostAlloc(&S->st_host, 4 * sizeof(double), cudaHostAllocMapped));
+  BAMG_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&S->st_dev), S->st_host, 0));
+  for (cudaEvent_t& e : S->done) BAMG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   BAMG_CUDA(cudaStreamSynchronize(cs));
   uint64_t before = t_launches;
   BAMG_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  bamg_status st = arnoldi_body(h, *S, cs);
+  bamg_status st;
+  {
+    PdlScope pdl;
+    st = arnoldi_body(h, *S, cs);
+  }
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &g);
   if (st != BAMG_OK) {
@@ -534,6 +691,15 @@ static bamg_status gmres_prepare(bamg_hierarchy* h, int m, int plain) {
   BAMG_CUDA(cudaGraphInstantiate(&S->exec, g, 0));
   S->kernels = t_launches - before;
   g_launches.fetch_sub(S->kernels);  // counted at each replay
+  return BAMG_OK;
+}
+
+// Launches the next Arnoldi step (the graph) and records its event.
+static bamg_status step_launch(GmresState& S, int& launched, cudaStream_t s) {
+  BAMG_CUDA(cudaGraphLaunch(S.exec, s));
+  g_launches.fetch_add(S.kernels);
+  BAMG_CUDA(cudaEventRecord(S.done[launched & 1], s));
+  ++launched;
   return BAMG_OK;
 }
 
@@ -578,11 +744,24 @@ bamg_status fgmres(bamg_hierarchy* h, double* x, const bamg_solve_params* sp, ba
     BAMG_TRY(launch(init_g_kernel, dim3(1), dim3(128), 0, s, m, (const double*)G.scal.as<double>(),
                     G.g.as<double>()));
     BAMG_CUDA(cudaMemsetAsync(S.dj.p, 0, sizeof(int), s));
+    // Step j + 1 is launched before the host waits for step j, so the GPU is
+    // not idle while the host reads the estimate, unless step j + 1 cannot be
+    // used (end of the cycle or of max_iter) or the estimates so far predict
+    // that step j meets the stopping test.  A step launched ahead and not
+    // used writes only the column j + 1 entries of the Arnoldi state, which
+    // the solution of step j does not read.
+    int launched = 0;
+    double est1 = -1.0, est2 = -1.0;   // estimates of the last two steps
     for (int j = 0; j < m && !done; ++j) {
-      BAMG_CUDA(cudaGraphLaunch(S.exec, s));
-      g_launches.fetch_add(S.kernels);
-      BAMG_CUDA(cudaStreamSynchronize(s));
-      const double st0 = S.st_host[0], st1 = S.st_host[1];
+      if (launched == j) BAMG_TRY(step_launch(S, launched, s));
+      bool ahead = j + 1 < m && its + 1 < sp->max_iter;
+      if (ahead && est1 > 0.0 && est2 > 0.0 && est1 * (est1 / est2) <= 2.0 * sp->tol * xn1_0) ahead = false;
+      if (ahead) BAMG_TRY(step_launch(S, launched, s));
+      BAMG_CUDA(cudaEventSynchronize(S.done[j & 1]));
+      const volatile double* sh = S.st_host + 2 * (j & 1);
+      const double st0 = sh[0], st1 = sh[1];
+      est2 = est1;
+      est1 = st0;
       const int K = j + 1;
       ++its;
       if (it7 < 0 && st0 <= 1e-7 * xn2_0) it7 = its;
@@ -683,7 +862,8 @@ bamg_status vcycle_factor(bamg_hierarchy* h, int iters, uint64_t seed, double* f
   return BAMG_OK;
 }
 
-template bamg_status vcycle_body<double>(bamg_hierarchy*, cudaStream_t);
-template bamg_status vcycle_body<float>(bamg_hierarchy*, cudaStream_t);
+template bamg_status vcycle_body<double>(bamg_hierarchy*, cudaStream_t, const double*, const int*, double*,
+                                         double*);
+template bamg_status vcycle_body<float>(bamg_hierarchy*, cudaStream_t, const double*, const int*, double*, double*);
 
 }  // namespace bamg

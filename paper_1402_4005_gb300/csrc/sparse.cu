@@ -11,6 +11,7 @@ namespace bamg {
 
 std::atomic<uint64_t> g_launches{0};
 thread_local uint64_t t_launches = 0;
+thread_local bool t_pdl = false;
 static thread_local char t_err[512] = "";
 
 void set_error(const char* fmt, ...) {

@@ -143,8 +143,9 @@ def test_ls_fit_counts_rank_deficient_rows_once(api, prec):
 @pytest.mark.parametrize("name", ["small", "delaunay", "tandem"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_csr_vec_modes_against_oracle(api, name, prec):
-    """The V-cycle / GMRES vector kernel in all five modes against the
-    oracle's Jacobi sweep and sparse products (1e-12 / 1e-5 scaled)."""
+    """The V-cycle / GMRES vector kernel in all six modes against the
+    oracle's Jacobi sweeps and sparse products (1e-12 / 1e-5 scaled); the
+    two sweeps from zero in one pass bit for bit equal to the two launches."""
     if name == "small":
         ch = cg.delaunay_walk(2999, seed=12)
         B = operators.build_B(ch.csr()); B.sort_indices()
@@ -169,3 +170,10 @@ def test_csr_vec_modes_against_oracle(api, name, prec):
     y = dev(y0).to(dt)
     api.bamg_step_csr_vec("spmv_add", rp, ci, va, x=xd, y=y)
     assert scaled_err(y.double().cpu().numpy(), y0 + B @ x, B, x, y0) <= tol
+    z1 = api.bamg_step_csr_vec("jacobi_zero", rp, ci, va, b=bd, dinv=dinv)
+    z2 = api.bamg_step_csr_vec("jacobi", rp, ci, va, x=z1, b=bd, dinv=dinv)
+    z2f = api.bamg_step_csr_vec("jacobi_zero2", rp, ci, va, b=bd, dinv=dinv)
+    assert torch.equal(z2f, z2)
+    r1 = smoothing.jacobi(B, d, np.zeros((n, 1)), b[:, None], 0.7)
+    r2 = smoothing.jacobi(B, d, r1, b[:, None], 0.7)[:, 0]
+    assert scaled_err(z2f.double().cpu().numpy(), r2, B, r1[:, 0], b) <= tol
