@@ -260,16 +260,39 @@ bamg_status vcycle_run(bamg_hierarchy* h, cudaStream_t s) {
 //   kGsDots:   out[k] = V_k . w;
 //   kGsUpDots: w -= sum_k hin[k] V_k, then out[k] = V_k . w (the first pass's
 //              update and the second pass's products: V read once for both);
-//   kGsUpNorm: w -= sum_k hin[k] V_k, then out[0] = ||w||_2.
+//   kGsUpNorm: w -= sum_k hin[k] V_k, then out[0] = ||w||_2, out[1] = 1 / out[0].
 // One wave of at most kRedBlocks blocks; each thread takes the rows
-// tid, tid + stride, ...; loads of eight columns are issued together.  A
-// block adds its warp sums in warp order into part (row stride m + 1); the
-// last block to finish adds the blocks' shares (thread t takes block t,
-// then warp sums in warp order) and resets the arrival counter.  The order
-// is fixed, so every run gives the same result.
+// tid, tid + stride, ...; loads of eight columns are issued together.
+// FP64 arithmetic is the scarce resource here, so the eight per-lane sums of
+// a chunk are reduced over the warp by a reduce-scatter (nine additions per
+// lane instead of five per column).  A block adds its warps' totals in warp
+// order into part (row stride m + 1); the last block to finish reduces the
+// blocks' shares the same way (thread t takes block t) and resets the
+// arrival counter.  The order is fixed, so every run gives the same result.
 constexpr int kMultidotMax = 65;   // m + 1 <= 65 (restart <= 64)
 constexpr int kRedBlocks = 256;
 enum { kGsDots = 0, kGsUpDots = 1, kGsUpNorm = 2 };
+
+// Warp reduce-scatter of eight per-lane values a[0..7]: returns, in every
+// lane, the warp total of column rs8_col(lane) (the four lanes that differ
+// only in bits 0 and 1 hold the same column).
+__device__ __forceinline__ int rs8_col(int lane) { return (lane >> 2) & 7; }
+__device__ __forceinline__ double rs8(const double (&a)[8], int lane) {
+  const unsigned full = 0xffffffffu;
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+  double b[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)      // lanes without bit 4 keep columns 0..3, the others 4..7
+    b[q] = (h16 ? a[q + 4] : a[q]) + __shfl_xor_sync(full, h16 ? a[q] : a[q + 4], 16);
+  double c[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+    c[q] = (h8 ? b[q + 2] : b[q]) + __shfl_xor_sync(full, h8 ? b[q] : b[q + 2], 8);
+  double d = (h4 ? c[1] : c[0]) + __shfl_xor_sync(full, h4 ? c[0] : c[1], 4);
+  d += __shfl_xor_sync(full, d, 2);
+  d += __shfl_xor_sync(full, d, 1);
+  return d;
+}
 
 template <int MODE>
 __global__ void __launch_bounds__(256) gs_kernel(int n, int m, const int* __restrict__ dj,
@@ -283,6 +306,7 @@ __global__ void __launch_bounds__(256) gs_kernel(int n, int m, const int* __rest
   __shared__ double hs[kMultidotMax];
   __shared__ bool last;
   const int K = dj[0] + 1, lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int col = rs8_col(lane);
   const int stride = gridDim.x * blockDim.x, i0 = blockIdx.x * blockDim.x + threadIdx.x;
   double ss = 0.0;
   if (MODE != kGsDots) {
@@ -322,13 +346,11 @@ __global__ void __launch_bounds__(256) gs_kernel(int n, int m, const int* __rest
 #pragma unroll
         for (int u = 0; u < 8; ++u) v[u] = kc + u < K ? V[(size_t)(kc + u) * ldv + i] : 0.0;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) sd[u] += v[u] * wi;
+        for (int u = 0; u < 8; ++u)
+          if (kc + u < K) sd[u] += v[u] * wi;
       }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const double r = warp_sum(sd[u]);
-        if (lane == 0 && kc + u < K) sh[wp][kc + u] = r;
-      }
+      const double r = rs8(sd, lane);
+      if ((lane & 3) == 0 && kc + col < K) sh[wp][kc + col] = r;
     }
     __syncthreads();
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
@@ -352,7 +374,9 @@ __global__ void __launch_bounds__(256) gs_kernel(int n, int m, const int* __rest
     if (t == 0) {
       double a = 0.0;
       for (int q = 0; q < 8; ++q) a += sh[q][0];
-      out[0] = sqrt(a);
+      const double nrm = sqrt(a);
+      out[0] = nrm;
+      out[1] = 1.0 / nrm;
       *arrived = 0u;
     }
     return;
@@ -361,11 +385,8 @@ __global__ void __launch_bounds__(256) gs_kernel(int n, int m, const int* __rest
     double v[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) v[u] = (kc + u < K && t < nb) ? __ldcg(part + (size_t)t * (m + 1) + kc + u) : 0.0;
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const double r = warp_sum(v[u]);
-      if (lane == 0 && kc + u < K) sh[wp][kc + u] = r;
-    }
+    const double r = rs8(v, lane);
+    if ((lane & 3) == 0 && kc + col < K) sh[wp][kc + col] = r;
   }
   __syncthreads();
   for (int k = t; k < K; k += blockDim.x) {
@@ -389,17 +410,18 @@ __global__ void plain_io_kernel(int n, const int* __restrict__ dj, const double*
   Z[o] = v;
 }
 
-// V_{j+1} = w / ||w||, then j <- j + 1: the last block to finish (every
-// block has read j by then) increments j and resets the arrival counter.
+// V_{j+1} = w * (1 / ||w||) (rinv holds the reciprocal), then j <- j + 1:
+// the last block to finish (every block has read j by then) increments j and
+// resets the arrival counter.
 __global__ void next_basis_kernel(int n, int* __restrict__ dj, const double* __restrict__ w,
-                                  const double* __restrict__ nrm, double* __restrict__ V,
+                                  const double* __restrict__ rinv, double* __restrict__ V,
                                   unsigned* __restrict__ arrived) {
   pdl_wait();
   pdl_trigger();
   __shared__ bool last;
   const int j = dj[0];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) V[(size_t)(j + 1) * n + i] = w[i] / nrm[0];
+  if (i < n) V[(size_t)(j + 1) * n + i] = w[i] * rinv[0];
   __syncthreads();
   if (threadIdx.x == 0) last = atomicAdd(arrived, 1u) == gridDim.x - 1;
   __syncthreads();
@@ -415,7 +437,14 @@ __global__ void combine_kernel(int n, int K, const double* __restrict__ Z, size_
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double acc = x[i];
-  for (int k = 0; k < K; ++k) acc += c[k] * Z[(size_t)k * ldz + i];
+  for (int kc = 0; kc < K; kc += 8) {       // eight column loads in flight
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = kc + u < K ? Z[(size_t)(kc + u) * ldz + i] : 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (kc + u < K) acc += c[kc + u] * v[u];
+  }
   y[i] = acc;
 }
 
@@ -469,22 +498,33 @@ __global__ void __launch_bounds__(256) norm2_kernel(int n, const double* __restr
 // Column j of the Hessenberg matrix (h1 + h2 from the two Gram-Schmidt
 // passes, then ||w||) through the previous rotations into R, a new rotation,
 // the rotated right-hand side g; st[2 (j mod 2) + {0, 1}] = {|g_{j+1}|, ||w||}
-// (two slots, so that step j + 1 may run while the host reads step j).  One thread; the
-// column is streamed (each rotation only needs the entry carried from the
-// previous one).
+// (two slots, so that step j + 1 may run while the host reads step j).  One
+// warp stages the column and the rotations in shared memory; one thread
+// then streams the column through the rotations (each only needs the entry
+// carried from the previous one).
 __global__ void givens_kernel(const int* __restrict__ dj, int m, const double* __restrict__ h1,
                               const double* __restrict__ h2, const double* __restrict__ wnorm,
                               double* __restrict__ R, double* __restrict__ cs, double* __restrict__ sn,
                               double* __restrict__ g, double* __restrict__ st) {
   pdl_wait();
   pdl_trigger();
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  __shared__ double hc[kMultidotMax], cc[kMultidotMax], sc[kMultidotMax];
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
   const int j = dj[0];
+  for (int k = threadIdx.x; k <= j; k += 32) {
+    hc[k] = h1[k] + h2[k];
+    if (k < j) {
+      cc[k] = cs[k];
+      sc[k] = sn[k];
+    }
+  }
+  __syncwarp();
+  if (threadIdx.x != 0) return;
   const double hn = wnorm[0];
-  double carry = h1[0] + h2[0];
+  double carry = hc[0];
   for (int k = 0; k < j; ++k) {
-    const double next = h1[k + 1] + h2[k + 1];
-    const double c = cs[k], sk = sn[k];
+    const double next = hc[k + 1];
+    const double c = cc[k], sk = sc[k];
     R[(size_t)k * m + j] = c * carry + sk * next;
     carry = -sk * carry + c * next;
   }
@@ -499,15 +539,27 @@ __global__ void givens_kernel(const int* __restrict__ dj, int m, const double* _
   st[2 * (j & 1) + 1] = hn;
 }
 
-// y = R^{-1} g for the leading (j+1) x (j+1) block (back substitution).
+// y = R^{-1} g for the leading (j+1) x (j+1) block (back substitution).  A
+// warp stages the upper triangle in shared memory (at most 64 x 64, stride
+// kYsolveLd), one thread substitutes.
+constexpr int kYsolveLd = 65;
 __global__ void ysolve_kernel(int j, int m, const double* __restrict__ R, const double* __restrict__ g,
                               double* __restrict__ y) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  extern __shared__ double rs[];      // (j + 1) x kYsolveLd, then g and y
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  double* gs = rs + (size_t)(j + 1) * kYsolveLd;
+  double* ys = gs + (j + 1);
+  for (int k = 0; k <= j; ++k)
+    for (int q = k + (int)threadIdx.x; q <= j; q += 32) rs[k * kYsolveLd + q] = R[(size_t)k * m + q];
+  for (int k = threadIdx.x; k <= j; k += 32) gs[k] = g[k];
+  __syncwarp();
+  if (threadIdx.x != 0) return;
   for (int k = j; k >= 0; --k) {
-    double acc = g[k];
-    for (int q = k + 1; q <= j; ++q) acc -= R[(size_t)k * m + q] * y[q];
-    const double rkk = R[(size_t)k * m + k];
-    y[k] = rkk != 0.0 ? acc / rkk : 0.0;
+    double acc = gs[k];
+    for (int q = k + 1; q <= j; ++q) acc -= rs[k * kYsolveLd + q] * ys[q];
+    const double rkk = rs[k * kYsolveLd + k];
+    ys[k] = rkk != 0.0 ? acc / rkk : 0.0;
+    y[k] = ys[k];
   }
 }
 
@@ -633,7 +685,7 @@ static bamg_status arnoldi_body(bamg_hierarchy* h, GmresState& S, cudaStream_t s
                   (const double*)G.scal.as<double>(), G.R.as<double>(), G.cs.as<double>(), G.sn.as<double>(),
                   G.g.as<double>(), S.st_dev));
   return launch(next_basis_kernel, dim3(gv), dim3(256), 0, s, n, dj, (const double*)G.w.as<double>(),
-                (const double*)G.scal.as<double>(), V, arr + kArrBasis);
+                (const double*)G.scal.as<double>() + 1, V, arr + kArrBasis);
 }
 
 static bamg_status gmres_prepare(bamg_hierarchy* h, int m, int plain) {
@@ -768,7 +820,7 @@ bamg_status fgmres(bamg_hierarchy* h, double* x, const bamg_solve_params* sp, ba
       breakdown = !(st1 > 0.0);
       bool last = (j == m - 1) || its >= sp->max_iter || breakdown;
       if (st0 <= 2.0 * sp->tol * xn1_0 || last) {
-        BAMG_TRY(launch(ysolve_kernel, dim3(1), dim3(32), 0, s, j, m, (const double*)G.R.as<double>(),
+        BAMG_TRY(launch(ysolve_kernel, dim3(1), dim3(32), sizeof(double) * ((size_t)(j + 1) * (kYsolveLd + 2)), s, j, m, (const double*)G.R.as<double>(),
                         (const double*)G.g.as<double>(), G.y.as<double>()));
         BAMG_TRY(launch(combine_kernel, dim3(gv), dim3(256), 0, s, n, K, (const double*)Z, (size_t)n,
                         (const double*)G.y.as<double>(), (const double*)x, G.xj.as<double>()));
