@@ -142,6 +142,7 @@ bamg_status setup_impl(const bamg_csr* A, const bamg_params* p, void* stream, ba
         break;
       }
     }
+    h->prep_early = prepare ? 1 : 0;
     st = setup_finest(h, A, s);
     if (st != BAMG_OK) break;
     st = h->mixed ? run_setup<float>(h, s) : run_setup<double>(h, s);

@@ -40,6 +40,7 @@
 
 #include <atomic>
 #include <cfloat>
+#include <chrono>
 #include <cstdio>
 #include <cstdlib>
 
@@ -1496,7 +1497,7 @@ static bamg_status side_stream(cudaStream_t* out) {
 
 template <typename T>
 static bamg_status coarsest_t(int n, int r, const double* B, const double* M, const double* N, double* sigma,
-                              double* U, double* V, double* Bpinv, cudaStream_t s) {
+                              double* U, double* V, double* Bpinv, cudaStream_t s, HostWork during) {
   // ---- triplets: Cholesky, C, bidiagonalization, SVD, back-transform
   DenseArgs<T> a = {};
   a.n = n; a.r = r; a.B = B; a.M = M; a.N = N;
@@ -1589,9 +1590,15 @@ static bamg_status coarsest_t(int n, int r, const double* B, const double* M, co
     cudaEventDestroy(ev1);
   }
   BAMG_TRY(st);
+  // (before the status read below: a copy into pageable memory returns only
+  // when the stream has drained)
+  const auto t_hw0 = std::chrono::steady_clock::now();
+  const bamg_status hw = during.fn ? during.fn(during.ctx) : BAMG_OK;
+  const auto t_hw1 = std::chrono::steady_clock::now();
   DenseCtl h[2];
   BAMG_CUDA(cudaMemcpyAsync(h, ctl.p, sizeof(h), cudaMemcpyDeviceToHost, s));
   BAMG_CUDA(cudaStreamSynchronize(s));
+  const auto t_hw2 = std::chrono::steady_clock::now();
   if (std::getenv("BAMG_TRACE")) {
     const char* nm[5] = {"cholesky", "form_C", "bidiag", "bidiag_svd", "triplets"};
     fprintf(stderr, "[bamg] coarsest n=%d prec=%s cluster=%d %s:", n, sizeof(T) == 4 ? "f32" : "f64", csize,
@@ -1601,23 +1608,27 @@ static bamg_status coarsest_t(int n, int r, const double* B, const double* M, co
         fprintf(stderr, " %s=%.1fus", nm[k], (h[0].tp[k + 1] - h[0].tp[k]) / 1e3);
     if (Bpinv && h[1].tp[1] >= h[1].tp[0])
       fprintf(stderr, " | pinv (%s, concurrent)=%.1fus", p_sm ? "smem" : "global", (h[1].tp[1] - h[1].tp[0]) / 1e3);
+    if (during.fn)
+      fprintf(stderr, " | host work meanwhile %.1fus, then waited %.1fus",
+              std::chrono::duration<double, std::micro>(t_hw1 - t_hw0).count(),
+              std::chrono::duration<double, std::micro>(t_hw2 - t_hw1).count());
     fprintf(stderr, "\n");
   }
   if (h[0].err == 2) {
     set_error("coarsest level: M or N is not positive definite");
     return BAMG_ERR_NUMERIC;
   }
-  return BAMG_OK;
+  return hw;
 }
 
 bamg_status coarsest_solve(int prec, int n, int r, const double* B, const double* M, const double* N,
-                           double* sigma, double* U, double* V, double* Bpinv, cudaStream_t s) {
+                           double* sigma, double* U, double* V, double* Bpinv, cudaStream_t s, HostWork during) {
   if (n < 2 || n > kDenseMaxN || r < 1 || r > n || r > kMaxR) {
     set_error("coarsest solve needs 1 <= r <= min(n, %d), 2 <= n <= %d (n = %d, r = %d)", kMaxR, kDenseMaxN, n, r);
     return BAMG_ERR_UNSUPPORTED;
   }
-  if (prec == 1) return coarsest_t<float>(n, r, B, M, N, sigma, U, V, Bpinv, s);
-  return coarsest_t<double>(n, r, B, M, N, sigma, U, V, Bpinv, s);
+  if (prec == 1) return coarsest_t<float>(n, r, B, M, N, sigma, U, V, Bpinv, s, during);
+  return coarsest_t<double>(n, r, B, M, N, sigma, U, V, Bpinv, s, during);
 }
 
 }  // namespace bamg

@@ -509,13 +509,27 @@ static bamg_status run_setup(bamg_hierarchy* h, cudaStream_t s) {
       BAMG_TRY(csr_to_dense(nL, LL.N.r(), LL.N.c(), LL.N.v(), Nd.as<double>(), s));
     }
     BAMG_TRY(h->Bpinv.alloc(sizeof(double) * nn, s));
+    if (h->mixed) BAMG_TRY(h->Bpinv32.alloc(sizeof(float) * nn, s));
+    // In the last bootstrap cycle every level the V-cycle reads exists now:
+    // its graph and the Arnoldi graph are captured on the host while the
+    // coarsest kernels run (capture records pointers only).
+    struct Early {
+      bamg_hierarchy* h;
+      cudaStream_t s;
+    } early{h, s};
+    HostWork during;
+    if (h->prep_early && cyc == cycles - 1 && p.smoother == BAMG_SMOOTH_JACOBI) {
+      during.ctx = &early;
+      during.fn = [](void* c) -> bamg_status {
+        Early* e = static_cast<Early*>(c);
+        BAMG_TRY(vcycle_prepare(e->h, e->s));
+        return gmres_prepare_default(e->h);
+      };
+    }
     // Ud/Vd are nL x rr row-major (rr <= r)
     BAMG_TRY(coarsest_solve(h->mixed ? 1 : 0, nL, rr, Bd.as<double>(), Md.as<double>(), Nd.as<double>(),
-                            sg.as<double>(), Ud.as<double>(), Vd.as<double>(), h->Bpinv.as<double>(), s));
-    if (h->mixed) {
-      BAMG_TRY(h->Bpinv32.alloc(sizeof(float) * nn, s));
-      BAMG_TRY(convert<double, float>(nn, h->Bpinv.as<double>(), h->Bpinv32.as<float>(), s));
-    }
+                            sg.as<double>(), Ud.as<double>(), Vd.as<double>(), h->Bpinv.as<double>(), s, during));
+    if (h->mixed) BAMG_TRY(convert<double, float>(nn, h->Bpinv.as<double>(), h->Bpinv32.as<float>(), s));
     tr.mark(s, "coarsest solve", l);
     if (learned) return learned_unwind(h, l, rr, Vd.as<double>(), sg.as<double>(), s);
     // triplets into padded blocks

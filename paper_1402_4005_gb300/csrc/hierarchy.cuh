@@ -83,6 +83,7 @@ struct bamg_hierarchy {
   double op_cplx = 0.0, grid_cplx = 0.0;
   int rankdef = 0;
   bamg::GmresState* gm = nullptr;       // FGMRES workspace (first solve)
+  int prep_early = 0;                   // capture the V-cycle and Arnoldi graphs during the coarsest solve
   int learned = 0;                      // fits from the interpolation network
   bamg::DevMem mlp;                     // its parameters (float, copied at setup)
 };
@@ -94,6 +95,9 @@ template <typename T>
 bamg_status vcycle_body(bamg_hierarchy* h, cudaStream_t s, const double* in, const int* col, double* out,
                         double* out_col);
 bamg_status vcycle_prepare(bamg_hierarchy* h, cudaStream_t s);
+// solve.cu: FGMRES workspace and Arnoldi graph for the default restart
+// (20), unpreconditioned = false; a solve with other settings re-captures
+bamg_status gmres_prepare_default(bamg_hierarchy* h);
 bamg_status vcycle_run(bamg_hierarchy* h, cudaStream_t s);
 bamg_status promote_fp64(bamg_hierarchy* h, cudaStream_t s);
 bamg_status fgmres(bamg_hierarchy* h, double* x, const bamg_solve_params* sp, bamg_solve_info* info,

@@ -164,9 +164,16 @@ bamg_status ls_fit(int n, int ld, int r, const int32_t* J_rp, const int32_t* J_c
 // mlp_tc.cu: network inference on the tensor cores (err_dev: timeout flag)
 bamg_status mlp_forward_tc(int M, const float* P, const void* X, float* Y, int* err_dev, cudaStream_t s);
 
-// dense.cu
+// dense.cu.  during (optional): host work run while the coarsest kernels
+// execute (after their launch, before the call waits for them); its status
+// is returned when the solve itself succeeds.
+struct HostWork {
+  bamg_status (*fn)(void* ctx) = nullptr;
+  void* ctx = nullptr;
+};
 bamg_status coarsest_solve(int prec, int n, int r, const double* B, const double* M, const double* N,
-                           double* sigma, double* U, double* V, double* Bpinv, cudaStream_t s);
+                           double* sigma, double* U, double* V, double* Bpinv, cudaStream_t s,
+                           HostWork during = HostWork());
 bamg_status csr_to_dense(int n, const int32_t* rp, const int32_t* ci, const double* va, double* D,
                          cudaStream_t s);
 

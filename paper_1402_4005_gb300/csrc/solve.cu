@@ -18,8 +18,11 @@
 // allows it to hold.  With the identity in place of the V-cycle and the
 // uniform start vector the same code is the unpreconditioned GMRES(m) the
 // paper compares against (Section 7).
+#include <cuda.h>
+
 #include <chrono>
 #include <cmath>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -170,7 +173,8 @@ bamg_status vcycle_prepare(bamg_hierarchy* h, cudaStream_t s) {
   }
   BAMG_TRY(h->io_in.alloc(sizeof(double) * h->lv[0].n, s));
   BAMG_TRY(h->io_out.alloc(sizeof(double) * h->lv[0].n, s));
-  if (h->p.smoother == BAMG_SMOOTH_MCGS)
+  const bool mcgs = h->p.smoother == BAMG_SMOOTH_MCGS;
+  if (mcgs)
     for (size_t l = 0; l + 1 < h->lv.size(); ++l) {     // colourings of the smoothed levels
       Level& L = h->lv[l];
       BAMG_TRY(L.colour.alloc(sizeof(int32_t) * L.n, s));
@@ -180,7 +184,9 @@ bamg_status vcycle_prepare(bamg_hierarchy* h, cudaStream_t s) {
       L.crp.assign(L.ncol + 1, 0);
       BAMG_TRY(colour_rows(L.n, L.colour.as<int32_t>(), L.ncol, L.crp.data(), L.crows.as<int32_t>(), s));
     }
-  BAMG_CUDA(cudaStreamSynchronize(s));
+  // (the Jacobi V-cycle needs no result of the stream's pending work: the
+  // capture only records pointers, and the graph runs after the setup)
+  if (mcgs) BAMG_CUDA(cudaStreamSynchronize(s));
   if (!h->cap_stream) BAMG_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   uint64_t before = t_launches;
   BAMG_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -637,13 +643,87 @@ static bamg_status true_residual(bamg_hierarchy* h, Gm& G, const double* x, doub
 // Persistent FGMRES workspace of a hierarchy and the captured Arnoldi step
 // (rebuilt when the restart length changes).  Buffers live on the
 // hierarchy's private stream, which outlives them.
+// Pinned, mapped host slots (four doubles) for the per-step Arnoldi status.
+// A pinned allocation per workspace may synchronise with the device (and a
+// pinned free does), so slots come from chunks allocated once per CUDA
+// context and kept for its life.  Slots are keyed by the context id: after a
+// device reset (a new context) the old chunks are gone, their slots are
+// dropped and never handed out again.
+namespace {
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+constexpr int kSlotDoubles = 4, kSlotsPerChunk = 256;
+std::mutex g_slot_mu;
+unsigned long long g_slot_ctx = 0;
+std::vector<double*> g_slot_free;
+
+unsigned long long slot_ctx_id() {
+  static CtxGetCurrentFn get_cur = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_cur = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+  });
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (!get_cur || !get_id || get_cur(&c) != CUDA_SUCCESS || c == nullptr || get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+}  // namespace
+
+// A slot of the current context (*ctx receives its id); nullptr on failure.
+static double* slot_get(unsigned long long* ctx) {
+  const unsigned long long id = slot_ctx_id();
+  std::lock_guard<std::mutex> lk(g_slot_mu);
+  if (id == 0 || id != g_slot_ctx) {
+    g_slot_free.clear();
+    g_slot_ctx = id;
+  }
+  if (id == 0) {   // no context id: a slot of its own, freed with the workspace
+    void* p = nullptr;
+    if (cudaHostAlloc(&p, sizeof(double) * kSlotDoubles, cudaHostAllocMapped) != cudaSuccess) return nullptr;
+    *ctx = 0;
+    return static_cast<double*>(p);
+  }
+  if (g_slot_free.empty()) {
+    void* c = nullptr;
+    if (cudaHostAlloc(&c, sizeof(double) * kSlotDoubles * kSlotsPerChunk, cudaHostAllocMapped | cudaHostAllocPortable) !=
+        cudaSuccess)
+      return nullptr;
+    for (int i = kSlotsPerChunk - 1; i >= 0; --i) g_slot_free.push_back(static_cast<double*>(c) + i * kSlotDoubles);
+  }
+  double* p = g_slot_free.back();
+  g_slot_free.pop_back();
+  *ctx = id;
+  return p;
+}
+
+static void slot_put(double* p, unsigned long long ctx) {
+  if (!p) return;
+  if (ctx == 0) {
+    cudaFreeHost(p);
+    return;
+  }
+  std::lock_guard<std::mutex> lk(g_slot_mu);
+  if (ctx == g_slot_ctx) g_slot_free.push_back(p);
+}
+
 struct GmresState {
   int m = 0;
   int plain = 0;             // 1: the identity instead of the V-cycle
   Gm G;
   DevMem dj;                 // step index j of the current restart cycle
-  double* st_host = nullptr; // pinned, mapped: {|g_{j+1}|, ||w||} of steps j even / odd
+  double* st_host = nullptr; // pinned, mapped slot: {|g_{j+1}|, ||w||} of steps j even / odd
   double* st_dev = nullptr;  // the same memory as the device sees it
+  unsigned long long st_ctx = 0;
   cudaEvent_t done[2] = {nullptr, nullptr};   // recorded after steps j even / odd
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -653,7 +733,7 @@ struct GmresState {
     if (graph) cudaGraphDestroy(graph);
     for (cudaEvent_t e : done)
       if (e) cudaEventDestroy(e);
-    if (st_host) cudaFreeHost(st_host);
+    slot_put(st_host, st_ctx);
   }
 };
 
@@ -735,7 +815,11 @@ static bamg_status gmres_prepare(bamg_hierarchy* h, int m, int plain) {
   BAMG_TRY(S->dj.alloc(sizeof(int), cs));
   BAMG_CUDA(cudaMemsetAsync(G.zeros.p, 0, sizeof(double) * n, cs));
   BAMG_CUDA(cudaMemsetAsync(G.arrived.p, 0, sizeof(unsigned) * kArrCount, cs));
-  BAMG_CUDA(cudaHostAlloc(&S->st_host, 4 * sizeof(double), cudaHostAllocMapped));
+  S->st_host = slot_get(&S->st_ctx);
+  if (!S->st_host) {
+    set_error("pinned host memory for the Arnoldi status could not be allocated");
+    return BAMG_ERR_OOM;
+  }
   BAMG_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&S->st_dev), S->st_host, 0));
   for (cudaEvent_t& e : S->done) BAMG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   BAMG_CUDA(cudaStreamSynchronize(cs));
@@ -759,6 +843,8 @@ static bamg_status gmres_prepare(bamg_hierarchy* h, int m, int plain) {
   g_launches.fetch_sub(S->kernels);  // counted at each replay
   return BAMG_OK;
 }
+
+bamg_status gmres_prepare_default(bamg_hierarchy* h) { return gmres_prepare(h, 20, 0); }
 
 // Launches the next Arnoldi step (the graph) and records its event.
 static bamg_status step_launch(GmresState& S, int& launched, cudaStream_t s) {
