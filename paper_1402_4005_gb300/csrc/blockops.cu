@@ -88,6 +88,8 @@ __device__ inline void row_times_block(int i, int q, const int32_t* __restrict__
 // selects the job.
 template <typename T, int LD, int W>
 __global__ void __launch_bounds__(256, 6) relax_block_kernel(RelaxJob<T> j0, RelaxJob<T> j1) {
+  pdl_wait();
+  pdl_trigger();
   using C = RowBlk<T, LD, W>;
   const RelaxJob<T>& a = blockIdx.y ? j1 : j0;
   int lane = threadIdx.x & 31;
@@ -124,6 +126,8 @@ __global__ void __launch_bounds__(256, 6) relax_block_kernel(RelaxJob<T> j0, Rel
 // launch (blockIdx.y selects one).
 template <typename T, int LD, int W>
 __global__ void __launch_bounds__(256, 6) spmm_block_kernel(SpmmJob<T> j0, SpmmJob<T> j1, SpmmJob<T> j2) {
+  pdl_wait();
+  pdl_trigger();
   using C = RowBlk<T, LD, W>;
   const SpmmJob<T>& a = blockIdx.y == 0 ? j0 : (blockIdx.y == 1 ? j1 : j2);
   int lane = threadIdx.x & 31;
@@ -147,6 +151,8 @@ coldot_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__
               const T* __restrict__ B0, const T* __restrict__ A1, const T* __restrict__ B1,
               const T* __restrict__ A2, const T* __restrict__ B2, int npairs,
               double* __restrict__ part) {
+  pdl_wait();
+  pdl_trigger();
   using C = Blk<T, LD>;
   // per-thread sums in the block precision (a thread covers a few rows; the
   // FP64 pipes of GB300 are narrow), block and grid sums in FP64
@@ -249,6 +255,8 @@ __global__ void scale_cols_kernel(int n, T* __restrict__ X, const T* __restrict_
 template <typename T>
 __global__ void rayleigh_finalize_kernel(const double* __restrict__ sums, int LD, int r,
                                          T* __restrict__ sig, double* __restrict__ sig64) {
+  pdl_wait();
+  pdl_trigger();
   int k = threadIdx.x;
   if (k >= LD) return;
   double num = sums[k], um = sums[LD + k], vn = sums[2 * LD + k];

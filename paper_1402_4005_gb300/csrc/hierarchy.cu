@@ -192,11 +192,14 @@ static bamg_status coarsen_level(bamg_hierarchy* h, int l, DevMem& U, DevMem& V,
   // Algorithm 1, first smoothing loop: relax V with B and U with B^T
   // (not needed when the network proposes the fits)
   if (inhomog && !learned) BAMG_TRY(relax_triplets<T>(h, l, U, V, sig, sig64, s));
-  for (int it = 0; !learned && !inhomog && it < p.nu_setup; ++it) {
-    BAMG_TRY(relax_block2<T>(L.n, ld, L.B.r(), L.B.c(), Bv, L.Bt.r(), L.Bt.c(), Btv, dv, V.as<T>(), tmpV.as<T>(),
-                             U.as<T>(), tmpU.as<T>(), nullptr, nullptr, nullptr, om, 1, s));
-    std::swap(V, tmpV);
-    std::swap(U, tmpU);
+  {
+    PdlScope pdl;   // block relaxations only, each waiting for its predecessor
+    for (int it = 0; !learned && !inhomog && it < p.nu_setup; ++it) {
+      BAMG_TRY(relax_block2<T>(L.n, ld, L.B.r(), L.B.c(), Bv, L.Bt.r(), L.Bt.c(), Btv, dv, V.as<T>(),
+                               tmpV.as<T>(), U.as<T>(), tmpU.as<T>(), nullptr, nullptr, nullptr, om, 1, s));
+      std::swap(V, tmpV);
+      std::swap(U, tmpU);
+    }
   }
   tr.mark(s, "relax", l);
   // eq. ls_weights with unit vectors
@@ -328,6 +331,10 @@ static bamg_status coarsen_level(bamg_hierarchy* h, int l, DevMem& U, DevMem& V,
 template <typename T>
 static bamg_status relax_triplets(bamg_hierarchy* h, int l, DevMem& U, DevMem& V, DevMem& sig, DevMem& sig64,
                                   cudaStream_t s) {
+  // a chain of small dependent kernels (block relaxation, block products,
+  // column dots, partial sums, Rayleigh quotients), each of which waits for
+  // its predecessor first: launched with programmatic serialisation
+  PdlScope pdl;
   const bamg_params& p = h->p;
   const int ld = h->ld, r = p.r;
   Level& L = h->lv[l];
@@ -552,8 +559,11 @@ static bamg_status run_setup(bamg_hierarchy* h, cudaStream_t s) {
     // bottom-up: interpolate and relax (Algorithm 1, last loop)
     for (int k = l - 1; k >= 0; --k) {
       Level& L = h->lv[k];
-      BAMG_TRY(spmm_block<T>(L.n, ld, L.Qt.r(), L.Qt.c(), L.Qt.vals<T>(), U[k + 1].as<T>(), U[k].as<T>(), s));
-      BAMG_TRY(spmm_block<T>(L.n, ld, L.P.r(), L.P.c(), L.P.vals<T>(), V[k + 1].as<T>(), V[k].as<T>(), s));
+      {
+        PdlScope pdl;
+        BAMG_TRY(spmm_block<T>(L.n, ld, L.Qt.r(), L.Qt.c(), L.Qt.vals<T>(), U[k + 1].as<T>(), U[k].as<T>(), s));
+        BAMG_TRY(spmm_block<T>(L.n, ld, L.P.r(), L.P.c(), L.P.vals<T>(), V[k + 1].as<T>(), V[k].as<T>(), s));
+      }
       BAMG_TRY(relax_triplets<T>(h, k, U[k], V[k], sig, sig64, s));
       tr.mark(s, "bottom-up relax", k);
       U[k + 1].release();

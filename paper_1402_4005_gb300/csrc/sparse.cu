@@ -224,6 +224,8 @@ bamg_status scan_counts(const int32_t* counts, int32_t* out, int n, cudaStream_t
 constexpr int kReduceThreads = 256;
 __global__ void __launch_bounds__(kReduceThreads) reduce_partials_kernel(const double* __restrict__ part, int nb,
                                                                          int K, double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sh[kReduceThreads / 32];
   const int k = blockIdx.x;
   double s = 0.0;
