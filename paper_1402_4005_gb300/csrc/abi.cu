@@ -128,6 +128,11 @@ bamg_status setup_impl(const bamg_csr* A, const bamg_params* p, void* stream, ba
   cudaStream_t s = S(stream);
   double t0 = now_ms();
   bamg_status st = BAMG_OK;
+  // every kernel of the library waits for its predecessor before it touches
+  // memory (pdl_wait() first, or after loads of data written before the
+  // setup), so the setup's chains of small kernels launch with programmatic
+  // serialisation and each launch overlaps the previous kernel
+  PdlScope pdl;
   do {
     if (cudaGetDevice(&h->device) != cudaSuccess) { st = BAMG_ERR_CUDA; break; }
     configure_pool(h->device);

@@ -61,6 +61,8 @@ namespace bamg {
 
 // ------------------------------------------------------------ assembly
 __global__ void shift_kernel(int cnt, const int32_t* __restrict__ src, int32_t add, int32_t* __restrict__ dst) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < cnt) dst[i] = src[i] + add;
 }
@@ -257,6 +259,8 @@ template <typename T>
 __global__ void coarse_gemv_kernel(int rows, int row0, const long long* __restrict__ poff,
                                    const long long* __restrict__ base, const long long* __restrict__ len,
                                    const T* __restrict__ pinv, const T* __restrict__ b, T* __restrict__ z) {
+  pdl_wait();
+  pdl_trigger();
   int lane = threadIdx.x & 31;
   int g = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (g >= rows) return;
@@ -319,6 +323,8 @@ static bamg_status bvcycle_level(bamg_batch* bt, int l, cudaStream_t s) {
 }
 
 __global__ void copy_dd_kernel(size_t n, const double* __restrict__ a, double* __restrict__ b) {
+  pdl_wait();
+  pdl_trigger();
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) b[t] = a[t];
 }
@@ -372,6 +378,8 @@ static bamg_status bvcycle_run(bamg_batch* bt, cudaStream_t s) {
 // out[c * H + k] = sum over the rows of chain c of V_k . w
 __global__ void seg_multidot_kernel(const int* __restrict__ seg, int H, const double* __restrict__ V, size_t ldv,
                                     const double* __restrict__ w, double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   int c = blockIdx.x, k = blockIdx.y;
   const double* v = V + (size_t)k * ldv;
   double s = 0.0;
@@ -389,6 +397,8 @@ __global__ void seg_multidot_kernel(const int* __restrict__ seg, int H, const do
 
 // per chain: sums of x, |x| and x^2 -> out[3c .. 3c+2]
 __global__ void seg_sums_kernel(const int* __restrict__ seg, const double* __restrict__ x, double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   int c = blockIdx.x;
   double s = 0, a = 0, q = 0;
   for (int i = seg[c] + threadIdx.x; i < seg[c + 1]; i += blockDim.x) {
@@ -410,6 +420,8 @@ __global__ void seg_sums_kernel(const int* __restrict__ seg, const double* __res
 // w[i] -= sum_k h[c(i) * H + k] V_k[i]
 __global__ void seg_orth_kernel(int n, const int* __restrict__ rc, int K, int H, const double* __restrict__ V,
                                 size_t ldv, const double* __restrict__ h, double* __restrict__ w) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double* hc = h + (size_t)rc[i] * H;
@@ -422,6 +434,8 @@ __global__ void seg_orth_kernel(int n, const int* __restrict__ rc, int K, int H,
 __global__ void seg_normalise_kernel(int n, const int* __restrict__ rc, const double* __restrict__ a,
                                      const double* __restrict__ sums, const int* __restrict__ active,
                                      double* __restrict__ b) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int c = rc[i];
@@ -433,6 +447,8 @@ __global__ void seg_normalise_kernel(int n, const int* __restrict__ rc, const do
 __global__ void seg_combine_kernel(int n, const int* __restrict__ rc, int K, int H, const double* __restrict__ Z,
                                    size_t ldz, const double* __restrict__ coef, const int* __restrict__ active,
                                    const double* __restrict__ x, double* __restrict__ y) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int c = rc[i];
@@ -449,6 +465,8 @@ __global__ void seg_givens_kernel(int nch, int j, int m, const double* __restric
                                   const double* __restrict__ wsums, const int* __restrict__ active,
                                   double* __restrict__ R, double* __restrict__ cs, double* __restrict__ sn,
                                   double* __restrict__ g, double* __restrict__ y, double* __restrict__ st) {
+  pdl_wait();
+  pdl_trigger();
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nch) return;
   if (!active[c]) { st[2 * c] = 0.0; st[2 * c + 1] = 0.0; return; }
@@ -486,6 +504,8 @@ __global__ void seg_givens_kernel(int nch, int j, int m, const double* __restric
 }
 
 __global__ void seg_init_g_kernel(int nch, int m, const double* __restrict__ sums, double* __restrict__ g) {
+  pdl_wait();
+  pdl_trigger();
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nch) return;
   for (int k = 0; k <= m; ++k) g[(size_t)c * (m + 1) + k] = k == 0 ? sqrt(sums[3 * c + 2]) : 0.0;
@@ -494,6 +514,8 @@ __global__ void seg_init_g_kernel(int nch, int m, const double* __restrict__ sum
 // x <- x * sign(sum) / ||x||_1 per chain
 __global__ void seg_orient_kernel(int n, const int* __restrict__ rc, const double* __restrict__ sums,
                                   double* __restrict__ x) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int c = rc[i];
@@ -502,6 +524,8 @@ __global__ void seg_orient_kernel(int n, const int* __restrict__ rc, const doubl
 }
 
 __global__ void negate_kernel(int n, double* __restrict__ x) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) x[i] = -x[i];
 }

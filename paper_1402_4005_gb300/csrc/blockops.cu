@@ -229,6 +229,8 @@ template <typename T, int LD>
 __global__ void weights_finalize_kernel(const double* __restrict__ sums, int r, int skip0,
                                         T* __restrict__ scale, double* __restrict__ w,
                                         double* __restrict__ norms) {
+  pdl_wait();
+  pdl_trigger();
   int k = threadIdx.x;
   if (k >= LD) return;
   double xx = sums[k], bb = sums[LD + k];
@@ -246,6 +248,8 @@ __global__ void weights_finalize_kernel(const double* __restrict__ sums, int r, 
 
 template <typename T, int LD>
 __global__ void scale_cols_kernel(int n, T* __restrict__ X, const T* __restrict__ scale) {
+  pdl_wait();
+  pdl_trigger();
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (size_t)n * LD) return;
   X[t] *= scale[t % LD];
@@ -269,6 +273,8 @@ __global__ void rayleigh_finalize_kernel(const double* __restrict__ sums, int LD
 // uniform(-1,1), V column k from stream 2k, U column k from stream 2k+1.
 template <typename T, int LD>
 __global__ void init_vectors_kernel(int n, int r, uint64_t seed, T* __restrict__ U, T* __restrict__ V) {
+  pdl_wait();
+  pdl_trigger();
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (size_t)n * LD) return;
   int i = (int)(t / LD), k = (int)(t % LD);
@@ -284,6 +290,8 @@ __global__ void init_vectors_kernel(int n, int r, uint64_t seed, T* __restrict__
 template <typename T, int LD>
 __global__ void inject_kernel(int nc, const int32_t* __restrict__ cpt, const T* __restrict__ X,
                               T* __restrict__ Xc) {
+  pdl_wait();
+  pdl_trigger();
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (size_t)nc * LD) return;
   int I = (int)(t / LD), k = (int)(t % LD);
@@ -436,12 +444,16 @@ __global__ void dense_gemv_kernel(int n, const T* __restrict__ A, const T* __res
 
 template <typename S, typename D>
 __global__ void convert_kernel(size_t n, const S* __restrict__ a, D* __restrict__ b) {
+  pdl_wait();
+  pdl_trigger();
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) b[t] = D(a[t]);
 }
 
 // up to kConvMany double arrays to float in one launch (blockIdx.y = array)
 __global__ void convert_many_kernel(ConvMany job) {
+  pdl_wait();
+  pdl_trigger();
   const int q = blockIdx.y;
   const size_t n = job.n[q];
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
@@ -459,6 +471,8 @@ __global__ void diag_inv_kernel(int n, const int32_t* __restrict__ rp, const int
                                 const double* __restrict__ va, const int32_t* __restrict__ trp,
                                 const double* __restrict__ tva, T* __restrict__ dinv,
                                 int* __restrict__ bad_row, int* __restrict__ nsafe) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double d = 0.0, l1r = 0.0;

@@ -17,6 +17,8 @@ constexpr uint64_t kMisStream = 4096;
 
 __global__ void geo_split_kernel(int nx, int ny, int8_t* __restrict__ cf, int32_t* __restrict__ cmap,
                                  int32_t* __restrict__ jcnt) {
+  pdl_wait();
+  pdl_trigger();
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nx * ny) return;
   int i = s / ny, j = s % ny;
@@ -36,6 +38,8 @@ __global__ void geo_split_kernel(int nx, int ny, int8_t* __restrict__ cf, int32_
 }
 
 __global__ void geo_sets_kernel(int nx, int ny, const int32_t* __restrict__ jrp, int32_t* __restrict__ jci) {
+  pdl_wait();
+  pdl_trigger();
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nx * ny) return;
   int i = s / ny, j = s % ny;
@@ -70,6 +74,8 @@ __device__ inline bool beats(uint64_t ki, int i, uint64_t kj, int j) {
 __global__ void mis_select_kernel(int n, const int32_t* __restrict__ brp, const int32_t* __restrict__ bci,
                                   const int32_t* __restrict__ trp, const int32_t* __restrict__ tci,
                                   uint64_t seed, int level, int8_t* __restrict__ state) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || state[i] != 0) return;
   uint64_t ki = splitmix_draw(seed, kMisStream + level, i);
@@ -91,6 +97,8 @@ __global__ void mis_select_kernel(int n, const int32_t* __restrict__ brp, const 
 __global__ void mis_finalize_kernel(int n, const int32_t* __restrict__ brp, const int32_t* __restrict__ bci,
                                     const int32_t* __restrict__ trp, const int32_t* __restrict__ tci,
                                     int8_t* __restrict__ state, int* __restrict__ undecided) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int8_t si = state[i];
@@ -116,6 +124,8 @@ __global__ void mis_finalize_kernel(int n, const int32_t* __restrict__ brp, cons
 
 __global__ void state_to_cf_kernel(int n, const int8_t* __restrict__ state, int8_t* __restrict__ cf,
                                    int32_t* __restrict__ cnt) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int8_t c = state[i] == 1 ? 1 : 0;
@@ -125,6 +135,8 @@ __global__ void state_to_cf_kernel(int n, const int8_t* __restrict__ state, int8
 
 __global__ void cmap_kernel(int n, const int8_t* __restrict__ cf, const int32_t* __restrict__ pre,
                             int32_t* __restrict__ cmap) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   cmap[i] = cf[i] ? pre[i] : -1;
@@ -201,6 +213,8 @@ __global__ void graph_sets_kernel(int n, const int32_t* __restrict__ brp, const 
                                   const int8_t* __restrict__ cf, int c_min, int c_max,
                                   int32_t* __restrict__ cnt, int32_t* __restrict__ tmp,
                                   int* __restrict__ overflow) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (cf[i]) { cnt[i] = 0; return; }
@@ -251,6 +265,8 @@ __global__ void graph_sets_kernel(int n, const int32_t* __restrict__ brp, const 
 
 __global__ void compact_sets_kernel(int n, int c_max, const int32_t* __restrict__ tmp,
                                     const int32_t* __restrict__ jrp, int32_t* __restrict__ jci) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   for (int q = jrp[i]; q < jrp[i + 1]; ++q) jci[q] = tmp[(size_t)i * c_max + (q - jrp[i])];
@@ -285,6 +301,8 @@ bamg_status graph_sets(int n, const int32_t* brp, const int32_t* bci, const doub
 // ------------------------------------------------------- transfer patterns
 __global__ void coarse_points_kernel(int n, const int8_t* __restrict__ cf, const int32_t* __restrict__ cmap,
                                      int32_t* __restrict__ cpt) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n && cf[i]) cpt[cmap[i]] = i;
 }
@@ -295,6 +313,8 @@ bamg_status coarse_points(int n, const int8_t* cf, const int32_t* cmap, int32_t*
 
 __global__ void pattern_count_kernel(int n, const int8_t* __restrict__ cf, const int32_t* __restrict__ jrp,
                                      int32_t* __restrict__ cnt) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   cnt[i] = cf[i] ? 1 : jrp[i + 1] - jrp[i];
@@ -305,6 +325,8 @@ __global__ void pattern_fill_kernel(int n, const int8_t* __restrict__ cf, const 
                                     const int32_t* __restrict__ jrp, const int32_t* __restrict__ jci,
                                     const int32_t* __restrict__ prp, int32_t* __restrict__ pci,
                                     double* __restrict__ pva) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int q = prp[i];
@@ -333,6 +355,8 @@ bamg_status transfer_pattern(int n, const int8_t* cf, const int32_t* cmap, const
 __global__ void scatter_fits_kernel(int n, const int8_t* __restrict__ cf, const int32_t* __restrict__ jrp,
                                     const double* __restrict__ fit, const int32_t* __restrict__ prp,
                                     double* __restrict__ pva) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || cf[i]) return;
   int q = prp[i];
@@ -346,6 +370,8 @@ bamg_status scatter_fits(int n, const int8_t* cf, const int32_t* J_rp, const dou
 
 // Section 5 comparison: simple averaging, every entry of a column of Q = 1/c.
 __global__ void average_fits_kernel(int n, const int32_t* __restrict__ jrp, double* __restrict__ fit) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int c = jrp[i + 1] - jrp[i];

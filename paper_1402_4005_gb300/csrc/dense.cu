@@ -1341,6 +1341,8 @@ __host__ __device__ inline size_t smem_elems(int n, int r, int RP) {
 
 template <typename T, bool SM>
 __global__ void __launch_bounds__(kDenseThreads, 1) coarsest_kernel(DenseArgs<T> A) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char dyn[];
   T* sv = reinterpret_cast<T*>(dyn);
   __shared__ T red[kWarps];
@@ -1381,6 +1383,8 @@ __host__ __device__ inline size_t pinv_smem_elems(int n, int RP) {
 
 template <typename T, bool SM>
 __global__ void __launch_bounds__(kDenseThreads, 1) pinv_kernel(DenseArgs<T> A) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char dyn[];
   T* sv = reinterpret_cast<T*>(dyn);
   __shared__ T red[kWarps];
@@ -1402,6 +1406,8 @@ __global__ void __launch_bounds__(kDenseThreads, 1) pinv_kernel(DenseArgs<T> A) 
 
 __global__ void csr_to_dense_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                     const double* __restrict__ va, double* __restrict__ D) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x;
   for (int p = rp[i] + threadIdx.x; p < rp[i + 1]; p += blockDim.x) D[(size_t)i * n + ci[p]] = va[p];
 }

@@ -37,6 +37,8 @@ struct Trace {
 // ------------------------------------------------------------ small kernels
 __global__ void pad_block_kernel(int n, int r, int ld, const double* __restrict__ src, float* __restrict__ d32,
                                  double* __restrict__ d64) {
+  pdl_wait();
+  pdl_trigger();
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (size_t)n * ld) return;
   int i = (int)(t / ld), k = (int)(t % ld);
@@ -46,12 +48,16 @@ __global__ void pad_block_kernel(int n, int r, int ld, const double* __restrict_
 }
 
 __global__ void column_kernel(int n, int ld, int k, const double* __restrict__ X, double* __restrict__ x) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) x[i] = X[(size_t)i * ld + k];
 }
 
 // partial sums of x and |x| per block
 __global__ void sum_abs_kernel(int n, const double* __restrict__ x, double* __restrict__ part) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sh[2][8];
   double s = 0.0, a = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -72,6 +78,8 @@ __global__ void sum_abs_kernel(int n, const double* __restrict__ x, double* __re
 
 // x <- x * sign(sum) / ||x||_1  (positive orientation, unit 1-norm)
 __global__ void orient_kernel(int n, const double* __restrict__ sums, double* __restrict__ x) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double f = (sums[0] < 0.0 ? -1.0 : 1.0) / sums[1];

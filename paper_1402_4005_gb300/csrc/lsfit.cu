@@ -58,6 +58,8 @@ ls_fit_kernel(int n, int r, const int32_t* __restrict__ jrp, const int32_t* __re
               const T* __restrict__ X, const double* __restrict__ w, double* __restrict__ out,
               int* __restrict__ rankdef, const int8_t* __restrict__ only, int8_t* __restrict__ flag,
               R cond_tol, R ridge, int* __restrict__ oversize) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int PPW = 32 / S;
   int lane = threadIdx.x & 31;
   int gw = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);

@@ -170,6 +170,8 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_grad_kernel(int M, float inv_
                                                                const float* __restrict__ Tg,
                                                                const float* __restrict__ mask,
                                                                float* __restrict__ part, float* __restrict__ loss) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ unsigned char dyn[];
   MlpSmem& S = *reinterpret_cast<MlpSmem*>(dyn);
   GradSmem* Dall = reinterpret_cast<GradSmem*>(dyn + sizeof(MlpSmem));
@@ -343,6 +345,8 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_grad_kernel(int M, float inv_
 
 // G[i] += sum over the blocks of part[b][i], blocks in order.
 __global__ void grad_reduce_kernel(int nb, const float* __restrict__ part, float* __restrict__ G) {
+  pdl_wait();
+  pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= kNParam) return;
   float v = 0.f;
@@ -352,6 +356,8 @@ __global__ void grad_reduce_kernel(int nb, const float* __restrict__ part, float
 
 __global__ void adam_kernel(int np, float* __restrict__ P, float* __restrict__ m, float* __restrict__ v,
                             const float* __restrict__ G, float lr, float b1, float b2, float eps, float c1, float c2) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= np) return;
   float gr = G[i];
@@ -364,6 +370,8 @@ __global__ void adam_kernel(int np, float* __restrict__ P, float* __restrict__ m
 
 // He initialisation from SplitMix64 (stream 8192): uniform(-a, a), a = sqrt(6 / fan_in); biases 0.
 __global__ void mlp_init_kernel(float* __restrict__ P, uint64_t seed) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= kNParam) return;
   float a = 0.f;
@@ -392,6 +400,8 @@ __global__ void mlp_features_kernel(int n, int nx, int ny, const int32_t* __rest
                                     const int32_t* __restrict__ tci, const double* __restrict__ tva,
                                     const int8_t* __restrict__ cf, const int32_t* __restrict__ fidx,
                                     __nv_bfloat16* __restrict__ X) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || cf[i]) return;
   int row = fidx[i];
@@ -428,6 +438,8 @@ __global__ void mlp_targets_kernel(int n, int ny, const int8_t* __restrict__ cf,
                                    const int32_t* __restrict__ jrp, const int32_t* __restrict__ jci,
                                    const int32_t* __restrict__ prp, const double* __restrict__ pva,
                                    const double* __restrict__ qva, float* __restrict__ T, float* __restrict__ mask) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || cf[i]) return;
   int row = fidx[i];
@@ -453,6 +465,8 @@ __global__ void mlp_targets_kernel(int n, int ny, const int8_t* __restrict__ cf,
 __global__ void mlp_scatter_kernel(int n, int ny, const int8_t* __restrict__ cf, const int32_t* __restrict__ fidx,
                                    const int32_t* __restrict__ jrp, const int32_t* __restrict__ jci,
                                    const float* __restrict__ Y, double* __restrict__ fitP, double* __restrict__ fitQ) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || cf[i]) return;
   const float* y = Y + (size_t)fidx[i] * kO;
@@ -474,11 +488,15 @@ __global__ void mlp_scatter_kernel(int n, int ny, const int8_t* __restrict__ cf,
 
 __global__ void fine_index_kernel(int n, const int8_t* __restrict__ cf, const int32_t* __restrict__ pre,
                                   int32_t* __restrict__ fidx) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) fidx[i] = cf[i] ? -1 : i - pre[i];
 }
 
 __global__ void cf_count_kernel(int n, const int8_t* __restrict__ cf, int32_t* __restrict__ c) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) c[i] = cf[i] ? 1 : 0;
 }

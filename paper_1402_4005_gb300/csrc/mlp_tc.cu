@@ -187,6 +187,8 @@ __device__ inline void issue_layer(uint32_t sbase, uint32_t a_off, uint32_t b_of
 __global__ void __launch_bounds__(kTcThreads, 4)
 mlp_forward_tc_kernel(const __grid_constant__ CUtensorMap xmap, int M, const float* __restrict__ P,
                       float* __restrict__ Y, int* __restrict__ err) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ uint8_t dyn_smem[];
   uint8_t* base = dyn_smem + ((1024 - (smem_u32(dyn_smem) & 1023)) & 1023);
   const uint32_t sbase = smem_u32(base);

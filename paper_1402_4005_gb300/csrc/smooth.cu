@@ -58,6 +58,8 @@ __device__ int smallest_free(int i, const int32_t* __restrict__ brp, const int32
 __global__ void colour_round_kernel(int n, const int32_t* __restrict__ brp, const int32_t* __restrict__ bci,
                                     const int32_t* __restrict__ trp, const int32_t* __restrict__ tci,
                                     uint64_t seed, int level, int32_t* colour, int* __restrict__ left) {
+  pdl_wait();
+  pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || colour[i] >= 0) return;
   const uint64_t ki = splitmix_draw(seed, kColourStream + level, i);
@@ -76,6 +78,8 @@ __global__ void colour_round_kernel(int n, const int32_t* __restrict__ brp, cons
 }
 
 __global__ void colour_count_kernel(int n, const int32_t* __restrict__ colour, int* __restrict__ maxc) {
+  pdl_wait();
+  pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) atomicMax(maxc, colour[i]);
 }
@@ -110,12 +114,16 @@ bamg_status colour_graph(int n, const int32_t* brp, const int32_t* bci, const in
 
 // ------------------------------------------------------- rows by colour
 __global__ void colour_flag_kernel(int n, const int32_t* __restrict__ colour, int c, int32_t* __restrict__ flag) {
+  pdl_wait();
+  pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) flag[i] = colour[i] == c ? 1 : 0;
 }
 
 __global__ void colour_scatter_kernel(int n, const int32_t* __restrict__ colour, int c, int base,
                                       const int32_t* __restrict__ pos, int32_t* __restrict__ rows) {
+  pdl_wait();
+  pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n && colour[i] == c) rows[base + pos[i]] = i;
 }

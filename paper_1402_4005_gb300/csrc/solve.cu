@@ -113,11 +113,15 @@ static bamg_status vcycle_level(bamg_hierarchy* h, int l, cudaStream_t s) {
 }
 
 __global__ void copy_d_kernel(size_t n, const double* __restrict__ a, double* __restrict__ b) {
+  pdl_wait();
+  pdl_trigger();
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) b[t] = a[t];
 }
 
 __global__ void fill_kernel(size_t n, double v, double* __restrict__ b) {
+  pdl_wait();
+  pdl_trigger();
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) b[t] = v;
 }
@@ -453,6 +457,8 @@ __global__ void next_basis_kernel(int n, int* __restrict__ dj, const double* __r
 // y = x + sum_k c[k] Z_k
 __global__ void combine_kernel(int n, int K, const double* __restrict__ Z, size_t ldz,
                                const double* __restrict__ c, const double* __restrict__ x, double* __restrict__ y) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double acc = x[i];
@@ -469,6 +475,8 @@ __global__ void combine_kernel(int n, int K, const double* __restrict__ Z, size_
 
 __global__ void scale_by_kernel(int n, const double* __restrict__ a, const double* __restrict__ f, int inv,
                                 double* __restrict__ b) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double s = inv ? 1.0 / f[0] : f[0];
@@ -565,6 +573,8 @@ __global__ void givens_kernel(const int* __restrict__ dj, int m, const double* _
 constexpr int kYsolveLd = 65;
 __global__ void ysolve_kernel(int j, int m, const double* __restrict__ R, const double* __restrict__ g,
                               double* __restrict__ y) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ double rs[];      // (j + 1) x kYsolveLd, then g and y
   if (blockIdx.x != 0 || threadIdx.x >= 32) return;
   double* gs = rs + (size_t)(j + 1) * kYsolveLd;
@@ -584,12 +594,16 @@ __global__ void ysolve_kernel(int j, int m, const double* __restrict__ R, const 
 }
 
 __global__ void init_g_kernel(int m, const double* __restrict__ beta, double* __restrict__ g) {
+  pdl_wait();
+  pdl_trigger();
   int k = threadIdx.x;
   if (k <= m) g[k] = k == 0 ? beta[0] : 0.0;
 }
 
 // Smallest entry: per-block minima, then one block over them.
 __global__ void min_part_kernel(int n, const double* __restrict__ x, double* __restrict__ part) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sh[256];
   double m = INFINITY;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) m = fmin(m, x[i]);
@@ -966,11 +980,15 @@ bamg_status fgmres(bamg_hierarchy* h, double* x, const bamg_solve_params* sp, ba
 // ------------------------------------------------- V-cycle convergence factor
 // x_i = 1 + 0.5 * u_i with u_i uniform in [-1, 1) (SplitMix64 stream 8193)
 __global__ void factor_start_kernel(int n, uint64_t seed, double* __restrict__ x) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) x[i] = 1.0 + 0.5 * splitmix_pm1(seed, 8193, (uint64_t)i);
 }
 
 __global__ void add_kernel(int n, const double* __restrict__ z, double* __restrict__ x) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) x[i] += z[i];
 }

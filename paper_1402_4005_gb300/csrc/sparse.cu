@@ -75,6 +75,8 @@ __device__ inline long long block_excl_scan(long long v, long long* sh, long lon
 }
 
 __global__ void scan_tile_sums(const int32_t* __restrict__ in, int n, long long* __restrict__ part) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ long long sh[32];
   long long base = (long long)blockIdx.x * kScanTile;
   long long s = 0;
@@ -88,6 +90,8 @@ __global__ void scan_tile_sums(const int32_t* __restrict__ in, int n, long long*
 }
 
 __global__ void scan_partials(long long* part, int nb, long long* total_out) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ long long sh[32];
   long long carry = 0;
   for (int b0 = 0; b0 < nb; b0 += kScanThreads) {
@@ -103,6 +107,8 @@ __global__ void scan_partials(long long* part, int nb, long long* total_out) {
 
 __global__ void scan_apply(const int32_t* __restrict__ in, int n, const long long* __restrict__ part,
                            const long long* __restrict__ total, int32_t* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ long long sh[32];
   long long base = (long long)blockIdx.x * kScanTile;
   long long loc[kScanItems];
@@ -168,11 +174,15 @@ __device__ void scan_block_body(const int32_t* __restrict__ in, int n, int32_t* 
 
 __global__ void __launch_bounds__(kScanOneThreads) scan_one_block(const int32_t* __restrict__ in, int n,
                                                                    int32_t* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   scan_block_body(in, n, out);
 }
 
 // several independent scans, one block each (blockIdx.x = array)
 __global__ void __launch_bounds__(kScanOneThreads) scan_many_kernel(ScanMany job) {
+  pdl_wait();
+  pdl_trigger();
   const int q = blockIdx.x;
   scan_block_body(job.in[q], job.n[q], job.out[q]);
 }
@@ -247,6 +257,8 @@ bamg_status reduce_partials(const double* partial, int nb, int K, double* out, c
 // ------------------------------------------------------------- B = I - A
 __global__ void buildB_count_kernel(int n, const int32_t* __restrict__ rp,
                                     const int32_t* __restrict__ ci, int32_t* __restrict__ cnt) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int has = 0;
@@ -257,6 +269,8 @@ __global__ void buildB_count_kernel(int n, const int32_t* __restrict__ rp,
 __global__ void buildB_fill_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                    const double* __restrict__ va, const int32_t* __restrict__ brp,
                                    int32_t* __restrict__ bci, double* __restrict__ bva) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int q = brp[i];
@@ -279,6 +293,8 @@ __global__ void buildB_fill_kernel(int n, const int32_t* __restrict__ rp, const 
 __global__ void check_entries_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                      const double* __restrict__ va, double* __restrict__ colsum,
                                      unsigned long long* __restrict__ bad) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int prev = -1;
@@ -296,6 +312,8 @@ __global__ void check_entries_kernel(int n, const int32_t* __restrict__ rp, cons
 
 __global__ void check_colsum_kernel(int n, const double* __restrict__ colsum, double tol,
                                     unsigned long long* __restrict__ bad) {
+  pdl_wait();
+  pdl_trigger();
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   double c = colsum[j];
@@ -304,6 +322,8 @@ __global__ void check_colsum_kernel(int n, const double* __restrict__ colsum, do
 
 __global__ void check_rowptr_kernel(int n, const int32_t* __restrict__ rp, int64_t nnz,
                                     unsigned long long* __restrict__ bad) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i > n) return;
   if (i == 0 && rp[0] != 0) atomicAdd(bad, 1ull);
@@ -329,6 +349,8 @@ bamg_status check_rowptr(int n, const int32_t* rp, int64_t nnz, cudaStream_t s) 
 
 // ------------------------------------------------------------ transpose
 __global__ void col_count_kernel(int nnz, const int32_t* __restrict__ ci, int32_t* __restrict__ cnt) {
+  pdl_wait();
+  pdl_trigger();
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < nnz) atomicAdd(&cnt[ci[p]], 1);
 }
@@ -337,6 +359,8 @@ __global__ void transpose_scatter_kernel(int rows, const int32_t* __restrict__ r
                                          const int32_t* __restrict__ ci, const double* __restrict__ va,
                                          int32_t* __restrict__ fill, int32_t* __restrict__ tci,
                                          double* __restrict__ tva) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
   for (int p = rp[i]; p < rp[i + 1]; ++p) {
@@ -352,6 +376,8 @@ __global__ void transpose_scatter_kernel(int rows, const int32_t* __restrict__ r
 // distinct), longer rows by insertion on lane 0.
 __global__ void sort_rows_warp_kernel(int rows, const int32_t* __restrict__ rp, int32_t* __restrict__ ci,
                                       double* __restrict__ va) {
+  pdl_wait();
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (i >= rows) return;

@@ -26,6 +26,8 @@ constexpr int kBigThreads = 256;
 __global__ void count_products_kernel(int m, const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
                                       const int32_t* __restrict__ brp, int32_t* __restrict__ prod,
                                       int* __restrict__ stats) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   long long c = 0;
   if (i < m) {
@@ -233,6 +235,8 @@ spgemm_warp_kernel(int m, const int32_t* __restrict__ prod, const int32_t* __res
                    const int32_t* __restrict__ brp, const int32_t* __restrict__ bci,
                    const double* __restrict__ bva, int32_t* __restrict__ ccount,
                    const int32_t* __restrict__ crp, int32_t* __restrict__ cci, double* __restrict__ cva) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ unsigned long long skey[kWarpsPerBlock][kWarpCap];
   __shared__ double sval[kWarpsPerBlock][NUMERIC ? kWarpCap : 1];
   __shared__ int sflag[kWarpsPerBlock][kWarpCap];
@@ -250,6 +254,8 @@ spgemm_block_kernel(int m, const int32_t* __restrict__ prod, const int32_t* __re
                     const int32_t* __restrict__ brp, const int32_t* __restrict__ bci,
                     const double* __restrict__ bva, int32_t* __restrict__ ccount,
                     const int32_t* __restrict__ crp, int32_t* __restrict__ cci, double* __restrict__ cva) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ unsigned char dyn[];
   unsigned long long* key = reinterpret_cast<unsigned long long*>(dyn);
   double* val = reinterpret_cast<double*>(key + kBlockCap);
@@ -330,6 +336,8 @@ __global__ void compact_rows_kernel(int m, const int32_t* __restrict__ src_rp, c
                                     const int32_t* __restrict__ scol, const double* __restrict__ sval,
                                     const int32_t* __restrict__ crp, int32_t* __restrict__ cci,
                                     double* __restrict__ cva) {
+  pdl_wait();
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (i >= m) return;
@@ -360,6 +368,8 @@ struct SpJobs {
 // products per row, and per job their maximum and total (one atomic pair
 // per warp: a million rows updating two counters one by one serialise)
 __global__ void count_products_multi(SpJobs J) {
+  pdl_wait();
+  pdl_trigger();
   const int q = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   long long c = 0;
@@ -384,6 +394,8 @@ __global__ void count_products_multi(SpJobs J) {
 }
 
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) spgemm_warp_multi(SpJobs J) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ unsigned long long skey[kWarpsPerBlock][kWarpCap];
   __shared__ double sval[kWarpsPerBlock][kWarpCap];
   __shared__ int sflag[kWarpsPerBlock][kWarpCap];
@@ -396,6 +408,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) spgemm_warp_multi(SpJobs 
 }
 
 __global__ void compact_rows_multi(SpJobs J) {
+  pdl_wait();
+  pdl_trigger();
   const int q = blockIdx.y;
   const int lane = threadIdx.x & 31;
   const int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
