@@ -314,17 +314,13 @@ enum VecMode { kJacobi = 0, kJacobiZero = 1, kResid = 2, kSpmv = 3, kSpmvAdd = 4
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
-// Under a programmatic launch the matrix (rp, ci, va) and dinv must not be
-// written by the kernel that precedes this one: the row bounds and the first
-// kVecPre entries of every row and lane are loaded before pdl_wait(), so they
-// overlap the predecessor's work; x, b and y are touched only after it.
-constexpr int kVecPre = 2;
-
 template <typename T, int G, int MODE, int RU>
 __global__ void __launch_bounds__(256)
 csr_vec_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                const T* __restrict__ va, const T* __restrict__ dinv, T omega, const T* __restrict__ x,
                const T* __restrict__ b, T* __restrict__ y) {
+  pdl_wait();
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const size_t grp = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int g = lane % G;
@@ -332,12 +328,9 @@ csr_vec_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict_
   T acc[RU];
 #pragma unroll
   for (int u = 0; u < RU; ++u) acc[u] = T(0);
-  int p0[RU], p1[RU];
-  int len = 0;
-  int cpre[kVecPre][RU];
-  T apre[kVecPre][RU];
-  T dself[RU];
   if (MODE != kJacobiZero) {
+    int p0[RU], p1[RU];
+    int len = 0;
 #pragma unroll
     for (int u = 0; u < RU; ++u) {
       const bool v = i0 + u < n;
@@ -345,46 +338,15 @@ csr_vec_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict_
       p1[u] = v ? __ldg(rp + i0 + u + 1) : 0;
       len = max(len, p1[u] - p0[u]);
     }
-#pragma unroll
-    for (int q = 0; q < kVecPre; ++q)
-#pragma unroll
-      for (int u = 0; u < RU; ++u) {
-        const int p = p0[u] + g + q * G;
-        const bool in = p < p1[u];
-        cpre[q][u] = in ? __ldg(ci + p) : -1;
-        apre[q][u] = in ? __ldg(va + p) : T(0);
-      }
-  }
-  if (MODE == kJacobi || MODE == kJacobiZero || MODE == kJacobiZero2) {
-#pragma unroll
-    for (int u = 0; u < RU; ++u) dself[u] = (g == 0 && i0 + u < n) ? __ldg(dinv + i0 + u) : T(0);
-  }
-  pdl_wait();
-  pdl_trigger();
-  if (MODE != kJacobiZero) {
-    for (int off = g, q = 0; off < len; off += G, ++q) {
+    for (int off = g; off < len; off += G) {
       int c[RU];
       T a[RU];
-      if (q < kVecPre) {
 #pragma unroll
-        for (int u = 0; u < RU; ++u) {
-          c[u] = cpre[0][u];
-          a[u] = apre[0][u];
-#pragma unroll
-          for (int qq = 1; qq < kVecPre; ++qq)
-            if (q == qq) {
-              c[u] = cpre[qq][u];
-              a[u] = apre[qq][u];
-            }
-        }
-      } else {
-#pragma unroll
-        for (int u = 0; u < RU; ++u) {
-          const int p = p0[u] + off;
-          const bool in = p < p1[u];
-          c[u] = in ? __ldg(ci + p) : -1;
-          a[u] = in ? __ldg(va + p) : T(0);
-        }
+      for (int u = 0; u < RU; ++u) {
+        const int p = p0[u] + off;
+        const bool in = p < p1[u];
+        c[u] = in ? __ldg(ci + p) : -1;
+        a[u] = in ? __ldg(va + p) : T(0);
       }
       T xv[RU];
       if (MODE == kJacobiZero2) {
@@ -407,9 +369,9 @@ csr_vec_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict_
   for (int u = 0; u < RU; ++u) {
     const long long i = i0 + u;
     if (i >= n) break;
-    if (MODE == kJacobi) y[i] = x[i] + (omega * (b[i] - acc[u])) * dself[u];
-    else if (MODE == kJacobiZero2) y[i] = mul_rn(mul_rn(omega, b[i]), dself[u]) + (omega * (b[i] - acc[u])) * dself[u];
-    else if (MODE == kJacobiZero) y[i] = (omega * b[i]) * dself[u];
+    if (MODE == kJacobi) y[i] = x[i] + (omega * (b[i] - acc[u])) * dinv[i];
+    else if (MODE == kJacobiZero2) y[i] = mul_rn(mul_rn(omega, b[i]), dinv[i]) + (omega * (b[i] - acc[u])) * dinv[i];
+    else if (MODE == kJacobiZero) y[i] = (omega * b[i]) * dinv[i];
     else if (MODE == kResid) y[i] = b[i] - acc[u];
     else if (MODE == kSpmv) y[i] = acc[u];
     else y[i] = y[i] + acc[u];
@@ -418,26 +380,13 @@ csr_vec_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict_
 
 template <typename T>
 __global__ void dense_gemv_kernel(int n, const T* __restrict__ A, const T* __restrict__ x, T* __restrict__ y) {
-  // A is not written by the preceding kernel: its first eight entries per
-  // lane are loaded before pdl_wait()
-  int lane = threadIdx.x & 31;
-  int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  T apre[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int j = lane + 32 * q;
-    apre[q] = (i < n && j < n) ? __ldg(A + (size_t)i * n + j) : T(0);
-  }
   pdl_wait();
   pdl_trigger();
+  int lane = threadIdx.x & 31;
+  int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (i >= n) return;
   T acc = T(0);
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int j = lane + 32 * q;
-    if (j < n) acc = fma(apre[q], x[j], acc);
-  }
-  for (int j = lane + 256; j < n; j += 32) acc = fma(A[(size_t)i * n + j], x[j], acc);
+  for (int j = lane; j < n; j += 32) acc = fma(A[(size_t)i * n + j], x[j], acc);
   acc = warp_sum(acc);
   if (lane == 0) y[i] = acc;
 }

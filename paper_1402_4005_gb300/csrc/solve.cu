@@ -310,29 +310,14 @@ __global__ void __launch_bounds__(256) gs_kernel(int n, int m, const int* __rest
                                                  const double* __restrict__ hin, double* __restrict__ w,
                                                  double* __restrict__ part, unsigned* __restrict__ arrived,
                                                  double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sh[8][kMultidotMax];
   __shared__ double hs[kMultidotMax];
   __shared__ bool last;
-  // j and the basis columns were written by earlier steps (earlier graph
-  // launches): the first chunk of the first row is loaded before pdl_wait()
   const int K = dj[0] + 1, lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int col = rs8_col(lane);
   const int stride = gridDim.x * blockDim.x, i0 = blockIdx.x * blockDim.x + threadIdx.x;
-  double vpre[8];
-#pragma unroll
-  for (int u = 0; u < 8; ++u) vpre[u] = (i0 < n && u < K) ? V[(size_t)u * ldv + i0] : 0.0;
-  pdl_wait();
-  pdl_trigger();
-  // the eight columns kc .. kc + 7 of row i (zero beyond K)
-  auto load8 = [&](int kc, int i, double (&v)[8]) {
-    if (kc == 0 && i == i0) {
-#pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = vpre[u];
-    } else {
-#pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = kc + u < K ? V[(size_t)(kc + u) * ldv + i] : 0.0;
-    }
-  };
   double ss = 0.0;
   if (MODE != kGsDots) {
     for (int k = threadIdx.x; k < K; k += blockDim.x) hs[k] = hin[k];
@@ -341,7 +326,8 @@ __global__ void __launch_bounds__(256) gs_kernel(int n, int m, const int* __rest
       double acc = w[i];
       for (int kc = 0; kc < K; kc += 8) {
         double v[8];
-        load8(kc, i, v);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = kc + u < K ? V[(size_t)(kc + u) * ldv + i] : 0.0;
 #pragma unroll
         for (int u = 0; u < 8; ++u)
           if (kc + u < K) acc -= hs[kc + u] * v[u];
@@ -367,7 +353,8 @@ __global__ void __launch_bounds__(256) gs_kernel(int n, int m, const int* __rest
       for (int i = i0; i < n; i += stride) {
         const double wi = w[i];
         double v[8];
-        load8(kc, i, v);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = kc + u < K ? V[(size_t)(kc + u) * ldv + i] : 0.0;
 #pragma unroll
         for (int u = 0; u < 8; ++u)
           if (kc + u < K) sd[u] += v[u] * wi;
@@ -533,19 +520,18 @@ __global__ void givens_kernel(const int* __restrict__ dj, int m, const double* _
                               const double* __restrict__ h2, const double* __restrict__ wnorm,
                               double* __restrict__ R, double* __restrict__ cs, double* __restrict__ sn,
                               double* __restrict__ g, double* __restrict__ st) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double hc[kMultidotMax], cc[kMultidotMax], sc[kMultidotMax];
-  // j and the earlier rotations come from earlier steps (earlier graph
-  // launches): staged before pdl_wait()
-  const int j = (blockIdx.x == 0 && threadIdx.x < 32) ? dj[0] : 0;
-  if (blockIdx.x == 0)
-    for (int k = threadIdx.x; k < j; k += 32) {
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  const int j = dj[0];
+  for (int k = threadIdx.x; k <= j; k += 32) {
+    hc[k] = h1[k] + h2[k];
+    if (k < j) {
       cc[k] = cs[k];
       sc[k] = sn[k];
     }
-  pdl_wait();
-  pdl_trigger();
-  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
-  for (int k = threadIdx.x; k <= j; k += 32) hc[k] = h1[k] + h2[k];
+  }
   __syncwarp();
   if (threadIdx.x != 0) return;
   const double hn = wnorm[0];

@@ -5,19 +5,12 @@ Kernels launched with programmatic serialisation (the setup, and the
 captured V-cycle and Arnoldi graphs) may start while the previous kernel is
 still running; each must call pdl_wait() (griddepcontrol.wait) before its
 first access to data that kernel may write.  Checked on the sources: the
-first statement of every __global__ function is pdl_wait(), except for the
-kernels that deliberately load operands written before the solve (matrix
-rows, earlier basis columns and rotations) ahead of the wait."""
+first statement of every __global__ function is pdl_wait()."""
 import glob
 import os
 import re
 
 CSRC = os.path.join(os.path.dirname(__file__), "..", "paper_1402_4005_gb300", "csrc")
-
-# kernels whose loads before pdl_wait() read only data fixed before the
-# graph launch (documented at each kernel)
-LOAD_BEFORE_WAIT = {"csr_vec_kernel", "dense_gemv_kernel", "gs_kernel", "givens_kernel"}
-
 
 def kernels():
     for path in sorted(glob.glob(os.path.join(CSRC, "*.cu"))):
@@ -38,12 +31,5 @@ def test_every_kernel_waits_first():
         seen += 1
         stmts = [s.strip() for s in body.split(";") if s.strip() and not s.strip().startswith("//")]
         first = re.sub(r"//[^\n]*\n", "", stmts[0] + "\n").strip() if stmts else ""
-        assert "pdl_wait()" in body, (fname, name)
-        if name not in LOAD_BEFORE_WAIT:
-            assert first == "pdl_wait()", (fname, name, first[:80])
+        assert first == "pdl_wait()", (fname, name, first[:80])
     assert seen >= 90
-
-
-def test_load_before_wait_kernels_exist():
-    names = {n for _, n, _ in kernels()}
-    assert LOAD_BEFORE_WAIT <= names
