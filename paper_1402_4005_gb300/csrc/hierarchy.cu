@@ -124,6 +124,8 @@ static bamg_status csr_products(const std::vector<std::pair<const Csr*, const Cs
     const Csr& B = *ab[q].second;
     Csr& C = *out[q];
     jobs[q] = SpgemmJob{A.rows, A.r(), A.c(), A.v(), B.r(), B.c(), B.v(), &C.rp, &C.ci, &C.va, 0};
+    jobs[q].annz = A.nnz;
+    jobs[q].maxrow_b = B.maxrow;
   }
   BAMG_TRY(spgemm_multi(jobs.data(), (int)jobs.size(), s));
   for (size_t q = 0; q < ab.size(); ++q) {
@@ -131,6 +133,7 @@ static bamg_status csr_products(const std::vector<std::pair<const Csr*, const Cs
     C.rows = ab[q].first->rows;
     C.cols = ab[q].second->cols;
     C.nnz = (int)jobs[q].nnz;
+    C.maxrow = jobs[q].maxrow_c;
   }
   return BAMG_OK;
 }
@@ -276,8 +279,12 @@ static bamg_status coarsen_level(bamg_hierarchy* h, int l, DevMem& U, DevMem& V,
                          fitQ.as<double>(), rkd.as<int>(), s, p.ls_ridge));
   }
   int nnzP = njz + nc;
+  // rows of P and Q^T: |J_i| entries for an F point (at most 4 for the
+  // geometric sets, c_max for the graph sets), one for a C point
+  const int set_max = p.coarsening == BAMG_COARSEN_GEOMETRIC ? 4 : (p.c_max > 1 ? p.c_max : 1);
   for (Csr* X : {&L.P, &L.Qt}) {
     BAMG_TRY(X->alloc(L.n, nc, nnzP, s));
+    X->maxrow = set_max;
     BAMG_TRY(transfer_pattern(L.n, L.cf.as<int8_t>(), L.cmap.as<int32_t>(), L.Jrp.as<int32_t>(),
                               L.Jci.as<int32_t>(), X->rp.as<int32_t>(), X->ci.as<int32_t>(),
                               X->va.as<double>(), s));

@@ -9,6 +9,7 @@ namespace bamg {
 
 struct Csr {
   int rows = 0, cols = 0, nnz = 0;
+  int maxrow = -1;          // upper bound on the entries of a row (-1: unknown)
   DevMem rp, ci, va, va32;  // va32: float copy of the values (mixed precision)
   const int32_t* r() const { return rp.as<int32_t>(); }
   const int32_t* c() const { return ci.as<int32_t>(); }

@@ -48,7 +48,10 @@ bamg_status spgemm_symbolic(int m, const int32_t* arp, const int32_t* aci, const
 bamg_status spgemm_numeric(int m, const int32_t* arp, const int32_t* aci, const double* ava,
                            const int32_t* brp, const int32_t* bci, const double* bva,
                            const int32_t* crp, int32_t* cci, double* cva, cudaStream_t s);
-// Independent products C_q = A_q B_q, two host reads for all of them.
+// Independent products C_q = A_q B_q.  With annz (entries of A) and
+// maxrow_b (an upper bound on the entries of a row of B) given for every job,
+// the scratch is sized by annz * maxrow_b and one host read per call returns
+// nnz(C) and maxrow_c (entries of C's longest row); otherwise two host reads.
 struct SpgemmJob {
   int m;
   const int32_t *arp, *aci;
@@ -57,6 +60,9 @@ struct SpgemmJob {
   const double* bva;
   DevMem *crp, *cci, *cva;   // allocated on the stream
   int64_t nnz;
+  int64_t annz = -1;
+  int maxrow_b = -1;
+  int maxrow_c = -1;          // out (bounded path)
 };
 bamg_status spgemm_multi(SpgemmJob* jobs, int k, cudaStream_t s);
 // C = A B in one expansion pass; allocates C's arrays on s, nnz(C) to the host

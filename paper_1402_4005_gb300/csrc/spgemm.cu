@@ -363,6 +363,12 @@ struct SpJobs {
   const int32_t* crp[kMaxJobs];
   int32_t* cci[kMaxJobs];
   double* cva[kMaxJobs];
+  // bounded path (longl != nullptr): rows of more than kWarpCap products,
+  // their count in stats[1]; info = {overflow, nnz(C), entries of C's
+  // longest row, 0}; cap = scratch entries
+  int32_t* longl[kMaxJobs];
+  int* info[kMaxJobs];
+  long long cap[kMaxJobs];
 };
 
 // products per row, and per job their maximum and total (one atomic pair
@@ -379,6 +385,10 @@ __global__ void count_products_multi(SpJobs J) {
       c += J.brp[q][k + 1] - J.brp[q][k];
     }
     J.prod[q][i] = c > INT32_MAX ? INT32_MAX : (int)c;
+    if (J.longl[q] && c > kWarpCap) {
+      if (c > kBlockCap) atomicExch(J.info[q], 1);             // no kernel takes such a row
+      else J.longl[q][atomicAdd(J.stats[q] + 1, 1)] = i;
+    }
   }
   int mx = c > INT32_MAX ? INT32_MAX : (int)c;
   unsigned long long sum = (unsigned long long)c;
@@ -403,8 +413,52 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) spgemm_warp_multi(SpJobs 
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * kWarpsPerBlock + w;
   if (i >= J.m[q]) return;
+  if (J.info[q]) {   // bounded scratch: a row that would not fit is not written
+    const int c = J.prod[q][i];
+    if (c <= kWarpCap && (long long)J.offs[q][i] + c > J.cap[q]) {
+      if (lane == 0) atomicExch(J.info[q], 1);
+      return;
+    }
+  }
   row_product<32, true>(i, -1, kWarpCap, J.prod[q], J.arp[q], J.aci[q], J.ava[q], J.brp[q], J.bci[q], J.bva[q],
                         J.cnts[q], J.offs[q], J.scol[q], J.sval[q], skey[w], sval[w], sflag[w], lane);
+}
+
+// Bounded path: the rows of more than kWarpCap products, a block each, from
+// the list the count kernel built (blocks stride over it).
+__global__ void __launch_bounds__(kBigThreads) spgemm_block_list_multi(SpJobs J) {
+  pdl_wait();
+  pdl_trigger();
+  extern __shared__ unsigned char dyn[];
+  unsigned long long* key = reinterpret_cast<unsigned long long*>(dyn);
+  double* val = reinterpret_cast<double*>(key + kBlockCap);
+  int* flag = reinterpret_cast<int*>(val + kBlockCap);
+  const int q = blockIdx.y;
+  const int nl = J.stats[q][1];
+  for (int idx = blockIdx.x; idx < nl; idx += gridDim.x) {
+    const int i = J.longl[q][idx];
+    const int c = J.prod[q][i];
+    if ((long long)J.offs[q][i] + c > J.cap[q]) {
+      if (threadIdx.x == 0) atomicExch(J.info[q], 1);
+      continue;
+    }
+    row_product<kBigThreads, true>(i, kWarpCap, kBlockCap, J.prod[q], J.arp[q], J.aci[q], J.ava[q], J.brp[q],
+                                   J.bci[q], J.bva[q], J.cnts[q], J.offs[q], J.scol[q], J.sval[q], key, val, flag,
+                                   threadIdx.x);
+  }
+}
+
+// Bounded path: info[1] = nnz(C) = crp[m], info[2] = entries of the longest row.
+__global__ void spgemm_info_multi(SpJobs J) {
+  pdl_wait();
+  pdl_trigger();
+  const int q = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int c = i < J.m[q] ? J.cnts[q][i] : 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c = max(c, __shfl_xor_sync(0xffffffffu, c, o));
+  if ((threadIdx.x & 31) == 0 && c > 0) atomicMax(J.info[q] + 2, c);
+  if (blockIdx.x == 0 && threadIdx.x == 0) J.info[q][1] = J.crp[q][J.m[q]];
 }
 
 __global__ void compact_rows_multi(SpJobs J) {
@@ -451,12 +505,109 @@ bamg_status spgemm(int m, const int32_t* arp, const int32_t* aci, const double* 
 // Several independent products at once: each phase is issued for every
 // product before the one host read that phase needs (product statistics,
 // then the nnz of every result), so k products cost two host reads.
+// Bounded: the scratch of job q holds cap_q = annz_q * maxrow_b_q products (at
+// least the true count), so the counts need no host read; rows that would not
+// fit are not written and raise the overflow flag.  One host read: the flags,
+// nnz(C) and the longest row of C.
+static bamg_status spgemm_multi_bounded(SpgemmJob* jobs, int k, const long long* cap, cudaStream_t s) {
+  // per job: stats(4), info(4); then prod, offs, cnts (m + 1 each), long rows (m)
+  std::vector<size_t> ro(k + 1, 0);
+  for (int q = 0; q < k; ++q) ro[q + 1] = ro[q] + 3 * (size_t)(jobs[q].m + 1) + (size_t)jobs[q].m;
+  DevMem ints;
+  const size_t head = 8 * (size_t)k;
+  BAMG_TRY(ints.alloc(sizeof(int32_t) * (head + ro[k]), s));
+  BAMG_CUDA(cudaMemsetAsync(ints.p, 0, sizeof(int32_t) * (head + ro[k]), s));
+  int* hd = ints.as<int>();
+  int32_t* rows = ints.as<int32_t>() + head;
+  SpJobs J;
+  J.k = k;
+  int maxm = 0;
+  std::vector<size_t> so(k + 1, 0);
+  for (int q = 0; q < k; ++q) {
+    const SpgemmJob& S = jobs[q];
+    J.m[q] = S.m;
+    J.arp[q] = S.arp; J.aci[q] = S.aci; J.ava[q] = S.ava;
+    J.brp[q] = S.brp; J.bci[q] = S.bci; J.bva[q] = S.bva;
+    J.prod[q] = rows + ro[q];
+    J.offs[q] = rows + ro[q] + (S.m + 1);
+    J.cnts[q] = rows + ro[q] + 2 * (size_t)(S.m + 1);
+    J.longl[q] = rows + ro[q] + 3 * (size_t)(S.m + 1);
+    J.stats[q] = hd + 8 * q;
+    J.info[q] = hd + 8 * q + 4;
+    J.cap[q] = cap[q];
+    so[q + 1] = so[q] + (size_t)(cap[q] > 0 ? cap[q] : 1);
+    maxm = S.m > maxm ? S.m : maxm;
+  }
+  BAMG_TRY(launch(count_products_multi, dim3(cdiv(maxm, 256), k), dim3(256), 0, s, J));
+  DevMem scol, sval;
+  BAMG_TRY(scol.alloc(sizeof(int32_t) * so[k], s));
+  BAMG_TRY(sval.alloc(sizeof(double) * so[k], s));
+  ScanMany sc;
+  for (int q = 0; q < k; ++q) {
+    J.scol[q] = scol.as<int32_t>() + so[q];
+    J.sval[q] = sval.as<double>() + so[q];
+    sc.in[sc.k] = J.prod[q];
+    sc.out[sc.k] = J.offs[q];
+    sc.n[sc.k++] = jobs[q].m;
+  }
+  BAMG_TRY(scan_many(sc, s));
+  BAMG_TRY(launch(spgemm_warp_multi, dim3(cdiv(maxm, kWarpsPerBlock), k), dim3(kWarpsPerBlock * 32), 0, s, J));
+  {
+    static std::atomic<uint64_t> attr_done{0};
+    int max_dyn = 0;
+    BAMG_TRY(allow_max_smem((const void*)spgemm_block_list_multi, attr_done, &max_dyn));
+    BAMG_TRY(launch(spgemm_block_list_multi, dim3(64, k), dim3(kBigThreads), big_smem(true), s, J));
+  }
+  ScanMany sc2;
+  for (int q = 0; q < k; ++q) {
+    BAMG_TRY(jobs[q].crp->alloc(sizeof(int32_t) * (jobs[q].m + 1), s));
+    J.crp[q] = jobs[q].crp->as<int32_t>();
+    sc2.in[sc2.k] = J.cnts[q];
+    sc2.out[sc2.k] = jobs[q].crp->as<int32_t>();
+    sc2.n[sc2.k++] = jobs[q].m;
+  }
+  BAMG_TRY(scan_many(sc2, s));
+  BAMG_TRY(launch(spgemm_info_multi, dim3(cdiv(maxm, 256), k), dim3(256), 0, s, J));
+  std::vector<int> h(head);
+  BAMG_CUDA(cudaMemcpyAsync(h.data(), hd, sizeof(int) * head, cudaMemcpyDeviceToHost, s));
+  BAMG_CUDA(cudaStreamSynchronize(s));
+  for (int q = 0; q < k; ++q) {
+    const int* inf = &h[8 * q + 4];
+    if (inf[0]) {
+      set_error("sparse product: a row exceeds %d products or the products exceed their bound %lld", kBlockCap,
+                cap[q]);
+      return BAMG_ERR_NUMERIC;
+    }
+    SpgemmJob& S = jobs[q];
+    S.nnz = inf[1];
+    S.maxrow_c = inf[2];
+    BAMG_TRY(S.cci->alloc(sizeof(int32_t) * (S.nnz > 0 ? S.nnz : 1), s));
+    BAMG_TRY(S.cva->alloc(sizeof(double) * (S.nnz > 0 ? S.nnz : 1), s));
+    J.cci[q] = S.cci->as<int32_t>();
+    J.cva[q] = S.cva->as<double>();
+  }
+  return launch(compact_rows_multi, dim3(cdiv((long long)maxm * 32, 256), k), dim3(256), 0, s, J);
+}
+
 bamg_status spgemm_multi(SpgemmJob* jobs, int k, cudaStream_t s) {
   if (k <= 0) return BAMG_OK;
   if (k > kMaxJobs) {
     for (int q0 = 0; q0 < k; q0 += kMaxJobs)
       BAMG_TRY(spgemm_multi(jobs + q0, k - q0 < kMaxJobs ? k - q0 : kMaxJobs, s));
     return BAMG_OK;
+  }
+  {
+    long long cap[kMaxJobs];
+    bool bounded = true;
+    for (int q = 0; q < k; ++q) {
+      if (jobs[q].annz < 0 || jobs[q].maxrow_b < 0) {
+        bounded = false;
+        break;
+      }
+      cap[q] = jobs[q].annz * (long long)jobs[q].maxrow_b;
+      bounded = bounded && cap[q] <= INT32_MAX;
+    }
+    if (bounded) return spgemm_multi_bounded(jobs, k, cap, s);
   }
   // one int32 buffer for the statistics and the per-row arrays of all jobs
   // (product counts, their offsets, entry counts), one pair for the scratch
@@ -472,6 +623,9 @@ bamg_status spgemm_multi(SpgemmJob* jobs, int k, cudaStream_t s) {
   int maxm = 0;
   for (int q = 0; q < k; ++q) {
     const SpgemmJob& S = jobs[q];
+    J.longl[q] = nullptr;
+    J.info[q] = nullptr;
+    J.cap[q] = 0;
     J.m[q] = S.m;
     J.arp[q] = S.arp; J.aci[q] = S.aci; J.ava[q] = S.ava;
     J.brp[q] = S.brp; J.bci[q] = S.bci; J.bva[q] = S.bva;
@@ -544,6 +698,7 @@ bamg_status spgemm_multi(SpgemmJob* jobs, int k, cudaStream_t s) {
   for (int q = 0; q < k; ++q) {
     SpgemmJob& S = jobs[q];
     S.nnz = nz[q];
+    S.maxrow_c = -1;
     BAMG_TRY(S.cci->alloc(sizeof(int32_t) * (S.nnz > 0 ? S.nnz : 1), s));
     BAMG_TRY(S.cva->alloc(sizeof(double) * (S.nnz > 0 ? S.nnz : 1), s));
     J.cci[q] = S.cci->as<int32_t>();
