@@ -40,6 +40,7 @@
 
 #include <atomic>
 #include <cfloat>
+#include <cstddef>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -1503,7 +1504,8 @@ static bamg_status side_stream(cudaStream_t* out) {
 
 template <typename T>
 static bamg_status coarsest_t(int n, int r, const double* B, const double* M, const double* N, double* sigma,
-                              double* U, double* V, double* Bpinv, cudaStream_t s, HostWork during) {
+                              double* U, double* V, double* Bpinv, cudaStream_t s, HostWork during,
+                              int* err_out) {
   // ---- triplets: Cholesky, C, bidiagonalization, SVD, back-transform
   DenseArgs<T> a = {};
   a.n = n; a.r = r; a.B = B; a.M = M; a.N = N;
@@ -1601,6 +1603,13 @@ static bamg_status coarsest_t(int n, int r, const double* B, const double* M, co
   const auto t_hw0 = std::chrono::steady_clock::now();
   const bamg_status hw = during.fn ? during.fn(during.ctx) : BAMG_OK;
   const auto t_hw1 = std::chrono::steady_clock::now();
+  if (err_out && !std::getenv("BAMG_TRACE")) {
+    // status for the caller's later read; this call's buffers are released
+    // on the stream after the kernels (and after the side stream's event)
+    static_assert(offsetof(DenseCtl, err) == 0, "status word first");
+    BAMG_CUDA(cudaMemcpyAsync(err_out, ctl.p, sizeof(int), cudaMemcpyDeviceToDevice, s));
+    return hw;
+  }
   DenseCtl h[2];
   BAMG_CUDA(cudaMemcpyAsync(h, ctl.p, sizeof(h), cudaMemcpyDeviceToHost, s));
   BAMG_CUDA(cudaStreamSynchronize(s));
@@ -1624,17 +1633,19 @@ static bamg_status coarsest_t(int n, int r, const double* B, const double* M, co
     set_error("coarsest level: M or N is not positive definite");
     return BAMG_ERR_NUMERIC;
   }
+  if (err_out) BAMG_CUDA(cudaMemsetAsync(err_out, 0, sizeof(int), s));
   return hw;
 }
 
 bamg_status coarsest_solve(int prec, int n, int r, const double* B, const double* M, const double* N,
-                           double* sigma, double* U, double* V, double* Bpinv, cudaStream_t s, HostWork during) {
+                           double* sigma, double* U, double* V, double* Bpinv, cudaStream_t s, HostWork during,
+                           int* err_out) {
   if (n < 2 || n > kDenseMaxN || r < 1 || r > n || r > kMaxR) {
     set_error("coarsest solve needs 1 <= r <= min(n, %d), 2 <= n <= %d (n = %d, r = %d)", kMaxR, kDenseMaxN, n, r);
     return BAMG_ERR_UNSUPPORTED;
   }
-  if (prec == 1) return coarsest_t<float>(n, r, B, M, N, sigma, U, V, Bpinv, s, during);
-  return coarsest_t<double>(n, r, B, M, N, sigma, U, V, Bpinv, s, during);
+  if (prec == 1) return coarsest_t<float>(n, r, B, M, N, sigma, U, V, Bpinv, s, during, err_out);
+  return coarsest_t<double>(n, r, B, M, N, sigma, U, V, Bpinv, s, during, err_out);
 }
 
 }  // namespace bamg

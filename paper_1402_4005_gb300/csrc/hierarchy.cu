@@ -410,6 +410,83 @@ static bamg_status check_levels(bamg_hierarchy* h, cudaStream_t s) {
   return BAMG_OK;
 }
 
+// x = column k of the n x ld block V, k the first index of the smallest
+// |sigma_k| among k < rr
+__global__ void x0_column_kernel(int n, int ld, int rr, const double* __restrict__ sig,
+                                 const double* __restrict__ V, double* __restrict__ x) {
+  pdl_wait();
+  pdl_trigger();
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int kmin = 0;
+  for (int k = 1; k < rr; ++k)
+    if (fabs(sig[k]) < fabs(sig[kmin])) kmin = k;
+  x[i] = V[(size_t)i * ld + kmin];
+}
+
+// out = {dflags of every level (2 each), rankdef, coarsest status, sigma[0..ld)}
+constexpr int kFlagLevels = 64;
+struct SetupFlags {
+  const int* dflags[kFlagLevels];
+  int nlev;
+  const int* rkd;
+  const int* cerr;
+  const double* sig;
+  int ld;
+};
+__global__ void setup_flags_kernel(SetupFlags f, double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
+  const int t = threadIdx.x;
+  for (int l = t; l < f.nlev; l += blockDim.x) {
+    out[2 * l] = f.dflags[l][0];
+    out[2 * l + 1] = f.dflags[l][1];
+  }
+  if (t == 0) {
+    out[2 * f.nlev] = f.rkd[0];
+    out[2 * f.nlev + 1] = f.cerr ? f.cerr[0] : 0;
+  }
+  for (int k = t; k < f.ld; k += blockDim.x) out[2 * f.nlev + 2 + k] = f.sig[k];
+}
+
+static bamg_status setup_flags(bamg_hierarchy* h, cudaStream_t s, const int* rkd, const int* cerr,
+                               const double* sig, int ld) {
+  const int nlev = (int)h->lv.size();
+  if (nlev > kFlagLevels) {
+    set_error("%d levels exceed the %d the setup supports", nlev, kFlagLevels);
+    return BAMG_ERR_UNSUPPORTED;
+  }
+  SetupFlags f = {};
+  for (int l = 0; l < nlev; ++l) f.dflags[l] = h->lv[l].dflags.as<int>();
+  f.nlev = nlev;
+  f.rkd = rkd;
+  f.cerr = cerr;
+  f.sig = sig;
+  f.ld = ld;
+  const int total = 2 * nlev + 2 + ld;
+  DevMem out;
+  BAMG_TRY(out.alloc(sizeof(double) * total, s));
+  BAMG_TRY(launch(setup_flags_kernel, dim3(1), dim3(64), 0, s, f, out.as<double>()));
+  std::vector<double> hv(total);
+  BAMG_CUDA(cudaMemcpyAsync(hv.data(), out.p, sizeof(double) * total, cudaMemcpyDeviceToHost, s));
+  BAMG_CUDA(cudaStreamSynchronize(s));
+  if ((int)hv[2 * nlev + 1] == 2) {
+    set_error("coarsest level: M or N is not positive definite");
+    return BAMG_ERR_NUMERIC;
+  }
+  for (int l = 0; l < nlev; ++l) {
+    const int zr = (int)hv[2 * l];
+    if (zr != 0x7F7F7F7F) {
+      set_error("level %d: row and column %d of B are zero", l, zr);
+      return BAMG_ERR_NUMERIC;
+    }
+    h->lv[l].nsafe = (int)hv[2 * l + 1];
+  }
+  h->rankdef = (int)hv[2 * nlev];
+  h->sigma.assign(hv.begin() + 2 * nlev + 2, hv.end());
+  return BAMG_OK;
+}
+
 static void complexities(bamg_hierarchy* h) {
   // eq. operator_complexity_def; Section 7
   double nnz_sum = 0, n_sum = 0;
@@ -471,7 +548,7 @@ static bamg_status run_setup(bamg_hierarchy* h, cudaStream_t s) {
     BAMG_TRY(V[0].alloc(sizeof(T) * (size_t)n0 * ld, s));
     BAMG_TRY(init_vectors<T>(n0, ld, r, p.seed, U[0].as<T>(), V[0].as<T>(), s));
   }
-  DevMem scale, norms, rkd, sig, sig64;
+  DevMem scale, norms, rkd, sig, sig64, coarse_err;
   BAMG_TRY(scale.alloc(sizeof(T) * ld, s));
   BAMG_TRY(norms.alloc(sizeof(double) * ld, s));
   BAMG_TRY(rkd.alloc(2 * sizeof(int), s));
@@ -548,9 +625,16 @@ static bamg_status run_setup(bamg_hierarchy* h, cudaStream_t s) {
         return gmres_prepare_default(e->h);
       };
     }
-    // Ud/Vd are nL x rr row-major (rr <= r)
+    // Ud/Vd are nL x rr row-major (rr <= r).  The coarsest kernels' status is
+    // read with the setup's final flags (LS setups): the host queues the
+    // bottom-up work while they run.
+    if (!learned) {
+      BAMG_TRY(coarse_err.alloc(sizeof(int), s));
+      BAMG_CUDA(cudaMemsetAsync(coarse_err.p, 0, sizeof(int), s));
+    }
     BAMG_TRY(coarsest_solve(h->mixed ? 1 : 0, nL, rr, Bd.as<double>(), Md.as<double>(), Nd.as<double>(),
-                            sg.as<double>(), Ud.as<double>(), Vd.as<double>(), h->Bpinv.as<double>(), s, during));
+                            sg.as<double>(), Ud.as<double>(), Vd.as<double>(), h->Bpinv.as<double>(), s, during,
+                            learned ? nullptr : coarse_err.as<int>()));
     if (h->mixed) BAMG_TRY(convert<double, float>(nn, h->Bpinv.as<double>(), h->Bpinv32.as<float>(), s));
     tr.mark(s, "coarsest solve", l);
     if (learned) return learned_unwind(h, l, rr, Vd.as<double>(), sg.as<double>(), s);
@@ -585,26 +669,20 @@ static bamg_status run_setup(bamg_hierarchy* h, cudaStream_t s) {
       V[k + 1].release();
     }
   }
-  // finest triplets, x^(0) = v of the smallest |sigma|
-  h->sigma.assign(ld, 0.0);
-  BAMG_CUDA(cudaMemcpyAsync(h->sigma.data(), sig64.p, sizeof(double) * ld, cudaMemcpyDeviceToHost, s));
+  // finest triplets, x^(0) = v of the smallest |sigma| (chosen on the device)
   BAMG_TRY(h->U64.alloc(sizeof(double) * (size_t)n0 * ld, s));
   BAMG_TRY(h->V64.alloc(sizeof(double) * (size_t)n0 * ld, s));
   BAMG_TRY(convert<T, double>((size_t)n0 * ld, U[0].as<T>(), h->U64.as<double>(), s));
   BAMG_TRY(convert<T, double>((size_t)n0 * ld, V[0].as<T>(), h->V64.as<double>(), s));
-  int hr = 0;
-  BAMG_CUDA(cudaMemcpyAsync(&hr, rkd.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-  BAMG_CUDA(cudaStreamSynchronize(s));
-  h->rankdef = hr;
-  h->sigma.resize(r);
-  int kmin = 0;
-  for (int k = 1; k < rr; ++k)
-    if (std::fabs(h->sigma[k]) < std::fabs(h->sigma[kmin])) kmin = k;
   BAMG_TRY(h->x0.alloc(sizeof(double) * n0, s));
-  BAMG_TRY(launch(column_kernel, dim3(cdiv(n0, 256)), dim3(256), 0, s, n0, ld, kmin,
-                  (const double*)h->V64.as<double>(), h->x0.as<double>()));
+  BAMG_TRY(launch(x0_column_kernel, dim3(cdiv(n0, 256)), dim3(256), 0, s, n0, ld, rr,
+                  (const double*)sig64.as<double>(), (const double*)h->V64.as<double>(), h->x0.as<double>()));
   BAMG_TRY(orient_normalise(n0, h->x0.as<double>(), s));
-  BAMG_TRY(check_levels(h, s));
+  // the setup's one closing host read: divisor flags of every level, fits
+  // refitted or rank deficient, the coarsest status, the finest sigma
+  BAMG_TRY(setup_flags(h, s, rkd.as<int>(), coarse_err.p ? coarse_err.as<int>() : nullptr,
+                       sig64.as<double>(), ld));
+  h->sigma.resize(r);
   complexities(h);
   return BAMG_OK;
 }

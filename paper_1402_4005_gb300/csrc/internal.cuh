@@ -177,9 +177,11 @@ struct HostWork {
   bamg_status (*fn)(void* ctx) = nullptr;
   void* ctx = nullptr;
 };
+// err_out (optional, device int): the call returns without waiting for the
+// kernels and leaves their status there (2 = M or N not positive definite).
 bamg_status coarsest_solve(int prec, int n, int r, const double* B, const double* M, const double* N,
                            double* sigma, double* U, double* V, double* Bpinv, cudaStream_t s,
-                           HostWork during = HostWork());
+                           HostWork during = HostWork(), int* err_out = nullptr);
 bamg_status csr_to_dense(int n, const int32_t* rp, const int32_t* ci, const double* va, double* D,
                          cudaStream_t s);
 
