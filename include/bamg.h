@@ -190,7 +190,7 @@ uint64_t bamg_launch_count(void);
 
 /* -------------------------------------------------------------- batches --
  * Many independent chains solved together.  Each chain gets its own bootstrap
- * setup (run concurrently on `host_threads` host threads, 0 = 16, each with
+ * setup (run concurrently on `host_threads` host threads, 0 = 4, each with
  * its own stream); the hierarchies are then joined level by level into
  * block-diagonal operators so that one V-cycle (captured as a CUDA graph)
  * and one flexible GMRES run serve all chains, with per-chain dot products,

@@ -721,7 +721,7 @@ extern "C" bamg_status bamg_setup_batched(const bamg_csr* As, int nchains, const
   bt->h.assign(nchains, nullptr);
   std::vector<bamg_status> st(nchains, BAMG_OK);
   std::vector<std::string> err(nchains);
-  int T = host_threads > 0 ? host_threads : 16;
+  int T = host_threads > 0 ? host_threads : 4;   // more threads contend for the launch path
   if (T > nchains) T = nchains;
   bt->wstreams.assign(T, nullptr);
   for (int t = 0; t < T; ++t)
@@ -745,7 +745,8 @@ extern "C" bamg_status bamg_setup_batched(const bamg_csr* As, int nchains, const
   }
   for (auto& th : pool) th.join();
   const bool trace = std::getenv("BAMG_TRACE") != nullptr;
-  if (trace) fprintf(stderr, "[bamg] batch: %d chain setups done\n", nchains);
+  auto since = [&]() { return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count(); };
+  if (trace) fprintf(stderr, "[bamg] batch: %d chain setups done (%.1f ms)\n", nchains, since());
   for (int c = 0; c < nchains; ++c)
     if (st[c] != BAMG_OK) {
       set_error("chain %d: %s", c, err[c].c_str());
@@ -759,11 +760,11 @@ extern "C" bamg_status bamg_setup_batched(const bamg_csr* As, int nchains, const
                    [&](int a, int b) { return bt->h[a]->lv.size() > bt->h[b]->lv.size(); });
   bt->in_off.assign(nchains + 1, 0);
   for (int c = 0; c < nchains; ++c) bt->in_off[c + 1] = bt->in_off[c] + bt->h[c]->lv[0].n;
-  if (trace) fprintf(stderr, "[bamg] batch: sorted, n0 = %lld\n", (long long)bt->in_off[nchains]);
+  if (trace) fprintf(stderr, "[bamg] batch: sorted, n0 = %lld (%.1f ms)\n", (long long)bt->in_off[nchains], since());
   bamg_status r = build_levels(bt, s);
-  if (trace) fprintf(stderr, "[bamg] batch: levels built (%d), status %d\n", (int)bt->lv.size(), (int)r);
+  if (trace) fprintf(stderr, "[bamg] batch: levels built (%d), status %d (%.1f ms)\n", (int)bt->lv.size(), (int)r, since());
   if (r == BAMG_OK) r = bvcycle_prepare(bt);
-  if (trace) fprintf(stderr, "[bamg] batch: V-cycle graph status %d\n", (int)r);
+  if (trace) fprintf(stderr, "[bamg] batch: V-cycle graph status %d (%.1f ms)\n", (int)r, since());
   if (r != BAMG_OK) {
     cudaStreamSynchronize(s);
     bamg_destroy_batched(bt);

@@ -21,6 +21,7 @@
 #include <cuda.h>
 
 #include <chrono>
+#include <cstdlib>
 #include <cmath>
 #include <mutex>
 #include <new>
@@ -165,6 +166,21 @@ bamg_status vcycle_body(bamg_hierarchy* h, cudaStream_t s, const double* in, con
                 out_col);
 }
 
+// BAMG_TRACE: nodes of a captured graph and how many of its edges are
+// programmatic (kernel-to-kernel overlap) rather than full dependencies.
+static void trace_edges(const char* what, cudaGraph_t g) {
+  size_t nn = 0, ne = 0;
+  cudaGraphGetNodes(g, nullptr, &nn);
+  cudaGraphGetEdges(g, nullptr, nullptr, nullptr, &ne);
+  std::vector<cudaGraphNode_t> from(ne), to(ne);
+  std::vector<cudaGraphEdgeData> ed(ne);
+  size_t prog = 0;
+  if (ne && cudaGraphGetEdges(g, from.data(), to.data(), ed.data(), &ne) == cudaSuccess)
+    for (size_t e = 0; e < ne; ++e) prog += ed[e].type == cudaGraphDependencyTypeProgrammatic;
+  cudaGetLastError();
+  fprintf(stderr, "[bamg] %s graph: %zu nodes, %zu edges, %zu programmatic\n", what, nn, ne, prog);
+}
+
 // Allocates the V-cycle vectors and captures the V-cycle into a graph.
 bamg_status vcycle_prepare(bamg_hierarchy* h, cudaStream_t s) {
   if (h->vexec) return BAMG_OK;
@@ -210,6 +226,7 @@ bamg_status vcycle_prepare(bamg_hierarchy* h, cudaStream_t s) {
   }
   BAMG_CUDA(e);
   h->vgraph = g;
+  if (std::getenv("BAMG_TRACE")) trace_edges("V-cycle", g);
   BAMG_CUDA(cudaGraphInstantiate(&h->vexec, g, 0));
   h->vgraph_kernels = t_launches - before;
   g_launches.fetch_sub(h->vgraph_kernels);  // counted again at each replay
@@ -838,6 +855,7 @@ static bamg_status gmres_prepare(bamg_hierarchy* h, int m, int plain) {
   }
   BAMG_CUDA(e);
   S->graph = g;
+  if (std::getenv("BAMG_TRACE")) trace_edges("Arnoldi", g);
   BAMG_CUDA(cudaGraphInstantiate(&S->exec, g, 0));
   S->kernels = t_launches - before;
   g_launches.fetch_sub(S->kernels);  // counted at each replay
