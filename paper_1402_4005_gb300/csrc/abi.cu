@@ -133,6 +133,8 @@ bamg_status setup_impl(const bamg_csr* A, const bamg_params* p, void* stream, ba
   // setup), so the setup's chains of small kernels launch with programmatic
   // serialisation and each launch overlaps the previous kernel
   PdlScope pdl;
+  // temporaries released during the setup serve its later allocations
+  AllocScope cache;
   do {
     if (cudaGetDevice(&h->device) != cudaSuccess) { st = BAMG_ERR_CUDA; break; }
     configure_pool(h->device);

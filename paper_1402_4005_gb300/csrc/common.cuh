@@ -97,12 +97,32 @@ inline bamg_status launch(void (*k)(KArgs...), dim3 grid, dim3 block, size_t sme
 inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
 // --------------------------------------------------- stream-ordered buffers
+// Block cache of one call (sparse.cu).  While an AllocScope is active on the
+// calling thread (the setup), blocks of at most kScopeMax bytes are rounded
+// up to a power of two; those released during the call go to a free list of
+// their stream and serve later allocations on the same stream in the same
+// call (the stream orders the new uses after the old ones), instead of a
+// cudaFreeAsync / cudaMallocAsync pair each.  The rest are returned to the
+// pool when the scope ends.
+constexpr size_t kScopeMax = size_t(8) << 20;
+struct AllocScope {
+  AllocScope();
+  ~AllocScope();
+  AllocScope(const AllocScope&) = delete;
+  AllocScope& operator=(const AllocScope&) = delete;
+  bool owner;
+};
+bool scope_active();
+void* scope_get(size_t bytes, cudaStream_t s, size_t* got);
+bool scope_put(void* p, size_t bytes, cudaStream_t s);
+
 // Device memory from the stream-ordered pool (cudaMallocAsync); freed on the
 // same stream.  The pool keeps freed blocks, so repeated setups re-use them.
 struct DevMem {
   void* p = nullptr;
   size_t bytes = 0;
   cudaStream_t s = nullptr;
+  bool rounded = false;     // a power-of-two block allocated in a scope
   DevMem() = default;
   DevMem(const DevMem&) = delete;
   DevMem& operator=(const DevMem&) = delete;
@@ -110,21 +130,34 @@ struct DevMem {
   DevMem& operator=(DevMem&& o) noexcept {
     if (this != &o) {
       release();
-      p = o.p; bytes = o.bytes; s = o.s;
-      o.p = nullptr; o.bytes = 0;
+      p = o.p; bytes = o.bytes; s = o.s; rounded = o.rounded;
+      o.p = nullptr; o.bytes = 0; o.rounded = false;
     }
     return *this;
   }
   ~DevMem() { release(); }
   void release() {
-    if (p) cudaFreeAsync(p, s);
+    if (p && !(rounded && scope_put(p, bytes, s))) cudaFreeAsync(p, s);
     p = nullptr;
     bytes = 0;
+    rounded = false;
   }
   bamg_status alloc(size_t nbytes, cudaStream_t st) {
     release();
     s = st;
     if (nbytes == 0) nbytes = 16;
+    if (nbytes <= kScopeMax && scope_active()) {
+      size_t cls = 256;
+      while (cls < nbytes) cls <<= 1;
+      rounded = true;
+      size_t got = 0;
+      if (void* q = scope_get(cls, st, &got)) {
+        p = q;
+        bytes = got;
+        return BAMG_OK;
+      }
+      nbytes = cls;
+    }
     cudaError_t e = cudaMallocAsync(&p, nbytes, st);
     if (e != cudaSuccess) {
       p = nullptr;

@@ -5,6 +5,8 @@
 #include <mutex>
 #include <vector>
 
+#include <map>
+#include <array>
 #include "internal.cuh"
 
 namespace bamg {
@@ -22,6 +24,61 @@ void set_error(const char* fmt, ...) {
 }
 
 const char* last_error_text() { return t_err; }
+
+// ------------------------------------------------------------ block cache
+namespace {
+struct ScopeCache {
+  // free blocks per stream and size class (256 B << c)
+  std::map<cudaStream_t, std::array<std::vector<void*>, 16>> free;
+};
+thread_local ScopeCache* t_scope = nullptr;
+int class_of(size_t bytes) {
+  int c = 0;
+  for (size_t b = 256; b < bytes; b <<= 1) ++c;
+  return c;
+}
+}  // namespace
+
+AllocScope::AllocScope() : owner(t_scope == nullptr) {
+  if (owner) t_scope = new ScopeCache();
+}
+
+AllocScope::~AllocScope() {
+  if (!owner) return;
+  ScopeCache* c = t_scope;
+  t_scope = nullptr;
+  for (auto& kv : c->free)
+    for (auto& v : kv.second)
+      for (void* p : v) cudaFreeAsync(p, kv.first);
+  delete c;
+}
+
+bool scope_active() { return t_scope != nullptr; }
+
+// a free block of this class on stream s, else of the next two larger ones
+void* scope_get(size_t bytes, cudaStream_t s, size_t* got) {
+  auto it = t_scope->free.find(s);
+  if (it == t_scope->free.end()) return nullptr;
+  const int c0 = class_of(bytes);
+  for (int c = c0; c < c0 + 3 && c < 16; ++c) {
+    auto& v = it->second[c];
+    if (!v.empty()) {
+      void* p = v.back();
+      v.pop_back();
+      *got = size_t(256) << c;
+      return p;
+    }
+  }
+  return nullptr;
+}
+
+bool scope_put(void* p, size_t bytes, cudaStream_t s) {
+  if (!t_scope) return false;
+  const int c = class_of(bytes);
+  if (c >= 16 || (size_t(256) << c) != bytes) return false;
+  t_scope->free[s][c].push_back(p);
+  return true;
+}
 
 void configure_pool(int device) {
   static std::mutex mu;
