@@ -90,11 +90,12 @@ struct bamg_hierarchy {
 };
 
 namespace bamg {
-// z = C in (in: n doubles, or the column col[0] of an n-row array when col is
-// given); z is written to out and, with out_col, to the column col[0] of out_col.
+// z = C in (in: n doubles, or the column j = col[0] of an n-row array when col
+// is given; with w given and j > 0 that column is first formed as w * rinv[0]
+// and stored); z is written to out and, with out_col, to its column j.
 template <typename T>
-bamg_status vcycle_body(bamg_hierarchy* h, cudaStream_t s, const double* in, const int* col, double* out,
-                        double* out_col);
+bamg_status vcycle_body(bamg_hierarchy* h, cudaStream_t s, double* in, const int* col, double* out,
+                        double* out_col, const double* w, const double* rinv);
 bamg_status vcycle_prepare(bamg_hierarchy* h, cudaStream_t s);
 // solve.cu: FGMRES workspace and Arnoldi graph for the default restart
 // (20), unpreconditioned = false; a solve with other settings re-captures

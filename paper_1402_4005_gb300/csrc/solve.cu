@@ -127,16 +127,31 @@ __global__ void fill_kernel(size_t n, double v, double* __restrict__ b) {
   if (t < n) b[t] = v;
 }
 
-// V-cycle input: b = in, or the column col[0] of the n-row array in,
-// converted to the V-cycle precision.
+// V-cycle input: b = in, or the column j = col[0] of the n-row array in,
+// converted to the V-cycle precision.  With w given and j > 0 the column is
+// first formed as w * rinv[0] (the previous Arnoldi step's w / ||w||) and
+// stored.
 template <typename T>
-__global__ void vc_in_kernel(int n, const double* __restrict__ in, const int* __restrict__ col, T* __restrict__ b) {
+__global__ void vc_in_kernel(int n, double* __restrict__ in, const int* __restrict__ col, const double* __restrict__ w,
+                             const double* __restrict__ rinv, T* __restrict__ b) {
   pdl_wait();
   pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double* src = col ? in + (size_t)col[0] * n : in;
-  b[i] = T(src[i]);
+  double v;
+  if (col) {
+    const int j = col[0];
+    double* vc = in + (size_t)j * n;
+    if (w && j > 0) {
+      v = w[i] * rinv[0];
+      vc[i] = v;
+    } else {
+      v = vc[i];
+    }
+  } else {
+    v = in[i];
+  }
+  b[i] = T(v);
 }
 
 // V-cycle output: out = z in FP64, and the same values into the column
@@ -153,14 +168,15 @@ __global__ void vc_out_kernel(int n, const T* __restrict__ z, double* __restrict
   if (out_col) out_col[(size_t)col[0] * n + i] = v;
 }
 
-// z = C in (in: n doubles, or the column col[0] of an n-row array); z goes
-// to out and, with out_col, also to the column col[0] of out_col.
+// z = C in (in: n doubles, or the column j = col[0] of an n-row array, formed
+// from w and rinv first when w is given and j > 0); z goes to out and, with
+// out_col, also to the column j of out_col.
 template <typename T>
-bamg_status vcycle_body(bamg_hierarchy* h, cudaStream_t s, const double* in, const int* col, double* out,
-                        double* out_col) {
+bamg_status vcycle_body(bamg_hierarchy* h, cudaStream_t s, double* in, const int* col, double* out,
+                        double* out_col, const double* w, const double* rinv) {
   Level& L0 = h->lv[0];
   const int n = L0.n;
-  BAMG_TRY(launch(vc_in_kernel<T>, dim3(cdiv(n, 256)), dim3(256), 0, s, n, in, col, L0.vb.as<T>()));
+  BAMG_TRY(launch(vc_in_kernel<T>, dim3(cdiv(n, 256)), dim3(256), 0, s, n, in, col, w, rinv, L0.vb.as<T>()));
   BAMG_TRY(vcycle_level<T>(h, 0, s));
   return launch(vc_out_kernel<T>, dim3(cdiv(n, 256)), dim3(256), 0, s, n, (const T*)L0.vz.as<T>(), out, col,
                 out_col);
@@ -215,8 +231,8 @@ bamg_status vcycle_prepare(bamg_hierarchy* h, cudaStream_t s) {
     PdlScope pdl;
     double* in = h->io_in.as<double>();
     double* out = h->io_out.as<double>();
-    st = h->mixed ? vcycle_body<float>(h, h->cap_stream, in, nullptr, out, nullptr)
-                  : vcycle_body<double>(h, h->cap_stream, in, nullptr, out, nullptr);
+    st = h->mixed ? vcycle_body<float>(h, h->cap_stream, in, nullptr, out, nullptr, nullptr, nullptr)
+                  : vcycle_body<double>(h, h->cap_stream, in, nullptr, out, nullptr, nullptr, nullptr);
   }
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
@@ -300,6 +316,19 @@ constexpr int kMultidotMax = 65;   // m + 1 <= 65 (restart <= 64)
 constexpr int kRedBlocks = 256;
 enum { kGsDots = 0, kGsUpDots = 1, kGsUpNorm = 2 };
 
+// The Givens update of column j (kGsUpNorm, by its last block once ||w|| is
+// known): column j of the Hessenberg matrix, h1 + h2 from the two passes and
+// then ||w||, goes through the previous rotations into R (row stride m), a new
+// rotation (cs, sn) zeroes ||w||, the right-hand side g is rotated, the
+// status slot st[2 (j mod 2) + {0, 1}] = {|g_{j+1}|, ||w||} is written (two
+// slots, so that step j + 1 may run while the host reads step j) and j
+// advances.
+struct GivensArgs {
+  const double* h1;
+  double *R, *cs, *sn, *g, *st;
+  int* dj;
+};
+
 // Warp reduce-scatter of eight per-lane values a[0..7]: returns, in every
 // lane, the warp total of column rs8_col(lane) (the four lanes that differ
 // only in bits 0 and 1 hold the same column).
@@ -326,11 +355,12 @@ __global__ void __launch_bounds__(256) gs_kernel(int n, int m, const int* __rest
                                                  const double* __restrict__ V, size_t ldv,
                                                  const double* __restrict__ hin, double* __restrict__ w,
                                                  double* __restrict__ part, unsigned* __restrict__ arrived,
-                                                 double* __restrict__ out) {
+                                                 double* __restrict__ out, GivensArgs ga) {
   pdl_wait();
   pdl_trigger();
   __shared__ double sh[8][kMultidotMax];
   __shared__ double hs[kMultidotMax];
+  __shared__ double gc[kMultidotMax], gsn[kMultidotMax];
   __shared__ bool last;
   const int K = dj[0] + 1, lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int col = rs8_col(lane);
@@ -397,6 +427,13 @@ __global__ void __launch_bounds__(256) gs_kernel(int n, int m, const int* __rest
     double r = t < nb ? __ldcg(part + t) : 0.0;
     r = warp_sum(r);
     if (lane == 0) sh[wp][0] = r;
+    // column j of the Hessenberg matrix and the earlier rotations, staged
+    const int j = K - 1;
+    for (int k = t; k <= j; k += blockDim.x) hs[k] = ga.h1[k] + hs[k];
+    for (int k = t; k < j; k += blockDim.x) {
+      gc[k] = ga.cs[k];
+      gsn[k] = ga.sn[k];
+    }
     __syncthreads();
     if (t == 0) {
       double a = 0.0;
@@ -405,6 +442,24 @@ __global__ void __launch_bounds__(256) gs_kernel(int n, int m, const int* __rest
       out[0] = nrm;
       out[1] = 1.0 / nrm;
       *arrived = 0u;
+      // the rotations stream the column (each needs only the carried entry)
+      double carry = hs[0];
+      for (int k = 0; k < j; ++k) {
+        const double next = hs[k + 1];
+        const double c = gc[k], sk = gsn[k];
+        ga.R[(size_t)k * m + j] = c * carry + sk * next;
+        carry = -sk * carry + c * next;
+      }
+      const double d = hypot(carry, nrm);
+      const double c = d > 0.0 ? carry / d : 1.0, sk = d > 0.0 ? nrm / d : 0.0;
+      ga.cs[j] = c;
+      ga.sn[j] = sk;
+      ga.R[(size_t)j * m + j] = d;
+      ga.g[j + 1] = -sk * ga.g[j];
+      ga.g[j] = c * ga.g[j];
+      ga.st[2 * (j & 1)] = fabs(ga.g[j + 1]);
+      ga.st[2 * (j & 1) + 1] = nrm;
+      ga.dj[0] = j + 1;   // every block has read j (the arrival count is complete)
     }
     return;
   }
@@ -424,38 +479,26 @@ __global__ void __launch_bounds__(256) gs_kernel(int n, int m, const int* __rest
   if (t == 0) *arrived = 0u;
 }
 
-// Unpreconditioned step: out = V_j and Z_j = V_j.
-__global__ void plain_io_kernel(int n, const int* __restrict__ dj, const double* __restrict__ V,
+// Unpreconditioned step: V_j = w * rinv[0] for j > 0 (the previous step's
+// w / ||w||), then out = V_j and Z_j = V_j.
+__global__ void plain_io_kernel(int n, const int* __restrict__ dj, double* __restrict__ V,
+                                const double* __restrict__ w, const double* __restrict__ rinv,
                                 double* __restrict__ out, double* __restrict__ Z) {
   pdl_wait();
   pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const size_t o = (size_t)dj[0] * n + i;
-  const double v = V[o];
+  const int j = dj[0];
+  const size_t o = (size_t)j * n + i;
+  double v;
+  if (j > 0) {
+    v = w[i] * rinv[0];
+    V[o] = v;
+  } else {
+    v = V[o];
+  }
   out[i] = v;
   Z[o] = v;
-}
-
-// V_{j+1} = w * (1 / ||w||) (rinv holds the reciprocal), then j <- j + 1:
-// the last block to finish (every block has read j by then) increments j and
-// resets the arrival counter.
-__global__ void next_basis_kernel(int n, int* __restrict__ dj, const double* __restrict__ w,
-                                  const double* __restrict__ rinv, double* __restrict__ V,
-                                  unsigned* __restrict__ arrived) {
-  pdl_wait();
-  pdl_trigger();
-  __shared__ bool last;
-  const int j = dj[0];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) V[(size_t)(j + 1) * n + i] = w[i] * rinv[0];
-  __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(arrived, 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (last && threadIdx.x == 0) {
-    dj[0] = j + 1;
-    *arrived = 0u;
-  }
 }
 
 // y = x + sum_k c[k] Z_k
@@ -524,50 +567,6 @@ __global__ void __launch_bounds__(256) norm2_kernel(int n, const double* __restr
     out[0] = sqrt(t);
     *arrived = 0u;
   }
-}
-
-// Column j of the Hessenberg matrix (h1 + h2 from the two Gram-Schmidt
-// passes, then ||w||) through the previous rotations into R, a new rotation,
-// the rotated right-hand side g; st[2 (j mod 2) + {0, 1}] = {|g_{j+1}|, ||w||}
-// (two slots, so that step j + 1 may run while the host reads step j).  One
-// warp stages the column and the rotations in shared memory; one thread
-// then streams the column through the rotations (each only needs the entry
-// carried from the previous one).
-__global__ void givens_kernel(const int* __restrict__ dj, int m, const double* __restrict__ h1,
-                              const double* __restrict__ h2, const double* __restrict__ wnorm,
-                              double* __restrict__ R, double* __restrict__ cs, double* __restrict__ sn,
-                              double* __restrict__ g, double* __restrict__ st) {
-  pdl_wait();
-  pdl_trigger();
-  __shared__ double hc[kMultidotMax], cc[kMultidotMax], sc[kMultidotMax];
-  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
-  const int j = dj[0];
-  for (int k = threadIdx.x; k <= j; k += 32) {
-    hc[k] = h1[k] + h2[k];
-    if (k < j) {
-      cc[k] = cs[k];
-      sc[k] = sn[k];
-    }
-  }
-  __syncwarp();
-  if (threadIdx.x != 0) return;
-  const double hn = wnorm[0];
-  double carry = hc[0];
-  for (int k = 0; k < j; ++k) {
-    const double next = hc[k + 1];
-    const double c = cc[k], sk = sc[k];
-    R[(size_t)k * m + j] = c * carry + sk * next;
-    carry = -sk * carry + c * next;
-  }
-  const double a = carry, b = hn;
-  const double d = hypot(a, b);
-  const double c = d > 0.0 ? a / d : 1.0, sk = d > 0.0 ? b / d : 0.0;
-  cs[j] = c; sn[j] = sk;
-  R[(size_t)j * m + j] = d;
-  g[j + 1] = -sk * g[j];
-  g[j] = c * g[j];
-  st[2 * (j & 1)] = fabs(g[j + 1]);
-  st[2 * (j & 1) + 1] = hn;
 }
 
 // y = R^{-1} g for the leading (j+1) x (j+1) block (back substitution).  A
@@ -640,20 +639,23 @@ static bamg_status norm2_dev(Gm& G, const double* x, double* out, cudaStream_t s
 }
 
 
-// rel = ||B x||_1 / ||x||_1 (read back to the host); xn1 = ||x||_1
+// rel = ||B x||_1 / ||x||_1 (read back to the host); xn1 = ||x||_1; with
+// xn2 given also ||x||_2, in the same read
 static bamg_status true_residual(bamg_hierarchy* h, Gm& G, const double* x, double* rel, double* xn1,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, double* xn2 = nullptr) {
   Level& L = h->lv[0];
   BAMG_TRY(csr_vec<double>(VEC_SPMV, L.n, L.vec_g, L.B.r(), L.B.c(), L.B.v(), L.dinv.as<double>(), 1.0, x,
                            nullptr, G.w2.as<double>(), s));
   double* sm = G.sums.as<double>();
   BAMG_TRY(abs_sums(L.n, G.w2.as<double>(), sm, s));
   BAMG_TRY(abs_sums(L.n, x, sm + 2, s));
-  double hs[4];
-  BAMG_CUDA(cudaMemcpyAsync(hs, sm, sizeof(hs), cudaMemcpyDeviceToHost, s));
+  if (xn2) BAMG_TRY(norm2_dev(G, x, sm + 4, s));
+  double hs[5];
+  BAMG_CUDA(cudaMemcpyAsync(hs, sm, sizeof(double) * (xn2 ? 5 : 4), cudaMemcpyDeviceToHost, s));
   BAMG_CUDA(cudaStreamSynchronize(s));
   *xn1 = hs[3];
   *rel = hs[3] > 0.0 ? hs[1] / hs[3] : INFINITY;
+  if (xn2) *xn2 = hs[4];
   return BAMG_OK;
 }
 
@@ -759,11 +761,11 @@ void gmres_release(bamg_hierarchy* h) {
   h->gm = nullptr;
 }
 
-// One Arnoldi step j (read from the device): z_j = C v_j (V-cycle, into Z_j
-// and io_out), w = B z_j, two classical Gram-Schmidt passes, ||w||, the
-// Givens update of column j with {|g_{j+1}|, ||w||} to pinned memory,
-// v_{j+1} = w / ||w||, j <- j + 1.  Kernel nodes only (programmatic
-// dependent launches).
+// One Arnoldi step j (read from the device): for j > 0 v_j = w / ||w|| from
+// the previous step, z_j = C v_j (V-cycle, into Z_j and io_out), w = B z_j,
+// two classical Gram-Schmidt passes, ||w|| and the Givens update of column j
+// with {|g_{j+1}|, ||w||} to pinned memory, j <- j + 1.  Kernel nodes only
+// (programmatic dependent launches).
 static bamg_status arnoldi_body(bamg_hierarchy* h, GmresState& S, cudaStream_t s) {
   Level& L = h->lv[0];
   Gm& G = S.G;
@@ -775,10 +777,15 @@ static bamg_status arnoldi_body(bamg_hierarchy* h, GmresState& S, cudaStream_t s
   double* Z = G.Z.as<double>();
   double* zo = h->io_out.as<double>();
   unsigned* arr = G.arrived.as<unsigned>();
+  // for j > 0 the input kernel first forms v_j = w / ||w|| from the previous
+  // step's w and reciprocal norm (scal[1])
+  const double* wprev = G.w.as<double>();
+  const double* rinv = G.scal.as<double>() + 1;
   if (S.plain)
-    BAMG_TRY(launch(plain_io_kernel, dim3(gv), dim3(256), 0, s, n, (const int*)dj, (const double*)V, zo, Z));
+    BAMG_TRY(launch(plain_io_kernel, dim3(gv), dim3(256), 0, s, n, (const int*)dj, V, wprev, rinv, zo, Z));
   else
-    BAMG_TRY(h->mixed ? vcycle_body<float>(h, s, V, dj, zo, Z) : vcycle_body<double>(h, s, V, dj, zo, Z));
+    BAMG_TRY(h->mixed ? vcycle_body<float>(h, s, V, dj, zo, Z, wprev, rinv)
+                      : vcycle_body<double>(h, s, V, dj, zo, Z, wprev, rinv));
   BAMG_TRY(csr_vec<double>(VEC_SPMV, n, L.vec_g, L.B.r(), L.B.c(), L.B.v(), L.dinv.as<double>(), 1.0,
                            (const double*)zo, nullptr, G.w.as<double>(), s));
   // classical Gram-Schmidt, twice: h1 = V^T w; w -= V h1, h2 = V^T w;
@@ -786,17 +793,15 @@ static bamg_status arnoldi_body(bamg_hierarchy* h, GmresState& S, cudaStream_t s
   double* h1 = G.h1.as<double>();
   double* h2 = G.h2.as<double>();
   const double* Vc = V;
+  const GivensArgs none{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  const GivensArgs ga{h1, G.R.as<double>(), G.cs.as<double>(), G.sn.as<double>(), G.g.as<double>(), S.st_dev, dj};
   BAMG_TRY(launch(gs_kernel<kGsDots>, dim3(nb), dim3(256), 0, s, n, m, (const int*)dj, Vc, (size_t)n,
-                  (const double*)nullptr, G.w.as<double>(), G.part.as<double>(), arr + kArrMultidot, h1));
+                  (const double*)nullptr, G.w.as<double>(), G.part.as<double>(), arr + kArrMultidot, h1, none));
   BAMG_TRY(launch(gs_kernel<kGsUpDots>, dim3(nb), dim3(256), 0, s, n, m, (const int*)dj, Vc, (size_t)n,
-                  (const double*)h1, G.w.as<double>(), G.part.as<double>(), arr + kArrMultidot, h2));
-  BAMG_TRY(launch(gs_kernel<kGsUpNorm>, dim3(nb), dim3(256), 0, s, n, m, (const int*)dj, Vc, (size_t)n,
-                  (const double*)h2, G.w.as<double>(), G.part.as<double>(), arr + kArrNorm, G.scal.as<double>()));
-  BAMG_TRY(launch(givens_kernel, dim3(1), dim3(32), 0, s, (const int*)dj, m, (const double*)h1, (const double*)h2,
-                  (const double*)G.scal.as<double>(), G.R.as<double>(), G.cs.as<double>(), G.sn.as<double>(),
-                  G.g.as<double>(), S.st_dev));
-  return launch(next_basis_kernel, dim3(gv), dim3(256), 0, s, n, dj, (const double*)G.w.as<double>(),
-                (const double*)G.scal.as<double>() + 1, V, arr + kArrBasis);
+                  (const double*)h1, G.w.as<double>(), G.part.as<double>(), arr + kArrMultidot, h2, none));
+  // the update, ||w||, the Givens update of column j and j <- j + 1
+  return launch(gs_kernel<kGsUpNorm>, dim3(nb), dim3(256), 0, s, n, m, (const int*)dj, Vc, (size_t)n,
+                (const double*)h2, G.w.as<double>(), G.part.as<double>(), arr + kArrNorm, G.scal.as<double>(), ga);
 }
 
 static bamg_status gmres_prepare(bamg_hierarchy* h, int m, int plain) {
@@ -827,7 +832,7 @@ static bamg_status gmres_prepare(bamg_hierarchy* h, int m, int plain) {
   BAMG_TRY(G.g.alloc(sizeof(double) * (m + 1), cs));
   BAMG_TRY(G.y.alloc(sizeof(double) * m, cs));
   BAMG_TRY(G.scal.alloc(sizeof(double) * 2, cs));
-  BAMG_TRY(G.sums.alloc(sizeof(double) * 4, cs));
+  BAMG_TRY(G.sums.alloc(sizeof(double) * 5, cs));
   BAMG_TRY(G.arrived.alloc(sizeof(unsigned) * kArrCount, cs));
   BAMG_TRY(S->dj.alloc(sizeof(int), cs));
   BAMG_CUDA(cudaMemsetAsync(G.zeros.p, 0, sizeof(double) * n, cs));
@@ -886,13 +891,9 @@ bamg_status fgmres(bamg_hierarchy* h, double* x, const bamg_solve_params* sp, ba
   else
     BAMG_CUDA(cudaMemcpyAsync(x, h->x0.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
 
-  double rel = 0.0, xn1 = 1.0;
-  BAMG_TRY(true_residual(h, G, x, &rel, &xn1, s));
+  double rel = 0.0, xn1 = 1.0, xn2_0 = 0.0;
+  BAMG_TRY(true_residual(h, G, x, &rel, &xn1, s, &xn2_0));
   const double xn1_0 = xn1;
-  double xn2_0 = 0.0;
-  BAMG_TRY(norm2_dev(G, x, G.scal.as<double>() + 1, s));
-  BAMG_CUDA(cudaMemcpyAsync(&xn2_0, G.scal.as<double>() + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
-  BAMG_CUDA(cudaStreamSynchronize(s));
   int its = 0, it7 = -1;
   bool done = rel <= sp->tol;
   bool breakdown = false, stalled = false;
@@ -966,7 +967,9 @@ bamg_status fgmres(bamg_hierarchy* h, double* x, const bamg_solve_params* sp, ba
                     G.scal.as<double>()));
   }
   BAMG_CUDA(cudaMemcpyAsync(fin, G.scal.p, sizeof(double), cudaMemcpyDeviceToHost, s));
-  BAMG_TRY(true_residual(h, G, x, &rel, &xn1, s));
+  BAMG_CUDA(cudaStreamSynchronize(s));
+  // rel is that of the final iterate before orient_normalise, which only
+  // rescales it: ||B x||_1 / ||x||_1 does not change under scaling
   if (info) {
     info->iterations = its;
     info->iters_to_1e7 = it7;
@@ -1036,8 +1039,9 @@ bamg_status vcycle_factor(bamg_hierarchy* h, int iters, uint64_t seed, double* f
   return BAMG_OK;
 }
 
-template bamg_status vcycle_body<double>(bamg_hierarchy*, cudaStream_t, const double*, const int*, double*,
-                                         double*);
-template bamg_status vcycle_body<float>(bamg_hierarchy*, cudaStream_t, const double*, const int*, double*, double*);
+template bamg_status vcycle_body<double>(bamg_hierarchy*, cudaStream_t, double*, const int*, double*, double*,
+                                         const double*, const double*);
+template bamg_status vcycle_body<float>(bamg_hierarchy*, cudaStream_t, double*, const int*, double*, double*,
+                                        const double*, const double*);
 
 }  // namespace bamg
