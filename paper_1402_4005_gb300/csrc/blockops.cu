@@ -675,7 +675,58 @@ bamg_status diag_inv(int n, const int32_t* rp, const int32_t* ci, const double* 
                 nsafe);
 }
 
+// Prolongation and the first post-smoothing sweep in one pass:
+// y = z1 + omega dinv .* (b - B z1) with z1 = z0 + P e.  A row's group of G
+// lanes forms the z1 entries its B entries need from P's rows (the
+// prolongation is never stored), so the V-cycle takes one pass instead of
+// two.
+template <typename T, int G>
+__global__ void __launch_bounds__(256)
+prolong_jacobi_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                      const T* __restrict__ va, const T* __restrict__ dinv, T omega,
+                      const int32_t* __restrict__ prp, const int32_t* __restrict__ pci, const T* __restrict__ pva,
+                      const T* __restrict__ e, const T* __restrict__ z0, const T* __restrict__ b,
+                      T* __restrict__ y) {
+  pdl_wait();
+  pdl_trigger();
+  const int lane = threadIdx.x & 31;
+  const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;   // every lane joins the shuffles
+  const int g = lane % G;
+  auto z1 = [&](int k) {
+    T v = T(0);
+    for (int p = __ldg(prp + k); p < __ldg(prp + k + 1); ++p) v = fma(__ldg(pva + p), __ldg(e + __ldg(pci + p)), v);
+    return z0[k] + v;
+  };
+  T acc = T(0);
+  if (i < n) {
+    const int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
+    for (int p = p0 + g; p < p1; p += G) acc = fma(__ldg(va + p), z1(__ldg(ci + p)), acc);
+  }
+  acc = group_sum<G>(acc);
+  if (g == 0 && i < n) y[i] = z1((int)i) + (omega * (b[i] - acc)) * dinv[i];
+}
+
+template <typename T>
+bamg_status prolong_jacobi(int n, int G, const int32_t* rp, const int32_t* ci, const T* va, const T* dinv,
+                           T omega, const int32_t* prp, const int32_t* pci, const T* pva, const T* e,
+                           const T* z0, const T* b, T* y, cudaStream_t s) {
+  auto go = [&](auto kern, int g) {
+    return launch(kern, dim3(cdiv((long long)n * g, 256)), dim3(256), 0, s, n, rp, ci, va, dinv, omega, prp, pci,
+                  pva, e, z0, b, y);
+  };
+  switch (G) {
+    case 2: return go(prolong_jacobi_kernel<T, 2>, 2);
+    case 4: return go(prolong_jacobi_kernel<T, 4>, 4);
+    case 8: return go(prolong_jacobi_kernel<T, 8>, 8);
+    case 16: return go(prolong_jacobi_kernel<T, 16>, 16);
+    default: return go(prolong_jacobi_kernel<T, 32>, 32);
+  }
+}
+
 #define BAMG_INST(T)                                                                                       \
+  template bamg_status prolong_jacobi<T>(int, int, const int32_t*, const int32_t*, const T*, const T*, T,  \
+                                         const int32_t*, const int32_t*, const T*, const T*, const T*,     \
+                                         const T*, T*, cudaStream_t);                                      \
   template bamg_status relax_block<T>(int, int, const int32_t*, const int32_t*, const T*, const T*,       \
                                       const T*, T*, const T*, const T*, T, int, cudaStream_t);           \
   template bamg_status spmm_block<T>(int, int, const int32_t*, const int32_t*, const T*, const T*, T*,    \

@@ -121,6 +121,12 @@ bamg_status csr_vec(int mode, int n, int G, const int32_t* rp, const int32_t* ci
                     T omega, const T* x, const T* b, T* y, cudaStream_t s);
 template <typename T>
 bamg_status dense_gemv(int n, const T* A, const T* x, T* y, cudaStream_t s);
+// y = z1 + omega dinv .* (b - B z1), z1 = z0 + P e: the prolongation and the
+// first post-smoothing sweep in one pass (B: rp, ci, va with G lanes per row)
+template <typename T>
+bamg_status prolong_jacobi(int n, int G, const int32_t* rp, const int32_t* ci, const T* va, const T* dinv,
+                           T omega, const int32_t* prp, const int32_t* pci, const T* pva, const T* e,
+                           const T* z0, const T* b, T* y, cudaStream_t s);
 
 // smooth.cu: multicolour Gauss-Seidel (greedy colouring of the symmetrised
 // graph of B in SplitMix64 priority order, rows by colour, sweeps)

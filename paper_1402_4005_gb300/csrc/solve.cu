@@ -100,9 +100,19 @@ static bamg_status vcycle_level(bamg_hierarchy* h, int l, cudaStream_t s) {
   BAMG_TRY(csr_vec<T>(VEC_SPMV, L.nc, lanes_for(L.Q), L.Q.r(), L.Q.c(), L.Q.vals<T>(), dv, om, L.vr.as<T>(),
                       nullptr, C.vb.as<T>(), s));
   BAMG_TRY(vcycle_level<T>(h, l + 1, s));
-  BAMG_TRY(csr_vec<T>(VEC_SPMV_ADD, L.n, lanes_for(L.P), L.P.r(), L.P.c(), L.P.vals<T>(), dv, om,
-                      C.vz.as<T>(), nullptr, cur, s));
-  for (int it = 0; it < p.nu_post; ++it) {
+  int post = p.nu_post;
+  if (post > 0) {
+    // z += P e_c and the first post-sweep in one pass (writes alt, as the
+    // sweep did)
+    BAMG_TRY(prolong_jacobi<T>(L.n, L.vec_g, L.B.r(), L.B.c(), bv, dv, om, L.P.r(), L.P.c(), L.P.vals<T>(),
+                               C.vz.as<T>(), cur, b, alt, s));
+    std::swap(cur, alt);
+    --post;
+  } else {
+    BAMG_TRY(csr_vec<T>(VEC_SPMV_ADD, L.n, lanes_for(L.P), L.P.r(), L.P.c(), L.P.vals<T>(), dv, om,
+                        C.vz.as<T>(), nullptr, cur, s));
+  }
+  for (int it = 0; it < post; ++it) {
     BAMG_TRY(csr_vec<T>(VEC_JACOBI, L.n, L.vec_g, L.B.r(), L.B.c(), bv, dv, om, cur, b, alt, s));
     std::swap(cur, alt);
   }
