@@ -50,6 +50,12 @@ __global__ void zero_kernel(size_t n, T* __restrict__ y) {
   if (t < n) y[t] = T(0);
 }
 
+// Levels of at most this many rows take the prolongation and the first
+// post-sweep in one pass: there a pass costs its launch and latency, not its
+// bytes (on a 2^20-row level the fused pass, which gathers P's rows for every
+// neighbour, made the Delaunay solve 15 % slower).
+constexpr int kFuseProlongRows = 65536;
+
 template <typename T>
 static bamg_status vcycle_level(bamg_hierarchy* h, int l, cudaStream_t s) {
   Level& L = h->lv[l];
@@ -101,9 +107,9 @@ static bamg_status vcycle_level(bamg_hierarchy* h, int l, cudaStream_t s) {
                       nullptr, C.vb.as<T>(), s));
   BAMG_TRY(vcycle_level<T>(h, l + 1, s));
   int post = p.nu_post;
-  if (post > 0) {
+  if (post > 0 && L.n <= kFuseProlongRows) {
     // z += P e_c and the first post-sweep in one pass (writes alt, as the
-    // sweep did)
+    // sweep did); on larger levels the separate passes move fewer bytes
     BAMG_TRY(prolong_jacobi<T>(L.n, L.vec_g, L.B.r(), L.B.c(), bv, dv, om, L.P.r(), L.P.c(), L.P.vals<T>(),
                                C.vz.as<T>(), cur, b, alt, s));
     std::swap(cur, alt);
