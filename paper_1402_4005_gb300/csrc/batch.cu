@@ -353,7 +353,11 @@ static bamg_status bvcycle_prepare(bamg_batch* bt) {
   if (!bt->cap) BAMG_CUDA(cudaStreamCreateWithFlags(&bt->cap, cudaStreamNonBlocking));
   uint64_t before = t_launches;
   BAMG_CUDA(cudaStreamBeginCapture(bt->cap, cudaStreamCaptureModeThreadLocal));
-  bamg_status st = bt->mixed ? bvcycle_body<float>(bt, bt->cap) : bvcycle_body<double>(bt, bt->cap);
+  bamg_status st;
+  {
+    PdlScope pdl;   // kernel-to-kernel edges programmatic (every kernel waits first)
+    st = bt->mixed ? bvcycle_body<float>(bt, bt->cap) : bvcycle_body<double>(bt, bt->cap);
+  }
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(bt->cap, &g);
   if (st != BAMG_OK) {
@@ -532,6 +536,7 @@ __global__ void negate_kernel(int n, double* __restrict__ x) {
 
 static bamg_status batched_fgmres(bamg_batch* bt, double* x, const bamg_solve_params* sp, bamg_solve_info* infos,
                                   cudaStream_t s) {
+  PdlScope pdl;   // consecutive kernels overlap their launches (each waits for its predecessor first)
   const int nch = bt->nch, m = sp->restart, H = m + 1;
   BLevel& L0 = bt->lv[0];
   const int n = L0.n;
