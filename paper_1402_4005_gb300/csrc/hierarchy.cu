@@ -109,13 +109,6 @@ static bamg_status csr_transpose(const Csr& A, Csr& T, cudaStream_t s) {
                        T.va.as<double>(), s);
 }
 
-static bamg_status csr_product(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
-  int64_t nnz = 0;
-  BAMG_TRY(spgemm(A.rows, A.r(), A.c(), A.v(), B.r(), B.c(), B.v(), C.rp, C.ci, C.va, &nnz, s));
-  C.rows = A.rows; C.cols = B.cols; C.nnz = (int)nnz;
-  return BAMG_OK;
-}
-
 static bamg_status csr_products(const std::vector<std::pair<const Csr*, const Csr*>>& ab,
                                 const std::vector<Csr*>& out, cudaStream_t s) {
   std::vector<SpgemmJob> jobs(ab.size());

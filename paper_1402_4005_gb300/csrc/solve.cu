@@ -129,13 +129,6 @@ static bamg_status vcycle_level(bamg_hierarchy* h, int l, cudaStream_t s) {
   return BAMG_OK;
 }
 
-__global__ void copy_d_kernel(size_t n, const double* __restrict__ a, double* __restrict__ b) {
-  pdl_wait();
-  pdl_trigger();
-  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) b[t] = a[t];
-}
-
 __global__ void fill_kernel(size_t n, double v, double* __restrict__ b) {
   pdl_wait();
   pdl_trigger();
@@ -647,7 +640,7 @@ static int red_blocks(int n) {
   return nb < kRedBlocks ? (nb > 0 ? nb : 1) : kRedBlocks;
 }
 
-enum { kArrMultidot = 0, kArrNorm = 1, kArrBasis = 2, kArrCount = 3 };
+enum { kArrMultidot = 0, kArrNorm = 1, kArrCount = 2 };
 
 static bamg_status norm2_dev(Gm& G, const double* x, double* out, cudaStream_t s) {
   return launch(norm2_kernel, dim3(red_blocks(G.n)), dim3(256), 0, s, G.n, x, G.part.as<double>(),
