@@ -47,7 +47,9 @@ typedef enum {
   BAMG_ERR_NUMERIC = 7,        /* zero row and column in a coarse B, non-SPD M_l/N_l,
                                   singular fit, or a row beyond kernel limits   */
   BAMG_ERR_TIMEOUT = 8,        /* a bounded device-side wait gave up            */
-  BAMG_ERR_UNSUPPORTED = 9     /* valid request outside this build's limits     */
+  BAMG_ERR_UNSUPPORTED = 9,    /* valid request outside this build's limits     */
+  BAMG_ERR_IO = 10             /* a file could not be read or written, or is
+                                  not a well-formed parameter file              */
 } bamg_status;
 
 enum { BAMG_COARSEN_GEOMETRIC = 0, BAMG_COARSEN_MIS = 1 };
@@ -238,6 +240,19 @@ void bamg_destroy_batched(bamg_batch* b);
 int bamg_mlp_num_params(void);
 /* He-uniform weights from SplitMix64(seed, stream 8192), zero biases. */
 bamg_status bamg_mlp_init(float* params_dev, uint64_t seed, void* stream);
+/* Parameter files.  Layout (every field little-endian): the 8 bytes
+ * "BAMGMLP1", the entry count as uint32 (= bamg_mlp_num_params()), the
+ * 32-bit FNV-1a hash of the entry bytes as uint32, then the entries as IEEE
+ * binary32 in the order above; nothing follows them.  `params` is device
+ * memory when on_device != 0 (copied on `stream`, which is synchronised
+ * before the call returns), else host memory; the caller owns it.
+ * bamg_mlp_save writes (or replaces) the file at `path`.  bamg_mlp_load
+ * fills params[0, bamg_mlp_num_params()) and leaves it untouched on any
+ * error.  A file that cannot be opened, read or written, a wrong tag, count,
+ * length or hash is BAMG_ERR_IO; a non-finite entry (in the file or in the
+ * vector to save) is BAMG_ERR_NUMERIC. */
+bamg_status bamg_mlp_save(const char* path, const float* params, int on_device, void* stream);
+bamg_status bamg_mlp_load(const char* path, float* params, int on_device, void* stream);
 /* Y[M][16] = network(X[M][64]); device arrays, X in bf16. */
 bamg_status bamg_mlp_forward(const float* params_dev, int M, const void* X_bf16, float* Y, void* stream);
 /* Loss = sum(mask * (Y - T)^2) / sum(mask) over the M rows and its gradient:

@@ -13,7 +13,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libbamg.so")
 
 STATUS = {0: "BAMG_OK", 1: "BAMG_ERR_ARG", 2: "BAMG_ERR_NOT_STOCHASTIC", 3: "BAMG_ERR_CUDA",
           4: "BAMG_ERR_OOM", 5: "BAMG_ERR_NOT_CONVERGED", 6: "BAMG_ERR_BREAKDOWN",
-          7: "BAMG_ERR_NUMERIC", 8: "BAMG_ERR_TIMEOUT", 9: "BAMG_ERR_UNSUPPORTED"}
+          7: "BAMG_ERR_NUMERIC", 8: "BAMG_ERR_TIMEOUT", 9: "BAMG_ERR_UNSUPPORTED",
+          10: "BAMG_ERR_IO"}
 
 vp = C.c_void_p
 i32 = C.c_int
@@ -84,6 +85,8 @@ SIGNATURES = {
     "bamg_destroy_batched": (None, [vp]),
     "bamg_mlp_num_params": (i32, []),
     "bamg_mlp_init": (i32, [vp, u64, vp]),
+    "bamg_mlp_save": (i32, [C.c_char_p, vp, i32, vp]),
+    "bamg_mlp_load": (i32, [C.c_char_p, vp, i32, vp]),
     "bamg_mlp_forward": (i32, [vp, i32, vp, vp, vp]),
     "bamg_mlp_grad": (i32, [vp, i32, vp, vp, vp, vp, vp, vp]),
     "bamg_mlp_train": (i32, [vp, i32, vp, vp, vp, i32, i32, C.c_float, C.POINTER(C.c_float), vp]),

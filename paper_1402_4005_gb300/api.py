@@ -506,6 +506,24 @@ def bamg_mlp_init(seed: int = 5, stream=None) -> torch.Tensor:
     return p
 
 
+def bamg_mlp_save(params: torch.Tensor, path: str, stream=None) -> None:
+    """Write a parameter vector (CUDA or CPU float32 tensor) to a file."""
+    if params.dtype != torch.float32 or params.numel() != bamg_mlp_num_params() or not params.is_contiguous():
+        raise ValueError("params must be a contiguous float32 tensor of bamg_mlp_num_params() entries")
+    dev = 1 if params.is_cuda else 0
+    check(lib().bamg_mlp_save(str(path).encode(), _p(params), dev, _stream(stream) if dev else None),
+          "bamg_mlp_save")
+
+
+def bamg_mlp_load(path: str, device: str = "cuda", stream=None) -> torch.Tensor:
+    """Parameter vector read from a file, on the GPU (default) or the CPU."""
+    p = torch.empty(bamg_mlp_num_params(), dtype=torch.float32, device=device)
+    dev = 1 if p.is_cuda else 0
+    check(lib().bamg_mlp_load(str(path).encode(), _p(p), dev, _stream(stream) if dev else None),
+          "bamg_mlp_load")
+    return p
+
+
 def _bf16_rows(X) -> torch.Tensor:
     X = X if isinstance(X, torch.Tensor) else torch.as_tensor(np.asarray(X, dtype=np.float32))
     X = X.to(device="cuda", dtype=torch.bfloat16).contiguous()

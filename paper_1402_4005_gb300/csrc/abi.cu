@@ -70,6 +70,7 @@ const char* bamg_status_string(bamg_status s) {
     case BAMG_ERR_NUMERIC: return "numerical failure";
     case BAMG_ERR_TIMEOUT: return "device wait timed out";
     case BAMG_ERR_UNSUPPORTED: return "unsupported request";
+    case BAMG_ERR_IO: return "file error";
   }
   return "unknown status";
 }

@@ -24,6 +24,8 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdio>
+#include <cstring>
 #include <vector>
 
 #include "hierarchy.cuh"
@@ -589,6 +591,125 @@ extern "C" bamg_status bamg_mlp_init(float* params, uint64_t seed, void* stream)
   BAMG_CHECK_ARG(params);
   return launch(mlp_init_kernel, dim3(cdiv(kNParam, 256)), dim3(256), 0, reinterpret_cast<cudaStream_t>(stream),
                 params, seed);
+}
+
+// Parameter files: tag, entry count, FNV-1a hash (Fowler, Noll and Vo; 32-bit
+// offset basis 2166136261, prime 16777619) of the entry bytes, entries; all
+// fields little-endian, written byte by byte so the host's order is irrelevant.
+namespace {
+const unsigned char kMlpTag[8] = {'B', 'A', 'M', 'G', 'M', 'L', 'P', '1'};
+constexpr size_t kMlpHead = 16;
+
+void put_u32(unsigned char* b, uint32_t v) {
+  for (int k = 0; k < 4; ++k) b[k] = (unsigned char)(v >> (8 * k));
+}
+uint32_t get_u32(const unsigned char* b) {
+  uint32_t v = 0;
+  for (int k = 0; k < 4; ++k) v |= (uint32_t)b[k] << (8 * k);
+  return v;
+}
+uint32_t fnv1a32(const unsigned char* b, size_t n) {
+  uint32_t h = 2166136261u;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= b[i];
+    h *= 16777619u;
+  }
+  return h;
+}
+bool all_finite(const std::vector<float>& w) {
+  for (float v : w)
+    if (!std::isfinite(v)) return false;
+  return true;
+}
+}  // namespace
+
+extern "C" bamg_status bamg_mlp_save(const char* path, const float* params, int on_device, void* stream) {
+  BAMG_CHECK_ARG(path && params);
+  std::vector<float> w(kNParam);
+  if (on_device) {
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    BAMG_CUDA(cudaMemcpyAsync(w.data(), params, sizeof(float) * kNParam, cudaMemcpyDeviceToHost, s));
+    BAMG_CUDA(cudaStreamSynchronize(s));
+  } else {
+    std::memcpy(w.data(), params, sizeof(float) * kNParam);
+  }
+  if (!all_finite(w)) {
+    set_error("network parameters to save hold a non-finite entry");
+    return BAMG_ERR_NUMERIC;
+  }
+  std::vector<unsigned char> buf(kMlpHead + 4 * (size_t)kNParam);
+  for (int i = 0; i < kNParam; ++i) {
+    uint32_t u;
+    std::memcpy(&u, &w[i], 4);
+    put_u32(&buf[kMlpHead + 4 * (size_t)i], u);
+  }
+  std::memcpy(buf.data(), kMlpTag, 8);
+  put_u32(&buf[8], (uint32_t)kNParam);
+  put_u32(&buf[12], fnv1a32(&buf[kMlpHead], 4 * (size_t)kNParam));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) {
+    set_error("cannot open %s for writing", path);
+    return BAMG_ERR_IO;
+  }
+  bool ok = std::fwrite(buf.data(), 1, buf.size(), f) == buf.size();
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) {
+    set_error("writing %s failed", path);
+    return BAMG_ERR_IO;
+  }
+  return BAMG_OK;
+}
+
+extern "C" bamg_status bamg_mlp_load(const char* path, float* params, int on_device, void* stream) {
+  BAMG_CHECK_ARG(path && params);
+  FILE* f = std::fopen(path, "rb");
+  if (!f) {
+    set_error("cannot open %s for reading", path);
+    return BAMG_ERR_IO;
+  }
+  const size_t len = kMlpHead + 4 * (size_t)kNParam;
+  std::vector<unsigned char> buf(len + 1);
+  const size_t got = std::fread(buf.data(), 1, len + 1, f);   // one byte more detects trailing data
+  const bool rd_err = std::ferror(f) != 0;
+  std::fclose(f);
+  if (rd_err) {
+    set_error("reading %s failed", path);
+    return BAMG_ERR_IO;
+  }
+  if (got < kMlpHead || std::memcmp(buf.data(), kMlpTag, 8) != 0) {
+    set_error("%s is not a network parameter file", path);
+    return BAMG_ERR_IO;
+  }
+  const uint32_t count = get_u32(&buf[8]);
+  if (count != (uint32_t)kNParam) {
+    set_error("%s holds %u parameters, the network has %d", path, count, kNParam);
+    return BAMG_ERR_IO;
+  }
+  if (got != len) {
+    set_error("%s is %s", path, got < len ? "truncated" : "longer than its entries");
+    return BAMG_ERR_IO;
+  }
+  if (get_u32(&buf[12]) != fnv1a32(&buf[kMlpHead], 4 * (size_t)kNParam)) {
+    set_error("%s: hash of the entries does not match", path);
+    return BAMG_ERR_IO;
+  }
+  std::vector<float> w(kNParam);
+  for (int i = 0; i < kNParam; ++i) {
+    const uint32_t u = get_u32(&buf[kMlpHead + 4 * (size_t)i]);
+    std::memcpy(&w[i], &u, 4);
+  }
+  if (!all_finite(w)) {
+    set_error("%s holds a non-finite parameter", path);
+    return BAMG_ERR_NUMERIC;
+  }
+  if (on_device) {
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    BAMG_CUDA(cudaMemcpyAsync(params, w.data(), sizeof(float) * kNParam, cudaMemcpyHostToDevice, s));
+    BAMG_CUDA(cudaStreamSynchronize(s));
+  } else {
+    std::memcpy(params, w.data(), sizeof(float) * kNParam);
+  }
+  return BAMG_OK;
 }
 
 extern "C" bamg_status bamg_mlp_forward(const float* params, int M, const void* X_bf16, float* Y, void* stream) {

@@ -209,6 +209,25 @@ def test_learned_hierarchy_solves(api, trained, prec):
         assert np.allclose(np.asarray(Qt.sum(axis=1)).ravel(), 1.0, atol=1e-12)
 
 
+def test_trained_network_file_round_trip(api, trained, tmp_path):
+    """A trained network saved from the GPU and loaded back (to the GPU and
+    to the host) keeps every bit, and the loaded vector drives the same
+    forward pass."""
+    params, _ = trained
+    path = tmp_path / "trained.bin"
+    api.bamg_mlp_save(params, path)
+    dev = api.bamg_mlp_load(path)
+    host = api.bamg_mlp_load(path, device="cpu")
+    assert dev.is_cuda and not host.is_cuda
+    assert torch.equal(dev.cpu().view(torch.int32), params.cpu().view(torch.int32))
+    assert torch.equal(host.view(torch.int32), params.cpu().view(torch.int32))
+    X, _, _ = rand_rows(16 * 9 + 3, 21)
+    X = torch.from_numpy(X)
+    Y0 = api.bamg_mlp_forward(params, X)
+    Y1 = api.bamg_mlp_forward(dev, X)
+    assert torch.equal(Y0.view(torch.int32), Y1.view(torch.int32))
+
+
 def test_learned_gain_over_untrained_and_ls(api, trained):
     params, _ = trained
     ch = cg.tandem(96)
